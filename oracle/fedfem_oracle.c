@@ -1,0 +1,514 @@
+/*
+ * FED-FEM oracle: TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded FP64 CPU implementation of the fast explicit dynamics finite
+ * element method (FED-FEM) for transient heat conduction (Zhang & Chauhan, arXiv:1909.03355).
+ * Only the test suite, the smoke check and the CPU-baseline leg of bench.py may load it.  It
+ * shares no code with the CUDA library: it follows the paper's equations in their textbook
+ * form (full 8x8 / 4x4 element matrices, element loop and scatter, literal Eq. 7 radiation).
+ *
+ * Readings of the paper used here (where it is silent, garbled or at odds with itself):
+ *  - Sign (Eq. 2, 11-13): the element load F_e = theta_e f_k,e K0_e T_e is the positive
+ *    semidefinite conduction load and the update is T += dt (Q - F) / C.  The paper's K of
+ *    Eq. 2 is therefore -K0.
+ *  - Convection (Eq. 4): heat leaves when T > T_a, nodal load -A^c_i h (T_i - T_a).
+ *  - Hexahedra integrate Eq. 12 with 2x2x2 Gauss points (the one-point rule of Eq. 17 has
+ *    hourglass modes on distorted meshes); tetrahedra use Eq. 18 exactly.
+ *  - Temperature-dependent conductivity is evaluated at the element nodes and averaged over
+ *    the element (Section 4.2.2): f_k,e = mean_i f_k(T_i); c(T) is evaluated per node (Eq. 16).
+ *  - Lumped (diagonal) thermal mass by row sums, M_i = sum_e rho_e int_e N_i dV (Section 3.1).
+ *  - Surface loads use nodal-quadrature lumping: every face gives A_f / n_f to each node.
+ *  - Critical step (Section 3.4, Eq. 29): dt_crit = 2 / lambda_max of the linearised system,
+ *    lambda from FP64 power iteration on C0^-1/2 K0 C0^-1/2, scaled by max f_k / min f_c over
+ *    [T_lo, T_hi], plus the largest linearised surface rate.
+ *
+ * Parity pins live in tests/test_oracle_*.py (closed forms, patch tests, the slab recurrence,
+ * energy balance, dense brute force, finite differences).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_SIGMA 5.67e-8 /* Stefan-Boltzmann constant as printed with Eq. 7 */
+
+/* ------------------------------------------------------------------------------------------ */
+/* small dense helpers                                                                          */
+/* ------------------------------------------------------------------------------------------ */
+
+static double det3(const double J[3][3])
+{
+    return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1])
+         - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0])
+         + J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+static void inv3(const double J[3][3], double d, double Ji[3][3])
+{
+    Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / d;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / d;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / d;
+    Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / d;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / d;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / d;
+    Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / d;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / d;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / d;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* element matrices (pre-computation stage, Fig. 1 (i) 2)                                       */
+/* ------------------------------------------------------------------------------------------ */
+
+/* natural coordinates of the 8 hex nodes, VTK / C3D8 order */
+static const double HEX_NAT[8][3] = {
+    {-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+    {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+
+/*
+ * Eq. 12 for the trilinear hexahedron: K_ij = int_Ve (grad N_i)^T k (grad N_j) dV, evaluated by
+ * 2x2x2 Gauss quadrature (points +-1/sqrt(3), unit weights), together with w_i = int_Ve N_i dV
+ * and the element volume.  x: [8][3] node coordinates; k: 3x3 conductivity (row-major).
+ * Returns 0, or -1 when det J <= 0 at a Gauss point (inverted or degenerate element).
+ */
+int orc_hex_matrices(const double *x, const double *k, double *K, double *w, double *vol)
+{
+    const double g = 1.0 / sqrt(3.0);
+    memset(K, 0, 64 * sizeof(double));
+    memset(w, 0, 8 * sizeof(double));
+    *vol = 0.0;
+    for (int q = 0; q < 8; ++q) {
+        const double xi = HEX_NAT[q][0] * g, eta = HEX_NAT[q][1] * g, zeta = HEX_NAT[q][2] * g;
+        double N[8], dN[8][3];
+        for (int i = 0; i < 8; ++i) {
+            const double a = 1.0 + xi * HEX_NAT[i][0];
+            const double b = 1.0 + eta * HEX_NAT[i][1];
+            const double c = 1.0 + zeta * HEX_NAT[i][2];
+            N[i] = a * b * c / 8.0;
+            dN[i][0] = HEX_NAT[i][0] * b * c / 8.0;
+            dN[i][1] = a * HEX_NAT[i][1] * c / 8.0;
+            dN[i][2] = a * b * HEX_NAT[i][2] / 8.0;
+        }
+        double J[3][3] = {{0}};
+        for (int i = 0; i < 8; ++i)
+            for (int r = 0; r < 3; ++r)
+                for (int s = 0; s < 3; ++s) J[r][s] += x[3 * i + r] * dN[i][s];
+        const double d = det3(J);
+        if (!(d > 0.0)) return -1;
+        double Ji[3][3];
+        inv3(J, d, Ji);
+        double B[8][3]; /* grad_x N_i = J^-T grad_xi N_i */
+        for (int i = 0; i < 8; ++i)
+            for (int r = 0; r < 3; ++r) {
+                B[i][r] = 0.0;
+                for (int s = 0; s < 3; ++s) B[i][r] += Ji[s][r] * dN[i][s];
+            }
+        for (int i = 0; i < 8; ++i) {
+            double kB[3];
+            for (int r = 0; r < 3; ++r) {
+                kB[r] = 0.0;
+                for (int s = 0; s < 3; ++s) kB[r] += k[3 * r + s] * B[i][s];
+            }
+            for (int j = 0; j < 8; ++j)
+                K[8 * j + i] += d * (B[j][0] * kB[0] + B[j][1] * kB[1] + B[j][2] * kB[2]);
+            w[i] += d * N[i];
+        }
+        *vol += d;
+    }
+    return 0;
+}
+
+/* Solve the 4x4 system P X = I by Gaussian elimination with partial pivoting. */
+static int inv4(const double P[4][4], double X[4][4])
+{
+    double A[4][8];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 8; ++c) A[r][c] = c < 4 ? P[r][c] : (c - 4 == r ? 1.0 : 0.0);
+    for (int c = 0; c < 4; ++c) {
+        int p = c;
+        for (int r = c + 1; r < 4; ++r)
+            if (fabs(A[r][c]) > fabs(A[p][c])) p = r;
+        if (A[p][c] == 0.0) return -1;
+        if (p != c)
+            for (int j = 0; j < 8; ++j) {
+                double t = A[c][j];
+                A[c][j] = A[p][j];
+                A[p][j] = t;
+            }
+        for (int r = 0; r < 4; ++r) {
+            if (r == c) continue;
+            const double f = A[r][c] / A[c][c];
+            for (int j = 0; j < 8; ++j) A[r][j] -= f * A[c][j];
+        }
+    }
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) X[r][c] = A[r][4 + c] / A[r][r];
+    return 0;
+}
+
+/*
+ * Eq. 18 for the linear tetrahedron: K = V B^T k B with B the (constant) gradients of the
+ * barycentric shape functions, taken from the inverse of P = [1 x y z] (rows = nodes);
+ * w_i = V / 4.  Returns -1 for V <= 0.
+ */
+int orc_tet_matrices(const double *x, const double *k, double *K, double *w, double *vol)
+{
+    double P[4][4], C[4][4];
+    for (int i = 0; i < 4; ++i) {
+        P[i][0] = 1.0;
+        for (int r = 0; r < 3; ++r) P[i][1 + r] = x[3 * i + r];
+    }
+    const double J[3][3] = {
+        {x[3] - x[0], x[6] - x[0], x[9] - x[0]},
+        {x[4] - x[1], x[7] - x[1], x[10] - x[1]},
+        {x[5] - x[2], x[8] - x[2], x[11] - x[2]}};
+    const double V = det3(J) / 6.0;
+    if (!(V > 0.0)) return -1;
+    if (inv4(P, C)) return -1;
+    /* N_i(x) = C[0][i] + C[1][i] x + C[2][i] y + C[3][i] z  => grad N_i = C[1..3][i] */
+    for (int i = 0; i < 4; ++i) {
+        for (int j = 0; j < 4; ++j) {
+            double s = 0.0;
+            for (int r = 0; r < 3; ++r)
+                for (int t = 0; t < 3; ++t) s += C[1 + r][i] * k[3 * r + t] * C[1 + t][j];
+            K[4 * i + j] = V * s;
+        }
+        w[i] = V / 4.0;
+    }
+    *vol = V;
+    return 0;
+}
+
+/* Area of a boundary face: half the cross product for a triangle; for a quadrilateral the
+ * area of its bilinear patch, int |x_xi x x_eta| over [-1,1]^2 by 2x2 Gauss points. */
+double orc_face_area(const double *x, int nv)
+{
+    if (nv == 3) {
+        double a[3], b[3], c[3];
+        for (int r = 0; r < 3; ++r) {
+            a[r] = x[3 + r] - x[r];
+            b[r] = x[6 + r] - x[r];
+        }
+        c[0] = a[1] * b[2] - a[2] * b[1];
+        c[1] = a[2] * b[0] - a[0] * b[2];
+        c[2] = a[0] * b[1] - a[1] * b[0];
+        return 0.5 * sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    }
+    static const double S[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+    const double g = 1.0 / sqrt(3.0);
+    double A = 0.0;
+    for (int q = 0; q < 4; ++q) {
+        const double s = S[q][0] * g, t = S[q][1] * g;
+        double xs[3] = {0, 0, 0}, xt[3] = {0, 0, 0};
+        for (int i = 0; i < 4; ++i)
+            for (int r = 0; r < 3; ++r) {
+                xs[r] += x[3 * i + r] * S[i][0] * (1.0 + t * S[i][1]) / 4.0;
+                xt[r] += x[3 * i + r] * (1.0 + s * S[i][0]) * S[i][1] / 4.0;
+            }
+        const double c0 = xs[1] * xt[2] - xs[2] * xt[1];
+        const double c1 = xs[2] * xt[0] - xs[0] * xt[2];
+        const double c2 = xs[0] * xt[1] - xs[1] * xt[0];
+        A += sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+    }
+    return A;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* the model after pre-computation                                                              */
+/* ------------------------------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t nn, ne;
+    int32_t npe, pad;
+    const int32_t *conn;  /* [ne][npe] */
+    const double *K;      /* [ne][npe][npe]  K0_e (unit conductivity scale, f_k = 1) */
+    const double *theta;  /* [ne] conductivity scale theta_e */
+    const double *W;      /* [ne][npe] int_e N_i dV */
+    const double *C0;     /* [nn] sum_e rho_e c0_e int_e N_i dV (lumped thermal mass at f_c = 1) */
+    const double *Qext;   /* [nn] constant nodal heat flow (sources, concentrated fluxes) */
+    const double *Ac;     /* [nn] convection area share */
+    const double *Ar;     /* [nn] radiation area share */
+    const int32_t *isdir; /* [nn] 1 on Gamma_E */
+    double k_lin, c_lin;  /* f_k(T) = 1 + k_lin T, f_c(T) = 1 + c_lin T */
+    double h, T_inf, eps, T_amb, T_zero;
+} orc_model;
+
+/*
+ * Pre-computation (Fig. 1 (i)): element matrices K0_e and shape-function integrals, lumped
+ * thermal mass, constant external loads and boundary area shares.
+ *   mat_k0 [n_mats][9], mat_rho, mat_c0 [n_mats]; elem_mat [ne] or NULL (material 0);
+ *   source [ne] W/m^3 or NULL; nodal_Q [nn] W or NULL;
+ *   conv/rad faces [n][nvf] node ids; dir_nodes [nd].
+ * Outputs (caller-allocated): K [ne*npe*npe], W [ne*npe], C0, Qext, Ac, Ar [nn], isdir [nn].
+ * Returns 0, or 1 + e for the first element e with det J <= 0.
+ */
+int64_t orc_precompute(int64_t nn, int64_t ne, int32_t npe, const double *xyz, const int32_t *conn,
+                       const int32_t *elem_mat, const double *mat_k0, const double *mat_rho,
+                       const double *mat_c0, const double *source, const double *nodal_Q,
+                       int64_t n_conv, int32_t nv_conv, const int32_t *conv_faces,
+                       int64_t n_rad, int32_t nv_rad, const int32_t *rad_faces,
+                       int64_t n_dir, const int32_t *dir_nodes,
+                       double *K, double *W, double *C0, double *Qext, double *Ac, double *Ar,
+                       int32_t *isdir)
+{
+    memset(C0, 0, nn * sizeof(double));
+    memset(Qext, 0, nn * sizeof(double));
+    memset(Ac, 0, nn * sizeof(double));
+    memset(Ar, 0, nn * sizeof(double));
+    memset(isdir, 0, nn * sizeof(int32_t));
+    double xe[8 * 3];
+    for (int64_t e = 0; e < ne; ++e) {
+        const int m = elem_mat ? elem_mat[e] : 0;
+        for (int i = 0; i < npe; ++i)
+            for (int r = 0; r < 3; ++r) xe[3 * i + r] = xyz[3 * (int64_t)conn[npe * e + i] + r];
+        double vol;
+        const int rc = npe == 8 ? orc_hex_matrices(xe, mat_k0 + 9 * m, K + 64 * e, W + 8 * e, &vol)
+                                : orc_tet_matrices(xe, mat_k0 + 9 * m, K + 16 * e, W + 4 * e, &vol);
+        if (rc) return 1 + e;
+        for (int i = 0; i < npe; ++i) {
+            const int64_t n = conn[npe * e + i];
+            C0[n] += mat_rho[m] * mat_c0[m] * W[npe * e + i];
+            if (source) Qext[n] += source[e] * W[npe * e + i];
+        }
+    }
+    if (nodal_Q)
+        for (int64_t i = 0; i < nn; ++i) Qext[i] += nodal_Q[i];
+    double xf[4 * 3];
+    for (int64_t f = 0; f < n_conv; ++f) {
+        for (int i = 0; i < nv_conv; ++i)
+            for (int r = 0; r < 3; ++r) xf[3 * i + r] = xyz[3 * (int64_t)conv_faces[nv_conv * f + i] + r];
+        const double a = orc_face_area(xf, nv_conv) / nv_conv;
+        for (int i = 0; i < nv_conv; ++i) Ac[conv_faces[nv_conv * f + i]] += a;
+    }
+    for (int64_t f = 0; f < n_rad; ++f) {
+        for (int i = 0; i < nv_rad; ++i)
+            for (int r = 0; r < 3; ++r) xf[3 * i + r] = xyz[3 * (int64_t)rad_faces[nv_rad * f + i] + r];
+        const double a = orc_face_area(xf, nv_rad) / nv_rad;
+        for (int i = 0; i < nv_rad; ++i) Ar[rad_faces[nv_rad * f + i]] += a;
+    }
+    for (int64_t d = 0; d < n_dir; ++d) isdir[dir_nodes[d]] = 1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* time stepping (Fig. 1 (iii))                                                                 */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Eq. 11 / 20: F = sum_e F_e, F_e = theta_e f_k,e K0_e T_e with f_k,e the element mean of the
+ * nodal f_k(T_i) (Section 4.2.2).  F [nn] is overwritten. */
+void orc_internal_loads(const orc_model *m, const double *T, double *F)
+{
+    const int npe = m->npe;
+    memset(F, 0, m->nn * sizeof(double));
+    for (int64_t e = 0; e < m->ne; ++e) {
+        const int32_t *c = m->conn + npe * e;
+        const double *Ke = m->K + (int64_t)npe * npe * e;
+        double fk = 0.0;
+        for (int i = 0; i < npe; ++i) fk += 1.0 + m->k_lin * T[c[i]];
+        fk /= npe;
+        const double s = m->theta[e] * fk;
+        for (int i = 0; i < npe; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < npe; ++j) acc += Ke[npe * i + j] * T[c[j]];
+            F[c[i]] += s * acc;
+        }
+    }
+}
+
+/* Net external nodal heat flow Q_i (Eq. 4, 5, 7 lumped to nodes). */
+double orc_nodal_Q(const orc_model *m, int64_t i, double Ti)
+{
+    const double a = Ti - m->T_zero, b = m->T_amb - m->T_zero;
+    return m->Qext[i] - m->Ac[i] * m->h * (Ti - m->T_inf)
+         - m->Ar[i] * ORC_SIGMA * m->eps * (a * a * a * a - b * b * b * b);
+}
+
+/* dQ_i/dT_i */
+static double orc_nodal_dQ(const orc_model *m, int64_t i, double Ti)
+{
+    const double a = Ti - m->T_zero;
+    return -m->Ac[i] * m->h - m->Ar[i] * ORC_SIGMA * m->eps * 4.0 * a * a * a;
+}
+
+/*
+ * n explicit steps (Eq. 15 / 16) from T (in/out, Dirichlet values already imposed).
+ * energy (optional, [n][2]): per step S = sum_free C_i(T_i)(T_i' - T_i) and
+ * B = dt (sum_free Q_i + sum_Dirichlet F_i).
+ * trace (optional): T at the sensor nodes after every `sample_every`-th step, [n/sample_every][ns].
+ */
+void orc_run(const orc_model *m, double dt, int64_t nsteps, double *T, double *energy,
+             const int32_t *sensors, int32_t ns, int32_t sample_every, double *trace)
+{
+    double *F = (double *)malloc(m->nn * sizeof(double));
+    for (int64_t n = 0; n < nsteps; ++n) {
+        orc_internal_loads(m, T, F);
+        double S = 0.0, B = 0.0;
+        for (int64_t i = 0; i < m->nn; ++i) {
+            if (m->isdir[i]) {
+                B += dt * F[i];
+                continue;
+            }
+            const double Q = orc_nodal_Q(m, i, T[i]);
+            const double Ci = m->C0[i] * (1.0 + m->c_lin * T[i]);
+            const double Tn = T[i] + dt / Ci * (Q - F[i]);
+            S += Ci * (Tn - T[i]);
+            B += dt * Q;
+            T[i] = Tn;
+        }
+        if (energy) {
+            energy[2 * n] = S;
+            energy[2 * n + 1] = B;
+        }
+        if (trace && sample_every > 0 && (n + 1) % sample_every == 0) {
+            const int64_t k = (n + 1) / sample_every - 1;
+            for (int s = 0; s < ns; ++s) trace[k * ns + s] = T[sensors[s]];
+        }
+    }
+    free(F);
+}
+
+/*
+ * Critical time step (Section 3.4, Eq. 29).  lambda_cond = largest eigenvalue of
+ * C0^-1/2 K0 C0^-1/2 on the free nodes (K0 = sum_e theta_e K0_e) by FP64 power iteration
+ * (stops when the Rayleigh quotient changes by < tol relative, or after max_iter);
+ *   lambda = lambda_cond * max f_k / min f_c + max_i (A^c_i h + A^r_i 4 sigma eps max|T - T_z|^3)
+ *            / (C0_i min f_c),  extrema over [T_lo, T_hi];   dt_crit = 2 / lambda.
+ * out[0] = dt_crit, out[1] = lambda_cond, out[2] = iterations used.
+ */
+void orc_dt_crit(const orc_model *m, double T_lo, double T_hi, double tol, int64_t max_iter, double *out)
+{
+    const int64_t nn = m->nn;
+    double *x = (double *)malloc(nn * sizeof(double));
+    double *y = (double *)malloc(nn * sizeof(double));
+    double *F = (double *)malloc(nn * sizeof(double));
+    orc_model lin = *m;
+    lin.k_lin = 0.0;
+    double nrm = 0.0;
+    for (int64_t i = 0; i < nn; ++i) {
+        x[i] = m->isdir[i] ? 0.0 : 1.0 + 0.5 * sin(0.7 * (double)i + 0.3);
+        nrm += x[i] * x[i];
+    }
+    nrm = sqrt(nrm);
+    for (int64_t i = 0; i < nn; ++i) x[i] /= nrm;
+    double lam = 0.0;
+    int64_t it;
+    for (it = 0; it < max_iter; ++it) {
+        for (int64_t i = 0; i < nn; ++i) y[i] = m->isdir[i] ? 0.0 : x[i] / sqrt(m->C0[i]);
+        orc_internal_loads(&lin, y, F);
+        double rq = 0.0, yy = 0.0;
+        for (int64_t i = 0; i < nn; ++i) {
+            y[i] = m->isdir[i] ? 0.0 : F[i] / sqrt(m->C0[i]);
+            rq += x[i] * y[i];
+            yy += y[i] * y[i];
+        }
+        yy = sqrt(yy);
+        for (int64_t i = 0; i < nn; ++i) x[i] = y[i] / yy;
+        const double done = fabs(rq - lam) <= tol * fabs(rq);
+        lam = rq;
+        if (done) break;
+    }
+    const double fk_max = fmax(1.0 + m->k_lin * T_lo, 1.0 + m->k_lin * T_hi);
+    const double fc_min = fmin(1.0 + m->c_lin * T_lo, 1.0 + m->c_lin * T_hi);
+    const double rl = fabs(T_lo - m->T_zero), rh = fabs(T_hi - m->T_zero);
+    const double r3 = fmax(rl * rl * rl, rh * rh * rh);
+    double surf = 0.0;
+    for (int64_t i = 0; i < nn; ++i) {
+        if (m->isdir[i]) continue;
+        const double s = (m->Ac[i] * m->h + m->Ar[i] * 4.0 * ORC_SIGMA * m->eps * r3) / (m->C0[i] * fc_min);
+        if (s > surf) surf = s;
+    }
+    out[0] = 2.0 / (lam * fk_max / fc_min + surf);
+    out[1] = lam;
+    out[2] = (double)it;
+    free(x);
+    free(y);
+    free(F);
+}
+
+/*
+ * Discrete adjoint of n explicit steps (derived by hand from Eq. 16 and Eq. 20 for the loss
+ * L(trace) with trace sampled after every `sample_every`-th step).  All states T^0..T^n are
+ * kept (no checkpointing).  With a_i = dt / (C0_i f_c(T_i)) on free nodes (0 on Dirichlet),
+ * mu_i = a_i lambda_i^{n+1}:
+ *   lambda_j^n = dL/dT_j^n + lambda_j^{n+1} (1 + a_j'(T_j) R_j) + mu_j dQ_j/dT_j
+ *              - sum_{e∋j} theta_e [ f_k,e (K0_e mu_e)_j + (mu_e . K0_e T_e) k_lin / npe ],
+ *   R_j = Q_j - F_j,  a_j' = -a_j c_lin / f_c(T_j),
+ *   dL/dtheta_e = -sum_n f_k,e mu_e . K0_e T_e^n,   dL/ds_e = sum_n sum_{i in e} mu_i w_ie.
+ * T0 [nn]: initial state (Dirichlet imposed); dLdtrace [n/sample_every][ns];
+ * outputs g_theta [ne], g_source [ne] (overwritten); trace_out optional forward trace.
+ */
+void orc_adjoint(const orc_model *m, double dt, int64_t nsteps, const double *T0,
+                 const int32_t *sensors, int32_t ns, int32_t sample_every, const double *dLdtrace,
+                 double *g_theta, double *g_source)
+{
+    const int64_t nn = m->nn, ne = m->ne;
+    const int npe = m->npe;
+    double *states = (double *)malloc((size_t)(nsteps + 1) * nn * sizeof(double));
+    memcpy(states, T0, nn * sizeof(double));
+    for (int64_t n = 0; n < nsteps; ++n) {
+        memcpy(states + (n + 1) * nn, states + n * nn, nn * sizeof(double));
+        orc_run(m, dt, 1, states + (n + 1) * nn, NULL, NULL, 0, 0, NULL);
+    }
+    double *lam = (double *)calloc(nn, sizeof(double));
+    double *lnew = (double *)malloc(nn * sizeof(double));
+    double *mu = (double *)malloc(nn * sizeof(double));
+    double *F = (double *)malloc(nn * sizeof(double));
+    double *musum = (double *)calloc(nn, sizeof(double));
+    memset(g_theta, 0, ne * sizeof(double));
+    for (int64_t n = nsteps; n >= 1; --n) {
+        if (sample_every > 0 && n % sample_every == 0) {
+            const int64_t k = n / sample_every - 1;
+            for (int s = 0; s < ns; ++s) lam[sensors[s]] += dLdtrace[k * ns + s];
+        }
+        /* lam holds lambda^n; propagate through the step T^{n-1} -> T^n */
+        const double *T = states + (n - 1) * nn;
+        orc_internal_loads(m, T, F);
+        for (int64_t i = 0; i < nn; ++i) {
+            if (m->isdir[i]) {
+                mu[i] = 0.0;
+                lnew[i] = lam[i];
+                continue;
+            }
+            const double fc = 1.0 + m->c_lin * T[i];
+            const double a = dt / (m->C0[i] * fc);
+            const double R = orc_nodal_Q(m, i, T[i]) - F[i];
+            const double da = -a * m->c_lin / fc;
+            mu[i] = a * lam[i];
+            lnew[i] = lam[i] * (1.0 + da * R) + mu[i] * orc_nodal_dQ(m, i, T[i]);
+            musum[i] += mu[i];
+        }
+        for (int64_t e = 0; e < ne; ++e) {
+            const int32_t *c = m->conn + npe * e;
+            const double *Ke = m->K + (int64_t)npe * npe * e;
+            double fk = 0.0;
+            for (int i = 0; i < npe; ++i) fk += 1.0 + m->k_lin * T[c[i]];
+            fk /= npe;
+            double muKT = 0.0;
+            for (int i = 0; i < npe; ++i) {
+                double kt = 0.0;
+                for (int j = 0; j < npe; ++j) kt += Ke[npe * i + j] * T[c[j]];
+                muKT += mu[c[i]] * kt;
+            }
+            for (int j = 0; j < npe; ++j) {
+                double kmu = 0.0;
+                for (int i = 0; i < npe; ++i) kmu += Ke[npe * i + j] * mu[c[i]];
+                lnew[c[j]] -= m->theta[e] * (fk * kmu + muKT * m->k_lin / npe);
+            }
+            g_theta[e] -= fk * muKT;
+        }
+        double *t = lam;
+        lam = lnew;
+        lnew = t;
+    }
+    for (int64_t e = 0; e < ne; ++e) {
+        double s = 0.0;
+        for (int i = 0; i < npe; ++i) s += musum[m->conn[npe * e + i]] * m->W[npe * e + i];
+        g_source[e] = s;
+    }
+    free(states);
+    free(lam);
+    free(lnew);
+    free(mu);
+    free(F);
+    free(musum);
+}

@@ -1,0 +1,217 @@
+"""FED-FEM oracle (Python side): TEST INFRASTRUCTURE ONLY.
+
+Builds and loads ``fedfem_oracle.c`` (plain single-threaded FP64 C) and wraps it with numpy.
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this module.  It shares no code with the CUDA library ``paper_1909_03355_gb300``; the
+only common input is the problem statement built by ``fedfem_inputs``.
+
+Function map (paper passages):
+  OracleModel(...)            pre-computation stage, Fig. 1 (i): Eq. 12/17-19/22, lumped mass
+                              (Section 3.1), surface area shares (Eq. 4/7 lumped to nodes)
+  OracleModel.internal_loads  Eq. 11/20 with the element-mean k(T) of Section 4.2.2
+  OracleModel.run             time-stepping stage, Fig. 1 (iii): Eq. 15/16, Dirichlet re-imposed
+  OracleModel.dt_crit         Section 3.4, Eq. 29
+  OracleModel.adjoint         reverse-time discrete adjoint of Eq. 16/20 (derived, no paper
+                              counterpart)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fedfem_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SIGMA = 5.67e-8
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction, portable flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Model(C.Structure):
+    _fields_ = [("nn", C.c_int64), ("ne", C.c_int64), ("npe", C.c_int32), ("pad", C.c_int32),
+                ("conn", C.c_void_p), ("K", C.c_void_p), ("theta", C.c_void_p), ("W", C.c_void_p),
+                ("C0", C.c_void_p), ("Qext", C.c_void_p), ("Ac", C.c_void_p), ("Ar", C.c_void_p),
+                ("isdir", C.c_void_p), ("k_lin", C.c_double), ("c_lin", C.c_double),
+                ("h", C.c_double), ("T_inf", C.c_double), ("eps", C.c_double),
+                ("T_amb", C.c_double), ("T_zero", C.c_double)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            P = C.c_void_p
+            L.orc_hex_matrices.argtypes = [P, P, P, P, P]
+            L.orc_tet_matrices.argtypes = [P, P, P, P, P]
+            L.orc_face_area.argtypes = [P, C.c_int]
+            L.orc_face_area.restype = C.c_double
+            L.orc_precompute.argtypes = [C.c_int64, C.c_int64, C.c_int32, P, P, P, P, P, P, P, P,
+                                         C.c_int64, C.c_int32, P, C.c_int64, C.c_int32, P,
+                                         C.c_int64, P, P, P, P, P, P, P, P]
+            L.orc_precompute.restype = C.c_int64
+            L.orc_internal_loads.argtypes = [P, P, P]
+            L.orc_nodal_Q.argtypes = [P, C.c_int64, C.c_double]
+            L.orc_nodal_Q.restype = C.c_double
+            L.orc_run.argtypes = [P, C.c_double, C.c_int64, P, P, P, C.c_int32, C.c_int32, P]
+            L.orc_dt_crit.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_int64, P]
+            L.orc_adjoint.argtypes = [P, C.c_double, C.c_int64, P, P, C.c_int32, C.c_int32, P, P, P]
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.int32)
+
+
+def hex_matrices(x, k):
+    """(K [8,8], w [8], volume) of one hexahedron by 2x2x2 Gauss quadrature (Eq. 12)."""
+    x, k = _f64(x), _f64(k)
+    K, w, v = np.zeros((8, 8)), np.zeros(8), np.zeros(1)
+    if lib().orc_hex_matrices(_p(x), _p(k), _p(K), _p(w), _p(v)):
+        raise ValueError("det J <= 0")
+    return K, w, float(v[0])
+
+
+def tet_matrices(x, k):
+    """(K [4,4], w [4], volume) of one linear tetrahedron (Eq. 18)."""
+    x, k = _f64(x), _f64(k)
+    K, w, v = np.zeros((4, 4)), np.zeros(4), np.zeros(1)
+    if lib().orc_tet_matrices(_p(x), _p(k), _p(K), _p(w), _p(v)):
+        raise ValueError("V <= 0")
+    return K, w, float(v[0])
+
+
+def face_area(x):
+    x = _f64(x)
+    return lib().orc_face_area(_p(x), int(x.shape[0]))
+
+
+class OracleModel:
+    """Pre-computed FP64 model of one problem (Fig. 1 (i))."""
+
+    def __init__(self, p, theta=None, source=None):
+        L = lib()
+        self.p = p
+        nn, ne, npe = p.n_nodes, p.n_elems, p.npe
+        self.xyz = _f64(p.xyz)
+        self.conn = _i32(p.conn)
+        mats = p.mats
+        self.mat_k0 = np.ascontiguousarray(np.stack([np.asarray(m.k0, float).reshape(9) for m in mats]))
+        self.mat_rho = np.array([m.rho for m in mats], float)
+        self.mat_c0 = np.array([m.c0 for m in mats], float)
+        k_lin = {m.k_lin for m in mats}
+        c_lin = {m.c_lin for m in mats}
+        if len(k_lin) != 1 or len(c_lin) != 1:
+            raise ValueError("all materials must share k_lin and c_lin")
+        self.elem_mat = _i32(p.elem_mat)
+        th = theta if theta is not None else p.elem_kscale
+        self.theta = _f64(th) if th is not None else np.ones(ne)
+        src = source if source is not None else p.elem_source
+        self.source = _f64(src)
+        self.nodal_Q_in = _f64(p.nodal_Q)
+        conv = _i32(p.conv_faces) if p.conv_faces is not None and len(p.conv_faces) else None
+        rad = _i32(p.rad_faces) if p.rad_faces is not None and len(p.rad_faces) else None
+        dn = _i32(p.dir_nodes) if p.dir_nodes is not None and len(p.dir_nodes) else None
+        self.K = np.zeros((ne, npe, npe))
+        self.W = np.zeros((ne, npe))
+        self.C0 = np.zeros(nn)
+        self.Qext = np.zeros(nn)
+        self.Ac = np.zeros(nn)
+        self.Ar = np.zeros(nn)
+        self.isdir = np.zeros(nn, np.int32)
+        rc = L.orc_precompute(nn, ne, npe, _p(self.xyz), _p(self.conn), _p(self.elem_mat),
+                              _p(self.mat_k0), _p(self.mat_rho), _p(self.mat_c0), _p(self.source),
+                              _p(self.nodal_Q_in),
+                              0 if conv is None else conv.shape[0], 0 if conv is None else conv.shape[1], _p(conv),
+                              0 if rad is None else rad.shape[0], 0 if rad is None else rad.shape[1], _p(rad),
+                              0 if dn is None else dn.shape[0], _p(dn),
+                              _p(self.K), _p(self.W), _p(self.C0), _p(self.Qext), _p(self.Ac),
+                              _p(self.Ar), _p(self.isdir))
+        if rc:
+            raise ValueError(f"element {rc - 1} has det J <= 0")
+        self._keep = (conv, rad, dn)
+        self.m = _Model(nn=nn, ne=ne, npe=npe, pad=0, conn=_p(self.conn), K=_p(self.K),
+                        theta=_p(self.theta), W=_p(self.W), C0=_p(self.C0), Qext=_p(self.Qext),
+                        Ac=_p(self.Ac), Ar=_p(self.Ar), isdir=_p(self.isdir),
+                        k_lin=float(mats[0].k_lin), c_lin=float(mats[0].c_lin),
+                        h=float(p.h), T_inf=float(p.T_inf), eps=float(p.eps), T_amb=float(p.T_amb),
+                        T_zero=float(p.T_zero))
+        self.mref = C.byref(self.m)
+
+    # lumped thermal mass at f_c = 1 (Section 3.1, Eq. 14 / 21)
+    @property
+    def mass(self):
+        return self.C0
+
+    def internal_loads(self, T):
+        T = _f64(T)
+        F = np.zeros(self.p.n_nodes)
+        lib().orc_internal_loads(self.mref, _p(T), _p(F))
+        return F
+
+    def nodal_Q(self, T):
+        T = _f64(T)
+        L = lib()
+        return np.array([L.orc_nodal_Q(self.mref, i, float(T[i])) for i in range(len(T))])
+
+    def run(self, T, dt, nsteps, energy=False, sensors=None, sample_every=0):
+        """n explicit steps from T (copied); returns T (and per-step energy [n,2], trace)."""
+        T = np.array(T, dtype=np.float64, copy=True)
+        E = np.zeros((nsteps, 2)) if energy else None
+        sens = _i32(sensors)
+        trace = None
+        if sens is not None and sample_every > 0:
+            trace = np.zeros((nsteps // sample_every, len(sens)))
+        lib().orc_run(self.mref, float(dt), int(nsteps), _p(T), _p(E), _p(sens),
+                      0 if sens is None else len(sens), int(sample_every), _p(trace))
+        out = [T]
+        if energy:
+            out.append(E)
+        if trace is not None:
+            out.append(trace)
+        return out[0] if len(out) == 1 else tuple(out)
+
+    def dt_crit(self, T_lo=None, T_hi=None, tol=1e-12, max_iter=200000):
+        """(dt_crit, lambda_cond, iterations) of Section 3.4."""
+        T_lo = self.p.T_lo if T_lo is None else T_lo
+        T_hi = self.p.T_hi if T_hi is None else T_hi
+        out = np.zeros(3)
+        lib().orc_dt_crit(self.mref, float(T_lo), float(T_hi), float(tol), int(max_iter), _p(out))
+        return float(out[0]), float(out[1]), int(out[2])
+
+    def adjoint(self, dt, nsteps, T0, sensors, sample_every, dLdtrace):
+        """(dL/dtheta [E], dL/dsource [E]) for a loss of the sensor trace."""
+        T0 = _f64(T0)
+        sens = _i32(sensors)
+        g = _f64(dLdtrace)
+        gt = np.zeros(self.p.n_elems)
+        gs = np.zeros(self.p.n_elems)
+        lib().orc_adjoint(self.mref, float(dt), int(nsteps), _p(T0), _p(sens), len(sens),
+                          int(sample_every), _p(g), _p(gt), _p(gs))
+        return gt, gs

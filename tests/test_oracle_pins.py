@@ -1,0 +1,396 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: exact closed forms, textbook
+identities, the paper's patch test (Section 4.1, Fig. 2), an exact 1-D reduction, library
+eigen-solvers, and finite differences of its own forward loop for the adjoint.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+from scipy.special import erfc
+
+import fedfem_inputs as fi
+from oracle import oracle as O
+from tests import brute
+
+RNG = np.random.default_rng(1234)
+
+
+def _rand_spd(rng):
+    A = rng.standard_normal((3, 3))
+    return A @ A.T + 0.5 * np.eye(3)
+
+
+# ------------------------------------------------------------------------- element matrices --
+
+@pytest.mark.parametrize("seed", range(5))
+def test_brick_matches_tensor_product_closed_form(seed):
+    """Eq. 12 on a rectangular brick with a full anisotropic k vs exact 1-D integral products."""
+    rng = np.random.default_rng(seed)
+    dims = rng.uniform(0.2, 2.0, size=3)
+    k = _rand_spd(rng)
+    x0 = rng.uniform(-1, 1, size=3)
+    x = x0 + brute.VTK_CORNERS * dims
+    K, w, vol = O.hex_matrices(x, k)
+    Kc = brute.brick_K(dims, k)
+    assert np.max(np.abs(K - Kc)) <= 1e-14 * np.max(np.abs(Kc)) * 10
+    assert np.allclose(w, np.prod(dims) / 8, rtol=1e-14)
+    assert vol == pytest.approx(np.prod(dims), rel=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_tet_matches_face_vector_formula(seed):
+    """Eq. 18 (V B^T k B via the inverse of [1 x y z]) vs K_ij = S_i.k S_j / 9V."""
+    rng = np.random.default_rng(100 + seed)
+    x = rng.uniform(0, 1, size=(4, 3))
+    if np.dot(np.cross(x[1] - x[0], x[2] - x[0]), x[3] - x[0]) < 0:
+        x[[1, 2]] = x[[2, 1]]
+    k = _rand_spd(rng)
+    K, w, vol = O.tet_matrices(x, k)
+    Kf, V = brute.tet_K_facevec(x, k)
+    assert np.max(np.abs(K - Kf)) <= 1e-13 * np.max(np.abs(Kf))
+    assert vol == pytest.approx(V, rel=1e-14)
+    assert np.allclose(w, V / 4, rtol=1e-14)
+
+
+def test_distorted_elements_invariants(patch_nodes):
+    """K 1 = 0 (a constant field carries no heat), symmetry, sum_i w_i = volume."""
+    k = _rand_spd(np.random.default_rng(7))
+    for kind in ("hex", "tet"):
+        p = fi.patch_problem(patch_nodes, kind)
+        for c in p.conn:
+            x = p.xyz[c]
+            K, w, vol = (O.hex_matrices if kind == "hex" else O.tet_matrices)(x, k)
+            scale = np.max(np.abs(K))
+            assert np.max(np.abs(K.sum(axis=1))) <= 1e-13 * scale
+            assert np.max(np.abs(K - K.T)) <= 1e-14 * scale
+            assert w.sum() == pytest.approx(vol, rel=1e-13)
+        # the patch fills the unit cube exactly
+        tot = sum((O.hex_matrices if kind == "hex" else O.tet_matrices)(p.xyz[c], k)[2] for c in p.conn)
+        assert tot == pytest.approx(1.0, rel=1e-12)
+
+
+def test_face_areas():
+    """Quad area by bilinear-patch quadrature and triangle area vs closed forms."""
+    sq = np.array([[0, 0, 0], [2, 0, 0], [2, 3, 0], [0, 3, 0]], float)
+    assert O.face_area(sq) == pytest.approx(6.0, rel=1e-15)
+    par = np.array([[0, 0, 0], [2, 0, 0], [3, 1, 1], [1, 1, 1]], float)   # parallelogram
+    assert O.face_area(par) == pytest.approx(np.linalg.norm(np.cross(par[1] - par[0], par[3] - par[0])), rel=1e-14)
+    tri = np.array([[0, 0, 0], [1, 0, 0], [0, 2, 0]], float)
+    assert O.face_area(tri) == pytest.approx(1.0, rel=1e-15)
+
+
+# ---------------------------------------------------------------------- assembly / scatter --
+
+def _tiny_problems(patch_nodes):
+    out = []
+    for n in (2, 3):
+        xyz, conn = fi.cube_mesh(n, "hex")
+        out.append(("hex", n, xyz, conn))
+    xyz, conn = fi.cube_mesh(3, "tet")
+    out.append(("tet", 3, xyz, conn))
+    return out
+
+
+@pytest.mark.parametrize("which", range(3))
+def test_element_loop_matches_dense_assembly(which, patch_nodes):
+    """Eq. 11 / 20: the element loop with scatter equals a dense assembled K(T) T, including
+    the per-element scale theta_e and the element-mean f_k of Section 4.2.2."""
+    kind, n, xyz, conn = _tiny_problems(patch_nodes)[which]
+    rng = np.random.default_rng(50 + which)
+    k = _rand_spd(rng)
+    h = 1.0 / n
+    if kind == "hex":
+        Ke = np.array([brute.brick_K((h, h, h), k)] * len(conn))
+    else:
+        Ke = np.array([brute.tet_K_facevec(xyz[c], k)[0] for c in conn])
+    theta = rng.uniform(0.5, 2.0, size=len(conn))
+    k_lin = 0.003
+    p = fi.Problem("t", xyz, conn, [fi.Material(1.0, k, k_lin, 1.0, 0.0)], elem_kscale=theta,
+                   T0=np.zeros(len(xyz)))
+    m = O.OracleModel(p)
+    T = rng.uniform(0, 300, size=len(xyz))
+    fk = np.array([np.mean(1 + k_lin * T[c]) for c in conn])
+    Kd = brute.dense_assemble(conn, Ke, len(xyz), theta * fk)
+    ref = Kd @ T
+    got = m.internal_loads(T)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    # constant field: no internal load
+    Fc = m.internal_loads(np.full(len(xyz), 37.0))
+    assert np.max(np.abs(Fc)) <= 1e-13 * 37.0 * np.max(np.abs(Kd))
+    # internal loads sum to zero (conservation, Eq. 11)
+    assert abs(got.sum()) <= 1e-13 * np.abs(got).sum()
+
+
+# -------------------------------------------------------------------------- patch tests -----
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_patch_test_steady_state(kind, patch_nodes):
+    """Section 4.1: T = 200x + 100y + 200z on the cube corners; interior nodes must follow the
+    same linear field at steady state (direct solve and explicit run to steady state)."""
+    k = np.array([[3.0, 0.5, 0.2], [0.5, 2.0, 0.3], [0.2, 0.3, 1.0]])   # anisotropic too
+    for kk in (np.eye(3), k):
+        p = fi.patch_problem(patch_nodes, kind, k0=kk)
+        m = O.OracleModel(p)
+        lin = p.xyz @ np.array([200.0, 100.0, 200.0])
+        free = p.free_mask()
+        Kd = brute.dense_assemble(p.conn, m.K, p.n_nodes)
+        Tf = np.linalg.solve(Kd[np.ix_(free, free)], -Kd[np.ix_(free, ~free)] @ lin[~free])
+        assert np.max(np.abs(Tf - lin[free])) <= 1e-12 * np.max(np.abs(lin))
+        dt = 0.9 * m.dt_crit()[0]
+        T = m.run(p.initial_T(), dt, 20000)
+        assert np.max(np.abs(T - lin)) <= 1e-10 * np.max(np.abs(lin))
+
+
+# ----------------------------------------------------------- fully discrete closed form (C1) --
+
+@pytest.mark.parametrize("nsteps", [1, 10, 50, 100, 1000])
+def test_plain_cube_discrete_closed_form(nsteps):
+    """Plain cube (10^3 bricks, T0 = 100, T = 0 on the boundary): the oracle equals the exact
+    sine-mode solution of the lumped-mass forward-Euler system at every step count."""
+    p = fi.plain_cube(10)
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    ref, lam_max = brute.c1_closed_form(10, dt, nsteps)
+    T = m.run(p.initial_T(), dt, nsteps)
+    assert np.max(np.abs(T - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_plain_cube_critical_step_closed_form():
+    """Section 3.4: lambda_max of the plain cube is the largest sine-mode eigenvalue."""
+    p = fi.plain_cube(10)
+    m = O.OracleModel(p)
+    dtc, lam, _ = m.dt_crit(tol=1e-14)
+    _, lam_max = brute.c1_closed_form(10, 1e-3, 0)
+    assert lam == pytest.approx(lam_max, rel=1e-9)
+    assert dtc == pytest.approx(2.0 / lam_max, rel=1e-9)
+    assert 0.9 * dtc == pytest.approx(4.6836e-3, rel=1e-4)
+
+
+def test_plain_cube_vs_continuum_series():
+    """Reported error vs the continuum separable series (O(h^2) + O(dt)); a loose bound."""
+    p = fi.plain_cube(10)
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    T = m.run(p.initial_T(), dt, 10)
+    t = 10 * dt
+    x = p.xyz
+    ser = np.zeros(len(x))
+    for l in range(1, 60, 2):
+        for mm in range(1, 60, 2):
+            for q in range(1, 60, 2):
+                ser += (6400.0 / (np.pi ** 3 * l * mm * q)) * np.sin(l * np.pi * x[:, 0]) \
+                    * np.sin(mm * np.pi * x[:, 1]) * np.sin(q * np.pi * x[:, 2]) \
+                    * np.exp(-np.pi ** 2 * (l * l + mm * mm + q * q) * t)
+    centre = np.argmin(np.sum((x - 0.5) ** 2, axis=1))
+    assert abs(T[centre] - ser[centre]) / ser[centre] < 0.1
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_critical_step_vs_dense_eigensolver(n):
+    """Power iteration vs scipy's generalized symmetric eigen-solver on tiny meshes."""
+    for kind in ("hex", "tet"):
+        p = fi.nonlinear_cube(n, kind)
+        p.dir_nodes = np.array([0, 1], np.int32)
+        p.dir_T = np.array([20.0, 20.0])
+        m = O.OracleModel(p)
+        free = p.free_mask()
+        Kd = brute.dense_assemble(p.conn, m.K, p.n_nodes)
+        lam = scipy.linalg.eigh(Kd[np.ix_(free, free)], np.diag(m.C0[free]), eigvals_only=True).max()
+        _, lam_o, _ = m.dt_crit(tol=1e-15, max_iter=500000)
+        assert lam_o == pytest.approx(lam, rel=1e-8)
+
+
+# ------------------------------------------------------------------------------ slab ------
+
+@pytest.mark.parametrize("ny", [1, 2])
+@pytest.mark.parametrize("nonlinear", [False, True])
+def test_slab_reduces_to_1d_recurrence(ny, nonlinear):
+    """A bar of bricks with T held at x = 0 and fields constant over cross-sections reduces
+    exactly to the 1-D forward-Euler recurrence (consistent brick row sums = lumped mass);
+    the nonlinear variant pins the element-mean k(T) and nodal c(T)."""
+    nx, k, rho, c0 = 20, 2.0, 3.0, 1.5
+    kl, cl = (0.01, 0.004) if nonlinear else (0.0, 0.0)
+    src = 50.0
+    p = fi.slab(nx, ny, ny, Lx=1.0, k=(k, 7.0, 9.0), rho=rho, c0=c0, k_lin=kl, c_lin=cl,
+                T0=0.0, T_s=100.0, conv_end=(4.0, 10.0))
+    p.elem_source = np.full(p.n_elems, src)
+    m = O.OracleModel(p)
+    h = 1.0 / nx
+    dt = 0.2 * rho * c0 * h * h / (k * 3.0)
+    T = m.run(p.initial_T(), dt, 300)
+    ref = brute.ftcs_slab(nx, h, dt, 300, 0.0, 100.0, k, rho, c0, kl, cl, conv=(4.0, 10.0),
+                          source=src)
+    ix = np.rint(p.xyz[:, 0] / h).astype(int)
+    assert np.max(np.abs(T - ref[ix])) <= 1e-13 * 100.0
+
+
+def test_slab_erfc_convergence():
+    """Semi-infinite-slab closed form T0 + (Ts - T0) erfc(x / 2 sqrt(alpha t)): the error
+    shrinks as the mesh is refined (O(h^2) with dt ~ h^2)."""
+    errs = []
+    for nx in (20, 40, 80):
+        h = 1.0 / nx
+        p = fi.slab(nx, 1, 1, Lx=1.0, k=(1.0, 1.0, 1.0), rho=1.0, c0=1.0, T0=0.0, T_s=1.0)
+        m = O.OracleModel(p)
+        dt = 0.25 * h * h
+        t_end = 0.01
+        ns = int(round(t_end / dt))
+        T = m.run(p.initial_T(), dt, ns)
+        x = p.xyz[:, 0]
+        exact = erfc(x / (2.0 * np.sqrt(ns * dt)))
+        sel = x <= 0.5
+        errs.append(np.max(np.abs(T[sel] - exact[sel])))
+    assert errs[1] < 0.5 * errs[0] and errs[2] < 0.5 * errs[1]
+
+
+# ----------------------------------------------------------------------- surface loads ----
+
+def test_single_brick_surface_ode():
+    """One brick with convection and radiation on all faces: every node has the same
+    area / mass ratio, a uniform field stays uniform and each node follows the scalar
+    forward-Euler ODE  C(T) dT = -A [h (T - T_inf) + sigma eps (T_K^4 - T_aK^4)] dt  (Kelvin)."""
+    a, b, c = 0.3, 0.5, 0.7
+    rho, c0, cl = 800.0, 900.0, 0.002
+    hc, Tinf, eps, Ta = 40.0, 15.0, 0.7, -50.0
+    p = fi.single_brick(a, b, c, rho, c0, cl, T0=400.0, conv=(hc, Tinf), rad=(eps, Ta))
+    m = O.OracleModel(p)
+    A = (a * b + b * c + c * a) / 4.0
+    Cn = rho * c0 * a * b * c / 8.0
+    assert np.allclose(m.Ac, A, rtol=1e-14) and np.allclose(m.Ar, A, rtol=1e-14)
+    assert np.allclose(m.C0, Cn, rtol=1e-14)
+    dt = 0.5
+    T = m.run(p.initial_T(), dt, 200)
+    s = 400.0
+    for _ in range(200):
+        tk, tak = s + 273.15, Ta + 273.15
+        q = -A * (hc * (s - Tinf) + 5.67e-8 * eps * (tk ** 4 - tak ** 4))
+        s = s + dt / (Cn * (1 + cl * s)) * q
+    assert np.max(np.abs(T - s)) <= 1e-12 * abs(s)
+
+
+def test_single_brick_nodal_loads():
+    """Concentrated nodal heat flows (Eq. 5 applied as nodal loads): uniform heating
+    dT = dt q / C_i when every node receives the same q."""
+    p = fi.single_brick(0.2, 0.3, 0.4, rho=10.0, c0=3.0, T0=5.0)
+    p.nodal_Q = np.full(8, 0.7)
+    m = O.OracleModel(p)
+    Cn = 10.0 * 3.0 * 0.024 / 8
+    T = m.run(p.initial_T(), 0.01, 7)
+    assert np.allclose(T, 5.0 + 7 * 0.01 * 0.7 / Cn, rtol=1e-14)
+
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_surface_area_shares_sum_to_face_areas(kind):
+    """Nodal-quadrature lumping keeps the total area: sum A^c = 1 (top), sum A^r = 4 (sides)."""
+    p = fi.nonlinear_cube(4, kind)
+    m = O.OracleModel(p)
+    assert m.Ac.sum() == pytest.approx(1.0, rel=1e-13)
+    assert m.Ar.sum() == pytest.approx(4.0, rel=1e-13)
+    assert m.C0.sum() == pytest.approx(2700.0 * 500.0, rel=1e-13)
+    assert m.Qext.sum() == pytest.approx(1e5 / 8, rel=1e-13)
+
+
+def test_critical_step_surface_term():
+    """With negligible conduction, dt_crit reduces to the scalar forward-Euler limit of the
+    linearised surface ODE, 2 C min(f_c) / (A (h + 4 sigma eps max|T - T_z|^3))."""
+    p = fi.single_brick(0.5, 0.5, 0.5, rho=100.0, c0=10.0, c_lin=0.001, conv=(30.0, 20.0),
+                        rad=(0.5, 20.0))
+    p.mats[0].k0 = 1e-14 * np.eye(3)
+    p.T_lo, p.T_hi = 20.0, 500.0
+    m = O.OracleModel(p)
+    A = 3 * 0.25 / 4
+    Cn = 100.0 * 10.0 * 0.125 / 8
+    rate = A * (30.0 + 4 * 5.67e-8 * 0.5 * (500 + 273.15) ** 3) / (Cn * 1.02)
+    assert m.dt_crit()[0] == pytest.approx(2.0 / rate, rel=1e-9)
+
+
+def test_stefan_law_spot_value():
+    """Eq. 7 lumped on a node with unit radiating area: sigma eps ((T-Tz)^4 - (Ta-Tz)^4)."""
+    p = fi.single_brick(1, 1, 1, T0=0.0, rad=(0.66, -50.0))
+    m = O.OracleModel(p)
+    # isolate the radiation term at node 0 (Qext = 0, no convection)
+    q = m.nodal_Q(np.full(8, 37.0))[0]
+    expect = -m.Ar[0] * 5.67e-8 * 0.66 * (310.15 ** 4 - 223.15 ** 4)
+    assert q == pytest.approx(expect, rel=1e-13)
+
+
+# -------------------------------------------------------------------------- energy ---------
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_energy_balance(kind):
+    """Internal loads sum to zero, so the stored heat changes only by the boundary and source
+    flows: S^n = B^n every step (FP64)."""
+    p = fi.nonlinear_cube(5, kind)
+    p.dir_nodes = np.arange(0, 6, dtype=np.int32)
+    p.dir_T = np.full(6, 60.0)
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    T, E = m.run(p.initial_T(), dt, 60, energy=True)
+    scale = np.abs(E).max()
+    assert np.max(np.abs(E[:, 0] - E[:, 1])) <= 1e-12 * scale
+    # heat input of the source is positive early on
+    assert E[0, 1] > 0
+
+
+# ------------------------------------------------------------------------- adjoint ---------
+
+def _adjoint_setup():
+    p = fi.nonlinear_cube(3, "hex", steps=30)
+    rng = np.random.default_rng(9)
+    p.elem_kscale = rng.uniform(0.5, 2.0, size=p.n_elems)
+    p.elem_source = rng.uniform(0, 2e5, size=p.n_elems)
+    sensors = np.array([5, 13, 21, 40, 62], np.int32)
+    return p, sensors
+
+
+def test_adjoint_matches_central_differences():
+    """Reverse-time adjoint vs central finite differences of the forward loop (FP64)."""
+    p, sensors = _adjoint_setup()
+    m0 = O.OracleModel(p)
+    dt = 0.9 * m0.dt_crit()[0]
+    nsteps, se = 30, 5
+    rng = np.random.default_rng(11)
+    wts = rng.standard_normal((nsteps // se, len(sensors)))
+
+    def loss(theta, src):
+        m = O.OracleModel(p, theta=theta, source=src)
+        _, tr = m.run(p.initial_T(), dt, nsteps, sensors=sensors, sample_every=se)
+        return float(np.sum(wts * tr))
+
+    gt, gs = m0.adjoint(dt, nsteps, p.initial_T(), sensors, se, wts)
+    th, src = p.elem_kscale.copy(), p.elem_source.copy()
+    for e in (0, 4, 13, 26):
+        d = 1e-4 * th[e]
+        tp, tm = th.copy(), th.copy()
+        tp[e] += d
+        tm[e] -= d
+        fd = (loss(tp, src) - loss(tm, src)) / (2 * d)
+        assert gt[e] == pytest.approx(fd, rel=1e-6, abs=1e-9 * np.abs(gt).max())
+        d = 1e-4 * max(src[e], 1.0)
+        sp, sm = src.copy(), src.copy()
+        sp[e] += d
+        sm[e] -= d
+        fd = (loss(th, sp) - loss(th, sm)) / (2 * d)
+        assert gs[e] == pytest.approx(fd, rel=1e-6, abs=1e-9 * np.abs(gs).max())
+
+
+def test_adjoint_dot_product_linear():
+    """For a linear problem (constant k, c, no radiation) the map source -> trace is affine:
+    <J v, w> = <v, J^T w> for the Jacobian J of the trace wrt the element sources."""
+    p = fi.nonlinear_cube(3, "hex")
+    p.mats[0].k_lin = 0.0
+    p.mats[0].c_lin = 0.0
+    p.rad_faces = None
+    sensors = np.array([5, 13, 21, 40, 62], np.int32)
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    rng = np.random.default_rng(3)
+    w = rng.standard_normal((4, len(sensors)))
+    v = rng.standard_normal(p.n_elems)
+    src = p.elem_source
+    _, tr0 = O.OracleModel(p, source=src).run(p.initial_T(), dt, 20, sensors=sensors, sample_every=5)
+    _, tr1 = O.OracleModel(p, source=src + v).run(p.initial_T(), dt, 20, sensors=sensors, sample_every=5)
+    Jv = tr1 - tr0
+    _, gs = m.adjoint(dt, 20, p.initial_T(), sensors, 5, w)
+    assert np.sum(Jv * w) == pytest.approx(np.dot(v, gs), rel=1e-10)
