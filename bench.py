@@ -1,0 +1,332 @@
+"""Throughput benchmark of the FED-FEM hot path on GB300.
+
+Workload (one "step" = one explicit FED-FEM time step, Fig. 1 (iii), over the whole mesh):
+the large nonlinear cube, 128^3 trilinear hexahedra (2,097,152 elements, 2,146,689 nodes),
+orthotropic k = diag(1, 5, 20)(1 + 0.002 T), c = 500 (1 + 0.001 T), rho = 2700, convection and
+radiation on all six faces, 1e5 W/m^3 in the central 1/8, FP32 with a Kahan-compensated
+temperature accumulator.  Metric: element-steps/s (whole job, summed over ranks).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (oracle/) as it stands on the host cores, on a
+bounded sample (the same problem on a 64^3 mesh), and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "element-steps/s (128^3 hex nonlinear, FP32+Kahan; FP64 and adjoint/forward alongside)"
+UNIT = "element-steps/s"
+# algorithmic bytes per element-step (general-mesh operator, each array once per step):
+# 28 FP32 conductances + 8 int32 node ids per hexahedron, and per node T r/w (8 B), Kahan
+# compensation r/w (8 B), FP64 A (8 B), FP32 Q (4 B)
+ELEM_BYTES_FP32 = 28 * 4 + 8 * 4
+NODE_BYTES_FP32 = 8 + 8 + 8 + 4
+ELEM_BYTES_FP64 = 28 * 8 + 8 * 4
+NODE_BYTES_FP64 = 16 + 8 + 8
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_from_profile(kernel_src_hash):
+    """DRAM bytes per step of the step kernel from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "fed_step_kernel_large_hex.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("step.cu sha256") != kernel_src_hash:
+        return None
+    try:
+        return float(vals["dram bytes per element-step"])
+    except (KeyError, ValueError):
+        return None
+
+
+def src_hash():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1909_03355_gb300", "csrc", "step.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """FP64 CPU oracle timed on the host cores (the reference arm)."""
+    if rank != 0:
+        return
+    import fedfem_inputs as fi
+    from oracle import oracle as O
+    n = 64
+    p = fi.large_cube(n)
+    m = O.OracleModel(p)
+    T = p.initial_T()
+    dt = 0.9 * m.dt_crit(tol=1e-6, max_iter=300)[0]
+    steps = max(1, min(args.steps, 200))
+    warm = max(0, min(args.warmup, 3))
+    T = m.run(T, dt, warm)
+    t0 = time.perf_counter()
+    T = m.run(T, dt, steps)
+    el = time.perf_counter() - t0
+    v = p.n_elems * steps / el
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": steps, "warmup": warm,
+            "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"large_hex_{n} (bounded sample of large_hex_128: same problem on a {n}^3 mesh)",
+                       "elements": p.n_elems, "nodes": p.n_nodes},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{steps} explicit steps of the {n}^3 hex problem, single-threaded FP64 C"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    """Oracle element-steps/s on a bounded sample: 100 steps of the 128^3 problem (~10-30 s)."""
+    import fedfem_inputs as fi
+    from oracle import oracle as O
+    p = fi.large_cube(128)
+    m = O.OracleModel(p)
+    T = p.initial_T()
+    dt = 1.0
+    steps = 100
+    t0 = time.perf_counter()
+    m.run(T, dt, steps)
+    el = time.perf_counter() - t0
+    return {"value": p.n_elems * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} explicit steps of the 128^3 hex problem (dt = 1 s), single-threaded FP64 C oracle"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=400)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world, rank, local = dist_setup(args)
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import fedfem_inputs as fi
+    from paper_1909_03355_gb300.fedfem import FedFem
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # CPU baseline first (rank 0, N = 1 only), before the GPU work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample()
+
+    p = fi.large_cube(args.n)
+    stream = torch.cuda.Stream()
+    f = FedFem(p, precision=32, stream=stream)
+    dtc = f.precompute()
+    dt = 0.9 * dtc
+    f.set_dt(dt)
+    T0 = p.initial_T()
+    info = f.info()
+    spl = info["steps_per_launch"]
+
+    # ---- device-resident throughput (inputs in HBM), per-launch CUDA events on the stream
+    f.set_T(T0)
+    f.step(args.warmup)
+    K = args.steps
+    n_launch = int(math.ceil(K / spl))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch + 1)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        done = 0
+        for i in range(n_launch):
+            k = min(spl, K - done)
+            f.step_async(k)
+            done += k
+            ev[i + 1].record(stream)
+    stream.synchronize()
+    f.sync()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    durs = [ev[i].elapsed_time(ev[i + 1]) for i in range(n_launch)]
+    ms = sum(durs)
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    E, N = p.n_elems, p.n_nodes
+    value = world * E * K / (ms * 1e-3)
+
+    # roofline of the step kernel: algorithmic bytes per launch / average launch duration
+    bytes_step = ELEM_BYTES_FP32 * E + NODE_BYTES_FP32 * N
+    full = [d for i, d in enumerate(durs) if min(spl, K - i * spl) == spl] or durs
+    avg_launch_ms = sum(full) / len(full)
+    achieved = bytes_step * spl / (avg_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    tr = traffic_from_profile(src_hash())
+
+    # ---- end to end through the C ABI with host buffers (H2D of T0, D2H of T inside)
+    barrier()
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    f.set_T(T0)
+    f.step(K)
+    Tout = f.get_T()
+    e2e_s = time.perf_counter() - te
+    e2e_v = world * E * K / e2e_s
+    assert np.all(np.isfinite(Tout))
+
+    # ---- FP64 form on the same workload
+    f.close()
+    f64 = FedFem(p, precision=64, stream=stream)
+    f64.precompute()
+    f64.set_dt(dt)
+    f64.set_T(T0)
+    f64.step(20)
+    K64 = args.fp64_steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        f64.step_async(K64)
+        e1.record(stream)
+    f64.sync()
+    ms64 = e0.elapsed_time(e1)
+    v64 = world * E * K64 / (ms64 * 1e-3)
+    bytes64 = ELEM_BYTES_FP64 * E + NODE_BYTES_FP64 * N
+    f64.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"large_hex_{args.n}: {args.n}^3 hex nonlinear cube (orthotropic k(T), c(T), "
+                                   "conv+rad on all faces, central source), FP32 + Kahan",
+                       "elements": E, "nodes": N, "dt": dt, "steps_per_launch": spl, "grid": info["grid"],
+                       "block": info["block"], "tiles": info["n_tiles"], "stages": info["stages"],
+                       "element_stream_MB": info["elem_bytes"] / 1e6,
+                       "l2": "inputs larger than L2 (element stream > 129 MB), no flush",
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": None if tr is None else tr * E * spl,
+                         "algorithmic_bytes_per_launch": bytes_step * spl, "kernel": "fed_step_kernel<float,8,Kahan>",
+                         "avg_launch_ms": avg_launch_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 8 * N / K, "d2h_bytes_per_step": 8 * N / K,
+                    "seconds": e2e_s},
+            "gpu_launches": n_launch,
+            "clocks": clk,
+            "fp64": {"value": v64, "unit": UNIT, "ms_per_step": ms64 / K64, "steps": K64,
+                     "achieved_GBps": bytes64 / (ms64 * 1e-3 / K64) / 1e9},
+            "fp32_over_fp64": value / v64,
+            "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

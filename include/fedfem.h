@@ -1,0 +1,283 @@
+/*
+ * fedfem.h: C ABI of the GB300 (sm_103a) FED-FEM library, libfedfem.so.
+ *
+ * FED-FEM is the fast explicit dynamics finite element method for transient heat conduction
+ * of Zhang & Chauhan, "Fast explicit dynamics finite element algorithm for transient heat
+ * transfer" (arXiv:1909.03355).  The calls follow the paper's problem statement (Section 2,
+ * Eq. 1-7) and its three-stage algorithm (Section 3.5, Fig. 1): pre-computation, initialisation
+ * and time stepping.
+ *
+ * Conventions for every call:
+ *  - All arrays passed in are caller-owned HOST arrays unless a name ends in `_dev`; the
+ *    library copies what it needs during the call and keeps no pointer to them.
+ *  - Device memory is allocated and owned by the library (released by *_destroy).
+ *  - Node and element ids are 0-based int32; node coordinates are FP64 [n][3] row-major.
+ *  - Every call returns a fedfem_status; no exception crosses the ABI.  After an error the
+ *    context's message is available from fedfem_error_string().  A device-side failure
+ *    (watchdog or barrier timeout) leaves the context usable: restore a state and continue.
+ *  - Work is enqueued on the stream given in fedfem_options.stream (a cudaStream_t, NULL for
+ *    the legacy default stream).  Calls that return data to the host synchronise that stream.
+ *  - Temperatures are in the unit of T_zero (deg C by default, T_zero = -273.15).
+ *  - Sign convention (a reading of Eq. 2 and Eq. 13): F = K0 T is the positive-semidefinite
+ *    conduction load and the update is T <- T + dt (Q - F) / C.
+ */
+#ifndef FEDFEM_H
+#define FEDFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fedfem_ctx fedfem_ctx;
+typedef struct fedfem_batch fedfem_batch;
+
+typedef enum {
+    FEDFEM_OK = 0,
+    FEDFEM_ERR_ARG = 1,         /* invalid argument (NULL pointer, bad size, bad id)          */
+    FEDFEM_ERR_MESH = 2,        /* element with det J <= 0 / V <= 0, or a node id out of range */
+    FEDFEM_ERR_UNSTABLE = 3,    /* dt > dt_crit without force (Section 3.4, Eq. 29)           */
+    FEDFEM_ERR_DIVERGED = 4,    /* watchdog: a temperature became non-finite or > T_guard     */
+    FEDFEM_ERR_TIMEOUT = 5,     /* a device-side wait (grid barrier, TMA) exceeded its limit  */
+    FEDFEM_ERR_CUDA = 6,        /* CUDA runtime error                                         */
+    FEDFEM_ERR_OOM = 7,         /* device allocation failed                                   */
+    FEDFEM_ERR_STATE = 8,       /* call out of order (create -> precompute -> set_dt -> step) */
+    FEDFEM_ERR_UNSUPPORTED = 9  /* option combination not supported                           */
+} fedfem_status;
+
+/* Precision of the time-stepping hot path (the pre-computation is always FP64). */
+enum { FEDFEM_FP32 = 32, FEDFEM_FP64 = 64 };
+/* Accumulation of element loads into nodal loads. */
+enum {
+    FEDFEM_SCATTER_COLOR = 0,   /* deterministic: colour phases in shared memory + fixed-order halo sums */
+    FEDFEM_SCATTER_ATOMIC = 1   /* shared-memory atomics (non-deterministic order), measured variant */
+};
+
+/* Mesh (Section 2: the domain divided into elements).  nodes_per_elem = 8: trilinear
+ * hexahedra in VTK / C3D8 order (bottom face counter-clockwise, then top); 4: linear tets. */
+typedef struct {
+    int32_t nodes_per_elem;
+    int32_t reserved;
+    int64_t n_nodes;
+    int64_t n_elems;
+    const double *xyz;          /* [n_nodes][3]                                           */
+    const int32_t *conn;        /* [n_elems][nodes_per_elem]                              */
+    const int32_t *elem_mat;    /* [n_elems] material index, or NULL (all material 0)     */
+    const double *elem_kscale;  /* [n_elems] conductivity scale theta_e > 0, or NULL (1)  */
+} fedfem_mesh;
+
+/* Material (Eq. 1): density rho, conductivity k_ij(T) = k0_ij (1 + k_lin T) with k0 3x3
+ * symmetric positive definite (row-major), specific heat c(T) = c0 (1 + c_lin T).
+ * All materials of one context must share k_lin and c_lin. */
+typedef struct {
+    double rho;
+    double k0[9];
+    double k_lin;
+    double c0;
+    double c_lin;
+} fedfem_material;
+
+/* Boundary conditions and loads (Eq. 3-7).  Faces are boundary faces listed by node ids
+ * (4 per quad face of a hex mesh, 3 per triangle of a tet mesh); each face contributes
+ * area / n_vertices to each of its nodes (nodal-quadrature lumping). */
+typedef struct {
+    int64_t n_dir;              /* Eq. 3: Gamma_E                                          */
+    const int32_t *dir_nodes;   /* [n_dir]                                                 */
+    const double *dir_T;        /* [n_dir] prescribed temperatures T_Gamma                 */
+    int64_t n_conv_faces;       /* Eq. 4: Gamma_C, outward flux h (T - T_inf)              */
+    const int32_t *conv_faces;  /* [n_conv_faces][face_nv]                                 */
+    double h, T_inf;
+    int64_t n_rad_faces;        /* Eq. 7: Gamma_R, outward flux sigma eps ((T-T_z)^4 - (T_amb-T_z)^4) */
+    const int32_t *rad_faces;   /* [n_rad_faces][face_nv]                                  */
+    double eps, T_amb, T_zero;  /* T_zero: absolute zero in the temperature unit (-273.15) */
+    int32_t face_nv;            /* 4 (hex meshes) or 3 (tet meshes)                        */
+    int32_t reserved;
+    const double *nodal_Q;      /* Eq. 5 as concentrated nodal heat flows (W) [n_nodes], or NULL */
+    const double *elem_source;  /* Eq. 1 volumetric source Q (W/m^3) [n_elems], or NULL   */
+} fedfem_bcs;
+
+/* Options.  Zero-initialised fields select defaults (see fedfem_default_options). */
+typedef struct {
+    int32_t precision;          /* FEDFEM_FP32 (default) or FEDFEM_FP64                   */
+    int32_t kahan;              /* FP32 only: 1 (default) Kahan-compensated T accumulator  */
+    int32_t scatter;            /* FEDFEM_SCATTER_COLOR (default) or FEDFEM_SCATTER_ATOMIC */
+    int32_t block;              /* threads per CTA = elements per chunk (128/256/512), 0 = auto */
+    int32_t steps_per_launch;   /* explicit steps fused in one persistent launch, 0 = auto */
+    int32_t ctas_per_sm;        /* resident CTAs per SM, 0 = auto                          */
+    int32_t tiles_per_cta;      /* element tiles per CTA, 0 = auto                          */
+    int32_t stages;             /* depth of the element-chunk TMA ring, 0 = auto            */
+    double barrier_timeout_s;   /* device-side wait limit (default 1.0 s)                   */
+    double T_guard;             /* watchdog threshold on |T| (default 1e6)                  */
+    void *stream;               /* cudaStream_t, NULL = legacy default stream               */
+    int32_t device;             /* CUDA device ordinal, -1 = current device                 */
+    int32_t verbose;            /* 1: print the tiling / launch plan to stderr              */
+    int32_t debug_withhold_barrier; /* test hook: k > 0 makes CTA k-1 withhold its first grid-
+                                   barrier arrival in every launch, so the other CTAs' bounded
+                                   waits run out and the call returns FEDFEM_ERR_TIMEOUT; 0 = off */
+    int32_t reserved;
+} fedfem_options;
+
+/* Fill *opt with defaults (FP32 + Kahan, colour scatter, automatic launch plan). */
+void fedfem_default_options(fedfem_options *opt);
+
+/*
+ * Create a context: validates the problem (ids in range, one conductivity/heat law), copies
+ * it, builds the element tiling (space-filling-curve tiles, node renumbering, element
+ * colouring) on the host and allocates the device arrays.  Fig. 1 (i) 1 ("load object mesh
+ * and boundary conditions").  *out is NULL on failure.
+ * Errors: ARG (NULL / sizes / ids / laws), OOM, CUDA, UNSUPPORTED.
+ */
+fedfem_status fedfem_create(const fedfem_mesh *mesh, const fedfem_material *mats, int32_t n_mats,
+                            const fedfem_bcs *bcs, const fedfem_options *opt, fedfem_ctx **out);
+
+/*
+ * Pre-computation stage, Fig. 1 (i) 2-3, in FP64 on the device: element conduction matrices
+ * K0_e (Eq. 12 with 2x2x2 Gauss points for hexahedra, Eq. 18 for tets; the paper's G of
+ * Eq. 19/22 folded with D into 28 / 6 pair conductances), lumped thermal masses (Eq. 14/21),
+ * constant nodal loads and surface area shares; then the critical time step of Section 3.4
+ * (Eq. 29): dt_crit = 2 / lambda with lambda from FP64 power iteration on C0^-1/2 K0 C0^-1/2,
+ * scaled by max f_k / min f_c over [T_lo, T_hi], plus the largest linearised surface rate
+ * (h + 4 sigma eps max|T - T_z|^3) A_i / (C0_i min f_c).
+ * dt_crit_out may be NULL.  Errors: MESH (det J <= 0; the message names the element), CUDA.
+ */
+fedfem_status fedfem_precompute(fedfem_ctx *ctx, double T_lo, double T_hi, double *dt_crit_out);
+
+/* Set the time step (Eq. 8) and the coefficient A = dt / C0 of Eq. 14/21 (0 on Gamma_E).
+ * Errors: ARG (dt <= 0), UNSTABLE (dt > dt_crit and force == 0), STATE (before precompute). */
+fedfem_status fedfem_set_dt(fedfem_ctx *ctx, double dt, int32_t force);
+
+/* Initialisation stage, Fig. 1 (ii): T0 [n_nodes] host FP64; T_Gamma is re-imposed on the
+ * Dirichlet nodes and the step counter is reset to 0.  Errors: ARG, STATE. */
+fedfem_status fedfem_set_T(fedfem_ctx *ctx, const double *T0);
+
+/* Same as fedfem_set_T with a DEVICE array T0_dev [n_nodes] (FP64, original node order). */
+fedfem_status fedfem_set_T_device(fedfem_ctx *ctx, const double *T0_dev);
+
+/*
+ * Time-stepping stage, Fig. 1 (iii), n_steps times: element loads F_e = theta_e f_k,e K0_e T_e
+ * (Eq. 20 with the element-mean conductivity law of Section 4.2.2), accumulated to nodes in a
+ * fixed order, surface loads (Eq. 4, 7), explicit update (Eq. 16) and Dirichlet nodes held
+ * fixed (Fig. 1 (iii) 2.3).  Launches persistent kernels of up to steps_per_launch steps on
+ * the context stream and synchronises once at the end to read the device status word.
+ * Errors: STATE (no dt / no T), DIVERGED, TIMEOUT, CUDA.
+ */
+fedfem_status fedfem_step(fedfem_ctx *ctx, int64_t n_steps);
+
+/* Enqueue n_steps on the stream without synchronising; the device status is checked by the
+ * next synchronising call (fedfem_sync, fedfem_get_T, fedfem_step).  Errors: STATE, CUDA. */
+fedfem_status fedfem_step_async(fedfem_ctx *ctx, int64_t n_steps);
+
+/* Wait for the context stream and report the device status word.  Errors as fedfem_step. */
+fedfem_status fedfem_sync(fedfem_ctx *ctx);
+
+/* Copy the current temperatures to T_host [n_nodes] FP64 (original node order).  In FP32 +
+ * Kahan mode the value is T_hi - compensation evaluated in FP64. */
+fedfem_status fedfem_get_T(fedfem_ctx *ctx, double *T_host);
+
+/* Same into a DEVICE array T_dev [n_nodes] FP64 (original node order), stream-ordered. */
+fedfem_status fedfem_get_T_device(fedfem_ctx *ctx, double *T_dev);
+
+/* Number of explicit steps taken since the last set_T / set_state. */
+fedfem_status fedfem_get_step(fedfem_ctx *ctx, int64_t *step);
+
+/*
+ * Energy balance of the most recent step n-1 -> n, in FP64 (a consequence of Eq. 11: the
+ * internal loads sum to zero over all nodes):
+ *   stored_change = sum_free C0_i f_c(T_i^{n-1}) (T_i^n - T_i^{n-1}),
+ *   boundary_in   = dt (sum_free Q_i(T^{n-1}) + sum_Dirichlet F_i(T^{n-1})).
+ * Errors: STATE (no step taken yet).
+ */
+fedfem_status fedfem_energy(fedfem_ctx *ctx, double *stored_change, double *boundary_in);
+
+/* Internal conduction loads F = sum_e theta_e f_k,e K0_e T_e (Eq. 11/20) for a given field,
+ * evaluated in FP64 from the stored (working-precision) element operators.  T_host, F_host:
+ * [n_nodes] FP64, original order. */
+fedfem_status fedfem_internal_loads(fedfem_ctx *ctx, const double *T_host, double *F_host);
+
+/*
+ * Replace the per-element conductivity scales theta_e and / or volumetric sources s_e
+ * (NULL keeps the current values) and redo the dependent pre-computation (element operators,
+ * nodal loads).  The time step and dt_crit are left unchanged.  Arrays: [n_elems] FP64 host.
+ */
+fedfem_status fedfem_set_params(fedfem_ctx *ctx, const double *kscale, const double *source);
+
+/* Checkpoint / resume: the state is (T, Kahan compensation, step counter).  state_bytes
+ * returns the size of the opaque blob; get/set copy it to/from a host buffer. */
+fedfem_status fedfem_state_bytes(fedfem_ctx *ctx, size_t *bytes);
+fedfem_status fedfem_get_state(fedfem_ctx *ctx, void *buf);
+fedfem_status fedfem_set_state(fedfem_ctx *ctx, const void *buf);
+
+/*
+ * Forward run for the adjoint (no counterpart in the paper): n_steps explicit steps from the
+ * current state, writing T at the sensor nodes after every sample_every-th step into
+ * trace [n_steps / sample_every][n_sensors] (FP64 host) and keeping device checkpoints of the
+ * state every ckpt_every steps for fedfem_adjoint.  n_steps must be a multiple of both.
+ * Errors: ARG, STATE, DIVERGED, TIMEOUT, CUDA, OOM.
+ */
+fedfem_status fedfem_forward_record(fedfem_ctx *ctx, int64_t n_steps, const int32_t *sensors,
+                                    int32_t n_sensors, int32_t sample_every, int32_t ckpt_every,
+                                    double *trace);
+
+/*
+ * Reverse-time discrete adjoint of the recorded forward run (derived from Eq. 16 and Eq. 20;
+ * the paper has no adjoint).  dL_dtrace [n_samples][n_sensors] FP64 host; outputs
+ * dL_dkscale, dL_dsource [n_elems] FP64 host (original element order).  Each checkpoint
+ * segment is recomputed forward bit-identically before the backward sweep.  The state after
+ * the call is the state at the end of the recorded run.
+ * Errors: STATE (no recorded run), ARG, CUDA, OOM.
+ */
+fedfem_status fedfem_adjoint(fedfem_ctx *ctx, const double *dL_dtrace, double *dL_dkscale,
+                             double *dL_dsource);
+
+/* Launch plan and sizes chosen by create: a fixed-size record for logging and benchmarks. */
+typedef struct {
+    int64_t n_nodes, n_elems;
+    int32_t n_tiles, grid, block, stages;
+    int32_t steps_per_launch, max_tile_nodes, n_colors_max, smem_bytes;
+    int64_t n_shared_nodes, n_halo_slots, elem_bytes;   /* element stream bytes per step */
+    double dt, dt_crit;
+} fedfem_info;
+fedfem_status fedfem_get_info(fedfem_ctx *ctx, fedfem_info *info);
+
+/* Message of the last error on this context ("" if none).  Valid until the next call. */
+const char *fedfem_error_string(fedfem_ctx *ctx);
+/* Message of the last fedfem_create failure on this thread. */
+const char *fedfem_create_error(void);
+/* Release the context and all its device memory.  NULL is ignored. */
+void fedfem_destroy(fedfem_ctx *ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched scenarios (no counterpart in the paper): many independent problems, each with its
+ * own mesh, material, boundary data, time step and step count, advanced together.  Every
+ * scenario keeps its own dt = dt_scale * dt_crit (computed as in fedfem_precompute over
+ * [T_lo, T_hi]).  The launch sequence for all scenarios is captured once in a CUDA graph.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    fedfem_mesh mesh;
+    fedfem_material mat;
+    fedfem_bcs bcs;
+    const double *T0;           /* [n_nodes] */
+    int64_t n_steps;
+    double T_lo, T_hi;          /* range for the critical step                  */
+    double dt_scale;            /* dt = dt_scale * dt_crit (e.g. 0.9)           */
+} fedfem_scenario;
+
+fedfem_status fedfem_batch_create(const fedfem_scenario *sc, int32_t n_scenarios,
+                                  const fedfem_options *opt, fedfem_batch **out);
+/* Reset every scenario to its T0 and run all of them to their step counts (graph replay).
+ * Errors: DIVERGED, TIMEOUT, CUDA. */
+fedfem_status fedfem_batch_run(fedfem_batch *b);
+/* Completion time of each scenario in ns since the start of the last run, read from the
+ * device's global timer [n_scenarios]; total element-steps and the dt of each scenario. */
+fedfem_status fedfem_batch_times(fedfem_batch *b, double *t_done_ns, double *elem_steps_total,
+                                 double *dt);
+fedfem_status fedfem_batch_get_T(fedfem_batch *b, int32_t s, double *T_host);
+const char *fedfem_batch_error_string(fedfem_batch *b);
+void fedfem_batch_destroy(fedfem_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEDFEM_H */

@@ -1,0 +1,93 @@
+// The context behind the opaque fedfem_ctx handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "fedfem_internal.h"
+#include "precompute.cuh"
+
+struct fedfem_ctx {
+    // problem (host copies, original numbering)
+    int npe = 8;
+    int64_t nn = 0, ne = 0;
+    std::vector<double> xyz, kscale, source, nodal_Q, dir_T;
+    std::vector<int32_t> conn, elem_mat, dir_nodes, conv_faces, rad_faces;
+    std::vector<fedfem_material> mats;
+    int face_nv = 4;
+    int64_t n_conv = 0, n_rad = 0;
+    double h = 0, T_inf = 0, eps = 0, T_amb = 0, T_zero = -273.15;
+    double k_lin = 0, c_lin = 0;
+    fedfem_options opt;
+    int precision = 32, kahan = 1;
+
+    // launch plan
+    fedfem::Tiling til;
+    int grid = 0, block = 0, stages = 0, tpc = 0, chunk_bytes = 0;
+    size_t smem = 0;
+    int device = -1, num_sms = 0, max_smem = 0;
+    cudaStream_t stream = nullptr;
+
+    // device arrays (new node numbering unless noted)
+    std::vector<void *> allocs;
+    uint8_t *d_chunks = nullptr, *d_elem_col = nullptr, *d_chunk_col = nullptr;
+    fedfem::TileInfo *d_tiles = nullptr;
+    int4 *d_sh = nullptr;
+    int32_t *d_sptr = nullptr;
+    int2 *d_bnd = nullptr;
+    void *d_T[2] = {nullptr, nullptr};
+    float *d_comp[2] = {nullptr, nullptr};
+    void *d_part[2] = {nullptr, nullptr};
+    double *d_A = nullptr, *d_C0 = nullptr, *d_Qext64 = nullptr, *d_Ac64 = nullptr, *d_Ar64 = nullptr;
+    void *d_Qext = nullptr, *d_Ac = nullptr, *d_Ar = nullptr;
+    uint8_t *d_isdir = nullptr;
+    int32_t *d_dir_new = nullptr;
+    double *d_dir_T = nullptr;
+    unsigned int *d_barrier = nullptr;
+    int32_t *d_err = nullptr;
+    unsigned long long *d_bad_elem = nullptr;
+    // pre-computation inputs (original numbering for elements)
+    double *d_xyz = nullptr, *d_matk0 = nullptr, *d_matrhoc = nullptr, *d_kscale = nullptr, *d_source = nullptr;
+    double *d_nodalQ = nullptr;
+    int32_t *d_conn = nullptr, *d_gconn = nullptr, *d_mat = nullptr, *d_old_of_new = nullptr;
+    int64_t *d_slot_of_elem = nullptr, *d_n2e = nullptr;
+    int32_t *d_n2e_ptr = nullptr;
+    double *d_cond64 = nullptr, *d_W = nullptr;
+    int32_t *d_conv_faces = nullptr, *d_rad_faces = nullptr;
+    int32_t *d_fc_ptr = nullptr, *d_fc_idx = nullptr, *d_fr_ptr = nullptr, *d_fr_idx = nullptr;
+    double *d_fc_share = nullptr, *d_fr_share = nullptr;
+    // FP64 scratch
+    double *d_v[4] = {nullptr, nullptr, nullptr, nullptr};
+    double *d_Y = nullptr, *d_red = nullptr;
+
+    // state
+    bool precomputed = false, has_dt = false, has_T = false;
+    double dt = 0, dt_crit = 0, T_lo = 0, T_hi = 0, lambda_cond = 0;
+    int power_iters = 0, power_max_iter = 3000;
+    double power_tol = 1e-10;
+    int64_t step = 0;
+    std::string err;
+
+    // adjoint record (adjoint.cu)
+    std::vector<void *> adj_allocs;
+    bool recorded = false;
+    int64_t rec_steps = 0, rec_step0 = 0;
+    int32_t rec_sample_every = 0, rec_ckpt_every = 0, rec_n_sensors = 0;
+    int32_t *d_sensors = nullptr;     // new ids
+    void *d_ckpt = nullptr;           // [n_ckpt][state bytes]
+    size_t ckpt_bytes = 0;
+};
+
+namespace fedfem {
+fedfem_status fail(fedfem_ctx *c, fedfem_status s, const std::string &msg);
+fedfem_status cuda_fail(fedfem_ctx *c, cudaError_t e, const char *where);
+cudaError_t dalloc(fedfem_ctx *c, void **p, size_t bytes);
+cudaError_t upload(fedfem_ctx *c, void **p, const void *src, size_t bytes);
+fedfem_status fedfem_ctx_init_device(fedfem_ctx *c);
+fedfem_status install_T(fedfem_ctx *c, const double *T0_dev_old);
+fedfem_status state_f64_new(fedfem_ctx *c, int64_t step, double *dst);
+StepArgs step_args(fedfem_ctx *c);
+fedfem_status enqueue_steps(fedfem_ctx *c, int64_t n, void *rec, int64_t rec_stride);
+}  // namespace fedfem

@@ -1,0 +1,826 @@
+// C ABI of libfedfem.so: contexts, the launch plan, the pre-computation stage and the time
+// loop of Fig. 1, state transfer and diagnostics.  All arithmetic of the method runs in the
+// kernels of step.cu and precompute.cu; this file validates, lays out and orchestrates.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+
+using namespace fedfem;
+
+static thread_local std::string g_create_error;
+
+// ------------------------------------------------------------------------------------------
+// helpers
+// ------------------------------------------------------------------------------------------
+namespace fedfem {
+
+fedfem_status fail(fedfem_ctx *c, fedfem_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+fedfem_status cuda_fail(fedfem_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? FEDFEM_ERR_OOM : FEDFEM_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+cudaError_t dalloc(fedfem_ctx *c, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) c->allocs.push_back(*p);
+    return e;
+}
+
+cudaError_t upload(fedfem_ctx *c, void **p, const void *src, size_t bytes)
+{
+    cudaError_t e = dalloc(c, p, bytes);
+    if (e != cudaSuccess) return e;
+    if (bytes) e = cudaMemcpyAsync(*p, src, bytes, cudaMemcpyHostToDevice, c->stream);
+    return e;
+}
+
+}  // namespace fedfem
+
+#define CK(call, where)                                          \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where);   \
+    } while (0)
+
+static std::string status_message(int32_t bits)
+{
+    std::string m;
+    if (bits & ERRBIT_DIVERGED) m += "watchdog: a temperature became non-finite or exceeded T_guard; ";
+    if (bits & ERRBIT_TIMEOUT) m += "device wait exceeded its limit (grid barrier or TMA stage); ";
+    if (bits & ERRBIT_MESH) m += "element with non-positive Jacobian; ";
+    if (bits & ERRBIT_BOUNDS) m += "index out of bounds; ";
+    return m;
+}
+
+// Read and clear the device error word (synchronises the stream).
+static fedfem_status check_device(fedfem_ctx *c)
+{
+    int32_t bits = 0;
+    CK(cudaMemcpyAsync(&bits, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream), "read status");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    if (bits) {
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream), "clear status");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        const fedfem_status s = (bits & ERRBIT_TIMEOUT)    ? FEDFEM_ERR_TIMEOUT
+                                : (bits & ERRBIT_DIVERGED) ? FEDFEM_ERR_DIVERGED
+                                                           : FEDFEM_ERR_MESH;
+        return fail(c, s, status_message(bits));
+    }
+    return FEDFEM_OK;
+}
+
+extern "C" void fedfem_default_options(fedfem_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = FEDFEM_FP32;
+    o->kahan = 1;
+    o->scatter = FEDFEM_SCATTER_COLOR;
+    o->barrier_timeout_s = 1.0;
+    o->T_guard = 1e6;
+    o->device = -1;
+}
+
+// ------------------------------------------------------------------------------------------
+// create
+// ------------------------------------------------------------------------------------------
+static std::string validate(const fedfem_mesh *m, const fedfem_material *mats, int32_t n_mats, const fedfem_bcs *b)
+{
+    if (!m || !mats || !b) return "NULL mesh, materials or bcs";
+    if (m->nodes_per_elem != 8 && m->nodes_per_elem != 4) return "nodes_per_elem must be 8 or 4";
+    if (m->n_nodes <= 0 || m->n_elems <= 0) return "empty mesh";
+    if (m->n_nodes >= (1LL << 31) || m->n_elems >= (1LL << 31)) return "mesh too large for int32 ids";
+    if (!m->xyz || !m->conn) return "NULL xyz or conn";
+    if (n_mats < 1) return "n_mats must be >= 1";
+    const int npe = m->nodes_per_elem;
+    for (int64_t i = 0; i < m->n_elems * npe; ++i)
+        if (m->conn[i] < 0 || m->conn[i] >= m->n_nodes) return "connectivity id out of range at " + std::to_string(i);
+    for (int64_t i = 0; i < m->n_nodes * 3; ++i)
+        if (!std::isfinite(m->xyz[i])) return "non-finite coordinate";
+    if (m->elem_mat)
+        for (int64_t e = 0; e < m->n_elems; ++e)
+            if (m->elem_mat[e] < 0 || m->elem_mat[e] >= n_mats) return "elem_mat out of range";
+    if (m->elem_kscale)
+        for (int64_t e = 0; e < m->n_elems; ++e)
+            if (!(m->elem_kscale[e] > 0) || !std::isfinite(m->elem_kscale[e])) return "elem_kscale must be > 0";
+    for (int i = 0; i < n_mats; ++i) {
+        if (!(mats[i].rho > 0) || !(mats[i].c0 > 0)) return "rho and c0 must be > 0";
+        if (mats[i].k_lin != mats[0].k_lin || mats[i].c_lin != mats[0].c_lin)
+            return "all materials must share k_lin and c_lin";
+        for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 3; ++s)
+                if (mats[i].k0[3 * r + s] != mats[i].k0[3 * s + r]) return "k0 must be symmetric";
+    }
+    if (b->n_dir < 0 || b->n_conv_faces < 0 || b->n_rad_faces < 0) return "negative boundary counts";
+    if (b->n_dir > 0 && (!b->dir_nodes || !b->dir_T)) return "NULL Dirichlet arrays";
+    for (int64_t d = 0; d < b->n_dir; ++d)
+        if (b->dir_nodes[d] < 0 || b->dir_nodes[d] >= m->n_nodes) return "Dirichlet node out of range";
+    const int64_t nf = b->n_conv_faces + b->n_rad_faces;
+    if (nf > 0 && b->face_nv != 3 && b->face_nv != 4) return "face_nv must be 3 or 4";
+    for (int pass = 0; pass < 2; ++pass) {
+        const int64_t n = pass ? b->n_rad_faces : b->n_conv_faces;
+        const int32_t *f = pass ? b->rad_faces : b->conv_faces;
+        if (n > 0 && !f) return "NULL face array";
+        for (int64_t i = 0; i < n * b->face_nv; ++i)
+            if (f[i] < 0 || f[i] >= m->n_nodes) return "face node out of range";
+    }
+    return "";
+}
+
+static int default_block(int precision, int npe)
+{
+    if (precision == 64) return npe == 8 ? 128 : 256;
+    return npe == 8 ? 256 : 512;
+}
+
+// Choose tiles, grid and shared memory; builds c->til.
+static fedfem_status make_plan(fedfem_ctx *c, const std::vector<uint8_t> &is_bnd)
+{
+    const int npe = c->npe;
+    int block = c->opt.block ? c->opt.block : default_block(c->precision, npe);
+    if (block != 128 && block != 256 && block != 512) return fail(c, FEDFEM_ERR_ARG, "block must be 128, 256 or 512");
+    int stages = c->opt.stages ? c->opt.stages : 4;
+    if (stages < 2 || stages > 8) return fail(c, FEDFEM_ERR_ARG, "stages must be in [2, 8]");
+    int cps = c->opt.ctas_per_sm ? c->opt.ctas_per_sm : 1;
+    int tpc = c->opt.tiles_per_cta ? c->opt.tiles_per_cta : 2;
+    const int cb = chunk_bytes_for(c->precision, npe, block);
+    for (int attempt = 0; attempt < 10; ++attempt) {
+        const int64_t n_ctas = (int64_t)c->num_sms * cps;
+        int64_t n_tiles = n_ctas * tpc;
+        n_tiles = std::min<int64_t>(n_tiles, std::max<int64_t>(1, c->ne / block));
+        const int grid = (int)((n_tiles + tpc - 1) / tpc);
+        std::string e = build_tiling(npe, c->ne, c->nn, c->conn.data(), c->xyz.data(), is_bnd.data(), (int)n_tiles,
+                                     block, c->til);
+        if (!e.empty()) {
+            if (e.find("65535") != std::string::npos) {
+                tpc *= 2;
+                continue;
+            }
+            return fail(c, FEDFEM_ERR_MESH, e);
+        }
+        e = validate_tiling(c->til);
+        if (!e.empty()) return fail(c, FEDFEM_ERR_MESH, "tiling check failed: " + e);
+        const size_t smem = step_smem_bytes(c->precision, npe, block, stages, c->til.max_local);
+        int nb = 0;
+        if (smem <= (size_t)c->max_smem) nb = step_max_blocks_per_sm(c->precision, c->kahan, npe, block, smem);
+        if (nb * c->num_sms >= grid && nb >= 1) {
+            c->block = block;
+            c->stages = stages;
+            c->tpc = tpc;
+            c->grid = grid;
+            c->smem = smem;
+            c->chunk_bytes = cb;
+            if (c->opt.verbose)
+                std::fprintf(stderr,
+                             "fedfem plan: tiles=%d grid=%d block=%d stages=%d tpc=%d max_local=%d colours=%d "
+                             "smem=%zu chunks=%d\n",
+                             c->til.n_tiles, grid, block, stages, tpc, c->til.max_local, c->til.max_colors, smem,
+                             c->til.n_chunks);
+            return FEDFEM_OK;
+        }
+        tpc *= 2;
+    }
+    return fail(c, FEDFEM_ERR_UNSUPPORTED, "no launch plan fits in shared memory");
+}
+
+extern "C" fedfem_status fedfem_create(const fedfem_mesh *mesh, const fedfem_material *mats, int32_t n_mats,
+                                       const fedfem_bcs *bcs, const fedfem_options *opt_in, fedfem_ctx **out)
+{
+    if (!out) return FEDFEM_ERR_ARG;
+    *out = nullptr;
+    g_create_error.clear();
+    std::string v = validate(mesh, mats, n_mats, bcs);
+    if (!v.empty()) {
+        g_create_error = v;
+        return FEDFEM_ERR_ARG;
+    }
+    fedfem_ctx *c = new fedfem_ctx();
+    fedfem_options o;
+    fedfem_default_options(&o);
+    if (opt_in) {
+        o = *opt_in;
+        if (o.precision == 0) o.precision = FEDFEM_FP32;
+        if (o.barrier_timeout_s <= 0) o.barrier_timeout_s = 1.0;
+        if (o.T_guard <= 0) o.T_guard = 1e6;
+    }
+    if (o.precision != 32 && o.precision != 64) {
+        g_create_error = "precision must be 32 or 64";
+        delete c;
+        return FEDFEM_ERR_ARG;
+    }
+    c->opt = o;
+    c->precision = o.precision;
+    c->kahan = (o.precision == 32 && o.kahan) ? 1 : 0;
+    c->npe = mesh->nodes_per_elem;
+    c->nn = mesh->n_nodes;
+    c->ne = mesh->n_elems;
+    const int npe = c->npe;
+    c->xyz.assign(mesh->xyz, mesh->xyz + 3 * c->nn);
+    c->conn.assign(mesh->conn, mesh->conn + npe * c->ne);
+    if (mesh->elem_mat) c->elem_mat.assign(mesh->elem_mat, mesh->elem_mat + c->ne);
+    c->kscale.assign(c->ne, 1.0);
+    if (mesh->elem_kscale) c->kscale.assign(mesh->elem_kscale, mesh->elem_kscale + c->ne);
+    if (bcs->elem_source) c->source.assign(bcs->elem_source, bcs->elem_source + c->ne);
+    if (bcs->nodal_Q) c->nodal_Q.assign(bcs->nodal_Q, bcs->nodal_Q + c->nn);
+    c->mats.assign(mats, mats + n_mats);
+    c->k_lin = mats[0].k_lin;
+    c->c_lin = mats[0].c_lin;
+    c->dir_nodes.assign(bcs->dir_nodes, bcs->dir_nodes + bcs->n_dir);
+    c->dir_T.assign(bcs->dir_T, bcs->dir_T + bcs->n_dir);
+    c->face_nv = bcs->face_nv ? bcs->face_nv : (npe == 8 ? 4 : 3);
+    c->n_conv = bcs->n_conv_faces;
+    c->n_rad = bcs->n_rad_faces;
+    if (c->n_conv) c->conv_faces.assign(bcs->conv_faces, bcs->conv_faces + c->n_conv * c->face_nv);
+    if (c->n_rad) c->rad_faces.assign(bcs->rad_faces, bcs->rad_faces + c->n_rad * c->face_nv);
+    c->h = bcs->h;
+    c->T_inf = bcs->T_inf;
+    c->eps = bcs->eps;
+    c->T_amb = bcs->T_amb;
+    c->T_zero = (bcs->T_zero == 0.0 && bcs->n_rad_faces == 0) ? -273.15 : bcs->T_zero;
+
+    fedfem_status st = fedfem_ctx_init_device(c);
+    if (st != FEDFEM_OK) {
+        g_create_error = c->err;
+        fedfem_destroy(c);
+        return st;
+    }
+    *out = c;
+    return FEDFEM_OK;
+}
+
+namespace fedfem {
+
+fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
+{
+    if (c->opt.device >= 0) CK(cudaSetDevice(c->opt.device), "cudaSetDevice");
+    CK(cudaGetDevice(&c->device), "cudaGetDevice");
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, c->device), "cudaGetDeviceProperties");
+    c->num_sms = prop.multiProcessorCount;
+    c->max_smem = (int)prop.sharedMemPerBlockOptin;
+    if (!prop.cooperativeLaunch) return fail(c, FEDFEM_ERR_UNSUPPORTED, "device lacks cooperative launch");
+    c->stream = (cudaStream_t)c->opt.stream;
+
+    // boundary node flags (nodes with surface loads) for the tiling
+    std::vector<uint8_t> is_bnd(c->nn, 0);
+    for (int32_t v : c->conv_faces) is_bnd[v] = 1;
+    for (int32_t v : c->rad_faces) is_bnd[v] = 1;
+    fedfem_status s = make_plan(c, is_bnd);
+    if (s != FEDFEM_OK) return s;
+    const Tiling &T = c->til;
+    const int64_t nn = c->nn, ne = c->ne;
+    const int npe = c->npe;
+    const size_t rs = c->precision == 64 ? 8 : 4;
+
+    // element stream with tile-local ids (conductances are filled by the pre-computation)
+    {
+        std::vector<uint8_t> host((size_t)T.n_chunks * c->chunk_bytes, 0);
+        const size_t id_off = (size_t)n_pairs(npe) * rs * c->block;
+        for (int64_t ch = 0; ch < T.n_chunks; ++ch) {
+            uint16_t *ids = reinterpret_cast<uint16_t *>(host.data() + ch * c->chunk_bytes + id_off);
+            std::memcpy(ids, T.lconn.data() + (size_t)ch * c->block * npe, (size_t)c->block * npe * 2);
+        }
+        CK(upload(c, (void **)&c->d_chunks, host.data(), host.size()), "upload element stream");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+    }
+    CK(upload(c, (void **)&c->d_elem_col, T.elem_col.data(), T.elem_col.size()), "upload colours");
+    CK(upload(c, (void **)&c->d_chunk_col, T.chunk_col.data(), T.chunk_col.size()), "upload chunk colours");
+    CK(upload(c, (void **)&c->d_tiles, T.tiles.data(), T.tiles.size() * sizeof(TileInfo)), "upload tiles");
+    CK(upload(c, (void **)&c->d_sh, T.sh.data(), T.sh.size() * sizeof(int4)), "upload halo");
+    CK(upload(c, (void **)&c->d_sptr, T.sptr.data(), T.sptr.size() * sizeof(int32_t)), "upload halo ptr");
+    CK(upload(c, (void **)&c->d_bnd, T.bnd.data(), T.bnd.size() * sizeof(int2)), "upload boundary");
+    const size_t n_slots = T.sptr.empty() ? 0 : (size_t)T.sptr.back();
+    for (int b = 0; b < 2; ++b) {
+        CK(dalloc(c, &c->d_T[b], nn * rs), "alloc T");
+        CK(dalloc(c, &c->d_part[b], std::max<size_t>(n_slots, 1) * rs), "alloc halo partials");
+        if (c->kahan) CK(dalloc(c, (void **)&c->d_comp[b], nn * sizeof(float)), "alloc comp");
+    }
+    CK(dalloc(c, (void **)&c->d_A, nn * 8), "alloc A");
+    CK(dalloc(c, (void **)&c->d_C0, nn * 8), "alloc C0");
+    CK(dalloc(c, (void **)&c->d_Qext64, nn * 8), "alloc Q");
+    CK(dalloc(c, (void **)&c->d_Ac64, nn * 8), "alloc Ac");
+    CK(dalloc(c, (void **)&c->d_Ar64, nn * 8), "alloc Ar");
+    if (c->precision == 32) {
+        CK(dalloc(c, &c->d_Qext, nn * 4), "alloc Q32");
+        CK(dalloc(c, &c->d_Ac, nn * 4), "alloc Ac32");
+        CK(dalloc(c, &c->d_Ar, nn * 4), "alloc Ar32");
+    } else {
+        c->d_Qext = c->d_Qext64;
+        c->d_Ac = c->d_Ac64;
+        c->d_Ar = c->d_Ar64;
+    }
+    CK(dalloc(c, (void **)&c->d_barrier, 64), "alloc barrier");
+    CK(dalloc(c, (void **)&c->d_err, 64), "alloc status");
+    CK(cudaMemsetAsync(c->d_err, 0, 64, c->stream), "memset");
+    CK(dalloc(c, (void **)&c->d_bad_elem, 8), "alloc");
+
+    // pre-computation inputs
+    std::vector<uint8_t> isdir(nn, 0);
+    std::vector<int32_t> dir_new(c->dir_nodes.size());
+    for (size_t d = 0; d < c->dir_nodes.size(); ++d) {
+        isdir[T.new_of_old[c->dir_nodes[d]]] = 1;
+        dir_new[d] = T.new_of_old[c->dir_nodes[d]];
+    }
+    CK(upload(c, (void **)&c->d_isdir, isdir.data(), nn), "upload isdir");
+    CK(upload(c, (void **)&c->d_dir_new, dir_new.data(), dir_new.size() * 4), "upload dir");
+    CK(upload(c, (void **)&c->d_dir_T, c->dir_T.data(), c->dir_T.size() * 8), "upload dir T");
+    CK(upload(c, (void **)&c->d_xyz, c->xyz.data(), c->xyz.size() * 8), "upload xyz");
+    CK(upload(c, (void **)&c->d_conn, c->conn.data(), c->conn.size() * 4), "upload conn");
+    {
+        std::vector<int32_t> g(c->conn.size());
+        for (size_t i = 0; i < g.size(); ++i) g[i] = T.new_of_old[c->conn[i]];
+        CK(upload(c, (void **)&c->d_gconn, g.data(), g.size() * 4), "upload gconn");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+    }
+    if (!c->elem_mat.empty()) CK(upload(c, (void **)&c->d_mat, c->elem_mat.data(), ne * 4), "upload mat");
+    {
+        std::vector<double> k0(9 * c->mats.size()), rhoc(c->mats.size());
+        for (size_t m = 0; m < c->mats.size(); ++m) {
+            std::memcpy(&k0[9 * m], c->mats[m].k0, 9 * 8);
+            rhoc[m] = c->mats[m].rho * c->mats[m].c0;
+        }
+        CK(upload(c, (void **)&c->d_matk0, k0.data(), k0.size() * 8), "upload k0");
+        CK(upload(c, (void **)&c->d_matrhoc, rhoc.data(), rhoc.size() * 8), "upload rho c");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+    }
+    CK(dalloc(c, (void **)&c->d_kscale, ne * 8), "alloc kscale");
+    CK(dalloc(c, (void **)&c->d_source, ne * 8), "alloc source");
+    CK(cudaMemsetAsync(c->d_source, 0, ne * 8, c->stream), "memset");
+    if (!c->nodal_Q.empty()) CK(upload(c, (void **)&c->d_nodalQ, c->nodal_Q.data(), nn * 8), "upload nodal Q");
+    CK(upload(c, (void **)&c->d_slot_of_elem, T.slot_of_elem.data(), ne * 8), "upload slots");
+    CK(upload(c, (void **)&c->d_old_of_new, T.old_of_new.data(), nn * 4), "upload perm");
+    CK(upload(c, (void **)&c->d_n2e_ptr, T.n2e_ptr.data(), (nn + 1) * 4), "upload n2e");
+    CK(upload(c, (void **)&c->d_n2e, T.n2e.data(), T.n2e.size() * 8), "upload n2e");
+    CK(dalloc(c, (void **)&c->d_cond64, (size_t)ne * n_pairs(npe) * 8), "alloc cond64");
+    CK(dalloc(c, (void **)&c->d_W, (size_t)ne * npe * 8), "alloc W");
+    for (int pass = 0; pass < 2; ++pass) {
+        const int64_t nf = pass ? c->n_rad : c->n_conv;
+        const std::vector<int32_t> &faces = pass ? c->rad_faces : c->conv_faces;
+        std::vector<int32_t> ptr, idx;
+        build_face_csr(nn, T.new_of_old, faces.data(), nf, c->face_nv, ptr, idx);
+        int32_t **dp = pass ? &c->d_fr_ptr : &c->d_fc_ptr;
+        int32_t **di = pass ? &c->d_fr_idx : &c->d_fc_idx;
+        int32_t **df = pass ? &c->d_rad_faces : &c->d_conv_faces;
+        double **ds = pass ? &c->d_fr_share : &c->d_fc_share;
+        CK(upload(c, (void **)dp, ptr.data(), ptr.size() * 4), "upload face csr");
+        CK(upload(c, (void **)di, idx.data(), idx.size() * 4), "upload face csr");
+        CK(upload(c, (void **)df, faces.data(), faces.size() * 4), "upload faces");
+        CK(dalloc(c, (void **)ds, std::max<int64_t>(nf, 1) * 8), "alloc face share");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+    }
+    // FP64 scratch for power iteration / energy / state I/O
+    for (int i = 0; i < 4; ++i) CK(dalloc(c, (void **)&c->d_v[i], nn * 8), "alloc scratch");
+    CK(dalloc(c, (void **)&c->d_Y, (size_t)ne * npe * 8), "alloc scratch");
+    CK(dalloc(c, (void **)&c->d_red, 2 * 1024 * 8 + 64), "alloc scratch");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return FEDFEM_OK;
+}
+
+}  // namespace fedfem
+
+// ------------------------------------------------------------------------------------------
+// pre-computation
+// ------------------------------------------------------------------------------------------
+static fedfem_status run_precompute_arrays(fedfem_ctx *c)
+{
+    const int npe = c->npe;
+    CK(cudaMemcpyAsync(c->d_kscale, c->kscale.data(), c->ne * 8, cudaMemcpyHostToDevice, c->stream), "upload kscale");
+    if (!c->source.empty())
+        CK(cudaMemcpyAsync(c->d_source, c->source.data(), c->ne * 8, cudaMemcpyHostToDevice, c->stream), "upload source");
+    unsigned long long big = ~0ULL;
+    CK(cudaMemcpyAsync(c->d_bad_elem, &big, 8, cudaMemcpyHostToDevice, c->stream), "init");
+    ElemArgs ea;
+    ea.ne = c->ne;
+    ea.xyz = c->d_xyz;
+    ea.conn = c->d_conn;
+    ea.mat = c->d_mat;
+    ea.mat_k0 = c->d_matk0;
+    ea.kscale = c->d_kscale;
+    ea.slot_of_elem = c->d_slot_of_elem;
+    ea.CH = c->block;
+    ea.VW = (c->precision == 32 && npe == 8) ? 4 : 2;
+    ea.precision = c->precision;
+    ea.chunk_bytes = c->chunk_bytes;
+    ea.chunks = c->d_chunks;
+    ea.cond64 = c->d_cond64;
+    ea.W = c->d_W;
+    ea.err = c->d_err;
+    ea.bad_elem = c->d_bad_elem;
+    launch_elem(npe, ea, c->stream);
+    CK(cudaGetLastError(), "element pre-computation");
+    launch_face_share(c->n_conv, c->face_nv, c->d_conv_faces, c->d_xyz, c->d_fc_share, c->stream);
+    launch_face_share(c->n_rad, c->face_nv, c->d_rad_faces, c->d_xyz, c->d_fr_share, c->stream);
+    NodeArgs na;
+    na.nn = c->nn;
+    na.npe = npe;
+    na.n2e_ptr = c->d_n2e_ptr;
+    na.n2e = c->d_n2e;
+    na.W = c->d_W;
+    na.mat = c->d_mat;
+    na.mat_rhoc = c->d_matrhoc;
+    na.source = c->source.empty() ? nullptr : c->d_source;
+    na.nodal_Q = c->d_nodalQ;
+    na.old_of_new = c->d_old_of_new;
+    na.fc_ptr = c->n_conv ? c->d_fc_ptr : nullptr;
+    na.fc_idx = c->d_fc_idx;
+    na.fr_ptr = c->n_rad ? c->d_fr_ptr : nullptr;
+    na.fr_idx = c->d_fr_idx;
+    na.fc_share = c->d_fc_share;
+    na.fr_share = c->d_fr_share;
+    na.C0 = c->d_C0;
+    na.Qext64 = c->d_Qext64;
+    na.Ac64 = c->d_Ac64;
+    na.Ar64 = c->d_Ar64;
+    na.Qext32 = c->precision == 32 ? (float *)c->d_Qext : nullptr;
+    na.Ac32 = c->precision == 32 ? (float *)c->d_Ac : nullptr;
+    na.Ar32 = c->precision == 32 ? (float *)c->d_Ar : nullptr;
+    launch_node_sums(na, c->stream);
+    CK(cudaGetLastError(), "node pre-computation");
+    int32_t bits = 0;
+    unsigned long long bad = 0;
+    CK(cudaMemcpyAsync(&bits, c->d_err, 4, cudaMemcpyDeviceToHost, c->stream), "read status");
+    CK(cudaMemcpyAsync(&bad, c->d_bad_elem, 8, cudaMemcpyDeviceToHost, c->stream), "read status");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    if (bits & ERRBIT_MESH) {
+        CK(cudaMemsetAsync(c->d_err, 0, 4, c->stream), "clear");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        return fail(c, FEDFEM_ERR_MESH, "element " + std::to_string(bad) + " has det J <= 0 (inverted or degenerate)");
+    }
+    if (c->has_dt) launch_set_A(c->nn, c->dt, c->d_C0, c->d_isdir, c->d_A, c->stream);
+    return FEDFEM_OK;
+}
+
+extern "C" fedfem_status fedfem_precompute(fedfem_ctx *c, double T_lo, double T_hi, double *dt_crit_out)
+{
+    if (!c) return FEDFEM_ERR_ARG;
+    if (!(T_lo <= T_hi)) return fail(c, FEDFEM_ERR_ARG, "T_lo must be <= T_hi");
+    fedfem_status s = run_precompute_arrays(c);
+    if (s != FEDFEM_OK) return s;
+    // critical time step (Section 3.4): power iteration on C0^-1/2 K0 C0^-1/2 (free nodes)
+    const int64_t nn = c->nn;
+    double *x = c->d_v[0], *u = c->d_v[1], *F = c->d_v[2], *z = c->d_v[3];
+    double *partial = c->d_red, *sums = c->d_red + 2 * 1024;
+    launch_power_init(nn, c->d_isdir, x, c->stream);
+    double lam = 0.0;
+    int it = 0;
+    const int max_iter = c->power_max_iter;
+    const double tol = c->power_tol;
+    // x is normalised after the first iteration; the Rayleigh quotient x.z is read every
+    // 16 iterations and the iteration stops when it changes by < tol relative
+    for (it = 0; it < max_iter; ++it) {
+        launch_scale_free(nn, x, c->d_C0, c->d_isdir, u, c->stream);
+        launch_apply(c->npe, c->ne, nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, u, nullptr, 0.0, c->d_Y, F,
+                     c->stream);
+        launch_power_dots(nn, x, F, c->d_C0, c->d_isdir, z, partial, sums, c->stream);
+        launch_normalize(nn, z, sums, x, c->stream);
+        if ((it & 15) == 15 || it == max_iter - 1) {
+            double h2[2];
+            CK(cudaMemcpyAsync(h2, sums, 16, cudaMemcpyDeviceToHost, c->stream), "read");
+            CK(cudaStreamSynchronize(c->stream), "synchronize");
+            // Rayleigh quotient with a normalised x (x was normalised by the previous iteration)
+            const double rq = h2[0];
+            const bool done = it > 16 && std::fabs(rq - lam) <= tol * std::fabs(rq);
+            lam = rq;
+            if (done) break;
+        }
+    }
+    CK(cudaGetLastError(), "power iteration");
+    c->lambda_cond = lam;
+    c->power_iters = it;
+    const double fk_max = std::max(1.0 + c->k_lin * T_lo, 1.0 + c->k_lin * T_hi);
+    const double fc_min = std::min(1.0 + c->c_lin * T_lo, 1.0 + c->c_lin * T_hi);
+    if (!(fc_min > 0) || !(fk_max > 0)) return fail(c, FEDFEM_ERR_ARG, "conductivity or heat law not positive on [T_lo, T_hi]");
+    const double rl = std::fabs(T_lo - c->T_zero), rh = std::fabs(T_hi - c->T_zero);
+    const double r3 = std::max(rl * rl * rl, rh * rh * rh);
+    const int nb = launch_surface_rate(nn, c->d_Ac64, c->d_Ar64, c->d_C0, c->d_isdir, c->h,
+                                       4.0 * 5.67e-8 * c->eps * r3, fc_min, partial, c->stream);
+    std::vector<double> pr(2 * nb);
+    CK(cudaMemcpyAsync(pr.data(), partial, pr.size() * 8, cudaMemcpyDeviceToHost, c->stream), "read");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    double surf = 0.0;
+    for (int b = 0; b < nb; ++b) surf = std::max(surf, pr[2 * b]);
+    c->dt_crit = 2.0 / (lam * fk_max / fc_min + surf);
+    c->T_lo = T_lo;
+    c->T_hi = T_hi;
+    c->precomputed = true;
+    if (dt_crit_out) *dt_crit_out = c->dt_crit;
+    return FEDFEM_OK;
+}
+
+extern "C" fedfem_status fedfem_set_dt(fedfem_ctx *c, double dt, int32_t force)
+{
+    if (!c) return FEDFEM_ERR_ARG;
+    if (!c->precomputed) return fail(c, FEDFEM_ERR_STATE, "call fedfem_precompute first");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(c, FEDFEM_ERR_ARG, "dt must be > 0");
+    if (dt > c->dt_crit && !force)
+        return fail(c, FEDFEM_ERR_UNSTABLE, "dt = " + std::to_string(dt) + " exceeds dt_crit = " + std::to_string(c->dt_crit));
+    c->dt = dt;
+    c->has_dt = true;
+    launch_set_A(c->nn, dt, c->d_C0, c->d_isdir, c->d_A, c->stream);
+    CK(cudaGetLastError(), "set dt");
+    return FEDFEM_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// state
+// ------------------------------------------------------------------------------------------
+namespace fedfem {
+
+// Install a field given in original node order (device FP64) as the state at step 0.
+fedfem_status install_T(fedfem_ctx *c, const double *T0_dev_old)
+{
+    double *tmp = c->d_v[0];
+    CK(cudaMemcpyAsync(tmp, T0_dev_old, c->nn * 8, cudaMemcpyDeviceToDevice, c->stream), "copy T0");
+    launch_impose_dirichlet((int64_t)c->dir_nodes.size(), c->d_dir_new, c->d_dir_T, tmp, c->d_old_of_new, c->stream);
+    launch_set_state(c->precision, c->nn, tmp, c->d_old_of_new, c->d_T[0], c->kahan ? c->d_comp[0] : nullptr, c->stream);
+    CK(cudaGetLastError(), "set T");
+    c->step = 0;
+    c->has_T = true;
+    return FEDFEM_OK;
+}
+
+// Current state as FP64 in new node order into dst (device).
+fedfem_status state_f64_new(fedfem_ctx *c, int64_t step, double *dst)
+{
+    const int b = (int)(step & 1);
+    launch_state_to_f64(c->precision, c->nn, c->d_T[b], c->kahan ? c->d_comp[b] : nullptr, dst, c->stream);
+    CK(cudaGetLastError(), "state");
+    return FEDFEM_OK;
+}
+
+}  // namespace fedfem
+
+extern "C" fedfem_status fedfem_set_T(fedfem_ctx *c, const double *T0)
+{
+    if (!c || !T0) return c ? fail(c, FEDFEM_ERR_ARG, "NULL T0") : FEDFEM_ERR_ARG;
+    CK(cudaMemcpyAsync(c->d_v[1], T0, c->nn * 8, cudaMemcpyHostToDevice, c->stream), "upload T0");
+    return install_T(c, c->d_v[1]);
+}
+
+extern "C" fedfem_status fedfem_set_T_device(fedfem_ctx *c, const double *T0_dev)
+{
+    if (!c || !T0_dev) return c ? fail(c, FEDFEM_ERR_ARG, "NULL T0") : FEDFEM_ERR_ARG;
+    return install_T(c, T0_dev);
+}
+
+extern "C" fedfem_status fedfem_get_T_device(fedfem_ctx *c, double *T_dev)
+{
+    if (!c || !T_dev) return c ? fail(c, FEDFEM_ERR_ARG, "NULL output") : FEDFEM_ERR_ARG;
+    if (!c->has_T) return fail(c, FEDFEM_ERR_STATE, "no temperature field set");
+    fedfem_status s = state_f64_new(c, c->step, c->d_v[0]);
+    if (s != FEDFEM_OK) return s;
+    launch_permute_new_to_old(c->nn, c->d_v[0], c->d_old_of_new, T_dev, c->stream);
+    CK(cudaGetLastError(), "get T");
+    return FEDFEM_OK;
+}
+
+extern "C" fedfem_status fedfem_get_T(fedfem_ctx *c, double *T_host)
+{
+    if (!c || !T_host) return c ? fail(c, FEDFEM_ERR_ARG, "NULL output") : FEDFEM_ERR_ARG;
+    fedfem_status s = fedfem_get_T_device(c, c->d_v[1]);
+    if (s != FEDFEM_OK) return s;
+    CK(cudaMemcpyAsync(T_host, c->d_v[1], c->nn * 8, cudaMemcpyDeviceToHost, c->stream), "download T");
+    return check_device(c);
+}
+
+extern "C" fedfem_status fedfem_get_step(fedfem_ctx *c, int64_t *step)
+{
+    if (!c || !step) return FEDFEM_ERR_ARG;
+    *step = c->step;
+    return FEDFEM_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// time stepping
+// ------------------------------------------------------------------------------------------
+namespace fedfem {
+
+StepArgs step_args(fedfem_ctx *c)
+{
+    StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.chunks = c->d_chunks;
+    a.elem_col = c->d_elem_col;
+    a.chunk_col = c->d_chunk_col;
+    a.tiles = c->d_tiles;
+    a.sh = c->d_sh;
+    a.sptr = c->d_sptr;
+    a.bnd = c->d_bnd;
+    for (int b = 0; b < 2; ++b) {
+        a.T[b] = c->d_T[b];
+        a.comp[b] = c->d_comp[b];
+        a.part[b] = c->d_part[b];
+    }
+    a.A = c->d_A;
+    a.Qext = c->d_Qext;
+    a.Ac = c->d_Ac;
+    a.Ar = c->d_Ar;
+    a.barrier = c->d_barrier;
+    a.err = c->d_err;
+    a.k_lin = c->k_lin;
+    a.c_lin = c->c_lin;
+    a.h = c->h;
+    a.T_inf = c->T_inf;
+    a.eps_sigma = c->eps * 5.67e-8;
+    a.T_amb = c->T_amb;
+    a.T_zero = c->T_zero;
+    a.T_guard = c->opt.T_guard;
+    a.n_tiles = c->til.n_tiles;
+    a.tiles_per_cta = c->tpc;
+    a.chunk_bytes = c->chunk_bytes;
+    a.stages = c->stages;
+    a.scatter = c->opt.scatter;
+    a.withhold = c->opt.debug_withhold_barrier;
+    a.timeout_ns = (long long)(c->opt.barrier_timeout_s * 1e9);
+    return a;
+}
+
+// Enqueue n steps as persistent launches of at most steps_per_launch steps.
+fedfem_status enqueue_steps(fedfem_ctx *c, int64_t n, void *rec, int64_t rec_stride)
+{
+    StepArgs a = step_args(c);
+    const int64_t spl = c->opt.steps_per_launch > 0 ? c->opt.steps_per_launch : 200;
+    int64_t done = 0;
+    while (done < n) {
+        const int64_t k = std::min(spl, n - done);
+        a.n0 = c->step;
+        a.nsteps = (int32_t)k;
+        a.rec = rec ? (uint8_t *)rec + (size_t)done * rec_stride * (c->precision == 64 ? 8 : 4) : nullptr;
+        a.rec_stride = rec_stride;
+        CK(cudaMemsetAsync(c->d_barrier, 0, 4, c->stream), "reset barrier");
+        CK(launch_step(a, c->precision, c->kahan, c->npe, c->grid, c->block, c->smem, c->stream), "step launch");
+        c->step += k;
+        done += k;
+    }
+    return FEDFEM_OK;
+}
+
+}  // namespace fedfem
+
+extern "C" fedfem_status fedfem_step_async(fedfem_ctx *c, int64_t n_steps)
+{
+    if (!c) return FEDFEM_ERR_ARG;
+    if (n_steps < 0) return fail(c, FEDFEM_ERR_ARG, "n_steps < 0");
+    if (!c->has_dt) return fail(c, FEDFEM_ERR_STATE, "call fedfem_set_dt first");
+    if (!c->has_T) return fail(c, FEDFEM_ERR_STATE, "call fedfem_set_T first");
+    if (n_steps == 0) return FEDFEM_OK;
+    return enqueue_steps(c, n_steps, nullptr, 0);
+}
+
+extern "C" fedfem_status fedfem_sync(fedfem_ctx *c)
+{
+    if (!c) return FEDFEM_ERR_ARG;
+    return check_device(c);
+}
+
+extern "C" fedfem_status fedfem_step(fedfem_ctx *c, int64_t n_steps)
+{
+    fedfem_status s = fedfem_step_async(c, n_steps);
+    if (s != FEDFEM_OK) return s;
+    return check_device(c);
+}
+
+// ------------------------------------------------------------------------------------------
+// diagnostics
+// ------------------------------------------------------------------------------------------
+extern "C" fedfem_status fedfem_internal_loads(fedfem_ctx *c, const double *T_host, double *F_host)
+{
+    if (!c || !T_host || !F_host) return c ? fail(c, FEDFEM_ERR_ARG, "NULL array") : FEDFEM_ERR_ARG;
+    if (!c->precomputed) return fail(c, FEDFEM_ERR_STATE, "call fedfem_precompute first");
+    CK(cudaMemcpyAsync(c->d_v[0], T_host, c->nn * 8, cudaMemcpyHostToDevice, c->stream), "upload");
+    launch_permute_old_to_new(c->nn, c->d_v[0], c->d_old_of_new, c->d_v[1], c->stream);
+    launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, c->d_v[1], c->d_v[1], c->k_lin,
+                 c->d_Y, c->d_v[2], c->stream);
+    launch_permute_new_to_old(c->nn, c->d_v[2], c->d_old_of_new, c->d_v[3], c->stream);
+    CK(cudaGetLastError(), "internal loads");
+    CK(cudaMemcpyAsync(F_host, c->d_v[3], c->nn * 8, cudaMemcpyDeviceToHost, c->stream), "download");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return FEDFEM_OK;
+}
+
+extern "C" fedfem_status fedfem_energy(fedfem_ctx *c, double *stored_change, double *boundary_in)
+{
+    if (!c || !stored_change || !boundary_in) return c ? fail(c, FEDFEM_ERR_ARG, "NULL output") : FEDFEM_ERR_ARG;
+    if (c->step < 1 || !c->has_dt) return fail(c, FEDFEM_ERR_STATE, "no step taken yet");
+    double *T0 = c->d_v[0], *T1 = c->d_v[1], *F = c->d_v[2];
+    fedfem_status s = state_f64_new(c, c->step - 1, T0);
+    if (s != FEDFEM_OK) return s;
+    s = state_f64_new(c, c->step, T1);
+    if (s != FEDFEM_OK) return s;
+    launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, T0, T0, c->k_lin, c->d_Y, F,
+                 c->stream);
+    EnergyPhys ph{c->dt, c->c_lin, c->h, c->T_inf, c->eps * 5.67e-8, c->T_amb, c->T_zero};
+    double *partial = c->d_red, *sums = c->d_red + 2 * 1024;
+    launch_energy(c->nn, T0, T1, F, c->d_C0, c->d_Qext64, c->d_Ac64, c->d_Ar64, c->d_isdir, ph, partial, sums, c->stream);
+    CK(cudaGetLastError(), "energy");
+    double h2[2];
+    CK(cudaMemcpyAsync(h2, sums, 16, cudaMemcpyDeviceToHost, c->stream), "read");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    *stored_change = h2[0];
+    *boundary_in = h2[1];
+    return FEDFEM_OK;
+}
+
+extern "C" fedfem_status fedfem_set_params(fedfem_ctx *c, const double *kscale, const double *source)
+{
+    if (!c) return FEDFEM_ERR_ARG;
+    if (!c->precomputed) return fail(c, FEDFEM_ERR_STATE, "call fedfem_precompute first");
+    if (kscale) {
+        for (int64_t e = 0; e < c->ne; ++e)
+            if (!(kscale[e] > 0) || !std::isfinite(kscale[e])) return fail(c, FEDFEM_ERR_ARG, "kscale must be > 0");
+        c->kscale.assign(kscale, kscale + c->ne);
+    }
+    if (source) c->source.assign(source, source + c->ne);
+    return run_precompute_arrays(c);
+}
+
+extern "C" fedfem_status fedfem_state_bytes(fedfem_ctx *c, size_t *bytes)
+{
+    if (!c || !bytes) return FEDFEM_ERR_ARG;
+    const size_t rs = c->precision == 64 ? 8 : 4;
+    *bytes = 32 + c->nn * rs + (c->kahan ? c->nn * 4 : 0);
+    return FEDFEM_OK;
+}
+
+extern "C" fedfem_status fedfem_get_state(fedfem_ctx *c, void *buf)
+{
+    if (!c || !buf) return FEDFEM_ERR_ARG;
+    if (!c->has_T) return fail(c, FEDFEM_ERR_STATE, "no temperature field set");
+    const size_t rs = c->precision == 64 ? 8 : 4;
+    int64_t hdr[4] = {c->step, c->nn, c->precision, c->kahan};
+    std::memcpy(buf, hdr, 32);
+    const int b = (int)(c->step & 1);
+    uint8_t *p = (uint8_t *)buf + 32;
+    CK(cudaMemcpyAsync(p, c->d_T[b], c->nn * rs, cudaMemcpyDeviceToHost, c->stream), "download state");
+    if (c->kahan) CK(cudaMemcpyAsync(p + c->nn * rs, c->d_comp[b], c->nn * 4, cudaMemcpyDeviceToHost, c->stream), "download");
+    return check_device(c);
+}
+
+extern "C" fedfem_status fedfem_set_state(fedfem_ctx *c, const void *buf)
+{
+    if (!c || !buf) return FEDFEM_ERR_ARG;
+    int64_t hdr[4];
+    std::memcpy(hdr, buf, 32);
+    if (hdr[1] != c->nn || hdr[2] != c->precision || hdr[3] != c->kahan)
+        return fail(c, FEDFEM_ERR_ARG, "state blob does not match this context");
+    const size_t rs = c->precision == 64 ? 8 : 4;
+    c->step = hdr[0];
+    const int b = (int)(c->step & 1);
+    const uint8_t *p = (const uint8_t *)buf + 32;
+    CK(cudaMemcpyAsync(c->d_T[b], p, c->nn * rs, cudaMemcpyHostToDevice, c->stream), "upload state");
+    if (c->kahan) CK(cudaMemcpyAsync(c->d_comp[b], p + c->nn * rs, c->nn * 4, cudaMemcpyHostToDevice, c->stream), "upload");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    c->has_T = true;
+    return FEDFEM_OK;
+}
+
+extern "C" fedfem_status fedfem_get_info(fedfem_ctx *c, fedfem_info *info)
+{
+    if (!c || !info) return FEDFEM_ERR_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n_nodes = c->nn;
+    info->n_elems = c->ne;
+    info->n_tiles = c->til.n_tiles;
+    info->grid = c->grid;
+    info->block = c->block;
+    info->stages = c->stages;
+    info->steps_per_launch = c->opt.steps_per_launch > 0 ? c->opt.steps_per_launch : 200;
+    info->max_tile_nodes = c->til.max_local;
+    info->n_colors_max = c->til.max_colors;
+    info->smem_bytes = (int32_t)c->smem;
+    info->n_shared_nodes = c->til.sptr.empty() ? 0 : (int64_t)c->til.sptr.size() - 1;
+    info->n_halo_slots = c->til.sptr.empty() ? 0 : c->til.sptr.back();
+    info->elem_bytes = (int64_t)c->til.n_chunks * c->chunk_bytes;
+    info->dt = c->dt;
+    info->dt_crit = c->dt_crit;
+    return FEDFEM_OK;
+}
+
+extern "C" const char *fedfem_error_string(fedfem_ctx *c) { return c ? c->err.c_str() : "NULL context"; }
+
+extern "C" const char *fedfem_create_error(void) { return g_create_error.c_str(); }
+
+extern "C" void fedfem_destroy(fedfem_ctx *c)
+{
+    if (!c) return;
+    if (c->stream || c->device >= 0) cudaStreamSynchronize(c->stream);
+    for (void *p : c->allocs) cudaFree(p);
+    for (void *p : c->adj_allocs) cudaFree(p);
+    delete c;
+}

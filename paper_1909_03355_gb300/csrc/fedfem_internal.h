@@ -1,0 +1,118 @@
+// Internal declarations of libfedfem.so (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fedfem.h"
+
+namespace fedfem {
+
+// Pair order of the 28 (hex) / 6 (tet) off-diagonal conductances c_ij = -K0_e[i][j], i < j,
+// enumerated row by row: (0,1) (0,2) ... (0,n-1) (1,2) ...  The diagonal follows from the zero
+// row sums of K0_e (a constant field carries no heat), so F_i = sum_j c_ij (T_i - T_j).
+constexpr int n_pairs(int npe) { return npe * (npe - 1) / 2; }
+
+// Device error word bits.
+enum : int32_t {
+    ERRBIT_DIVERGED = 1,
+    ERRBIT_TIMEOUT = 2,
+    ERRBIT_MESH = 4,
+    ERRBIT_BOUNDS = 8,
+};
+
+// One element tile: a contiguous run of chunks of the element stream plus the nodes it
+// touches.  Local node numbering inside a tile: [interior | owned-shared | ghosts];
+// interior and owned-shared nodes are the contiguous global range node_begin + local.
+struct TileInfo {
+    int32_t chunk_begin, n_chunks;
+    int32_t node_begin, n_interior, n_owned, n_local;
+    int32_t sh_begin, sh_count;      // shared entries (owned-shared and ghosts)
+    int32_t bnd_begin, bnd_count;    // owned boundary nodes (surface loads)
+    int32_t pad0, pad1;
+};
+
+// Host-side result of the tiling pass.
+struct Tiling {
+    int npe = 0, CH = 0, n_tiles = 0, n_chunks = 0, max_local = 0, max_colors = 0;
+    int64_t ne = 0, nn = 0;
+    std::vector<int32_t> new_of_old, old_of_new;   // node renumbering
+    std::vector<TileInfo> tiles;
+    std::vector<int32_t> elem_of_slot;             // [n_chunks*CH], -1 for padding
+    std::vector<int64_t> slot_of_elem;             // [ne]
+    std::vector<uint16_t> lconn;                   // [n_chunks*CH][npe] tile-local node ids
+    std::vector<uint8_t> elem_col;                 // [n_chunks*CH] colour, 0xFF for padding
+    std::vector<uint8_t> chunk_col;                // [n_chunks][2] (first, last colour)
+    std::vector<int4> sh;                          // {local, gid, sid, slot}
+    std::vector<int32_t> sptr;                     // [n_shared+1] halo slot ranges
+    std::vector<int2> bnd;                         // {local, gid} owned boundary nodes
+    // incidence (new node ids), ascending element / face order inside each list
+    std::vector<int32_t> n2e_ptr;                  // [nn+1]
+    std::vector<int64_t> n2e;                      // (e << 3) | k
+};
+
+// Build the tiling.  conn [ne][npe] original ids; is_bnd [nn] (original ids) marks nodes
+// with surface loads.  Returns "" on success, else a message.
+std::string build_tiling(int npe, int64_t ne, int64_t nn, const int32_t *conn, const double *xyz,
+                         const uint8_t *is_bnd, int n_tiles, int CH, Tiling &out);
+
+// Check every index the step kernel will use against its buffers ("" if all in range).
+std::string validate_tiling(const Tiling &T);
+
+// Node -> face incidence CSR in new node ids (faces in ascending order).
+void build_face_csr(int64_t nn, const std::vector<int32_t> &new_of_old, const int32_t *faces,
+                    int64_t n_faces, int nv, std::vector<int32_t> &ptr, std::vector<int32_t> &idx);
+
+// A device allocation owned by a context.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Ctx;
+struct Batch;
+
+// Parameters of the persistent time-step kernel.
+struct StepArgs {
+    const uint8_t *chunks;      // element stream: [n_chunks][chunk_bytes]
+    const uint8_t *elem_col;    // [n_chunks*CH]
+    const uint8_t *chunk_col;   // [n_chunks][2]
+    const TileInfo *tiles;
+    const int4 *sh;
+    const int32_t *sptr;
+    const int2 *bnd;
+    void *T[2];                 // Real [nn]
+    float *comp[2];             // [nn] (FP32 + Kahan)
+    const double *A;            // [nn] dt / C0 (0 on Dirichlet nodes)
+    const void *Qext;           // Real [nn]
+    const void *Ac;             // Real [nn]
+    const void *Ar;             // Real [nn]
+    void *part[2];              // Real [n_slots] halo partial sums, step parity
+    unsigned int *barrier;      // grid barrier counter (zeroed before each launch)
+    int32_t *err;               // device error word
+    // physics
+    double k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero, T_guard;
+    // launch
+    int64_t n0;                 // global step index at launch start
+    int32_t nsteps;
+    int32_t n_tiles, tiles_per_cta;
+    int32_t chunk_bytes, stages;
+    int32_t scatter;
+    int32_t withhold;           // test hook: CTA withhold-1 skips its first barrier arrival
+    long long timeout_ns;
+    // optional per-step recording of the state (adjoint segments): rec + s*rec_stride
+    void *rec;
+    int64_t rec_stride;
+};
+
+// Launchers (step.cu).  Return cudaError_t of the launch.
+cudaError_t launch_step(const StepArgs &a, int precision, int kahan, int npe, int grid, int block,
+                        size_t smem, cudaStream_t st);
+size_t step_smem_bytes(int precision, int npe, int block, int stages, int max_local);
+int step_max_blocks_per_sm(int precision, int kahan, int npe, int block, size_t smem);
+int chunk_bytes_for(int precision, int npe, int CH);
+
+}  // namespace fedfem

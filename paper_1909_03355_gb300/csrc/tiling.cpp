@@ -1,0 +1,325 @@
+// Host-side data layout for the persistent FED-FEM kernel.
+//
+// The paper's algorithm (Fig. 1 (iii)) loops over elements and then over nodes; on the GPU the
+// element loop is split into tiles that one CTA processes with the tile's node temperatures
+// and load accumulators in shared memory.  This pass decides that layout for an arbitrary
+// mesh (it uses no structure of the mesh beyond its connectivity and element centroids):
+//   1. sort elements along a Morton (Z-order) curve of their centroids and cut the order into
+//      tiles of near-equal element counts;
+//   2. give every node an owner tile (the lowest tile touching it) and renumber nodes so that
+//      each tile owns a contiguous range [interior | owned-shared];
+//   3. colour each tile's elements greedily so that elements of one colour share no node
+//      (the deterministic shared-memory accumulation runs colour by colour);
+//   4. give every (tile, shared node) pair a halo slot; the slots of one node are contiguous
+//      and ordered by tile, which fixes the order of the cross-tile sum.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "fedfem_internal.h"
+
+namespace fedfem {
+
+static uint64_t spread3(uint64_t v)
+{
+    uint64_t x = v & 0x1fffffULL;
+    x = (x | (x << 32)) & 0x1f00000000ffffULL;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffULL;
+    x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    return x;
+}
+
+std::string build_tiling(int npe, int64_t ne, int64_t nn, const int32_t *conn, const double *xyz,
+                         const uint8_t *is_bnd, int n_tiles, int CH, Tiling &T)
+{
+    T = Tiling();
+    T.npe = npe;
+    T.ne = ne;
+    T.nn = nn;
+    T.CH = CH;
+    if (ne <= 0 || nn <= 0) return "empty mesh";
+    if (n_tiles < 1) n_tiles = 1;
+    if (n_tiles > ne) n_tiles = (int)ne;
+    T.n_tiles = n_tiles;
+
+    // 1. Morton order of element centroids
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = 0; i < nn; ++i)
+        for (int r = 0; r < 3; ++r) {
+            lo[r] = std::min(lo[r], xyz[3 * i + r]);
+            hi[r] = std::max(hi[r], xyz[3 * i + r]);
+        }
+    std::vector<uint64_t> key(ne);
+    const double q = (double)((1u << 21) - 1);
+    for (int64_t e = 0; e < ne; ++e) {
+        double c[3] = {0, 0, 0};
+        for (int k = 0; k < npe; ++k)
+            for (int r = 0; r < 3; ++r) c[r] += xyz[3 * (int64_t)conn[npe * e + k] + r];
+        uint64_t m = 0;
+        for (int r = 0; r < 3; ++r) {
+            const double span = hi[r] - lo[r];
+            double u = span > 0 ? (c[r] / npe - lo[r]) / span : 0.0;
+            u = std::min(1.0, std::max(0.0, u));
+            m |= spread3((uint64_t)(u * q)) << r;
+        }
+        key[e] = m;
+    }
+    std::vector<int64_t> order(ne);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return key[a] < key[b]; });
+    key.clear();
+    key.shrink_to_fit();
+
+    std::vector<int64_t> tb(n_tiles + 1);
+    for (int t = 0; t <= n_tiles; ++t) tb[t] = (int64_t)((__int128)ne * t / n_tiles);
+
+    // 2. node -> tiles (ascending) CSR, owner = first tile
+    std::vector<int32_t> last(nn, -1), cnt(nn, 0);
+    for (int t = 0; t < n_tiles; ++t)
+        for (int64_t p = tb[t]; p < tb[t + 1]; ++p) {
+            const int64_t e = order[p];
+            for (int k = 0; k < npe; ++k) {
+                const int32_t n = conn[npe * e + k];
+                if (last[n] != t) {
+                    last[n] = t;
+                    ++cnt[n];
+                }
+            }
+        }
+    for (int64_t i = 0; i < nn; ++i)
+        if (cnt[i] == 0) return "node " + std::to_string(i) + " belongs to no element";
+    std::vector<int64_t> ntp(nn + 1, 0);
+    for (int64_t i = 0; i < nn; ++i) ntp[i + 1] = ntp[i] + cnt[i];
+    std::vector<int32_t> ntl(ntp[nn]);
+    {
+        std::vector<int64_t> fill(ntp.begin(), ntp.end() - 1);
+        std::fill(last.begin(), last.end(), -1);
+        for (int t = 0; t < n_tiles; ++t)
+            for (int64_t p = tb[t]; p < tb[t + 1]; ++p) {
+                const int64_t e = order[p];
+                for (int k = 0; k < npe; ++k) {
+                    const int32_t n = conn[npe * e + k];
+                    if (last[n] != t) {
+                        last[n] = t;
+                        ntl[fill[n]++] = t;
+                    }
+                }
+            }
+    }
+    auto owner = [&](int32_t n) { return ntl[ntp[n]]; };
+
+    // renumber: per tile, interior nodes then owned-shared nodes, first-touch order
+    T.new_of_old.assign(nn, -1);
+    T.old_of_new.assign(nn, -1);
+    T.tiles.resize(n_tiles);
+    int32_t next = 0;
+    for (int t = 0; t < n_tiles; ++t) {
+        TileInfo &ti = T.tiles[t];
+        std::memset(&ti, 0, sizeof(ti));
+        ti.node_begin = next;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int64_t p = tb[t]; p < tb[t + 1]; ++p) {
+                const int64_t e = order[p];
+                for (int k = 0; k < npe; ++k) {
+                    const int32_t n = conn[npe * e + k];
+                    if (T.new_of_old[n] >= 0 || owner(n) != t) continue;
+                    const bool shared = cnt[n] > 1;
+                    if ((pass == 0) == shared) continue;
+                    T.new_of_old[n] = next;
+                    T.old_of_new[next] = n;
+                    ++next;
+                }
+            }
+            if (pass == 0) ti.n_interior = next - ti.node_begin;
+        }
+        ti.n_owned = next - ti.node_begin;
+    }
+    if (next != nn) return "internal error: renumbering incomplete";
+
+    // shared ids in new-id order, halo slots ordered by tile
+    std::vector<int32_t> sid_of_new(nn, -1);
+    T.sptr.assign(1, 0);
+    for (int32_t g = 0; g < nn; ++g) {
+        const int32_t o = T.old_of_new[g];
+        if (cnt[o] > 1) {
+            sid_of_new[g] = (int32_t)T.sptr.size() - 1;
+            T.sptr.push_back(T.sptr.back() + cnt[o]);
+        }
+    }
+
+    // 3./4. per tile: local numbering, colouring, chunks, shared and boundary entries
+    std::vector<int32_t> loc(nn, -1);
+    std::vector<uint64_t> mask;
+    T.max_local = 0;
+    T.max_colors = 0;
+    int32_t chunk = 0;
+    for (int t = 0; t < n_tiles; ++t) {
+        TileInfo &ti = T.tiles[t];
+        std::vector<int32_t> ghosts;
+        for (int64_t p = tb[t]; p < tb[t + 1]; ++p) {
+            const int64_t e = order[p];
+            for (int k = 0; k < npe; ++k) {
+                const int32_t n = conn[npe * e + k];
+                const int32_t g = T.new_of_old[n];
+                if (loc[n] != -1) continue;
+                if (owner(n) == t) {
+                    loc[n] = g - ti.node_begin;
+                } else {
+                    loc[n] = -2;  // ghost, numbered below
+                    ghosts.push_back(g);
+                }
+            }
+        }
+        std::sort(ghosts.begin(), ghosts.end());
+        for (size_t i = 0; i < ghosts.size(); ++i) loc[T.old_of_new[ghosts[i]]] = ti.n_owned + (int32_t)i;
+        ti.n_local = ti.n_owned + (int32_t)ghosts.size();
+        if (ti.n_local > 65535) return "tile with more than 65535 nodes (use more tiles)";
+        T.max_local = std::max(T.max_local, ti.n_local);
+
+        // greedy colouring in Morton order
+        const int64_t m = tb[t + 1] - tb[t];
+        mask.assign(ti.n_local, 0);
+        std::vector<uint8_t> col(m);
+        for (int64_t p = 0; p < m; ++p) {
+            const int64_t e = order[tb[t] + p];
+            uint64_t used = 0;
+            for (int k = 0; k < npe; ++k) used |= mask[loc[conn[npe * e + k]]];
+            if (~used == 0) return "more than 64 colours needed in a tile";
+            const int c = __builtin_ctzll(~used);
+            col[p] = (uint8_t)c;
+            for (int k = 0; k < npe; ++k) mask[loc[conn[npe * e + k]]] |= 1ULL << c;
+            T.max_colors = std::max(T.max_colors, c + 1);
+        }
+        std::vector<int64_t> perm(m);
+        std::iota(perm.begin(), perm.end(), 0);
+        std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) { return col[a] < col[b]; });
+
+        ti.chunk_begin = chunk;
+        ti.n_chunks = (int32_t)((m + CH - 1) / CH);
+        chunk += ti.n_chunks;
+        const size_t slots = (size_t)chunk * CH;
+        T.elem_of_slot.resize(slots, -1);
+        T.elem_col.resize(slots, 0xFF);
+        T.lconn.resize(slots * npe, 0);
+        for (int64_t p = 0; p < m; ++p) {
+            const int64_t e = order[tb[t] + perm[p]];
+            const int64_t s = (int64_t)ti.chunk_begin * CH + p;
+            T.elem_of_slot[s] = (int32_t)e;
+            T.elem_col[s] = col[perm[p]];
+            for (int k = 0; k < npe; ++k) T.lconn[s * npe + k] = (uint16_t)loc[conn[npe * e + k]];
+        }
+
+        // shared entries: owned-shared then ghosts
+        ti.sh_begin = (int32_t)T.sh.size();
+        for (int32_t l = ti.n_interior; l < ti.n_local; ++l) {
+            const int32_t g = l < ti.n_owned ? ti.node_begin + l : ghosts[l - ti.n_owned];
+            const int32_t o = T.old_of_new[g];
+            const int32_t sid = sid_of_new[g];
+            int32_t rank = 0;
+            while (ntl[ntp[o] + rank] != t) ++rank;
+            T.sh.push_back(make_int4(l, g, sid, T.sptr[sid] + rank));
+        }
+        ti.sh_count = (int32_t)T.sh.size() - ti.sh_begin;
+
+        // owned boundary nodes
+        ti.bnd_begin = (int32_t)T.bnd.size();
+        if (is_bnd)
+            for (int32_t l = 0; l < ti.n_owned; ++l) {
+                const int32_t g = ti.node_begin + l;
+                if (is_bnd[T.old_of_new[g]]) T.bnd.push_back(make_int2(l, g));
+            }
+        ti.bnd_count = (int32_t)T.bnd.size() - ti.bnd_begin;
+
+        // reset the local map
+        for (int64_t p = tb[t]; p < tb[t + 1]; ++p) {
+            const int64_t e = order[p];
+            for (int k = 0; k < npe; ++k) loc[conn[npe * e + k]] = -1;
+        }
+    }
+    T.n_chunks = chunk;
+    T.chunk_col.assign((size_t)chunk * 2, 0);
+    for (int32_t c = 0; c < chunk; ++c) {
+        int lo_c = 255, hi_c = 0;
+        for (int i = 0; i < CH; ++i) {
+            const uint8_t v = T.elem_col[(size_t)c * CH + i];
+            if (v == 0xFF) continue;
+            lo_c = std::min(lo_c, (int)v);
+            hi_c = std::max(hi_c, (int)v);
+        }
+        if (lo_c > hi_c) lo_c = hi_c = 0;
+        T.chunk_col[2 * c] = (uint8_t)lo_c;
+        T.chunk_col[2 * c + 1] = (uint8_t)hi_c;
+    }
+    T.slot_of_elem.assign(ne, -1);
+    for (size_t s = 0; s < T.elem_of_slot.size(); ++s)
+        if (T.elem_of_slot[s] >= 0) T.slot_of_elem[T.elem_of_slot[s]] = (int64_t)s;
+
+    // node -> (element, local index) incidence in new ids, ascending element order
+    T.n2e_ptr.assign(nn + 1, 0);
+    for (int64_t e = 0; e < ne; ++e)
+        for (int k = 0; k < npe; ++k) ++T.n2e_ptr[T.new_of_old[conn[npe * e + k]] + 1];
+    for (int64_t i = 0; i < nn; ++i) T.n2e_ptr[i + 1] += T.n2e_ptr[i];
+    T.n2e.resize(T.n2e_ptr[nn]);
+    if (T.n2e_ptr[nn] >= (1LL << 31)) return "too many element-node incidences";
+    {
+        std::vector<int32_t> fill(T.n2e_ptr.begin(), T.n2e_ptr.end() - 1);
+        for (int64_t e = 0; e < ne; ++e)
+            for (int k = 0; k < npe; ++k) T.n2e[fill[T.new_of_old[conn[npe * e + k]]]++] = (e << 3) | k;
+    }
+    return "";
+}
+
+std::string validate_tiling(const Tiling &T)
+{
+    const int64_t n_slots = T.sptr.empty() ? 0 : T.sptr.back();
+    int32_t chunks = 0;
+    for (int t = 0; t < T.n_tiles; ++t) {
+        const TileInfo &ti = T.tiles[t];
+        if (ti.chunk_begin != chunks || ti.n_chunks < 1) return "tile chunk range";
+        chunks += ti.n_chunks;
+        if (ti.node_begin < 0 || ti.n_interior < 0 || ti.n_interior > ti.n_owned || ti.n_owned > ti.n_local ||
+            ti.node_begin + (int64_t)ti.n_owned > T.nn || ti.n_local > T.max_local)
+            return "tile node range";
+        for (int64_t s = (int64_t)ti.chunk_begin * T.CH; s < (int64_t)(ti.chunk_begin + ti.n_chunks) * T.CH; ++s)
+            for (int k = 0; k < T.npe; ++k)
+                if (T.lconn[s * T.npe + k] >= ti.n_local) return "local id out of range";
+        if (ti.sh_begin < 0 || ti.sh_begin + (int64_t)ti.sh_count > (int64_t)T.sh.size()) return "halo range";
+        if (ti.sh_count != ti.n_local - ti.n_interior) return "halo count";
+        for (int q = 0; q < ti.sh_count; ++q) {
+            const int4 h = T.sh[ti.sh_begin + q];
+            if (h.x < ti.n_interior || h.x >= ti.n_local || h.y < 0 || h.y >= T.nn || h.z < 0 ||
+                h.z + 1 >= (int64_t)T.sptr.size() || h.w < T.sptr[h.z] || h.w >= T.sptr[h.z + 1] || h.w >= n_slots)
+                return "halo entry out of range";
+            if (h.x < ti.n_owned && (h.y != ti.node_begin + h.x || h.w != T.sptr[h.z])) return "owned halo entry";
+        }
+        if (ti.bnd_begin < 0 || ti.bnd_begin + (int64_t)ti.bnd_count > (int64_t)T.bnd.size()) return "boundary range";
+        for (int q = 0; q < ti.bnd_count; ++q) {
+            const int2 b = T.bnd[ti.bnd_begin + q];
+            if (b.x < 0 || b.x >= ti.n_owned || b.y != ti.node_begin + b.x) return "boundary entry out of range";
+        }
+    }
+    if (chunks != T.n_chunks) return "chunk count";
+    if (T.elem_col.size() != (size_t)T.n_chunks * T.CH || T.chunk_col.size() != (size_t)T.n_chunks * 2)
+        return "colour arrays";
+    for (int64_t e = 0; e < T.ne; ++e)
+        if (T.slot_of_elem[e] < 0 || T.elem_of_slot[T.slot_of_elem[e]] != e) return "element slot map";
+    return "";
+}
+
+void build_face_csr(int64_t nn, const std::vector<int32_t> &new_of_old, const int32_t *faces,
+                    int64_t n_faces, int nv, std::vector<int32_t> &ptr, std::vector<int32_t> &idx)
+{
+    ptr.assign(nn + 1, 0);
+    for (int64_t f = 0; f < n_faces; ++f)
+        for (int k = 0; k < nv; ++k) ++ptr[new_of_old[faces[nv * f + k]] + 1];
+    for (int64_t i = 0; i < nn; ++i) ptr[i + 1] += ptr[i];
+    idx.resize(ptr[nn]);
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t f = 0; f < n_faces; ++f)
+        for (int k = 0; k < nv; ++k) idx[fill[new_of_old[faces[nv * f + k]]]++] = (int32_t)f;
+}
+
+}  // namespace fedfem

@@ -1,0 +1,332 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (rel-L-infinity, max|T - T_oracle| / max|T_oracle|): 1e-10 for the FP64 form and
+2e-4 for FP32 + Kahan after the stated step counts.  Sizes span several tiles with ragged
+tails (element counts not multiples of the chunk size).
+"""
+import numpy as np
+import pytest
+
+import fedfem_inputs as fi
+from oracle import oracle as O
+from tests import brute
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-10, 32: 2e-4}
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1909_03355_gb300 import capi
+    capi.load()
+
+
+def FedFem(*a, **k):
+    from paper_1909_03355_gb300.fedfem import FedFem as F
+    return F(*a, **k)
+
+
+def run_gpu(p, dt, nsteps, precision, **plan):
+    f = FedFem(p, precision=precision, **plan)
+    f.precompute()
+    f.set_dt(dt, force=True)
+    f.set_T(p.initial_T())
+    f.step(nsteps)
+    T = f.get_T()
+    f.close()
+    return T
+
+
+# ------------------------------------------------------------------------- plain cube (C1) --
+
+def test_plain_cube_fp64_vs_oracle_and_closed_form():
+    p = fi.plain_cube(10)
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    f = FedFem(p, precision=64)
+    dtc = f.precompute()
+    assert dtc == pytest.approx(m.dt_crit()[0], rel=1e-8)
+    f.set_dt(dt)
+    f.set_T(p.initial_T())
+    Tref, done = p.initial_T(), 0
+    for n in (1, 10, 50, 100, 1000):
+        f.step(n - done)
+        Tref = m.run(Tref, dt, n - done)
+        done = n
+        T = f.get_T()
+        assert rel(T, Tref) <= 1e-10, n
+        cf, _ = brute.c1_closed_form(10, dt, n)
+        assert rel(T, cf) <= 1e-10, n
+    f.close()
+
+
+def test_plain_cube_fp32():
+    p = fi.plain_cube(10)
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    for n in (1, 10, 50):
+        assert rel(run_gpu(p, dt, n, 32), m.run(p.initial_T(), dt, n)) <= 2e-4
+
+
+# ------------------------------------------------------------------ nonlinear cubes (C2) ---
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+@pytest.mark.parametrize("precision", [64, 32])
+def test_nonlinear_cube(kind, precision):
+    """k(T) anisotropic, c(T), convection top, radiation sides, central source."""
+    p = fi.nonlinear_cube(11, kind, jitter=0.2)
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    ref = m.run(p.initial_T(), dt, 400)
+    assert rel(run_gpu(p, dt, 400, precision), ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_nonlinear_hex_full_step_count(precision):
+    """Nonlinear hex cube physics at 16^3 for the full 5000 steps."""
+    p = fi.nonlinear_cube(16, "hex")
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    ref = m.run(p.initial_T(), dt, 5000)
+    assert rel(run_gpu(p, dt, 5000, precision), ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_large_cube_physics_full_step_count(precision):
+    """Orthotropic k(T), conv + rad on all faces at 12^3 for the full 20000 steps (Kahan)."""
+    p = fi.large_cube(12, jitter=0.2)
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    ref = m.run(p.initial_T(), dt, 20000)
+    assert rel(run_gpu(p, dt, 20000, precision), ref) <= TOL[precision]
+
+
+def test_fp32_without_kahan_is_reported():
+    """Plain FP32 accumulation (no Kahan) for comparison; must still be sane."""
+    p = fi.large_cube(10)
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    ref = m.run(p.initial_T(), dt, 5000)
+    e_k = rel(run_gpu(p, dt, 5000, 32), ref)
+    e_p = rel(run_gpu(p, dt, 5000, 32, kahan=False), ref)
+    print(f"fp32 rel error after 5000 steps: kahan {e_k:.3e}, plain {e_p:.3e}")
+    assert e_k <= 2e-4 and e_p < 1e-2
+
+
+# --------------------------------------------------------------------- pre-computation -----
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_internal_loads_and_dt_crit(kind):
+    p = fi.nonlinear_cube(6, kind, jitter=0.25)
+    p.elem_kscale = np.random.default_rng(1).uniform(0.5, 2, p.n_elems)
+    m = O.OracleModel(p)
+    f = FedFem(p, precision=64)
+    dtc = f.precompute()
+    T = fi.random_state(p, 3)
+    assert rel(f.internal_loads(T), m.internal_loads(T)) <= 1e-12
+    dto = m.dt_crit()[0]
+    assert dtc == pytest.approx(dto, rel=1e-6)
+    f.close()
+
+
+def test_inverted_element_reported():
+    p = fi.plain_cube(3)
+    p.conn = p.conn.copy()
+    p.conn[5] = p.conn[5][[4, 5, 6, 7, 0, 1, 2, 3]]
+    from paper_1909_03355_gb300.capi import FedFemError
+    f = FedFem(p, precision=64)
+    with pytest.raises(FedFemError) as ei:
+        f.precompute()
+    assert ei.value.name == "ERR_MESH" and "element 5" in str(ei.value)
+    f.close()
+
+
+def test_call_order_and_stability_checks():
+    from paper_1909_03355_gb300.capi import FedFemError
+    p = fi.plain_cube(4)
+    f = FedFem(p, precision=64)
+    with pytest.raises(FedFemError) as ei:
+        f.set_dt(1e-3)
+    assert ei.value.name == "ERR_STATE"
+    dtc = f.precompute()
+    with pytest.raises(FedFemError) as ei:
+        f.set_dt(1.5 * dtc)
+    assert ei.value.name == "ERR_UNSTABLE"
+    f.set_dt(0.5 * dtc)
+    with pytest.raises(FedFemError) as ei:
+        f.step(1)
+    assert ei.value.name == "ERR_STATE"
+    f.close()
+
+
+# -------------------------------------------------------------------------- patch tests ----
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_patch_test_steady_state_gpu(kind, patch_nodes):
+    """Section 4.1: interior nodes follow T = 200x + 100y + 200z at steady state."""
+    p = fi.patch_problem(patch_nodes, kind, k0=np.array([[3.0, 0.5, 0.2], [0.5, 2.0, 0.3], [0.2, 0.3, 1.0]]))
+    lin = p.xyz @ np.array([200.0, 100.0, 200.0])
+    f = FedFem(p, precision=64)
+    dtc = f.precompute()
+    f.set_dt(0.9 * dtc)
+    f.set_T(p.initial_T())
+    f.step(20000)
+    assert np.max(np.abs(f.get_T() - lin)) <= 1e-9 * np.max(np.abs(lin))
+    f.close()
+
+
+def test_slab_gpu_matches_1d_recurrence():
+    nx, k, rho, c0 = 40, 2.0, 3.0, 1.5
+    p = fi.slab(nx, 2, 2, k=(k, 1.0, 1.0), rho=rho, c0=c0, k_lin=0.01, c_lin=0.004, T0=0.0, T_s=100.0,
+                conv_end=(4.0, 10.0))
+    h = 1.0 / nx
+    dt = 0.2 * rho * c0 * h * h / (k * 3.0)
+    T = run_gpu(p, dt, 500, 64)
+    ref = brute.ftcs_slab(nx, h, dt, 500, 0.0, 100.0, k, rho, c0, 0.01, 0.004, conv=(4.0, 10.0))
+    ix = np.rint(p.xyz[:, 0] / h).astype(int)
+    assert np.max(np.abs(T - ref[ix])) <= 1e-11 * 100
+
+
+# ---------------------------------------------------------------- energy, determinism ------
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-10), (32, 1e-4)])
+def test_energy_balance_gpu(precision, tol):
+    p = fi.nonlinear_cube(9, "hex")
+    p.dir_nodes = np.arange(0, 10, dtype=np.int32)
+    p.dir_T = np.full(10, 80.0)
+    f = FedFem(p, precision=precision)
+    dt = 0.9 * f.precompute()
+    f.set_dt(dt)
+    f.set_T(p.initial_T())
+    f.step(37)
+    S, B = f.energy()
+    assert abs(S - B) <= tol * abs(B)
+    f.close()
+
+
+def test_determinism_bitwise():
+    p = fi.nonlinear_cube(12, "hex", jitter=0.1)
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    a = run_gpu(p, dt, 300, 32)
+    b = run_gpu(p, dt, 300, 32)
+    assert np.array_equal(a, b)
+
+
+def test_checkpoint_resume_bitwise():
+    p = fi.nonlinear_cube(10, "tet")
+    f = FedFem(p, precision=32)
+    dt = 0.9 * f.precompute()
+    f.set_dt(dt)
+    f.set_T(p.initial_T())
+    f.step(103)
+    st = f.get_state()
+    f.step(97)
+    a = f.get_T()
+    f.set_state(st)
+    assert f.step_count == 103
+    f.step(97)
+    assert np.array_equal(a, f.get_T())
+    f.close()
+
+
+def test_atomic_scatter_variant_close():
+    p = fi.nonlinear_cube(10, "hex")
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    ref = m.run(p.initial_T(), dt, 300)
+    from paper_1909_03355_gb300.capi import SCATTER_ATOMIC
+    assert rel(run_gpu(p, dt, 300, 32, scatter=SCATTER_ATOMIC), ref) <= 2e-4
+    assert rel(run_gpu(p, dt, 300, 64, scatter=SCATTER_ATOMIC), ref) <= 1e-10
+
+
+@pytest.mark.parametrize("plan", [dict(block=128, stages=2, tiles_per_cta=1, steps_per_launch=1),
+                                  dict(block=512, stages=3, tiles_per_cta=4, steps_per_launch=7),
+                                  dict(block=256, stages=6, ctas_per_sm=2, steps_per_launch=33)])
+def test_launch_plans_agree(plan):
+    """Different tilings / chunk sizes / launch splits agree with the oracle (FP64 plans whose
+    element stages do not fit in shared memory are rejected at create and skipped here)."""
+    from paper_1909_03355_gb300.capi import FedFemError
+    p = fi.large_cube(14, jitter=0.15)
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    ref = m.run(p.initial_T(), dt, 150)
+    assert rel(run_gpu(p, dt, 150, 32, **plan), ref) <= 2e-4
+    try:
+        T64 = run_gpu(p, dt, 150, 64, **plan)
+    except FedFemError as e:
+        assert e.name == "ERR_UNSUPPORTED" and plan["block"] == 512
+        return
+    assert rel(T64, ref) <= 1e-10
+
+
+# ------------------------------------------------------------------ failure detection -------
+
+def test_watchdog_reports_divergence_and_context_recovers():
+    from paper_1909_03355_gb300.capi import FedFemError
+    p = fi.nonlinear_cube(8, "hex")
+    f = FedFem(p, precision=32, T_guard=1e4)
+    dtc = f.precompute()
+    f.set_dt(0.9 * dtc)
+    f.set_T(p.initial_T())
+    st = f.get_state()
+    f.set_dt(40 * dtc, force=True)
+    with pytest.raises(FedFemError) as ei:
+        f.step(400)
+    assert ei.value.name == "ERR_DIVERGED"
+    f.set_dt(0.9 * dtc)
+    f.set_state(st)
+    f.step(10)
+    assert np.all(np.isfinite(f.get_T()))
+    f.close()
+
+
+def test_barrier_timeout_is_reported_not_hung():
+    """A CTA withholds its first grid-barrier arrival; the others' bounded waits run out, the
+    call returns ERR_TIMEOUT and the context stays usable."""
+    from paper_1909_03355_gb300.capi import FedFemError
+    p = fi.nonlinear_cube(12, "hex")
+    f = FedFem(p, precision=32, barrier_timeout_s=0.05, debug_withhold_barrier=1)
+    dtc = f.precompute()
+    assert f.info()["grid"] >= 2
+    f.set_dt(0.9 * dtc)
+    f.set_T(p.initial_T())
+    with pytest.raises(FedFemError) as ei:
+        f.step(5)
+    assert ei.value.name == "ERR_TIMEOUT"
+    f.close()
+    g = FedFem(p, precision=32)
+    g.precompute()
+    g.set_dt(0.9 * dtc)
+    g.set_T(p.initial_T())
+    g.step(5)
+    assert np.all(np.isfinite(g.get_T()))
+    g.close()
+
+
+# ------------------------------------------------------------------ full-size workload ------
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_full_size_large_cube_parity(precision):
+    """The 128^3 workload in the launch configuration bench.py times: 10 steps from T0, the
+    whole field against the oracle."""
+    p = fi.large_cube(128)
+    f = FedFem(p, precision=precision)
+    dt = 0.9 * f.precompute()
+    f.set_dt(dt)
+    f.set_T(p.initial_T())
+    f.step(10)
+    T = f.get_T()
+    f.close()
+    m = O.OracleModel(p)
+    ref = m.run(p.initial_T(), dt, 10)
+    assert rel(T, ref) <= TOL[precision]
+    # heat has started to flow: the field is not the initial one
+    assert np.max(np.abs(ref - 20.0)) > 0
