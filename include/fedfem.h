@@ -103,11 +103,15 @@ typedef struct {
     int32_t precision;          /* FEDFEM_FP32 (default) or FEDFEM_FP64                   */
     int32_t kahan;              /* FP32 only: 1 (default) Kahan-compensated T accumulator  */
     int32_t scatter;            /* FEDFEM_SCATTER_COLOR (default) or FEDFEM_SCATTER_ATOMIC */
-    int32_t block;              /* threads per CTA = elements per chunk (128/256/512), 0 = auto */
+    int32_t block;              /* consumer threads per CTA (multiple of 32, <= 480; one producer
+                                   warp is added), 0 = auto                                  */
     int32_t steps_per_launch;   /* explicit steps fused in one persistent launch, 0 = auto */
     int32_t ctas_per_sm;        /* resident CTAs per SM, 0 = auto                          */
     int32_t tiles_per_cta;      /* element tiles per CTA, 0 = auto                          */
-    int32_t stages;             /* depth of the element-chunk TMA ring, 0 = auto            */
+    int32_t stages;             /* depth of the element-chunk TMA ring (2..63), 0 = auto     */
+    int32_t chunk;              /* elements per TMA chunk, 32 or 64 (one chunk per warp), 0 = auto */
+    int32_t l2_policy;          /* element stream L2 policy: 0 = auto, 1 = evict_normal, 2 = evict_first
+                                   (node operands are then prefetched evict_last) */
     double barrier_timeout_s;   /* device-side wait limit (default 1.0 s)                   */
     double T_guard;             /* watchdog threshold on |T| (default 1e6)                  */
     void *stream;               /* cudaStream_t, NULL = legacy default stream               */
@@ -234,7 +238,7 @@ fedfem_status fedfem_adjoint(fedfem_ctx *ctx, const double *dL_dtrace, double *d
 /* Launch plan and sizes chosen by create: a fixed-size record for logging and benchmarks. */
 typedef struct {
     int64_t n_nodes, n_elems;
-    int32_t n_tiles, grid, block, stages;
+    int32_t n_tiles, grid, block, stages, chunk, reserved;
     int32_t steps_per_launch, max_tile_nodes, n_colors_max, smem_bytes;
     int64_t n_shared_nodes, n_halo_slots, elem_bytes;   /* element stream bytes per step */
     double dt, dt_crit;

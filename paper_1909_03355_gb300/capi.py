@@ -42,13 +42,13 @@ class Bcs(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", I32), ("kahan", I32), ("scatter", I32), ("block", I32),
                 ("steps_per_launch", I32), ("ctas_per_sm", I32), ("tiles_per_cta", I32), ("stages", I32),
-                ("barrier_timeout_s", F64), ("T_guard", F64), ("stream", P), ("device", I32),
+                ("chunk", I32), ("l2_policy", I32), ("barrier_timeout_s", F64), ("T_guard", F64), ("stream", P), ("device", I32),
                 ("verbose", I32), ("debug_withhold_barrier", I32), ("reserved", I32)]
 
 
 class Info(C.Structure):
     _fields_ = [("n_nodes", I64), ("n_elems", I64), ("n_tiles", I32), ("grid", I32), ("block", I32),
-                ("stages", I32), ("steps_per_launch", I32), ("max_tile_nodes", I32), ("n_colors_max", I32),
+                ("stages", I32), ("chunk", I32), ("reserved", I32), ("steps_per_launch", I32), ("max_tile_nodes", I32), ("n_colors_max", I32),
                 ("smem_bytes", I32), ("n_shared_nodes", I64), ("n_halo_slots", I64), ("elem_bytes", I64),
                 ("dt", F64), ("dt_crit", F64)]
 

@@ -25,21 +25,23 @@ struct fedfem_ctx {
 
     // launch plan
     fedfem::Tiling til;
-    int grid = 0, block = 0, stages = 0, tpc = 0, chunk_bytes = 0;
+    int grid = 0, block = 0, stages = 0, tpc = 0, chunk_bytes = 0, chunk = 0, ts_cap = 0;
     size_t smem = 0;
     int device = -1, num_sms = 0, max_smem = 0;
     cudaStream_t stream = nullptr;
 
     // device arrays (new node numbering unless noted)
     std::vector<void *> allocs;
-    uint8_t *d_chunks = nullptr, *d_elem_col = nullptr, *d_chunk_col = nullptr;
+    uint8_t *d_chunks = nullptr;
     fedfem::TileInfo *d_tiles = nullptr;
     int4 *d_sh = nullptr;
     int32_t *d_sptr = nullptr;
     int2 *d_bnd = nullptr;
+    int32_t *d_colptr = nullptr;
     void *d_T[2] = {nullptr, nullptr};
     float *d_comp[2] = {nullptr, nullptr};
     void *d_part[2] = {nullptr, nullptr};
+    float2 *d_A2 = nullptr;
     double *d_A = nullptr, *d_C0 = nullptr, *d_Qext64 = nullptr, *d_Ac64 = nullptr, *d_Ar64 = nullptr;
     void *d_Qext = nullptr, *d_Ac = nullptr, *d_Ar = nullptr;
     uint8_t *d_isdir = nullptr;

@@ -77,9 +77,10 @@ static fedfem_status check_device(fedfem_ctx *c)
     if (bits) {
         CK(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream), "clear status");
         CK(cudaStreamSynchronize(c->stream), "synchronize");
-        const fedfem_status s = (bits & ERRBIT_TIMEOUT)    ? FEDFEM_ERR_TIMEOUT
-                                : (bits & ERRBIT_DIVERGED) ? FEDFEM_ERR_DIVERGED
-                                                           : FEDFEM_ERR_MESH;
+        // a divergence can leave secondary timeouts behind: report the root cause first
+        const fedfem_status s = (bits & ERRBIT_DIVERGED) ? FEDFEM_ERR_DIVERGED
+                                : (bits & ERRBIT_MESH)   ? FEDFEM_ERR_MESH
+                                                         : FEDFEM_ERR_TIMEOUT;
         return fail(c, s, status_message(bits));
     }
     return FEDFEM_OK;
@@ -143,30 +144,41 @@ static std::string validate(const fedfem_mesh *m, const fedfem_material *mats, i
     return "";
 }
 
-static int default_block(int precision, int npe)
+static int default_chunk(int precision, int npe)
 {
-    if (precision == 64) return npe == 8 ? 128 : 256;
-    return npe == 8 ? 256 : 512;
+    (void)precision;
+    (void)npe;
+    return 32;
 }
 
-// Choose tiles, grid and shared memory; builds c->til.
+// Choose tiles, grid, chunking and shared memory; builds c->til.
 static fedfem_status make_plan(fedfem_ctx *c, const std::vector<uint8_t> &is_bnd)
 {
     const int npe = c->npe;
-    int block = c->opt.block ? c->opt.block : default_block(c->precision, npe);
-    if (block != 128 && block != 256 && block != 512) return fail(c, FEDFEM_ERR_ARG, "block must be 128, 256 or 512");
-    int stages = c->opt.stages ? c->opt.stages : 4;
-    if (stages < 2 || stages > 8) return fail(c, FEDFEM_ERR_ARG, "stages must be in [2, 8]");
-    int cps = c->opt.ctas_per_sm ? c->opt.ctas_per_sm : 1;
-    int tpc = c->opt.tiles_per_cta ? c->opt.tiles_per_cta : 2;
-    const int cb = chunk_bytes_for(c->precision, npe, block);
-    for (int attempt = 0; attempt < 10; ++attempt) {
+    // consumer threads per CTA (one producer warp is added at launch); the FP32 default runs
+    // two CTAs of 7 consumer warps + 1 producer warp per SM (16 warps, 128 registers each)
+    const int block = c->opt.block ? c->opt.block : (c->precision == 64 ? 256 : 224);
+    if (block % 32 || block < 64 || block > 480) return fail(c, FEDFEM_ERR_ARG, "block must be a multiple of 32 in [64, 480]");
+    const int chunk = c->opt.chunk ? c->opt.chunk : default_chunk(c->precision, npe);
+    if (chunk != 32 && chunk != 64) return fail(c, FEDFEM_ERR_ARG, "chunk must be 32 or 64");
+    // two CTAs per SM only while (block + 32) threads x 128 registers fit twice per SM
+    const int cps = c->opt.ctas_per_sm ? c->opt.ctas_per_sm : (c->precision == 32 && block <= 224 ? 2 : 1);
+    // every consumer warp can hold one staged chunk; the rest of the ring is read-ahead
+    const int per_round = block / 32;
+    if (c->opt.stages && (c->opt.stages < 2 || c->opt.stages > 63))
+        return fail(c, FEDFEM_ERR_ARG, "stages must be in [2, 63]");
+    const int target_bytes = (cps >= 2 ? 40 : 64) * 1024;  // element bytes in flight per CTA
+    int stages = c->opt.stages ? c->opt.stages
+                               : std::min(63, std::max(per_round + 2, target_bytes / chunk_bytes_for(c->precision, npe, chunk)));
+    int tpc = c->opt.tiles_per_cta ? c->opt.tiles_per_cta : 1;
+    const int cb = chunk_bytes_for(c->precision, npe, chunk);
+    for (int attempt = 0; attempt < 12; ++attempt) {
         const int64_t n_ctas = (int64_t)c->num_sms * cps;
         int64_t n_tiles = n_ctas * tpc;
         n_tiles = std::min<int64_t>(n_tiles, std::max<int64_t>(1, c->ne / block));
         const int grid = (int)((n_tiles + tpc - 1) / tpc);
         std::string e = build_tiling(npe, c->ne, c->nn, c->conn.data(), c->xyz.data(), is_bnd.data(), (int)n_tiles,
-                                     block, c->til);
+                                     chunk, c->til);
         if (!e.empty()) {
             if (e.find("65535") != std::string::npos) {
                 tpc *= 2;
@@ -176,21 +188,29 @@ static fedfem_status make_plan(fedfem_ctx *c, const std::vector<uint8_t> &is_bnd
         }
         e = validate_tiling(c->til);
         if (!e.empty()) return fail(c, FEDFEM_ERR_MESH, "tiling check failed: " + e);
-        const size_t smem = step_smem_bytes(c->precision, npe, block, stages, c->til.max_local);
+        // fewer stages before smaller tiles, unless the stage count was given
+        int st = stages;
+        size_t smem = step_smem_bytes(c->precision, npe, chunk, st, c->til.max_local);
+        while (!c->opt.stages && st > 4 && smem > (size_t)c->max_smem / cps) {
+            --st;
+            smem = step_smem_bytes(c->precision, npe, chunk, st, c->til.max_local);
+        }
         int nb = 0;
         if (smem <= (size_t)c->max_smem) nb = step_max_blocks_per_sm(c->precision, c->kahan, npe, block, smem);
-        if (nb * c->num_sms >= grid && nb >= 1) {
+        if (nb >= cps && nb * c->num_sms >= grid) {
             c->block = block;
-            c->stages = stages;
+            c->chunk = chunk;
+            c->stages = st;
             c->tpc = tpc;
             c->grid = grid;
             c->smem = smem;
             c->chunk_bytes = cb;
+            c->ts_cap = step_ts_cap(c->precision, c->til.max_local);
             if (c->opt.verbose)
                 std::fprintf(stderr,
-                             "fedfem plan: tiles=%d grid=%d block=%d stages=%d tpc=%d max_local=%d colours=%d "
-                             "smem=%zu chunks=%d\n",
-                             c->til.n_tiles, grid, block, stages, tpc, c->til.max_local, c->til.max_colors, smem,
+                             "fedfem plan: tiles=%d grid=%d block=%d chunk=%d stages=%d tpc=%d max_local=%d "
+                             "colours=%d smem=%zu chunks=%d\n",
+                             c->til.n_tiles, grid, block, chunk, st, tpc, c->til.max_local, c->til.max_colors, smem,
                              c->til.n_chunks);
             return FEDFEM_OK;
         }
@@ -288,36 +308,51 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
     const int npe = c->npe;
     const size_t rs = c->precision == 64 ? 8 : 4;
 
-    // element stream with tile-local ids (conductances are filled by the pre-computation)
+    // element stream: tile-local ids, colours and chunk headers (the conductances are filled
+    // in by the pre-computation)
     {
+        const int CH = c->chunk;
         std::vector<uint8_t> host((size_t)T.n_chunks * c->chunk_bytes, 0);
-        const size_t id_off = (size_t)n_pairs(npe) * rs * c->block;
+        const size_t id_off = (size_t)n_pairs(npe) * rs * CH;
+        const size_t col_off = chunk_colour_offset(c->precision, npe, CH);
+        const size_t hdr_off = chunk_header_offset(c->precision, npe, CH);
         for (int64_t ch = 0; ch < T.n_chunks; ++ch) {
-            uint16_t *ids = reinterpret_cast<uint16_t *>(host.data() + ch * c->chunk_bytes + id_off);
-            std::memcpy(ids, T.lconn.data() + (size_t)ch * c->block * npe, (size_t)c->block * npe * 2);
+            uint8_t *blk = host.data() + ch * c->chunk_bytes;
+            std::memcpy(blk + id_off, T.lconn.data() + (size_t)ch * CH * npe, (size_t)CH * npe * 2);
+            std::memcpy(blk + col_off, T.elem_col.data() + (size_t)ch * CH, CH);
+            blk[hdr_off] = T.chunk_col[2 * ch];
+            blk[hdr_off + 1] = T.chunk_col[2 * ch + 1];
         }
         CK(upload(c, (void **)&c->d_chunks, host.data(), host.size()), "upload element stream");
         CK(cudaStreamSynchronize(c->stream), "synchronize");
     }
-    CK(upload(c, (void **)&c->d_elem_col, T.elem_col.data(), T.elem_col.size()), "upload colours");
-    CK(upload(c, (void **)&c->d_chunk_col, T.chunk_col.data(), T.chunk_col.size()), "upload chunk colours");
     CK(upload(c, (void **)&c->d_tiles, T.tiles.data(), T.tiles.size() * sizeof(TileInfo)), "upload tiles");
     CK(upload(c, (void **)&c->d_sh, T.sh.data(), T.sh.size() * sizeof(int4)), "upload halo");
     CK(upload(c, (void **)&c->d_sptr, T.sptr.data(), T.sptr.size() * sizeof(int32_t)), "upload halo ptr");
     CK(upload(c, (void **)&c->d_bnd, T.bnd.data(), T.bnd.size() * sizeof(int2)), "upload boundary");
+    CK(upload(c, (void **)&c->d_colptr, T.colptr.data(), T.colptr.size() * sizeof(int32_t)), "upload colours");
     const size_t n_slots = T.sptr.empty() ? 0 : (size_t)T.sptr.back();
     for (int b = 0; b < 2; ++b) {
-        CK(dalloc(c, &c->d_T[b], nn * rs), "alloc T");
+        CK(dalloc(c, &c->d_T[b], (nn + NODE_PAD) * rs), "alloc T");
+        CK(cudaMemsetAsync(c->d_T[b], 0, (nn + NODE_PAD) * rs, c->stream), "memset");
         CK(dalloc(c, &c->d_part[b], std::max<size_t>(n_slots, 1) * rs), "alloc halo partials");
-        if (c->kahan) CK(dalloc(c, (void **)&c->d_comp[b], nn * sizeof(float)), "alloc comp");
+        if (c->kahan) {
+            CK(dalloc(c, (void **)&c->d_comp[b], (nn + NODE_PAD) * sizeof(float)), "alloc comp");
+            CK(cudaMemsetAsync(c->d_comp[b], 0, (nn + NODE_PAD) * sizeof(float), c->stream), "memset");
+        }
     }
-    CK(dalloc(c, (void **)&c->d_A, nn * 8), "alloc A");
+    CK(dalloc(c, (void **)&c->d_A, (nn + NODE_PAD) * 8), "alloc A");
+    CK(cudaMemsetAsync(c->d_A, 0, (nn + NODE_PAD) * 8, c->stream), "memset");
+    if (c->precision == 32) {
+        CK(dalloc(c, (void **)&c->d_A2, (nn + NODE_PAD) * 8), "alloc A2");
+        CK(cudaMemsetAsync(c->d_A2, 0, (nn + NODE_PAD) * 8, c->stream), "memset");
+    }
     CK(dalloc(c, (void **)&c->d_C0, nn * 8), "alloc C0");
-    CK(dalloc(c, (void **)&c->d_Qext64, nn * 8), "alloc Q");
+    CK(dalloc(c, (void **)&c->d_Qext64, (nn + NODE_PAD) * 8), "alloc Q");
     CK(dalloc(c, (void **)&c->d_Ac64, nn * 8), "alloc Ac");
     CK(dalloc(c, (void **)&c->d_Ar64, nn * 8), "alloc Ar");
     if (c->precision == 32) {
-        CK(dalloc(c, &c->d_Qext, nn * 4), "alloc Q32");
+        CK(dalloc(c, &c->d_Qext, (nn + NODE_PAD) * 4), "alloc Q32");
         CK(dalloc(c, &c->d_Ac, nn * 4), "alloc Ac32");
         CK(dalloc(c, &c->d_Ar, nn * 4), "alloc Ar32");
     } else {
@@ -413,7 +448,7 @@ static fedfem_status run_precompute_arrays(fedfem_ctx *c)
     ea.mat_k0 = c->d_matk0;
     ea.kscale = c->d_kscale;
     ea.slot_of_elem = c->d_slot_of_elem;
-    ea.CH = c->block;
+    ea.CH = c->chunk;
     ea.VW = (c->precision == 32 && npe == 8) ? 4 : 2;
     ea.precision = c->precision;
     ea.chunk_bytes = c->chunk_bytes;
@@ -462,7 +497,7 @@ static fedfem_status run_precompute_arrays(fedfem_ctx *c)
         CK(cudaStreamSynchronize(c->stream), "synchronize");
         return fail(c, FEDFEM_ERR_MESH, "element " + std::to_string(bad) + " has det J <= 0 (inverted or degenerate)");
     }
-    if (c->has_dt) launch_set_A(c->nn, c->dt, c->d_C0, c->d_isdir, c->d_A, c->stream);
+    if (c->has_dt) launch_set_A(c->nn, c->dt, c->d_C0, c->d_isdir, c->d_A, c->d_A2, c->stream);
     return FEDFEM_OK;
 }
 
@@ -532,7 +567,7 @@ extern "C" fedfem_status fedfem_set_dt(fedfem_ctx *c, double dt, int32_t force)
         return fail(c, FEDFEM_ERR_UNSTABLE, "dt = " + std::to_string(dt) + " exceeds dt_crit = " + std::to_string(c->dt_crit));
     c->dt = dt;
     c->has_dt = true;
-    launch_set_A(c->nn, dt, c->d_C0, c->d_isdir, c->d_A, c->stream);
+    launch_set_A(c->nn, dt, c->d_C0, c->d_isdir, c->d_A, c->d_A2, c->stream);
     CK(cudaGetLastError(), "set dt");
     return FEDFEM_OK;
 }
@@ -616,18 +651,18 @@ StepArgs step_args(fedfem_ctx *c)
     StepArgs a;
     std::memset(&a, 0, sizeof(a));
     a.chunks = c->d_chunks;
-    a.elem_col = c->d_elem_col;
-    a.chunk_col = c->d_chunk_col;
     a.tiles = c->d_tiles;
     a.sh = c->d_sh;
     a.sptr = c->d_sptr;
     a.bnd = c->d_bnd;
+    a.colptr = c->d_colptr;
     for (int b = 0; b < 2; ++b) {
         a.T[b] = c->d_T[b];
         a.comp[b] = c->d_comp[b];
         a.part[b] = c->d_part[b];
     }
     a.A = c->d_A;
+    a.A2 = c->d_A2;
     a.Qext = c->d_Qext;
     a.Ac = c->d_Ac;
     a.Ar = c->d_Ar;
@@ -645,6 +680,12 @@ StepArgs step_args(fedfem_ctx *c)
     a.tiles_per_cta = c->tpc;
     a.chunk_bytes = c->chunk_bytes;
     a.stages = c->stages;
+    a.chunk = c->chunk;
+    a.colour_offset = chunk_colour_offset(c->precision, c->npe, c->chunk);
+    // the element stream is evicted first when it cannot stay resident in L2 (> 64 MB);
+    // smaller meshes keep it cached from step to step
+    const bool big = (int64_t)c->til.n_chunks * c->chunk_bytes > (64LL << 20);
+    a.l2_stream_policy = c->opt.l2_policy == 2 || (c->opt.l2_policy == 0 && big) ? 1 : 0;
     a.scatter = c->opt.scatter;
     a.withhold = c->opt.debug_withhold_barrier;
     a.timeout_ns = (long long)(c->opt.barrier_timeout_s * 1e9);
@@ -655,7 +696,15 @@ StepArgs step_args(fedfem_ctx *c)
 fedfem_status enqueue_steps(fedfem_ctx *c, int64_t n, void *rec, int64_t rec_stride)
 {
     StepArgs a = step_args(c);
-    const int64_t spl = c->opt.steps_per_launch > 0 ? c->opt.steps_per_launch : 200;
+    int64_t spl = c->opt.steps_per_launch > 0 ? c->opt.steps_per_launch : 200;
+    // the kernel counts the chunks of one launch in 32 bits
+    int64_t max_chunks = 1;
+    for (int t = 0; t < c->til.n_tiles; t += c->tpc) {
+        int64_t n = 0;
+        for (int u = t; u < std::min(t + c->tpc, c->til.n_tiles); ++u) n += c->til.tiles[u].n_chunks;
+        max_chunks = std::max(max_chunks, n);
+    }
+    spl = std::max<int64_t>(1, std::min<int64_t>(spl, ((int64_t)1 << 30) / max_chunks));
     int64_t done = 0;
     while (done < n) {
         const int64_t k = std::min(spl, n - done);
@@ -664,7 +713,7 @@ fedfem_status enqueue_steps(fedfem_ctx *c, int64_t n, void *rec, int64_t rec_str
         a.rec = rec ? (uint8_t *)rec + (size_t)done * rec_stride * (c->precision == 64 ? 8 : 4) : nullptr;
         a.rec_stride = rec_stride;
         CK(cudaMemsetAsync(c->d_barrier, 0, 4, c->stream), "reset barrier");
-        CK(launch_step(a, c->precision, c->kahan, c->npe, c->grid, c->block, c->smem, c->stream), "step launch");
+        CK(launch_step(a, c->precision, c->kahan, c->npe, c->grid, c->block, c->smem, c->ts_cap, c->stream), "step launch");
         c->step += k;
         done += k;
     }
@@ -800,6 +849,7 @@ extern "C" fedfem_status fedfem_get_info(fedfem_ctx *c, fedfem_info *info)
     info->grid = c->grid;
     info->block = c->block;
     info->stages = c->stages;
+    info->chunk = c->chunk;
     info->steps_per_launch = c->opt.steps_per_launch > 0 ? c->opt.steps_per_launch : 200;
     info->max_tile_nodes = c->til.max_local;
     info->n_colors_max = c->til.max_colors;

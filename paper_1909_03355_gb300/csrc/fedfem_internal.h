@@ -32,7 +32,7 @@ struct TileInfo {
     int32_t node_begin, n_interior, n_owned, n_local;
     int32_t sh_begin, sh_count;      // shared entries (owned-shared and ghosts)
     int32_t bnd_begin, bnd_count;    // owned boundary nodes (surface loads)
-    int32_t pad0, pad1;
+    int32_t col_begin, n_colors;     // colour classes: chunks colptr[col_begin + c] .. [.. + c + 1]
 };
 
 // Host-side result of the tiling pass.
@@ -46,9 +46,10 @@ struct Tiling {
     std::vector<uint16_t> lconn;                   // [n_chunks*CH][npe] tile-local node ids
     std::vector<uint8_t> elem_col;                 // [n_chunks*CH] colour, 0xFF for padding
     std::vector<uint8_t> chunk_col;                // [n_chunks][2] (first, last colour)
-    std::vector<int4> sh;                          // {local, gid, sid, slot}
+    std::vector<int4> sh;                          // {local, gid, first slot, count | rank << 16}
     std::vector<int32_t> sptr;                     // [n_shared+1] halo slot ranges
     std::vector<int2> bnd;                         // {local, gid} owned boundary nodes
+    std::vector<int32_t> colptr;                   // per tile: first chunk of each colour class
     // incidence (new node ids), ascending element / face order inside each list
     std::vector<int32_t> n2e_ptr;                  // [nn+1]
     std::vector<int64_t> n2e;                      // (e << 3) | k
@@ -78,15 +79,15 @@ struct Batch;
 // Parameters of the persistent time-step kernel.
 struct StepArgs {
     const uint8_t *chunks;      // element stream: [n_chunks][chunk_bytes]
-    const uint8_t *elem_col;    // [n_chunks*CH]
-    const uint8_t *chunk_col;   // [n_chunks][2]
     const TileInfo *tiles;
     const int4 *sh;
     const int32_t *sptr;
     const int2 *bnd;
+    const int32_t *colptr;      // tile-relative chunk offsets of the colour classes
     void *T[2];                 // Real [nn]
     float *comp[2];             // [nn] (FP32 + Kahan)
-    const double *A;            // [nn] dt / C0 (0 on Dirichlet nodes)
+    const double *A;            // [nn] dt / C0 (0 on Dirichlet nodes), FP64 form
+    const float2 *A2;           // [nn] the same as a float pair (hi, lo), FP32 form
     const void *Qext;           // Real [nn]
     const void *Ac;             // Real [nn]
     const void *Ar;             // Real [nn]
@@ -99,7 +100,8 @@ struct StepArgs {
     int64_t n0;                 // global step index at launch start
     int32_t nsteps;
     int32_t n_tiles, tiles_per_cta;
-    int32_t chunk_bytes, stages;
+    int32_t chunk_bytes, stages, chunk, colour_offset;
+    int32_t l2_stream_policy;   // 0: evict_normal, 1: evict_first for the element stream
     int32_t scatter;
     int32_t withhold;           // test hook: CTA withhold-1 skips its first barrier arrival
     long long timeout_ns;
@@ -110,9 +112,13 @@ struct StepArgs {
 
 // Launchers (step.cu).  Return cudaError_t of the launch.
 cudaError_t launch_step(const StepArgs &a, int precision, int kahan, int npe, int grid, int block,
-                        size_t smem, cudaStream_t st);
-size_t step_smem_bytes(int precision, int npe, int block, int stages, int max_local);
+                        size_t smem, int ts_cap, cudaStream_t st);
+size_t step_smem_bytes(int precision, int npe, int chunk, int stages, int max_local);
+int step_ts_cap(int precision, int max_local);
 int step_max_blocks_per_sm(int precision, int kahan, int npe, int block, size_t smem);
 int chunk_bytes_for(int precision, int npe, int CH);
+int chunk_colour_offset(int precision, int npe, int CH);
+int chunk_header_offset(int precision, int npe, int CH);
+constexpr int NODE_PAD = 16;    // node arrays carry this many trailing pad entries (aligned bulk copies)
 
 }  // namespace fedfem

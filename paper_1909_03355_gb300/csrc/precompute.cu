@@ -244,11 +244,18 @@ __global__ void k_node_sums(NodeArgs a)
     }
 }
 
-// A_i = dt / C0_i (Eq. 14 / 21), 0 on Dirichlet nodes.
-__global__ void k_set_A(int64_t nn, double dt, const double *C0, const uint8_t *isdir, double *A)
+// A_i = dt / C0_i (Eq. 14 / 21) in FP64, 0 on Dirichlet nodes; optionally also as the float
+// pair (hi, lo) with hi = fl32(A), lo = fl32(A - hi) used by the FP32 form.
+__global__ void k_set_A(int64_t nn, double dt, const double *C0, const uint8_t *isdir, double *A, float2 *A2)
 {
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x)
-        A[g] = isdir[g] ? 0.0 : dt / C0[g];
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
+        const double v = isdir[g] ? 0.0 : dt / C0[g];
+        A[g] = v;
+        if (A2) {
+            const float hi = (float)v;
+            A2[g] = make_float2(hi, (float)(v - (double)hi));
+        }
+    }
 }
 
 // y_e = f_k,e (K0_e x_e) in FP64 with K0_e x = sum_{j != i} c_ij (x_i - x_j); f_k,e from the
@@ -483,9 +490,10 @@ void launch_face_share(int64_t nf, int nv, const int32_t *faces, const double *x
 
 void launch_node_sums(const NodeArgs &a, cudaStream_t st) { k_node_sums<<<nblk(a.nn), 256, 0, st>>>(a); }
 
-void launch_set_A(int64_t nn, double dt, const double *C0, const uint8_t *isdir, double *A, cudaStream_t st)
+void launch_set_A(int64_t nn, double dt, const double *C0, const uint8_t *isdir, double *A, float2 *A2,
+                  cudaStream_t st)
 {
-    k_set_A<<<nblk(nn), 256, 0, st>>>(nn, dt, C0, isdir, A);
+    k_set_A<<<nblk(nn), 256, 0, st>>>(nn, dt, C0, isdir, A, A2);
 }
 
 void launch_apply(int npe, int64_t ne, int64_t nn, const int32_t *gconn, const double *cond64, const int32_t *n2e_ptr,

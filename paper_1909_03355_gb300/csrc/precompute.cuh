@@ -46,7 +46,8 @@ struct EnergyPhys {
 void launch_elem(int npe, const ElemArgs &a, cudaStream_t st);
 void launch_face_share(int64_t nf, int nv, const int32_t *faces, const double *xyz, double *share, cudaStream_t st);
 void launch_node_sums(const NodeArgs &a, cudaStream_t st);
-void launch_set_A(int64_t nn, double dt, const double *C0, const uint8_t *isdir, double *A, cudaStream_t st);
+void launch_set_A(int64_t nn, double dt, const double *C0, const uint8_t *isdir, double *A, float2 *A2,
+                  cudaStream_t st);
 void launch_apply(int npe, int64_t ne, int64_t nn, const int32_t *gconn, const double *cond64, const int32_t *n2e_ptr,
                   const int64_t *n2e, const double *x, const double *Tk, double k_lin, double *Y, double *F,
                   cudaStream_t st);

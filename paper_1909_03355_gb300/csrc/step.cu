@@ -2,11 +2,12 @@
 //
 // One cooperative launch advances the mesh by `nsteps` explicit steps.  Each CTA owns a fixed
 // contiguous run of element tiles.  Per step and tile:
-//   load     T^n of the tile's nodes into shared memory; for halo (shared) nodes T^n is
-//            finished here from T^{n-1} and the fixed-order sum of last step's halo partials
-//            (the owner tile writes it back), so one grid barrier per step suffices;
-//   elements the element stream (pair conductances + tile-local node ids) arrives by TMA bulk
-//            copies (cp.async.bulk) through a ring of shared-memory stages; each thread forms
+//   load     T^n of the tile's owned nodes arrives by one TMA bulk copy (cp.async.bulk) into
+//            shared memory; for halo (shared) nodes T^n is finished here from T^{n-1} and the
+//            fixed-order sum of last step's halo partials (the owner tile writes it back), so
+//            one grid barrier per step suffices;
+//   elements the element stream (pair conductances, tile-local node ids, colours) arrives by
+//            TMA bulk copies through a ring of shared-memory stages; each thread forms
 //            F_e = f_k,e sum_j c_ij (T_i - T_j) for one element (Eq. 20 with the element-mean
 //            conductivity law of Section 4.2.2; theta_e is folded into c_ij) and the CTA adds
 //            the element loads into shared-memory accumulators colour by colour, so the
@@ -18,11 +19,17 @@
 //   halo     write the tile's partial loads of its shared nodes.
 // Then a grid barrier with a deadline.  Every device wait is bounded: on timeout the kernel
 // sets an error bit, drains its own copies in flight and returns.
+//
+// Element chunk layout (CH elements, chunk_bytes = CH (NC rs + 2 npe + 1) + 16):
+//   [NV][CH] vectors of conductances | [CH] id vectors (npe x u16) | [CH] u8 colours |
+//   16-byte header {u8 first colour, u8 last colour, ...}
 #include <cuda_runtime.h>
 
 #include "fedfem_internal.h"
 
 namespace fedfem {
+
+constexpr int MBAR_BYTES = 1536;  // 2 x 63 ring barriers, the node barrier, 63 slot tags
 
 // ------------------------------------------------------------------------------------------
 // PTX helpers (TMA bulk copies, mbarriers, timers)
@@ -74,18 +81,91 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
     }
 }
 
-__device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+// Bounded wait that also gives up (without reporting a timeout) once any part of the grid has
+// raised an error; the error word is polled only while the wait is still pending.
+// Returns true when the phase completed.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, long long timeout_ns,
+                                                   int32_t *err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned spin = 1;; ++spin) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((spin & 63u) == 0) {
+            if (*(volatile int32_t *)err) return false;
+            if ((long long)(global_ns() - t0) > timeout_ns) {
+                atomicOr(err, ERRBIT_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// Wait until stage `slot` holds chunk k: the parity test alone can match the phase of the
+// chunk two generations back when this warp runs ahead of the ring, so the slot's tag (written
+// by the producer before it arms the barrier) must also name chunk k.
+__device__ __forceinline__ bool wait_chunk(uint64_t *bar, volatile int *tag, int k, uint32_t parity,
+                                           long long timeout_ns, int32_t *err)
+{
+    if (mbar_try_wait(bar, parity) && *tag == k) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned spin = 1;; ++spin) {
+        if (mbar_try_wait(bar, parity) && *tag == k) return true;
+        if ((spin & 63u) == 0) {
+            if (*(volatile int32_t *)err) return false;
+            if ((long long)(global_ns() - t0) > timeout_ns) {
+                atomicOr(err, ERRBIT_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                             uint64_t policy)
 {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
         : "memory");
+}
+
+__device__ __forceinline__ void l2_prefetch_bulk(const void *src, uint32_t bytes, uint64_t policy)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(src), "r"(bytes), "l"(policy)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_normal()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 __device__ __forceinline__ void fence_mbar_init()
@@ -99,13 +179,40 @@ __device__ __forceinline__ R ld_cg(const R *p)
     return __ldcg(p);
 }
 
-// Grid-wide barrier on a monotonically increasing counter with a deadline.  Returns false if
-// the deadline passed or another CTA raised an error (every CTA then leaves the kernel).
-__device__ bool grid_sync(unsigned int *bar, unsigned int target, int32_t *err, long long timeout_ns,
-                          bool withhold)
+// Barrier among the NC consumer threads of the CTA (named barrier 1; the producer warp of the
+// element ring never takes part).
+__device__ __forceinline__ void csync(int nc)
 {
-    __shared__ int s_ok;
-    __syncthreads();
+    asm volatile("bar.sync 1, %0;" ::"r"(nc) : "memory");
+}
+
+__device__ __forceinline__ int csync_or(int nc, int pred)
+{
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.s32 p, %2, 0;\n\t"
+        "bar.red.or.pred q, 1, %1, p;\n\t"
+        "selp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(nc), "r"(pred)
+        : "memory");
+    return r;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Grid-wide barrier on a monotonically increasing counter with a deadline, entered by the NC
+// consumer threads of every CTA.  Returns false if the deadline passed or another CTA raised
+// an error (every CTA then leaves the kernel).  `withhold` (test hook) skips this CTA's arrival.
+__device__ bool grid_sync(unsigned int *bar, unsigned int target, int32_t *err, long long timeout_ns,
+                          bool withhold, int nc, int *s_ok)
+{
+    fence_proxy_async_global();  // order this thread's global writes before later TMA reads
+    csync(nc);
     if (threadIdx.x == 0) {
         int ok = 1;
         __threadfence();
@@ -124,13 +231,14 @@ __device__ bool grid_sync(unsigned int *bar, unsigned int target, int32_t *err, 
                 ok = 0;
                 break;
             }
-            __nanosleep(40);
+            __nanosleep(32);
         }
         __threadfence();
-        s_ok = ok;
+        fence_proxy_async_global();
+        *s_ok = ok;
     }
-    __syncthreads();
-    return s_ok != 0;
+    csync(nc);
+    return *s_ok != 0;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -209,7 +317,55 @@ __device__ __forceinline__ void unpack_ids(const uint2 &v, int *id)
 int chunk_bytes_for(int precision, int npe, int CH)
 {
     const int rs = precision == 64 ? 8 : 4;
+    return CH * (n_pairs(npe) * rs + npe * 2 + 1) + 16;
+}
+
+int chunk_colour_offset(int precision, int npe, int CH)
+{
+    const int rs = precision == 64 ? 8 : 4;
     return CH * (n_pairs(npe) * rs + npe * 2);
+}
+
+int chunk_header_offset(int precision, int npe, int CH) { return chunk_bytes_for(precision, npe, CH) - 16; }
+
+// Four consecutive node values (16-byte aligned for float, 32-byte for double).
+template <typename R>
+struct Vec4 {
+    R v[4];
+};
+template <typename R>
+__device__ __forceinline__ Vec4<R> load4(const R *p);
+template <>
+__device__ __forceinline__ Vec4<float> load4<float>(const float *p)
+{
+    const float4 x = __ldcg(reinterpret_cast<const float4 *>(p));
+    return Vec4<float>{{x.x, x.y, x.z, x.w}};
+}
+template <>
+__device__ __forceinline__ Vec4<double> load4<double>(const double *p)
+{
+    const double2 x = __ldcg(reinterpret_cast<const double2 *>(p));
+    const double2 y = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    return Vec4<double>{{x.x, x.y, y.x, y.y}};
+}
+__device__ __forceinline__ void load4d(const double *p, double *o)
+{
+    const double2 x = __ldcg(reinterpret_cast<const double2 *>(p));
+    const double2 y = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    o[0] = x.x, o[1] = x.y, o[2] = y.x, o[3] = y.y;
+}
+template <typename R>
+__device__ __forceinline__ void store4(R *p, const Vec4<R> &v);
+template <>
+__device__ __forceinline__ void store4<float>(float *p, const Vec4<float> &v)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v.v[0], v.v[1], v.v[2], v.v[3]);
+}
+template <>
+__device__ __forceinline__ void store4<double>(double *p, const Vec4<double> &v)
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v.v[0], v.v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v.v[2], v.v[3]);
 }
 
 // Element conduction loads of the element in lane `lane` of a staged chunk (Eq. 20):
@@ -222,6 +378,9 @@ __device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int la
     const typename L::V *cv = reinterpret_cast<const typename L::V *>(blk);
     const typename L::I *iv = reinterpret_cast<const typename L::I *>(blk + (size_t)L::NV * CH * sizeof(typename L::V));
     unpack_ids(iv[lane], id);
+    R c[L::NC];
+#pragma unroll
+    for (int v = 0; v < L::NV; ++v) unpack(cv[v * CH + lane], c + v * L::VW);
     R T[NPE];
     R sum = 0;
 #pragma unroll
@@ -230,9 +389,6 @@ __device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int la
         sum += T[k];
         F[k] = 0;
     }
-    R c[L::NC];
-#pragma unroll
-    for (int v = 0; v < L::NV; ++v) unpack(cv[v * CH + lane], c + v * L::VW);
     int p = 0;
 #pragma unroll
     for (int i = 0; i < NPE; ++i)
@@ -247,58 +403,127 @@ __device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int la
     for (int k = 0; k < NPE; ++k) F[k] *= fk;
 }
 
-// Explicit nodal update (Eq. 16): T' = T + A / f_c(T) (Q - F).
+// Physical constants of the step in the working precision (converted once per launch).
+template <typename R>
+struct Phys {
+    R k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero, T_guard;
+    __device__ explicit Phys(const StepArgs &a)
+        : k_lin((R)a.k_lin), c_lin((R)a.c_lin), h((R)a.h), T_inf((R)a.T_inf), eps_sigma((R)a.eps_sigma),
+          T_amb((R)a.T_amb), T_zero((R)a.T_zero), T_guard((R)a.T_guard)
+    {
+    }
+};
+
+// A_i = dt / C0_i: FP64 in the FP64 form; in the FP32 form the FP64 value is kept as an
+// unevaluated pair of floats (hi + lo, 48 significant bits) and A q is formed with one FMA and
+// rounded once.
+template <typename R>
+struct ACoef;
+template <>
+struct ACoef<float> {
+    float2 v;
+    __device__ __forceinline__ float mul(float q) const { return fmaf(v.x, q, v.y * q); }
+};
+template <>
+struct ACoef<double> {
+    double v;
+    __device__ __forceinline__ double mul(double q) const { return v * q; }
+};
+
+template <typename R>
+__device__ __forceinline__ ACoef<R> load_A(const StepArgs &a, int g);
+template <>
+__device__ __forceinline__ ACoef<float> load_A<float>(const StepArgs &a, int g)
+{
+    return ACoef<float>{__ldg(a.A2 + g)};
+}
+template <>
+__device__ __forceinline__ ACoef<double> load_A<double>(const StepArgs &a, int g)
+{
+    return ACoef<double>{__ldg(a.A + g)};
+}
+
+// Add one element's nodal loads into the tile accumulators.
+template <typename R, int NPE, int SCATTER>
+__device__ __forceinline__ void add_loads(R *Fs, const R *F, const int *id)
+{
+#pragma unroll
+    for (int q = 0; q < NPE; ++q) {
+        if (SCATTER == FEDFEM_SCATTER_ATOMIC)
+            atomicAdd(&Fs[id[q]], F[q]);
+        else
+            Fs[id[q]] += F[q];
+    }
+}
+
+// Explicit nodal update (Eq. 16): T' = T + A / f_c(T) (Q - F), Kahan-compensated in FP32.
 template <typename R, bool KAHAN>
-__device__ __forceinline__ R node_update(R T, float comp, double A, R Q, R F, const StepArgs &a, float &comp_out,
+__device__ __forceinline__ R node_update(R T, float comp, ACoef<R> A, R Q, R F, const Phys<R> &ph, float &comp_out,
                                          int32_t *err)
 {
+    const R fc = (R)1 + ph.c_lin * T;
+    const R inc = A.mul((Q - F) / fc);
     R Tn;
     if constexpr (KAHAN) {
-        const float fc = 1.0f + (float)a.c_lin * T;
-        const float r = (float)Q - (float)F;
-        const float inc = (float)(A * (double)(r / fc));
         const float y = inc - comp;
-        const float t = (float)T + y;
-        comp_out = (t - (float)T) - y;
+        const float t = T + y;
+        comp_out = (t - T) - y;
         Tn = t;
-    } else if constexpr (sizeof(R) == 4) {
-        const float fc = 1.0f + (float)a.c_lin * T;
-        Tn = T + (float)(A * (double)((Q - F) / fc));
-        comp_out = 0.0f;
     } else {
-        const double fc = 1.0 + a.c_lin * (double)T;
-        Tn = T + A / fc * ((double)Q - (double)F);
+        Tn = T + inc;
         comp_out = 0.0f;
     }
-    if (!(fabs((double)Tn) <= a.T_guard)) atomicOr(err, ERRBIT_DIVERGED);
+    if (!(fabs(Tn) <= ph.T_guard)) atomicOr(err, ERRBIT_DIVERGED);
     return Tn;
 }
 
 // Convection + radiation outflow of a boundary node (Eq. 4 and Eq. 7 lumped to the node);
 // the quartic difference is evaluated as (a-b)(a+b)(a^2+b^2).
 template <typename R>
-__device__ __forceinline__ R surface_outflow(R T, R Ac, R Ar, const StepArgs &a)
+__device__ __forceinline__ R surface_outflow(R T, R Ac, R Ar, const Phys<R> &ph)
 {
-    const R u = T - (R)a.T_zero, b = (R)a.T_amb - (R)a.T_zero;
-    const R rad = (R)a.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
-    return Ac * (R)a.h * (T - (R)a.T_inf) + Ar * rad;
+    const R u = T - ph.T_zero, b = ph.T_amb - ph.T_zero;
+    const R rad = ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
+    return Ac * ph.h * (T - ph.T_inf) + Ar * rad;
 }
 
+// T^n of a halo node from T^{n-1}, its compensation and the fixed-order sum of the halo
+// partials of step n-1.
+template <typename R, bool KAHAN>
+__device__ __forceinline__ R finish_halo(const int4 sh, const R *Tprev, const float *cprev, const R *part,
+                                         const R *Qext, const StepArgs &a, const Phys<R> &ph, float &cn)
+{
+    const int cnt = sh.w & 0xFFFF;
+    R F = 0;
+    for (int q = 0; q < cnt; ++q) F += ld_cg(part + sh.z + q);
+    const float cp = KAHAN ? ld_cg(cprev + sh.y) : 0.0f;
+    return node_update<R, KAHAN>(ld_cg(Tprev + sh.y), cp, load_A<R>(a, sh.y), Qext[sh.y], F, ph, cn, a.err);
+}
+
+// Shared-memory layout: [stages][chunk_bytes] ring | MBAR_BYTES of mbarriers (full[S], empty[S],
+// node) | Ts[ts_cap] | Fs[ts_cap].  Threads [0, NC) are consumers; the last warp is the
+// producer of the element ring.  With at most 15 consumer warps + 1 producer warp every SM
+// sub-partition holds at most 4 warps, which leaves 128 registers per thread.
 template <typename R, int NPE, bool KAHAN, int SCATTER>
-__global__ void __launch_bounds__(512) fed_step_kernel(const StepArgs a, int max_local)
+__global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    const int CH = blockDim.x;
+    __shared__ int s_ok;
+    constexpr int ALN = 16 / sizeof(R);  // nodes per 16 bytes
+    const int NC = blockDim.x - 32;      // consumer threads
+    const int NW = NC / 32;              // consumer warps
+    const int CH = a.chunk;              // elements per chunk: 32 or 64
+    const int EPT = CH / 32;             // elements per thread and chunk
     const int tid = threadIdx.x;
+    const int wid = tid >> 5, lane32 = tid & 31;
     const int S = a.stages;
     uint8_t *ring = smem;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + (size_t)S * a.chunk_bytes);
-    R *Ts = reinterpret_cast<R *>(smem + (size_t)S * a.chunk_bytes + 64);
-    R *Fs = Ts + ((max_local + 3) & ~3);
-
-    const R *Qext = reinterpret_cast<const R *>(a.Qext);
-    const R *Ac = reinterpret_cast<const R *>(a.Ac);
-    const R *Ar = reinterpret_cast<const R *>(a.Ar);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * a.chunk_bytes);
+    uint64_t *empty = full + S;
+    uint64_t *tbar = empty + S;
+    volatile int *tag = reinterpret_cast<volatile int *>(tbar + 1);  // chunk index held by each slot
+    R *Ts_raw = reinterpret_cast<R *>(smem + (size_t)S * a.chunk_bytes + MBAR_BYTES);
+    R *Fs = Ts_raw + ts_cap;
 
     const int t0 = blockIdx.x * a.tiles_per_cta;
     const int t1 = min(t0 + a.tiles_per_cta, a.n_tiles);
@@ -307,23 +532,52 @@ __global__ void __launch_bounds__(512) fed_step_kernel(const StepArgs a, int max
     const long long total = (long long)nch * a.nsteps;
 
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&mbar[s], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);  // released by the warp that consumed it
+        }
+        mbar_init(tbar, 1);
+        for (int s2 = 0; s2 < S; ++s2) tag[s2] = -1;
         fence_mbar_init();
         fence_proxy_async_smem();
     }
-    __syncthreads();
-    long long issued = 0;  // meaningful in thread 0 only
-    if (tid == 0) {
-        for (; issued < S && issued < total; ++issued) {
-            const int slot = (int)issued;
-            const int ch = cb + (int)(issued % nch);
-            mbar_arrive_expect_tx(&mbar[slot], (uint32_t)a.chunk_bytes);
-            tma_bulk_g2s(ring + (size_t)slot * a.chunk_bytes, a.chunks + (size_t)ch * a.chunk_bytes,
-                         (uint32_t)a.chunk_bytes, &mbar[slot]);
+    __syncthreads();  // the only CTA-wide barrier (before the roles split)
+
+    // ---------------------------------------------------------------- producer warp
+    if (tid >= NC) {
+        if (tid == NC) {
+            const uint64_t pol = a.l2_stream_policy == 1 ? policy_evict_first() : policy_evict_normal();
+            // 32-bit incremental ring bookkeeping (the counts of one launch fit in 32 bits)
+            const int tot = (int)total;
+            int k = 0, slot = 0, ch = 0;
+            uint32_t ephase = 0;  // parity of the empty-barrier phase awaited for this slot
+            for (; k < tot; ++k) {
+                if (k >= S && !mbar_wait_or_abort(&empty[slot], ephase, a.timeout_ns, a.err)) break;
+                tag[slot] = k;  // consumers check the tag after the parity test
+                mbar_arrive_expect_tx(&full[slot], (uint32_t)a.chunk_bytes);
+                tma_bulk_g2s(ring + (size_t)slot * a.chunk_bytes, a.chunks + (size_t)(cb + ch) * a.chunk_bytes,
+                             (uint32_t)a.chunk_bytes, &full[slot], pol);
+                if (++ch == nch) ch = 0;
+                if (++slot == S) {
+                    slot = 0;
+                    if (k >= S) ephase ^= 1;
+                }
+            }
+            // wait (bounded) until this CTA's last copies have landed before the warp leaves
+            for (int j = k > S ? k - S : 0; j < k; ++j) mbar_wait(&full[j % S], (uint32_t)((j / S) & 1), a.timeout_ns);
         }
+        return;
     }
 
-    long long kc = 0;  // chunks consumed
+    // ---------------------------------------------------------------- consumers
+    const Phys<R> ph(a);
+    const R *Qext = reinterpret_cast<const R *>(a.Qext);
+    const R *Ac = reinterpret_cast<const R *>(a.Ac);
+    const R *Ar = reinterpret_cast<const R *>(a.Ar);
+    const int col_off = a.colour_offset;
+
+    int kc = 0;           // chunks consumed (fits in 32 bits per launch)
+    uint32_t tphase = 0;  // phase of the node-load barrier
     bool ok = true;
     unsigned int bar_target = 0;
     for (int s = 0; s < a.nsteps && ok; ++s) {
@@ -333,104 +587,191 @@ __global__ void __launch_bounds__(512) fed_step_kernel(const StepArgs a, int max
         R *Tn = reinterpret_cast<R *>(a.T[nxt]);
         for (int t = t0; t < t1 && ok; ++t) {
             const TileInfo ti = a.tiles[t];
-            // ---- load T^n
-            for (int l = tid; l < ti.n_owned; l += CH) Ts[l] = ld_cg(Tc + ti.node_begin + l);
-            __syncthreads();
-            for (int q = tid; q < ti.sh_count; q += CH) {
-                const int4 sh = a.sh[ti.sh_begin + q];
-                R v;
-                if (s == 0) {
-                    v = ld_cg(Tc + sh.y);
-                } else {
-                    const int q0 = a.sptr[sh.z], q1 = a.sptr[sh.z + 1];
-                    const R *part = reinterpret_cast<const R *>(a.part[nxt]);
-                    R F = 0;
-                    for (int qq = q0; qq < q1; ++qq) F += ld_cg(part + qq);
-                    const float cp = KAHAN ? ld_cg(a.comp[nxt] + sh.y) : 0.0f;
-                    float cn;
-                    v = node_update<R, KAHAN>(ld_cg(Tn + sh.y), cp, a.A[sh.y], Qext[sh.y], F, a, cn, a.err);
-                    if (sh.w == q0) {
-                        Tc[sh.y] = v;
-                        if (KAHAN) a.comp[cur][sh.y] = cn;
-                    }
+            const int nb = ti.node_begin;
+            const int a0 = nb & ~(ALN - 1);
+            const int a1 = (nb + ti.n_owned + ALN - 1) & ~(ALN - 1);
+            R *Ts = Ts_raw + (nb - a0);
+            // ---- load T^n: owned range by one bulk copy; L2 prefetch of the update operands
+            if (tid == 0) {
+                mbar_arrive_expect_tx(tbar, (uint32_t)((a1 - a0) * sizeof(R)));
+                tma_bulk_g2s(Ts_raw, Tc + a0, (uint32_t)((a1 - a0) * sizeof(R)), tbar, policy_evict_normal());
+                const int i0 = nb & ~3, i1 = (nb + ti.n_interior + 3) & ~3;
+                if (i1 > i0) {
+                    const uint64_t pk = a.l2_stream_policy == 1 ? policy_evict_last() : policy_evict_normal();
+                    if (sizeof(R) == 4)
+                        l2_prefetch_bulk(a.A2 + i0, (uint32_t)((i1 - i0) * 8), pk);
+                    else
+                        l2_prefetch_bulk(a.A + i0, (uint32_t)((i1 - i0) * 8), pk);
+                    l2_prefetch_bulk(Qext + i0, (uint32_t)((i1 - i0) * sizeof(R)), pk);
+                    if (KAHAN) l2_prefetch_bulk(a.comp[cur] + i0, (uint32_t)((i1 - i0) * 4), pk);
                 }
-                Ts[sh.x] = v;
             }
-            for (int l = tid; l < ti.n_local; l += CH) Fs[l] = (R)0;
-            __syncthreads();
-            if (a.rec) {
-                R *rec = reinterpret_cast<R *>(a.rec) + (size_t)s * a.rec_stride;
-                for (int l = tid; l < ti.n_owned; l += CH) rec[ti.node_begin + l] = Ts[l];
+            // halo nodes: values into Fs (free until the element phase) while the bulk copy is
+            // in flight; four entries per thread in flight
+            for (int q0 = tid; q0 < ti.sh_count; q0 += 4 * NC) {
+                int4 sh[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (q0 + u * NC < ti.sh_count) sh[u] = __ldg(a.sh + ti.sh_begin + q0 + u * NC);
+                R v[4];
+                float cn[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (q0 + u * NC >= ti.sh_count) continue;
+                    if (s == 0)
+                        v[u] = ld_cg(Tc + sh[u].y);
+                    else
+                        v[u] = finish_halo<R, KAHAN>(sh[u], Tn, KAHAN ? a.comp[nxt] : nullptr,
+                                                     reinterpret_cast<const R *>(a.part[nxt]), Qext, a, ph, cn[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (q0 + u * NC >= ti.sh_count) continue;
+                    if (s > 0 && (sh[u].w >> 16) == 0) {  // owner writes T^n back
+                        Tc[sh[u].y] = v[u];
+                        if (KAHAN) a.comp[cur][sh[u].y] = cn[u];
+                    }
+                    Fs[sh[u].x] = v[u];
+                }
             }
-            // ---- element loads, accumulated colour by colour
-            for (int c = 0; c < ti.n_chunks; ++c, ++kc) {
-                const int slot = (int)(kc % S);
-                const uint32_t par = (uint32_t)((kc / S) & 1);
-                const int bad = mbar_wait(&mbar[slot], par, a.timeout_ns) ? 0 : 1;
-                if (__syncthreads_or(bad)) {
-                    if (tid == 0) atomicOr(a.err, ERRBIT_TIMEOUT);
+            {
+                const int bad = mbar_wait_or_abort(tbar, tphase, a.timeout_ns, a.err) ? 0 : 1;
+                tphase ^= 1;
+                if (csync_or(NC, bad)) {
                     ok = false;
                     break;
                 }
-                const uint8_t *blk = ring + (size_t)slot * a.chunk_bytes;
-                const int chunk = ti.chunk_begin + c;
-                const int col = a.elem_col[(size_t)chunk * CH + tid];
-                R F[NPE];
-                int id[NPE];
-                element_loads<R, NPE>(blk, CH, tid, Ts, (R)a.k_lin, F, id);
-                if (SCATTER == FEDFEM_SCATTER_ATOMIC) {
-                    if (col != 0xFF)
-#pragma unroll
-                        for (int k = 0; k < NPE; ++k) atomicAdd(&Fs[id[k]], F[k]);
-                    __syncthreads();
-                } else {
-                    const int c_lo = a.chunk_col[2 * chunk], c_hi = a.chunk_col[2 * chunk + 1];
-                    for (int cc = c_lo; cc <= c_hi; ++cc) {
-                        if (col == cc)
-#pragma unroll
-                            for (int k = 0; k < NPE; ++k) Fs[id[k]] += F[k];
-                        __syncthreads();
+            }
+            for (int q = tid; q < ti.sh_count; q += NC) {
+                const int l = a.sh[ti.sh_begin + q].x;
+                Ts[l] = Fs[l];
+            }
+            csync(NC);
+            for (int l = tid; l < ti.n_local; l += NC) Fs[l] = (R)0;
+            if (a.rec) {
+                R *rec = reinterpret_cast<R *>(a.rec) + (size_t)s * a.rec_stride;
+                for (int l = tid; l < ti.n_owned; l += NC) rec[nb + l] = Ts[l];
+            }
+            csync(NC);
+            // ---- element loads (Eq. 20), colour class by colour class.  Every chunk holds one
+            //      colour; chunk u of the tile is consumed by warp (kbase + u) mod NW, which adds
+            //      its elements into the shared-memory accumulators with plain read-modify-writes
+            //      (elements of one colour share no node).  The CTA synchronises only between
+            //      classes, so every node receives its contributions in a fixed order.  The
+            //      atomic variant treats the whole tile as one class and adds with atomics.
+            {
+                const int kbase = kc;
+                const int ncls = SCATTER == FEDFEM_SCATTER_ATOMIC ? 1 : ti.n_colors;
+                for (int c = 0; c < ncls; ++c) {
+                    int u0 = 0, u1 = ti.n_chunks;
+                    if (SCATTER != FEDFEM_SCATTER_ATOMIC) {
+                        u0 = __ldg(a.colptr + ti.col_begin + c);
+                        u1 = __ldg(a.colptr + ti.col_begin + c + 1);
+                    }
+                    int bad = 0;
+                    for (int u = u0 + (wid - (kbase + u0) % NW + NW) % NW; u < u1; u += NW) {
+                        const int k = kbase + u;
+                        const int slot = k % S;
+                        if (!wait_chunk(&full[slot], tag + slot, k, (uint32_t)((k / S) & 1), a.timeout_ns, a.err)) {
+                            bad = 1;
+                            break;
+                        }
+                        const uint8_t *blk = ring + (size_t)slot * a.chunk_bytes;
+                        if (EPT == 1) {
+                            R F[NPE];
+                            int id[NPE];
+                            const int col = blk[col_off + lane32];
+                            element_loads<R, NPE>(blk, CH, lane32, Ts, ph.k_lin, F, id);
+                            __syncwarp();
+                            if (lane32 == 0) mbar_arrive(&empty[slot]);  // stage back to the producer
+                            if (col != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F, id);
+                        } else {
+                            R F0[NPE], F1[NPE];
+                            int id0[NPE], id1[NPE];
+                            const int col0 = blk[col_off + lane32], col1 = blk[col_off + lane32 + 32];
+                            element_loads<R, NPE>(blk, CH, lane32, Ts, ph.k_lin, F0, id0);
+                            element_loads<R, NPE>(blk, CH, lane32 + 32, Ts, ph.k_lin, F1, id1);
+                            __syncwarp();
+                            if (lane32 == 0) mbar_arrive(&empty[slot]);
+                            if (col0 != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F0, id0);
+                            if (col1 != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F1, id1);
+                        }
+                    }
+                    if (csync_or(NC, bad)) {
+                        ok = false;
+                        break;
                     }
                 }
-                // every thread is done with this stage: refill it
-                if (tid == 0 && issued < total) {
-                    const int slot2 = (int)(issued % S);
-                    const int ch = cb + (int)(issued % nch);
-                    fence_proxy_async_smem();
-                    mbar_arrive_expect_tx(&mbar[slot2], (uint32_t)a.chunk_bytes);
-                    tma_bulk_g2s(ring + (size_t)slot2 * a.chunk_bytes, a.chunks + (size_t)ch * a.chunk_bytes,
-                                 (uint32_t)a.chunk_bytes, &mbar[slot2]);
-                    ++issued;
-                }
+                kc += ti.n_chunks;
             }
             if (!ok) break;
             // ---- surface loads of owned boundary nodes
-            for (int q = tid; q < ti.bnd_count; q += CH) {
+            for (int q = tid; q < ti.bnd_count; q += NC) {
                 const int2 b = a.bnd[ti.bnd_begin + q];
-                Fs[b.x] += surface_outflow<R>(Ts[b.x], Ac[b.y], Ar[b.y], a);
+                Fs[b.x] += surface_outflow<R>(Ts[b.x], Ac[b.y], Ar[b.y], ph);
             }
-            __syncthreads();
-            // ---- update interior nodes
-            for (int l = tid; l < ti.n_interior; l += CH) {
-                const int g = ti.node_begin + l;
-                const float cp = KAHAN ? ld_cg(a.comp[cur] + g) : 0.0f;
-                float cn;
-                const R v = node_update<R, KAHAN>(Ts[l], cp, a.A[g], Qext[g], Fs[l], a, cn, a.err);
-                Tn[g] = v;
-                if (KAHAN) a.comp[nxt][g] = cn;
+            csync(NC);
+            // ---- update interior nodes: aligned groups of four consecutive nodes per thread
+            //      (vector loads), two groups in flight; scalar head and tail
+            {
+                const int head = min(ti.n_interior, (4 - (nb & 3)) & 3);
+                const int ngrp = (ti.n_interior - head) >> 2;
+                const int tail0 = head + 4 * ngrp;
+                for (int j0 = tid; j0 < ngrp; j0 += 2 * NC) {
+                    Vec4<R> Qv[2], cpv[2];
+                    ACoef<R> Av[2][4];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int j = j0 + u * NC;
+                        if (j < ngrp) {
+                            const int g = nb + head + 4 * j;
+                            Qv[u] = load4<R>(Qext + g);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) Av[u][e] = load_A<R>(a, g + e);
+                            if (KAHAN) cpv[u] = load4<R>(reinterpret_cast<const R *>(a.comp[cur] + g));
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int j = j0 + u * NC;
+                        if (j < ngrp) {
+                            const int l = head + 4 * j;
+                            const int g = nb + l;
+                            Vec4<R> out, cout;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                float cn;
+                                out.v[e] = node_update<R, KAHAN>(Ts[l + e], KAHAN ? (float)cpv[u].v[e] : 0.0f, Av[u][e],
+                                                                  Qv[u].v[e], Fs[l + e], ph, cn, a.err);
+                                cout.v[e] = (R)cn;
+                            }
+                            store4<R>(Tn + g, out);
+                            if (KAHAN) store4<R>(reinterpret_cast<R *>(a.comp[nxt] + g), cout);
+                        }
+                    }
+                }
+                for (int l = tid; l < ti.n_interior; l += NC) {
+                    if (l >= head && l < tail0) continue;
+                    const int g = nb + l;
+                    float cn;
+                    const R v = node_update<R, KAHAN>(Ts[l], KAHAN ? ld_cg(a.comp[cur] + g) : 0.0f, load_A<R>(a, g),
+                                                      Qext[g], Fs[l], ph, cn, a.err);
+                    Tn[g] = v;
+                    if (KAHAN) a.comp[nxt][g] = cn;
+                }
             }
             // ---- halo partials
             R *part = reinterpret_cast<R *>(a.part[cur]);
-            for (int q = tid; q < ti.sh_count; q += CH) {
+            for (int q = tid; q < ti.sh_count; q += NC) {
                 const int4 sh = a.sh[ti.sh_begin + q];
-                part[sh.w] = Fs[sh.x];
+                part[sh.z + (sh.w >> 16)] = Fs[sh.x];
             }
-            __syncthreads();
+            csync(NC);
         }
         if (!ok) break;
         bar_target += gridDim.x;
         const bool withhold = s == 0 && a.withhold > 0 && (int)blockIdx.x == a.withhold - 1;
-        if (!grid_sync(a.barrier, bar_target, a.err, a.timeout_ns, withhold)) ok = false;
+        if (!grid_sync(a.barrier, bar_target, a.err, a.timeout_ns, withhold, NC, &s_ok)) ok = false;
     }
 
     if (ok) {
@@ -442,30 +783,29 @@ __global__ void __launch_bounds__(512) fed_step_kernel(const StepArgs a, int max
         const R *part = reinterpret_cast<const R *>(a.part[prv]);
         for (int t = t0; t < t1; ++t) {
             const TileInfo ti = a.tiles[t];
-            for (int q = tid; q < ti.sh_count; q += CH) {
+            for (int q = tid; q < ti.sh_count; q += NC) {
                 const int4 sh = a.sh[ti.sh_begin + q];
-                if (sh.x >= ti.n_owned) continue;
-                const int q0 = a.sptr[sh.z], q1 = a.sptr[sh.z + 1];
-                R F = 0;
-                for (int qq = q0; qq < q1; ++qq) F += ld_cg(part + qq);
-                const float cp = KAHAN ? ld_cg(a.comp[prv] + sh.y) : 0.0f;
+                if ((sh.w >> 16) != 0) continue;
                 float cn;
-                const R v = node_update<R, KAHAN>(ld_cg(Tp + sh.y), cp, a.A[sh.y], Qext[sh.y], F, a, cn, a.err);
+                const R v = finish_halo<R, KAHAN>(sh, Tp, KAHAN ? a.comp[prv] : nullptr, part, Qext, a, ph, cn);
                 Tc[sh.y] = v;
                 if (KAHAN) a.comp[cur][sh.y] = cn;
             }
         }
-    } else if (tid == 0) {
-        // drain this CTA's copies in flight before leaving (bounded)
-        for (long long k = kc; k < issued; ++k) mbar_wait(&mbar[k % S], (uint32_t)((k / S) & 1), a.timeout_ns);
     }
 }
 
-size_t step_smem_bytes(int precision, int npe, int block, int stages, int max_local)
+int step_ts_cap(int precision, int max_local)
+{
+    const int aln = precision == 64 ? 2 : 4;
+    return ((max_local + 2 * aln) + 3) & ~3;
+}
+
+size_t step_smem_bytes(int precision, int npe, int chunk, int stages, int max_local)
 {
     const size_t rs = precision == 64 ? 8 : 4;
-    const size_t nodes = (size_t)((max_local + 3) & ~3) * rs;
-    return (size_t)stages * chunk_bytes_for(precision, npe, block) + 64 + 2 * nodes;
+    return (size_t)stages * chunk_bytes_for(precision, npe, chunk) + MBAR_BYTES +
+           2 * (size_t)step_ts_cap(precision, max_local) * rs;
 }
 
 template <typename R, int NPE, bool KAHAN, int SCATTER>
@@ -497,23 +837,20 @@ int step_max_blocks_per_sm(int precision, int kahan, int npe, int block, size_t 
     void *k = select_kernel(precision, kahan, npe, FEDFEM_SCATTER_COLOR);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block + 32, smem) != cudaSuccess) return 0;
     return nb;
 }
 
 cudaError_t launch_step(const StepArgs &a, int precision, int kahan, int npe, int grid, int block, size_t smem,
-                        cudaStream_t st)
+                        int ts_cap, cudaStream_t st)
 {
     void *k = select_kernel(precision, kahan, npe, a.scatter);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int max_local = 0;
-    // max_local is recovered from the shared-memory size by the caller's plan
-    const size_t rs = precision == 64 ? 8 : 4;
-    max_local = (int)((smem - (size_t)a.stages * a.chunk_bytes - 64) / (2 * rs));
     StepArgs args = a;
-    void *params[] = {(void *)&args, (void *)&max_local};
-    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(block), params, smem, st);
+    void *params[] = {(void *)&args, (void *)&ts_cap};
+    // block consumer threads plus one producer warp for the element ring
+    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(block + 32), params, smem, st);
 }
 
 }  // namespace fedfem

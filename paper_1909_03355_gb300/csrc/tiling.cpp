@@ -197,19 +197,39 @@ std::string build_tiling(int npe, int64_t ne, int64_t nn, const int32_t *conn, c
         std::iota(perm.begin(), perm.end(), 0);
         std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) { return col[a] < col[b]; });
 
+        // chunks: every colour class starts a new chunk (padding slots have colour 0xFF), so
+        // each chunk holds elements of a single colour
+        int ncol = 0;
+        for (int64_t p = 0; p < m; ++p) ncol = std::max(ncol, (int)col[p] + 1);
+        std::vector<int64_t> cnt_c(ncol, 0);
+        for (int64_t p = 0; p < m; ++p) ++cnt_c[col[p]];
         ti.chunk_begin = chunk;
-        ti.n_chunks = (int32_t)((m + CH - 1) / CH);
-        chunk += ti.n_chunks;
+        ti.col_begin = (int32_t)T.colptr.size();
+        ti.n_colors = ncol;
+        int32_t nchk = 0;
+        for (int c = 0; c < ncol; ++c) {
+            T.colptr.push_back(nchk);
+            nchk += (int32_t)((cnt_c[c] + CH - 1) / CH);
+        }
+        T.colptr.push_back(nchk);
+        ti.n_chunks = nchk;
+        chunk += nchk;
         const size_t slots = (size_t)chunk * CH;
         T.elem_of_slot.resize(slots, -1);
         T.elem_col.resize(slots, 0xFF);
         T.lconn.resize(slots * npe, 0);
-        for (int64_t p = 0; p < m; ++p) {
-            const int64_t e = order[tb[t] + perm[p]];
-            const int64_t s = (int64_t)ti.chunk_begin * CH + p;
-            T.elem_of_slot[s] = (int32_t)e;
-            T.elem_col[s] = col[perm[p]];
-            for (int k = 0; k < npe; ++k) T.lconn[s * npe + k] = (uint16_t)loc[conn[npe * e + k]];
+        {
+            int64_t p = 0;
+            for (int c = 0; c < ncol; ++c) {
+                const int64_t base = ((int64_t)ti.chunk_begin + T.colptr[ti.col_begin + c]) * CH;
+                for (int64_t i = 0; i < cnt_c[c]; ++i, ++p) {
+                    const int64_t e = order[tb[t] + perm[p]];
+                    const int64_t s = base + i;
+                    T.elem_of_slot[s] = (int32_t)e;
+                    T.elem_col[s] = col[perm[p]];
+                    for (int k = 0; k < npe; ++k) T.lconn[s * npe + k] = (uint16_t)loc[conn[npe * e + k]];
+                }
+            }
         }
 
         // shared entries: owned-shared then ghosts
@@ -220,7 +240,7 @@ std::string build_tiling(int npe, int64_t ne, int64_t nn, const int32_t *conn, c
             const int32_t sid = sid_of_new[g];
             int32_t rank = 0;
             while (ntl[ntp[o] + rank] != t) ++rank;
-            T.sh.push_back(make_int4(l, g, sid, T.sptr[sid] + rank));
+            T.sh.push_back(make_int4(l, g, T.sptr[sid], (T.sptr[sid + 1] - T.sptr[sid]) | (rank << 16)));
         }
         ti.sh_count = (int32_t)T.sh.size() - ti.sh_begin;
 
@@ -290,10 +310,12 @@ std::string validate_tiling(const Tiling &T)
         if (ti.sh_count != ti.n_local - ti.n_interior) return "halo count";
         for (int q = 0; q < ti.sh_count; ++q) {
             const int4 h = T.sh[ti.sh_begin + q];
-            if (h.x < ti.n_interior || h.x >= ti.n_local || h.y < 0 || h.y >= T.nn || h.z < 0 ||
-                h.z + 1 >= (int64_t)T.sptr.size() || h.w < T.sptr[h.z] || h.w >= T.sptr[h.z + 1] || h.w >= n_slots)
+            const int cnt = h.w & 0xFFFF, rank = h.w >> 16;
+            if (h.x < ti.n_interior || h.x >= ti.n_local || h.y < 0 || h.y >= T.nn || cnt < 2 || rank >= cnt ||
+                h.z < 0 || h.z + (int64_t)cnt > n_slots)
                 return "halo entry out of range";
-            if (h.x < ti.n_owned && (h.y != ti.node_begin + h.x || h.w != T.sptr[h.z])) return "owned halo entry";
+            if (h.x < ti.n_owned && (h.y != ti.node_begin + h.x || rank != 0)) return "owned halo entry";
+            if (h.x >= ti.n_owned && rank == 0) return "ghost entry marked as owner";
         }
         if (ti.bnd_begin < 0 || ti.bnd_begin + (int64_t)ti.bnd_count > (int64_t)T.bnd.size()) return "boundary range";
         for (int q = 0; q < ti.bnd_count; ++q) {
@@ -302,6 +324,18 @@ std::string validate_tiling(const Tiling &T)
         }
     }
     if (chunks != T.n_chunks) return "chunk count";
+    for (int t = 0; t < T.n_tiles; ++t) {
+        const TileInfo &ti = T.tiles[t];
+        if (ti.n_colors < 1 || ti.col_begin < 0 || ti.col_begin + ti.n_colors >= (int)T.colptr.size() ||
+            T.colptr[ti.col_begin] != 0 || T.colptr[ti.col_begin + ti.n_colors] != ti.n_chunks)
+            return "colour boundaries";
+        for (int c = 0; c < ti.n_colors; ++c) {
+            const int u0 = T.colptr[ti.col_begin + c], u1 = T.colptr[ti.col_begin + c + 1];
+            if (u1 <= u0) return "empty colour class";
+            for (int64_t sl = ((int64_t)ti.chunk_begin + u0) * T.CH; sl < ((int64_t)ti.chunk_begin + u1) * T.CH; ++sl)
+                if (T.elem_col[sl] != c && T.elem_col[sl] != 0xFF) return "chunk with two colours";
+        }
+    }
     if (T.elem_col.size() != (size_t)T.n_chunks * T.CH || T.chunk_col.size() != (size_t)T.n_chunks * 2)
         return "colour arrays";
     for (int64_t e = 0; e < T.ne; ++e)

@@ -57,7 +57,7 @@ def problem_structs(p, keep):
 
 
 def make_options(precision=32, kahan=True, scatter=0, block=0, steps_per_launch=0, ctas_per_sm=0,
-                 tiles_per_cta=0, stages=0, barrier_timeout_s=1.0, T_guard=1e6, stream=None, device=-1,
+                 tiles_per_cta=0, stages=0, chunk=0, l2_policy=0, barrier_timeout_s=1.0, T_guard=1e6, stream=None, device=-1,
                  verbose=False, debug_withhold_barrier=0):
     L = capi.load()
     o = capi.Options()
@@ -70,6 +70,8 @@ def make_options(precision=32, kahan=True, scatter=0, block=0, steps_per_launch=
     o.ctas_per_sm = ctas_per_sm
     o.tiles_per_cta = tiles_per_cta
     o.stages = stages
+    o.chunk = chunk
+    o.l2_policy = l2_policy
     o.barrier_timeout_s = barrier_timeout_s
     o.T_guard = T_guard
     o.stream = stream
