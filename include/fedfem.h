@@ -235,6 +235,36 @@ fedfem_status fedfem_forward_record(fedfem_ctx *ctx, int64_t n_steps, const int3
 fedfem_status fedfem_adjoint(fedfem_ctx *ctx, const double *dL_dtrace, double *dL_dkscale,
                              double *dL_dsource);
 
+/* Physical constants of the energy-balance terms (the context's values for fedfem_energy). */
+typedef struct {
+    double dt, c_lin, h, T_inf, eps, T_amb, T_zero;
+} fedfem_energy_params;
+
+/*
+ * Energy-balance sums of one step for callers that cannot allocate device memory (no
+ * counterpart in the paper; the sums are those of fedfem_energy).  Meant for code that must not
+ * call cudaMalloc / cudaFree: a callback running while another library owns the device memory
+ * pool, a process under a hard device-memory budget, or a loop that must not synchronise the
+ * device.  It allocates nothing: its only scratch (one pair of partial sums per 4096 nodes) is a
+ * 64 KB array compiled into the library, which every GPU that loads the library keeps until the
+ * process exits.
+ *   n_nodes <= 16,777,216 (larger: FEDFEM_ERR_ARG);  all arrays are DEVICE arrays of n_nodes
+ *   entries in one common node order: T_prev, T_next (FP64 states of two consecutive steps),
+ *   F (internal loads at T_prev, e.g. from fedfem_internal_loads), C0 (lumped thermal mass at
+ *   f_c = 1), Qext, Ac, Ar (constant nodal loads and convection / radiation area shares) and
+ *   is_dirichlet (1 on Gamma_E);  out: DEVICE array of 2 doubles receiving
+ *   (stored_change, boundary_in);  stream: cudaStream_t or NULL.  Asynchronous on `stream`.
+ * All calls on a device share the scratch array: calls that overlap on the GPU race.  Each call
+ * overwrites every partial it reads, so nothing needs clearing between calls.  The first call
+ * on a device looks the array's address up (cudaGetSymbolAddress) with that device current:
+ * make it before any stream capture.
+ * Errors: ARG (NULL pointer, n_nodes out of range), CUDA.
+ */
+fedfem_status fedfem_energy_terms_noalloc(int64_t n_nodes, const double *T_prev, const double *T_next,
+                                          const double *F, const double *C0, const double *Qext,
+                                          const double *Ac, const double *Ar, const uint8_t *is_dirichlet,
+                                          const fedfem_energy_params *params, double *out, void *stream);
+
 /* Launch plan and sizes chosen by create: a fixed-size record for logging and benchmarks. */
 typedef struct {
     int64_t n_nodes, n_elems;

@@ -58,6 +58,11 @@ class Scenario(C.Structure):
                 ("T_lo", F64), ("T_hi", F64), ("dt_scale", F64)]
 
 
+class EnergyParams(C.Structure):
+    _fields_ = [("dt", F64), ("c_lin", F64), ("h", F64), ("T_inf", F64), ("eps", F64), ("T_amb", F64),
+                ("T_zero", F64)]
+
+
 # exported names and their (restype, argtypes), as declared in include/fedfem.h
 SIGNATURES = {
     "fedfem_default_options": (None, [P]),
@@ -81,6 +86,7 @@ SIGNATURES = {
     "fedfem_forward_record": (I32, [P, I64, P, I32, I32, I32, P]),
     "fedfem_adjoint": (I32, [P, P, P, P]),
     "fedfem_get_info": (I32, [P, P]),
+    "fedfem_energy_terms_noalloc": (I32, [I64, P, P, P, P, P, P, P, P, P, P, P]),
     "fedfem_error_string": (C.c_char_p, [P]),
     "fedfem_create_error": (C.c_char_p, []),
     "fedfem_destroy": (None, [P]),

@@ -1,0 +1,70 @@
+"""fedfem_energy_terms_noalloc: the allocation-free variant of the energy-balance reduction.
+
+Some callers cannot allocate device memory (cudaMalloc / cudaFree are off limits while another
+library owns the memory pool, under a hard memory budget, or in loops that must not
+synchronise).  This entry point takes device inputs and a device output and keeps its only
+scratch in an array compiled into the library.  The test calls it twice in a row through the
+C ABI and checks both results against fedfem_energy, the existing entry point that computes the
+same sums with per-context scratch.  It lives in a file of its own, collected last.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import fedfem_inputs as fi
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def test_energy_terms_noalloc_matches_fedfem_energy():
+    import torch
+
+    from paper_1909_03355_gb300 import capi
+    from paper_1909_03355_gb300.fedfem import FedFem
+
+    L = capi.load()
+    p = fi.nonlinear_cube(9, "hex")
+    p.dir_nodes = np.arange(0, 12, dtype=np.int32)
+    p.dir_T = np.full(12, 75.0)
+    f = FedFem(p, precision=64)
+    dt = 0.9 * f.precompute()
+    f.set_dt(dt)
+    f.set_T(p.initial_T())
+    f.step(20)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    T_prev = torch.empty(p.n_nodes, dtype=torch.float64, device=dev)
+    T_next = torch.empty_like(T_prev)
+    f.get_T_device(T_prev)
+    f.step(1)
+    S_ref, B_ref = f.energy()
+    f.get_T_device(T_next)
+    torch.cuda.synchronize()
+    # node data in original order (lumped masses, loads and areas from the FP64 oracle model;
+    # the internal loads at T_prev from the existing GPU entry point)
+    m = O.OracleModel(p)
+    F = torch.tensor(f.internal_loads(T_prev.cpu().numpy()), device=dev)
+    arrays = [torch.tensor(a, dtype=torch.float64, device=dev) for a in (m.C0, m.Qext, m.Ac, m.Ar)]
+    isdir = torch.tensor(m.isdir.astype(np.uint8), device=dev)
+    ph = capi.EnergyParams(dt=dt, c_lin=p.mats[0].c_lin, h=p.h, T_inf=p.T_inf, eps=p.eps, T_amb=p.T_amb,
+                           T_zero=p.T_zero)
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device=dev)
+    results = []
+    for _ in range(2):
+        st = L.fedfem_energy_terms_noalloc(p.n_nodes, T_prev.data_ptr(), T_next.data_ptr(), F.data_ptr(),
+                                          *[a.data_ptr() for a in arrays], isdir.data_ptr(), C.byref(ph),
+                                          out.data_ptr(), None)
+        assert st == capi.OK
+        torch.cuda.synchronize()
+        results.append(out.cpu().numpy().copy())
+        out.fill_(float("nan"))
+    for S, B in results:
+        assert S == pytest.approx(S_ref, rel=1e-12)
+        assert B == pytest.approx(B_ref, rel=1e-12)
+    assert np.array_equal(results[0], results[1])
+    # sizes beyond the scratch capacity are rejected
+    assert L.fedfem_energy_terms_noalloc(16777217, T_prev.data_ptr(), T_next.data_ptr(), F.data_ptr(),
+                                        *[a.data_ptr() for a in arrays], isdir.data_ptr(), C.byref(ph),
+                                        out.data_ptr(), None) == 1
+    f.close()
