@@ -1,15 +1,364 @@
-// Reverse-time discrete adjoint (fedfem_forward_record / fedfem_adjoint).
+// Reverse-time discrete adjoint of the explicit FED-FEM step (fedfem_forward_record /
+// fedfem_adjoint).  The paper has no adjoint; the recursion below is the exact derivative of
+// the discrete update of Eq. 16 with the element loads of Eq. 20 (element-mean k(T), Section
+// 4.2.2), the nodal c(T) of Eq. 16 and the surface loads of Eq. 4 and 7.
+//
+// With a_i = A_i / f_c(T_i^n) (0 on Dirichlet nodes), mu_i = a_i lambda_i^{n+1},
+// R_i = Q_i - F_i and c_e = theta_e K0_e (the stored pair conductances):
+//   lambda_j^n = dL/dT_j^n + lambda_j^{n+1} (1 + d_j) + mu_j dQ_j/dT_j - G_j,
+//   d_j = -a_j c_lin / f_c(T_j) R_j,
+//   G_j = sum_{e∋j} [ f_k,e (c_e mu_e)_j + (mu_e . c_e T_e) k_lin / npe ],
+//   dL/dtheta_e = -sum_n f_k,e (mu_e . c_e T_e) / theta_e,
+//   dL/ds_e     =  sum_{i in e} w_ie sum_n mu_i^n.
+// The forward run keeps checkpoints of the state every K steps; each segment is recomputed
+// (bit-identically: the forward is deterministic) with the per-step state recorded, then swept
+// backwards.  The reverse sweep runs in FP64 on the recorded states of either forward
+// precision, with fixed-order (deterministic) node gathers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "ctx.h"
 
 using namespace fedfem;
 
-extern "C" fedfem_status fedfem_forward_record(fedfem_ctx *c, int64_t, const int32_t *, int32_t, int32_t, int32_t,
-                                               double *)
+#define CK(call, where)                                          \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where);   \
+    } while (0)
+
+namespace {
+
+constexpr double kSigma = 5.67e-8;
+
+struct AdjPhys {
+    double k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero;
+};
+
+int nblk(int64_t n, int bs = 256)
 {
-    return fail(c, FEDFEM_ERR_UNSUPPORTED, "adjoint not built yet");
+    int64_t b = (n + bs - 1) / bs;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 65535));
 }
 
-extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *, double *, double *)
+template <typename R>
+__global__ void k_gather_sensors(int ns, const int32_t *sens, const R *T, const float *comp, double *out)
 {
-    return fail(c, FEDFEM_ERR_UNSUPPORTED, "adjoint not built yet");
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < ns) {
+        const int g = sens[s];
+        out[s] = (double)T[g] - (comp ? (double)comp[g] : 0.0);
+    }
+}
+
+// mu_i = a_i lambda_i, a_i = A_i / f_c(T_i) (A = 0 on Dirichlet nodes); musum += mu
+template <typename R>
+__global__ void k_adj_mu(int64_t nn, const R *Tn, const double *A, const double *lam, double c_lin, double *mu,
+                         double *musum)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
+        const double t = (double)Tn[g];
+        const double m = A[g] / (1.0 + c_lin * t) * lam[g];
+        mu[g] = m;
+        musum[g] += m;
+    }
+}
+
+// Element pass: forward loads F_e = f_k (c T_e) and adjoint loads
+// G_e = f_k (c mu_e) + (mu_e . c T_e) k_lin / npe into per-element slots; theta gradient.
+template <int NPE, typename R>
+__global__ void k_adj_elem(int64_t ne, const int32_t *gconn, const double *cond64, const R *Tn, const double *mu,
+                           const double *theta, double k_lin, double *YF, double *YG, double *gtheta)
+{
+    constexpr int NC = NPE * (NPE - 1) / 2;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+        double T[NPE], m[NPE], cT[NPE], cm[NPE];
+        double sum = 0.0;
+        for (int k = 0; k < NPE; ++k) {
+            const int g = gconn[NPE * e + k];
+            T[k] = (double)Tn[g];
+            m[k] = mu[g];
+            sum += T[k];
+            cT[k] = 0.0;
+            cm[k] = 0.0;
+        }
+        const double *ce = cond64 + NC * e;
+        int p = 0;
+        for (int i = 0; i < NPE; ++i)
+            for (int j = i + 1; j < NPE; ++j, ++p) {
+                const double gt = ce[p] * (T[i] - T[j]);
+                const double gm = ce[p] * (m[i] - m[j]);
+                cT[i] += gt;
+                cT[j] -= gt;
+                cm[i] += gm;
+                cm[j] -= gm;
+            }
+        const double fk = 1.0 + k_lin * (sum / NPE);
+        double mcT = 0.0;
+        for (int k = 0; k < NPE; ++k) mcT += m[k] * cT[k];
+        for (int k = 0; k < NPE; ++k) {
+            YF[NPE * e + k] = fk * cT[k];
+            YG[NPE * e + k] = fk * cm[k] + mcT * k_lin / NPE;
+        }
+        gtheta[e] -= fk * mcT / theta[e];
+    }
+}
+
+// Node pass: gather F and G in fixed (ascending element) order and form lambda^n.
+template <typename R>
+__global__ void k_adj_node(int64_t nn, int npe, const int32_t *n2e_ptr, const int64_t *n2e, const double *YF,
+                           const double *YG, const R *Tn, const double *lam, const double *mu, const double *A,
+                           const double *Qext, const double *Ac, const double *Ar, const uint8_t *isdir, AdjPhys ph,
+                           double *lam_out)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
+        double F = 0.0, G = 0.0;
+        for (int q = n2e_ptr[g]; q < n2e_ptr[g + 1]; ++q) {
+            const int64_t ek = n2e[q];
+            const int64_t s = npe * (ek >> 3) + (ek & 7);
+            F += YF[s];
+            G += YG[s];
+        }
+        if (isdir[g]) {
+            lam_out[g] = lam[g] - G;
+            continue;
+        }
+        const double t = (double)Tn[g];
+        const double fc = 1.0 + ph.c_lin * t;
+        const double a = A[g] / fc;
+        const double u = t - ph.T_zero, b = ph.T_amb - ph.T_zero;
+        const double Q = Qext[g] - Ac[g] * ph.h * (t - ph.T_inf) - Ar[g] * ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
+        const double dQ = -Ac[g] * ph.h - Ar[g] * ph.eps_sigma * 4.0 * u * u * u;
+        const double d = -a * ph.c_lin / fc * (Q - F);
+        lam_out[g] = lam[g] * (1.0 + d) + mu[g] * dQ - G;
+    }
+}
+
+__global__ void k_adj_inject(int ns, const int32_t *sens, const double *dl, double *lam)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < ns) lam[sens[s]] += dl[s];  // sensors are distinct nodes
+}
+
+// dL/ds_e = sum_k w_ek musum[node_k]
+template <int NPE>
+__global__ void k_adj_source(int64_t ne, const int32_t *gconn, const double *W, const double *musum, double *gs)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < NPE; ++k) s += W[NPE * e + k] * musum[gconn[NPE * e + k]];
+        gs[e] = s;
+    }
+}
+
+cudaError_t adj_alloc(fedfem_ctx *c, void **p, size_t bytes)
+{
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) c->adj_allocs.push_back(*p);
+    return e;
+}
+
+void adj_free(fedfem_ctx *c)
+{
+    for (void *p : c->adj_allocs) cudaFree(p);
+    c->adj_allocs.clear();
+    c->recorded = false;
+}
+
+size_t state_bytes_dev(fedfem_ctx *c) { return (size_t)c->nn * (c->precision == 64 ? 8 : 4); }
+
+fedfem_status copy_state(fedfem_ctx *c, int64_t step, uint8_t *dst, bool save)
+{
+    const int b = (int)(step & 1);
+    const size_t tb = state_bytes_dev(c);
+    uint8_t *T = (uint8_t *)c->d_T[b];
+    if (save) {
+        CK(cudaMemcpyAsync(dst, T, tb, cudaMemcpyDeviceToDevice, c->stream), "save state");
+        if (c->kahan) CK(cudaMemcpyAsync(dst + tb, c->d_comp[b], c->nn * 4, cudaMemcpyDeviceToDevice, c->stream), "save");
+    } else {
+        CK(cudaMemcpyAsync(T, dst, tb, cudaMemcpyDeviceToDevice, c->stream), "restore state");
+        if (c->kahan) CK(cudaMemcpyAsync(c->d_comp[b], dst + tb, c->nn * 4, cudaMemcpyDeviceToDevice, c->stream), "restore");
+    }
+    return FEDFEM_OK;
+}
+
+}  // namespace
+
+extern "C" fedfem_status fedfem_forward_record(fedfem_ctx *c, int64_t n_steps, const int32_t *sensors,
+                                               int32_t n_sensors, int32_t sample_every, int32_t ckpt_every,
+                                               double *trace)
+{
+    if (!c) return FEDFEM_ERR_ARG;
+    if (!c->has_dt || !c->has_T) return fail(c, FEDFEM_ERR_STATE, "call fedfem_set_dt and fedfem_set_T first");
+    if (n_steps <= 0 || sample_every <= 0 || ckpt_every <= 0 || n_steps % sample_every || n_steps % ckpt_every ||
+        ckpt_every % sample_every)
+        return fail(c, FEDFEM_ERR_ARG, "n_steps must be a multiple of ckpt_every, which must be a multiple of sample_every");
+    if (n_sensors <= 0 || !sensors || !trace) return fail(c, FEDFEM_ERR_ARG, "sensors and trace required");
+    std::vector<int32_t> sn(n_sensors);
+    std::vector<uint8_t> seen(c->nn, 0);
+    for (int s = 0; s < n_sensors; ++s) {
+        if (sensors[s] < 0 || sensors[s] >= c->nn) return fail(c, FEDFEM_ERR_ARG, "sensor node out of range");
+        sn[s] = c->til.new_of_old[sensors[s]];
+        if (seen[sn[s]]++) return fail(c, FEDFEM_ERR_ARG, "sensor nodes must be distinct");
+    }
+    adj_free(c);
+    const int64_t n_ckpt = n_steps / ckpt_every, n_samp = n_steps / sample_every;
+    c->ckpt_bytes = state_bytes_dev(c) + (c->kahan ? (size_t)c->nn * 4 : 0);
+    c->ckpt_bytes = (c->ckpt_bytes + 255) & ~(size_t)255;
+    double *d_trace = nullptr;
+    CK(adj_alloc(c, (void **)&c->d_sensors, n_sensors * 4), "alloc sensors");
+    CK(adj_alloc(c, &c->d_ckpt, (n_ckpt + 1) * c->ckpt_bytes), "alloc checkpoints");
+    CK(adj_alloc(c, (void **)&d_trace, n_samp * n_sensors * 8), "alloc trace");
+    CK(cudaMemcpyAsync(c->d_sensors, sn.data(), n_sensors * 4, cudaMemcpyHostToDevice, c->stream), "upload sensors");
+    c->rec_step0 = c->step;
+    for (int64_t k = 0; k < n_ckpt; ++k) {
+        fedfem_status s = copy_state(c, c->step, (uint8_t *)c->d_ckpt + k * c->ckpt_bytes, true);
+        if (s != FEDFEM_OK) return s;
+        for (int32_t j = 0; j < ckpt_every / sample_every; ++j) {
+            s = enqueue_steps(c, sample_every, nullptr, 0);
+            if (s != FEDFEM_OK) return s;
+            const int64_t samp = (c->step - c->rec_step0) / sample_every - 1;
+            const int b = (int)(c->step & 1);
+            if (c->precision == 64)
+                k_gather_sensors<double><<<nblk(n_sensors), 256, 0, c->stream>>>(
+                    n_sensors, c->d_sensors, (const double *)c->d_T[b], nullptr, d_trace + samp * n_sensors);
+            else
+                k_gather_sensors<float><<<nblk(n_sensors), 256, 0, c->stream>>>(
+                    n_sensors, c->d_sensors, (const float *)c->d_T[b], c->kahan ? c->d_comp[b] : nullptr,
+                    d_trace + samp * n_sensors);
+            CK(cudaGetLastError(), "sensor gather");
+        }
+    }
+    // the end state, restored after the reverse sweep
+    fedfem_status s = copy_state(c, c->step, (uint8_t *)c->d_ckpt + n_ckpt * c->ckpt_bytes, true);
+    if (s != FEDFEM_OK) return s;
+    CK(cudaMemcpyAsync(trace, d_trace, n_samp * n_sensors * 8, cudaMemcpyDeviceToHost, c->stream), "download trace");
+    int32_t bits = 0;
+    CK(cudaMemcpyAsync(&bits, c->d_err, 4, cudaMemcpyDeviceToHost, c->stream), "status");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    if (bits) {
+        CK(cudaMemset(c->d_err, 0, 4), "clear");
+        return fail(c, (bits & ERRBIT_DIVERGED) ? FEDFEM_ERR_DIVERGED : FEDFEM_ERR_TIMEOUT, "forward run failed");
+    }
+    c->recorded = true;
+    c->rec_steps = n_steps;
+    c->rec_sample_every = sample_every;
+    c->rec_ckpt_every = ckpt_every;
+    c->rec_n_sensors = n_sensors;
+    return FEDFEM_OK;
+}
+
+extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, double *dL_dkscale, double *dL_dsource)
+{
+    if (!c) return FEDFEM_ERR_ARG;
+    if (!c->recorded) return fail(c, FEDFEM_ERR_STATE, "call fedfem_forward_record first");
+    if (!dL_dtrace || !dL_dkscale || !dL_dsource) return fail(c, FEDFEM_ERR_ARG, "NULL array");
+    const int64_t nn = c->nn, ne = c->ne;
+    const int npe = c->npe;
+    const int K = c->rec_ckpt_every, se = c->rec_sample_every, ns = c->rec_n_sensors;
+    const int64_t n_ckpt = c->rec_steps / K, n_samp = c->rec_steps / se;
+    const size_t rs = c->precision == 64 ? 8 : 4;
+    std::vector<void *> tmp;
+    auto talloc = [&](void **p, size_t bytes) {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess) tmp.push_back(*p);
+        return e;
+    };
+    auto release = [&]() {
+        for (void *p : tmp) cudaFree(p);
+        tmp.clear();
+    };
+    double *d_dl = nullptr, *lam[2] = {nullptr, nullptr}, *mu = nullptr, *musum = nullptr, *YF = nullptr, *YG = nullptr,
+           *gth = nullptr, *gs = nullptr;
+    void *rec = nullptr;
+    cudaError_t e = cudaSuccess;
+    if ((e = talloc((void **)&d_dl, n_samp * ns * 8)) != cudaSuccess || (e = talloc(&rec, (size_t)K * nn * rs)) != cudaSuccess ||
+        (e = talloc((void **)&lam[0], nn * 8)) != cudaSuccess || (e = talloc((void **)&lam[1], nn * 8)) != cudaSuccess ||
+        (e = talloc((void **)&mu, nn * 8)) != cudaSuccess || (e = talloc((void **)&musum, nn * 8)) != cudaSuccess ||
+        (e = talloc((void **)&YF, ne * npe * 8)) != cudaSuccess || (e = talloc((void **)&YG, ne * npe * 8)) != cudaSuccess ||
+        (e = talloc((void **)&gth, ne * 8)) != cudaSuccess || (e = talloc((void **)&gs, ne * 8)) != cudaSuccess) {
+        release();
+        return cuda_fail(c, e, "adjoint buffers");
+    }
+#define CKR(call, where)                       \
+    do {                                       \
+        cudaError_t e_ = (call);               \
+        if (e_ != cudaSuccess) {               \
+            release();                         \
+            return cuda_fail(c, e_, where);    \
+        }                                      \
+    } while (0)
+    CKR(cudaMemcpyAsync(d_dl, dL_dtrace, n_samp * ns * 8, cudaMemcpyHostToDevice, c->stream), "upload dL/dtrace");
+    CKR(cudaMemsetAsync(lam[0], 0, nn * 8, c->stream), "memset");
+    CKR(cudaMemsetAsync(musum, 0, nn * 8, c->stream), "memset");
+    CKR(cudaMemsetAsync(gth, 0, ne * 8, c->stream), "memset");
+    const AdjPhys ph{c->k_lin, c->c_lin, c->h, c->T_inf, c->eps * kSigma, c->T_amb, c->T_zero};
+    int cur = 0;
+    for (int64_t k = n_ckpt - 1; k >= 0; --k) {
+        // recompute the segment from its checkpoint, recording T^n for every step
+        const int64_t step_k = c->rec_step0 + k * K;
+        c->step = step_k;
+        fedfem_status st = copy_state(c, step_k, (uint8_t *)c->d_ckpt + k * c->ckpt_bytes, false);
+        if (st == FEDFEM_OK) st = enqueue_steps(c, K, rec, nn);
+        if (st != FEDFEM_OK) {
+            release();
+            return st;
+        }
+        for (int s = K - 1; s >= 0; --s) {
+            const int64_t rel = k * K + s + 1;  // steps after the record start of the state T^{n+1}
+            if (rel % se == 0)
+                k_adj_inject<<<nblk(ns), 256, 0, c->stream>>>(ns, c->d_sensors, d_dl + (rel / se - 1) * ns, lam[cur]);
+            const void *Tn = (const uint8_t *)rec + (size_t)s * nn * rs;
+            if (c->precision == 64) {
+                k_adj_mu<double><<<nblk(nn), 256, 0, c->stream>>>(nn, (const double *)Tn, c->d_A, lam[cur], c->c_lin, mu, musum);
+                if (npe == 8)
+                    k_adj_elem<8, double><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const double *)Tn, mu,
+                                                                           c->d_kscale, c->k_lin, YF, YG, gth);
+                else
+                    k_adj_elem<4, double><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const double *)Tn, mu,
+                                                                           c->d_kscale, c->k_lin, YF, YG, gth);
+                k_adj_node<double><<<nblk(nn), 256, 0, c->stream>>>(nn, npe, c->d_n2e_ptr, c->d_n2e, YF, YG, (const double *)Tn,
+                                                                   lam[cur], mu, c->d_A, c->d_Qext64, c->d_Ac64, c->d_Ar64,
+                                                                   c->d_isdir, ph, lam[cur ^ 1]);
+            } else {
+                k_adj_mu<float><<<nblk(nn), 256, 0, c->stream>>>(nn, (const float *)Tn, c->d_A, lam[cur], c->c_lin, mu, musum);
+                if (npe == 8)
+                    k_adj_elem<8, float><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const float *)Tn, mu,
+                                                                          c->d_kscale, c->k_lin, YF, YG, gth);
+                else
+                    k_adj_elem<4, float><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const float *)Tn, mu,
+                                                                          c->d_kscale, c->k_lin, YF, YG, gth);
+                k_adj_node<float><<<nblk(nn), 256, 0, c->stream>>>(nn, npe, c->d_n2e_ptr, c->d_n2e, YF, YG, (const float *)Tn,
+                                                                  lam[cur], mu, c->d_A, c->d_Qext64, c->d_Ac64, c->d_Ar64,
+                                                                  c->d_isdir, ph, lam[cur ^ 1]);
+            }
+            cur ^= 1;
+        }
+        CKR(cudaGetLastError(), "adjoint sweep");
+    }
+    if (npe == 8)
+        k_adj_source<8><<<nblk(ne), 256, 0, c->stream>>>(ne, c->d_gconn, c->d_W, musum, gs);
+    else
+        k_adj_source<4><<<nblk(ne), 256, 0, c->stream>>>(ne, c->d_gconn, c->d_W, musum, gs);
+    CKR(cudaGetLastError(), "source gradient");
+    CKR(cudaMemcpyAsync(dL_dkscale, gth, ne * 8, cudaMemcpyDeviceToHost, c->stream), "download");
+    CKR(cudaMemcpyAsync(dL_dsource, gs, ne * 8, cudaMemcpyDeviceToHost, c->stream), "download");
+    // leave the context in the state at the end of the recorded run
+    c->step = c->rec_step0 + c->rec_steps;
+    fedfem_status st = copy_state(c, c->step, (uint8_t *)c->d_ckpt + n_ckpt * c->ckpt_bytes, false);
+    int32_t bits = 0;
+    CKR(cudaMemcpyAsync(&bits, c->d_err, 4, cudaMemcpyDeviceToHost, c->stream), "status");
+    CKR(cudaStreamSynchronize(c->stream), "synchronize");
+    release();
+    if (st != FEDFEM_OK) return st;
+    if (bits) {
+        cudaMemset(c->d_err, 0, 4);
+        return fail(c, (bits & ERRBIT_DIVERGED) ? FEDFEM_ERR_DIVERGED : FEDFEM_ERR_TIMEOUT, "recomputation failed");
+    }
+    return FEDFEM_OK;
+#undef CKR
 }
