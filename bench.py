@@ -187,6 +187,7 @@ def main():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=400)
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_setup(args)
@@ -296,6 +297,32 @@ def main():
     bytes64 = ELEM_BYTES_FP64 * E + NODE_BYTES_FP64 * N
     f64.close()
 
+    # ---- adjoint / forward on the 32^3 inverse problem (2000 FP32 steps, 512 sensors sampled
+    #      every 10 steps, checkpoints every 100)
+    adj = None
+    if not args.no_adjoint:
+        setup = fi.inverse_problem()
+        pi = setup.problem
+        fa = FedFem(pi, precision=32, stream=stream)
+        dta = 0.9 * fa.precompute()
+        fa.set_dt(dta)
+        fa.set_T(pi.initial_T())
+        fa.forward_record(200, setup.sensors, 10, 100)  # warm-up
+        fa.adjoint(np.zeros((20, len(setup.sensors))))
+        fa.set_T(pi.initial_T())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        trc = fa.forward_record(2000, setup.sensors, 10, 100)
+        t_fwd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        fa.adjoint(np.ones_like(trc))
+        t_adj = time.perf_counter() - t0
+        adj = {"workload": "inverse_32: 32^3 hex, 2000 FP32 steps, 512 sensors every 10 steps, checkpoints every 100",
+               "forward_ms": 1e3 * t_fwd, "adjoint_ms": 1e3 * t_adj, "adjoint_over_forward": t_adj / t_fwd,
+               "extra_device_MB": (21 * pi.n_nodes * 8 + 100 * pi.n_nodes * 4 + 4 * pi.n_nodes * 8
+                                   + 2 * pi.n_elems * 8 * 8 + 2 * pi.n_elems * 8) / 1e6}
+        fa.close()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -321,6 +348,7 @@ def main():
             "fp64": {"value": v64, "unit": UNIT, "ms_per_step": ms64 / K64, "steps": K64,
                      "achieved_GBps": bytes64 / (ms64 * 1e-3 / K64) / 1e9},
             "fp32_over_fp64": value / v64,
+            "adjoint": adj,
             "wall_s": wall,
         }
         print(json.dumps(line), flush=True)

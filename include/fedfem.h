@@ -298,6 +298,11 @@ typedef struct {
     double dt_scale;            /* dt = dt_scale * dt_crit (e.g. 0.9)           */
 } fedfem_scenario;
 
+/* Pack, tile, pre-compute (including every scenario's dt_crit) and capture the run.  All
+ * scenarios use one element type and one material each; the fedfem_scenario arrays are host
+ * arrays copied during the call.  *out is set even on failure, so that
+ * fedfem_batch_error_string can explain it; release it with fedfem_batch_destroy.
+ * Errors: ARG, MESH, UNSUPPORTED, CUDA, OOM. */
 fedfem_status fedfem_batch_create(const fedfem_scenario *sc, int32_t n_scenarios,
                                   const fedfem_options *opt, fedfem_batch **out);
 /* Reset every scenario to its T0 and run all of them to their step counts (graph replay).

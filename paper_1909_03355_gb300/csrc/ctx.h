@@ -23,6 +23,8 @@ struct fedfem_ctx {
     fedfem_options opt;
     int precision = 32, kahan = 1;
 
+    std::vector<int64_t> group_elem;  // batched scenarios: element range of each packed mesh
+
     // launch plan
     fedfem::Tiling til;
     int grid = 0, block = 0, stages = 0, tpc = 0, chunk_bytes = 0, chunk = 0, ts_cap = 0;
@@ -38,6 +40,8 @@ struct fedfem_ctx {
     int32_t *d_sptr = nullptr;
     int2 *d_bnd = nullptr;
     int32_t *d_colptr = nullptr;
+    fedfem::PhysParams *d_phys = nullptr;
+    int32_t *d_cta_tile = nullptr;  // NULL: tiles_per_cta consecutive tiles per CTA
     void *d_T[2] = {nullptr, nullptr};
     float *d_comp[2] = {nullptr, nullptr};
     void *d_part[2] = {nullptr, nullptr};
@@ -88,6 +92,11 @@ fedfem_status cuda_fail(fedfem_ctx *c, cudaError_t e, const char *where);
 cudaError_t dalloc(fedfem_ctx *c, void **p, size_t bytes);
 cudaError_t upload(fedfem_ctx *c, void **p, const void *src, size_t bytes);
 fedfem_status fedfem_ctx_init_device(fedfem_ctx *c);
+fedfem_status create_ctx(const fedfem_mesh *mesh, const fedfem_material *mats, int32_t n_mats, const fedfem_bcs *bcs,
+                         const fedfem_options *opt_in, const std::vector<int64_t> *group_elem, fedfem_ctx **out,
+                         std::string &err);
+fedfem_status check_device(fedfem_ctx *c);
+fedfem_status run_precompute_arrays(fedfem_ctx *c);
 fedfem_status install_T(fedfem_ctx *c, const double *T0_dev_old);
 fedfem_status state_f64_new(fedfem_ctx *c, int64_t step, double *dst);
 StepArgs step_args(fedfem_ctx *c);

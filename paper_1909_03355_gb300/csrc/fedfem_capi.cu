@@ -69,7 +69,7 @@ static std::string status_message(int32_t bits)
 }
 
 // Read and clear the device error word (synchronises the stream).
-static fedfem_status check_device(fedfem_ctx *c)
+fedfem_status fedfem::check_device(fedfem_ctx *c)
 {
     int32_t bits = 0;
     CK(cudaMemcpyAsync(&bits, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream), "read status");
@@ -101,7 +101,8 @@ extern "C" void fedfem_default_options(fedfem_options *o)
 // ------------------------------------------------------------------------------------------
 // create
 // ------------------------------------------------------------------------------------------
-static std::string validate(const fedfem_mesh *m, const fedfem_material *mats, int32_t n_mats, const fedfem_bcs *b)
+static std::string validate(const fedfem_mesh *m, const fedfem_material *mats, int32_t n_mats, const fedfem_bcs *b,
+                            bool per_material_laws)
 {
     if (!m || !mats || !b) return "NULL mesh, materials or bcs";
     if (m->nodes_per_elem != 8 && m->nodes_per_elem != 4) return "nodes_per_elem must be 8 or 4";
@@ -122,7 +123,7 @@ static std::string validate(const fedfem_mesh *m, const fedfem_material *mats, i
             if (!(m->elem_kscale[e] > 0) || !std::isfinite(m->elem_kscale[e])) return "elem_kscale must be > 0";
     for (int i = 0; i < n_mats; ++i) {
         if (!(mats[i].rho > 0) || !(mats[i].c0 > 0)) return "rho and c0 must be > 0";
-        if (mats[i].k_lin != mats[0].k_lin || mats[i].c_lin != mats[0].c_lin)
+        if (!per_material_laws && (mats[i].k_lin != mats[0].k_lin || mats[i].c_lin != mats[0].c_lin))
             return "all materials must share k_lin and c_lin";
         for (int r = 0; r < 3; ++r)
             for (int s = 0; s < 3; ++s)
@@ -176,9 +177,21 @@ static fedfem_status make_plan(fedfem_ctx *c, const std::vector<uint8_t> &is_bnd
         const int64_t n_ctas = (int64_t)c->num_sms * cps;
         int64_t n_tiles = n_ctas * tpc;
         n_tiles = std::min<int64_t>(n_tiles, std::max<int64_t>(1, c->ne / block));
-        const int grid = (int)((n_tiles + tpc - 1) / tpc);
-        std::string e = build_tiling(npe, c->ne, c->nn, c->conn.data(), c->xyz.data(), is_bnd.data(), (int)n_tiles,
-                                     chunk, c->til);
+        int grid = (int)((n_tiles + tpc - 1) / tpc);
+        std::string e;
+        if (c->group_elem.empty()) {
+            e = build_tiling(npe, c->ne, c->nn, c->conn.data(), c->xyz.data(), is_bnd.data(), (int)n_tiles, chunk,
+                             c->til);
+        } else {
+            // batched scenarios: tiles of about ne / n_tiles elements, never spanning two scenarios
+            const int64_t te = std::max<int64_t>(block, (c->ne + n_tiles - 1) / n_tiles);
+            std::vector<int> per;
+            for (size_t g = 0; g + 1 < c->group_elem.size(); ++g)
+                per.push_back((int)((c->group_elem[g + 1] - c->group_elem[g] + te - 1) / te));
+            e = build_tiling_groups(npe, c->ne, c->nn, c->conn.data(), c->xyz.data(), is_bnd.data(), c->group_elem,
+                                    per, chunk, c->til);
+            grid = (int)std::min<int64_t>(n_ctas, c->til.n_tiles);
+        }
         if (!e.empty()) {
             if (e.find("65535") != std::string::npos) {
                 tpc *= 2;
@@ -219,15 +232,18 @@ static fedfem_status make_plan(fedfem_ctx *c, const std::vector<uint8_t> &is_bnd
     return fail(c, FEDFEM_ERR_UNSUPPORTED, "no launch plan fits in shared memory");
 }
 
-extern "C" fedfem_status fedfem_create(const fedfem_mesh *mesh, const fedfem_material *mats, int32_t n_mats,
-                                       const fedfem_bcs *bcs, const fedfem_options *opt_in, fedfem_ctx **out)
+namespace fedfem {
+
+// Host copy of the problem and device set-up; group_elem (optional) packs independent meshes
+// (batched scenarios) whose tiles must not mix.
+fedfem_status create_ctx(const fedfem_mesh *mesh, const fedfem_material *mats, int32_t n_mats, const fedfem_bcs *bcs,
+                         const fedfem_options *opt_in, const std::vector<int64_t> *group_elem, fedfem_ctx **out,
+                         std::string &err)
 {
-    if (!out) return FEDFEM_ERR_ARG;
     *out = nullptr;
-    g_create_error.clear();
-    std::string v = validate(mesh, mats, n_mats, bcs);
+    std::string v = validate(mesh, mats, n_mats, bcs, group_elem != nullptr);
     if (!v.empty()) {
-        g_create_error = v;
+        err = v;
         return FEDFEM_ERR_ARG;
     }
     fedfem_ctx *c = new fedfem_ctx();
@@ -240,7 +256,7 @@ extern "C" fedfem_status fedfem_create(const fedfem_mesh *mesh, const fedfem_mat
         if (o.T_guard <= 0) o.T_guard = 1e6;
     }
     if (o.precision != 32 && o.precision != 64) {
-        g_create_error = "precision must be 32 or 64";
+        err = "precision must be 32 or 64";
         delete c;
         return FEDFEM_ERR_ARG;
     }
@@ -250,6 +266,7 @@ extern "C" fedfem_status fedfem_create(const fedfem_mesh *mesh, const fedfem_mat
     c->npe = mesh->nodes_per_elem;
     c->nn = mesh->n_nodes;
     c->ne = mesh->n_elems;
+    if (group_elem) c->group_elem = *group_elem;
     const int npe = c->npe;
     c->xyz.assign(mesh->xyz, mesh->xyz + 3 * c->nn);
     c->conn.assign(mesh->conn, mesh->conn + npe * c->ne);
@@ -276,12 +293,22 @@ extern "C" fedfem_status fedfem_create(const fedfem_mesh *mesh, const fedfem_mat
 
     fedfem_status st = fedfem_ctx_init_device(c);
     if (st != FEDFEM_OK) {
-        g_create_error = c->err;
+        err = c->err;
         fedfem_destroy(c);
         return st;
     }
     *out = c;
     return FEDFEM_OK;
+}
+
+}  // namespace fedfem
+
+extern "C" fedfem_status fedfem_create(const fedfem_mesh *mesh, const fedfem_material *mats, int32_t n_mats,
+                                       const fedfem_bcs *bcs, const fedfem_options *opt_in, fedfem_ctx **out)
+{
+    if (!out) return FEDFEM_ERR_ARG;
+    g_create_error.clear();
+    return create_ctx(mesh, mats, n_mats, bcs, opt_in, nullptr, out, g_create_error);
 }
 
 namespace fedfem {
@@ -360,6 +387,11 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
         c->d_Ac = c->d_Ac64;
         c->d_Ar = c->d_Ar64;
     }
+    {
+        const PhysParams ph{c->k_lin, c->c_lin, c->h, c->T_inf, c->eps * 5.67e-8, c->T_amb, c->T_zero, c->opt.T_guard};
+        CK(upload(c, (void **)&c->d_phys, &ph, sizeof(ph)), "upload physics");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+    }
     CK(dalloc(c, (void **)&c->d_barrier, 64), "alloc barrier");
     CK(dalloc(c, (void **)&c->d_err, 64), "alloc status");
     CK(cudaMemsetAsync(c->d_err, 0, 64, c->stream), "memset");
@@ -432,7 +464,7 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
 // ------------------------------------------------------------------------------------------
 // pre-computation
 // ------------------------------------------------------------------------------------------
-static fedfem_status run_precompute_arrays(fedfem_ctx *c)
+fedfem_status fedfem::run_precompute_arrays(fedfem_ctx *c)
 {
     const int npe = c->npe;
     CK(cudaMemcpyAsync(c->d_kscale, c->kscale.data(), c->ne * 8, cudaMemcpyHostToDevice, c->stream), "upload kscale");
@@ -668,14 +700,8 @@ StepArgs step_args(fedfem_ctx *c)
     a.Ar = c->d_Ar;
     a.barrier = c->d_barrier;
     a.err = c->d_err;
-    a.k_lin = c->k_lin;
-    a.c_lin = c->c_lin;
-    a.h = c->h;
-    a.T_inf = c->T_inf;
-    a.eps_sigma = c->eps * 5.67e-8;
-    a.T_amb = c->T_amb;
-    a.T_zero = c->T_zero;
-    a.T_guard = c->opt.T_guard;
+    a.phys = c->d_phys;
+    a.cta_tile = c->d_cta_tile;
     a.n_tiles = c->til.n_tiles;
     a.tiles_per_cta = c->tpc;
     a.chunk_bytes = c->chunk_bytes;

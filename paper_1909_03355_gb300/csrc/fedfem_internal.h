@@ -33,6 +33,13 @@ struct TileInfo {
     int32_t sh_begin, sh_count;      // shared entries (owned-shared and ghosts)
     int32_t bnd_begin, bnd_count;    // owned boundary nodes (surface loads)
     int32_t col_begin, n_colors;     // colour classes: chunks colptr[col_begin + c] .. [.. + c + 1]
+    int32_t scenario;                // index into the physics table (batched scenarios)
+    int32_t pad0, pad1, pad2;
+};
+
+// Physical constants of one problem (one scenario of a batch).
+struct PhysParams {
+    double k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero, T_guard;
 };
 
 // Host-side result of the tiling pass.
@@ -59,6 +66,13 @@ struct Tiling {
 // with surface loads.  Returns "" on success, else a message.
 std::string build_tiling(int npe, int64_t ne, int64_t nn, const int32_t *conn, const double *xyz,
                          const uint8_t *is_bnd, int n_tiles, int CH, Tiling &out);
+
+// Tiling of a batch of independent meshes packed one after the other: elements
+// [group_elem[g], group_elem[g+1]) form scenario g and get tiles_per_group[g] tiles of their
+// own (tiles never span scenarios); tiles, chunks and node numbers follow the group order.
+std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *conn, const double *xyz,
+                                const uint8_t *is_bnd, const std::vector<int64_t> &group_elem,
+                                const std::vector<int> &tiles_per_group, int CH, Tiling &out);
 
 // Check every index the step kernel will use against its buffers ("" if all in range).
 std::string validate_tiling(const Tiling &T);
@@ -94,8 +108,10 @@ struct StepArgs {
     void *part[2];              // Real [n_slots] halo partial sums, step parity
     unsigned int *barrier;      // grid barrier counter (zeroed before each launch)
     int32_t *err;               // device error word
-    // physics
-    double k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero, T_guard;
+    // physics: one table entry per scenario, selected by TileInfo::scenario
+    const PhysParams *phys;
+    // CTA c processes tiles [cta_tile[c], cta_tile[c + 1]) (NULL: tiles_per_cta consecutive tiles)
+    const int32_t *cta_tile;
     // launch
     int64_t n0;                 // global step index at launch start
     int32_t nsteps;
@@ -113,6 +129,7 @@ struct StepArgs {
 // Launchers (step.cu).  Return cudaError_t of the launch.
 cudaError_t launch_step(const StepArgs &a, int precision, int kahan, int npe, int grid, int block,
                         size_t smem, int ts_cap, cudaStream_t st);
+cudaError_t prepare_step(int precision, int kahan, int npe, int scatter, size_t smem);
 size_t step_smem_bytes(int precision, int npe, int chunk, int stages, int max_local);
 int step_ts_cap(int precision, int max_local);
 int step_max_blocks_per_sm(int precision, int kahan, int npe, int block, size_t smem);

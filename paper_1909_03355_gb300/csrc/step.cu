@@ -407,9 +407,9 @@ __device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int la
 template <typename R>
 struct Phys {
     R k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero, T_guard;
-    __device__ explicit Phys(const StepArgs &a)
-        : k_lin((R)a.k_lin), c_lin((R)a.c_lin), h((R)a.h), T_inf((R)a.T_inf), eps_sigma((R)a.eps_sigma),
-          T_amb((R)a.T_amb), T_zero((R)a.T_zero), T_guard((R)a.T_guard)
+    __device__ explicit Phys(const PhysParams &p)
+        : k_lin((R)p.k_lin), c_lin((R)p.c_lin), h((R)p.h), T_inf((R)p.T_inf), eps_sigma((R)p.eps_sigma),
+          T_amb((R)p.T_amb), T_zero((R)p.T_zero), T_guard((R)p.T_guard)
     {
     }
 };
@@ -525,8 +525,8 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
     R *Ts_raw = reinterpret_cast<R *>(smem + (size_t)S * a.chunk_bytes + MBAR_BYTES);
     R *Fs = Ts_raw + ts_cap;
 
-    const int t0 = blockIdx.x * a.tiles_per_cta;
-    const int t1 = min(t0 + a.tiles_per_cta, a.n_tiles);
+    const int t0 = a.cta_tile ? a.cta_tile[blockIdx.x] : blockIdx.x * a.tiles_per_cta;
+    const int t1 = a.cta_tile ? a.cta_tile[blockIdx.x + 1] : min(t0 + a.tiles_per_cta, a.n_tiles);
     const int cb = t0 < t1 ? a.tiles[t0].chunk_begin : 0;
     const int nch = t0 < t1 ? a.tiles[t1 - 1].chunk_begin + a.tiles[t1 - 1].n_chunks - cb : 0;
     const long long total = (long long)nch * a.nsteps;
@@ -570,7 +570,6 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
     }
 
     // ---------------------------------------------------------------- consumers
-    const Phys<R> ph(a);
     const R *Qext = reinterpret_cast<const R *>(a.Qext);
     const R *Ac = reinterpret_cast<const R *>(a.Ac);
     const R *Ar = reinterpret_cast<const R *>(a.Ar);
@@ -587,6 +586,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
         R *Tn = reinterpret_cast<R *>(a.T[nxt]);
         for (int t = t0; t < t1 && ok; ++t) {
             const TileInfo ti = a.tiles[t];
+            const Phys<R> ph(a.phys[ti.scenario]);
             const int nb = ti.node_begin;
             const int a0 = nb & ~(ALN - 1);
             const int a1 = (nb + ti.n_owned + ALN - 1) & ~(ALN - 1);
@@ -783,6 +783,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
         const R *part = reinterpret_cast<const R *>(a.part[prv]);
         for (int t = t0; t < t1; ++t) {
             const TileInfo ti = a.tiles[t];
+            const Phys<R> ph(a.phys[ti.scenario]);
             for (int q = tid; q < ti.sh_count; q += NC) {
                 const int4 sh = a.sh[ti.sh_begin + q];
                 if ((sh.w >> 16) != 0) continue;
@@ -841,16 +842,38 @@ int step_max_blocks_per_sm(int precision, int kahan, int npe, int block, size_t 
     return nb;
 }
 
+cudaError_t prepare_step(int precision, int kahan, int npe, int scatter, size_t smem)
+{
+    return cudaFuncSetAttribute(select_kernel(precision, kahan, npe, scatter), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
 cudaError_t launch_step(const StepArgs &a, int precision, int kahan, int npe, int grid, int block, size_t smem,
                         int ts_cap, cudaStream_t st)
 {
     void *k = select_kernel(precision, kahan, npe, a.scatter);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
     if (e != cudaSuccess) return e;
+    if (cs == cudaStreamCaptureStatusNone) {  // while capturing, prepare_step has done this
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     StepArgs args = a;
     void *params[] = {(void *)&args, (void *)&ts_cap};
-    // block consumer threads plus one producer warp for the element ring
-    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(block + 32), params, smem, st);
+    // block consumer threads plus one producer warp for the element ring; a cooperative launch
+    // (all CTAs co-resident for the grid barrier) that can also be captured in a CUDA graph
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block + 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, k, params);
 }
 
 }  // namespace fedfem

@@ -32,29 +32,21 @@ static uint64_t spread3(uint64_t v)
     return x;
 }
 
-std::string build_tiling(int npe, int64_t ne, int64_t nn, const int32_t *conn, const double *xyz,
-                         const uint8_t *is_bnd, int n_tiles, int CH, Tiling &T)
+// Morton (Z-order) sort of elements [e0, e1) by centroid, appended to `order`.
+static void morton_sort(int npe, int64_t e0, int64_t e1, const int32_t *conn, const double *xyz,
+                        std::vector<int64_t> &order)
 {
-    T = Tiling();
-    T.npe = npe;
-    T.ne = ne;
-    T.nn = nn;
-    T.CH = CH;
-    if (ne <= 0 || nn <= 0) return "empty mesh";
-    if (n_tiles < 1) n_tiles = 1;
-    if (n_tiles > ne) n_tiles = (int)ne;
-    T.n_tiles = n_tiles;
-
-    // 1. Morton order of element centroids
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int64_t i = 0; i < nn; ++i)
-        for (int r = 0; r < 3; ++r) {
-            lo[r] = std::min(lo[r], xyz[3 * i + r]);
-            hi[r] = std::max(hi[r], xyz[3 * i + r]);
-        }
-    std::vector<uint64_t> key(ne);
+    for (int64_t e = e0; e < e1; ++e)
+        for (int k = 0; k < npe; ++k)
+            for (int r = 0; r < 3; ++r) {
+                const double v = xyz[3 * (int64_t)conn[npe * e + k] + r];
+                lo[r] = std::min(lo[r], v);
+                hi[r] = std::max(hi[r], v);
+            }
+    std::vector<std::pair<uint64_t, int64_t>> key(e1 - e0);
     const double q = (double)((1u << 21) - 1);
-    for (int64_t e = 0; e < ne; ++e) {
+    for (int64_t e = e0; e < e1; ++e) {
         double c[3] = {0, 0, 0};
         for (int k = 0; k < npe; ++k)
             for (int r = 0; r < 3; ++r) c[r] += xyz[3 * (int64_t)conn[npe * e + k] + r];
@@ -65,16 +57,50 @@ std::string build_tiling(int npe, int64_t ne, int64_t nn, const int32_t *conn, c
             u = std::min(1.0, std::max(0.0, u));
             m |= spread3((uint64_t)(u * q)) << r;
         }
-        key[e] = m;
+        key[e - e0] = {m, e};
     }
-    std::vector<int64_t> order(ne);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return key[a] < key[b]; });
-    key.clear();
-    key.shrink_to_fit();
+    std::sort(key.begin(), key.end());
+    for (const auto &kv : key) order.push_back(kv.second);
+}
 
-    std::vector<int64_t> tb(n_tiles + 1);
-    for (int t = 0; t <= n_tiles; ++t) tb[t] = (int64_t)((__int128)ne * t / n_tiles);
+std::string build_tiling(int npe, int64_t ne, int64_t nn, const int32_t *conn, const double *xyz,
+                         const uint8_t *is_bnd, int n_tiles, int CH, Tiling &T)
+{
+    if (n_tiles < 1) n_tiles = 1;
+    if (n_tiles > ne) n_tiles = (int)std::max<int64_t>(1, ne);
+    return build_tiling_groups(npe, ne, nn, conn, xyz, is_bnd, {0, ne}, {n_tiles}, CH, T);
+}
+
+std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *conn, const double *xyz,
+                                const uint8_t *is_bnd, const std::vector<int64_t> &group_elem,
+                                const std::vector<int> &tiles_per_group, int CH, Tiling &T)
+{
+    T = Tiling();
+    T.npe = npe;
+    T.ne = ne;
+    T.nn = nn;
+    T.CH = CH;
+    if (ne <= 0 || nn <= 0) return "empty mesh";
+    const int G = (int)tiles_per_group.size();
+    if ((int)group_elem.size() != G + 1 || group_elem[0] != 0 || group_elem[G] != ne) return "bad element groups";
+
+    // 1. Morton order of element centroids inside each group; each group cut into its tiles
+    std::vector<int64_t> order;
+    order.reserve(ne);
+    std::vector<int64_t> tb(1, 0);
+    std::vector<int32_t> tile_group;
+    for (int g = 0; g < G; ++g) {
+        const int64_t e0 = group_elem[g], e1 = group_elem[g + 1];
+        if (e1 <= e0) return "empty element group";
+        morton_sort(npe, e0, e1, conn, xyz, order);
+        const int nt = std::max<int>(1, (int)std::min<int64_t>(tiles_per_group[g], e1 - e0));
+        for (int t = 1; t <= nt; ++t) {
+            tb.push_back(e0 + (int64_t)((__int128)(e1 - e0) * t / nt));
+            tile_group.push_back(g);
+        }
+    }
+    const int n_tiles = (int)tile_group.size();
+    T.n_tiles = n_tiles;
 
     // 2. node -> tiles (ascending) CSR, owner = first tile
     std::vector<int32_t> last(nn, -1), cnt(nn, 0);
@@ -119,6 +145,7 @@ std::string build_tiling(int npe, int64_t ne, int64_t nn, const int32_t *conn, c
     for (int t = 0; t < n_tiles; ++t) {
         TileInfo &ti = T.tiles[t];
         std::memset(&ti, 0, sizeof(ti));
+        ti.scenario = tile_group[t];
         ti.node_begin = next;
         for (int pass = 0; pass < 2; ++pass) {
             for (int64_t p = tb[t]; p < tb[t + 1]; ++p) {
