@@ -205,18 +205,27 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// Grid-wide barrier on a monotonically increasing counter with a deadline, entered by the NC
-// consumer threads of every CTA.  Returns false if the deadline passed or another CTA raised
-// an error (every CTA then leaves the kernel).  `withhold` (test hook) skips this CTA's arrival.
-__device__ bool grid_sync(unsigned int *bar, unsigned int target, int32_t *err, long long timeout_ns,
-                          bool withhold, int nc, int *s_ok)
+// Grid-wide barrier on a monotonically increasing counter, split into an arrival and a wait so
+// that work which touches only this CTA's own data can run in between.  Entered by the NC
+// consumer threads of every CTA.  `withhold` (test hook) skips this CTA's arrival.
+__device__ __forceinline__ void grid_arrive(unsigned int *bar, bool withhold, int nc)
+{
+    csync(nc);  // every consumer's halo writes precede the arrival
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (!withhold) atomicAdd(bar, 1u);
+    }
+}
+
+// Wait (with a deadline) until every CTA has arrived.  Returns false if the deadline passed or
+// another CTA raised an error (every CTA then leaves the kernel).
+__device__ bool grid_wait(unsigned int *bar, unsigned int target, int32_t *err, long long timeout_ns, int nc,
+                          int *s_ok)
 {
     fence_proxy_async_global();  // order this thread's global writes before later TMA reads
     csync(nc);
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
-        if (!withhold) atomicAdd(bar, 1u);
         const unsigned long long t0 = global_ns();
         for (unsigned spin = 0;; ++spin) {
             unsigned int v;
@@ -711,6 +720,18 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                 Fs[b.x] += surface_outflow<R>(Ts[b.x], Ac[b.y], Ar[b.y], ph);
             }
             csync(NC);
+            // ---- halo partials (the only data other tiles read after the barrier)
+            R *part = reinterpret_cast<R *>(a.part[cur]);
+            for (int q = tid; q < ti.sh_count; q += NC) {
+                const int4 sh = a.sh[ti.sh_begin + q];
+                part[sh.z + (sh.w >> 16)] = Fs[sh.x];
+            }
+            if (t == t1 - 1) {
+                // last tile of this CTA: arrive at the grid barrier now; the interior updates
+                // below touch only this CTA's own nodes and overlap the other CTAs' arrivals
+                const bool withhold = s == 0 && a.withhold > 0 && (int)blockIdx.x == a.withhold - 1;
+                grid_arrive(a.barrier, withhold, NC);
+            }
             // ---- update interior nodes: aligned groups of four consecutive nodes per thread
             //      (vector loads), two groups in flight; scalar head and tail
             {
@@ -760,18 +781,12 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                     if (KAHAN) a.comp[nxt][g] = cn;
                 }
             }
-            // ---- halo partials
-            R *part = reinterpret_cast<R *>(a.part[cur]);
-            for (int q = tid; q < ti.sh_count; q += NC) {
-                const int4 sh = a.sh[ti.sh_begin + q];
-                part[sh.z + (sh.w >> 16)] = Fs[sh.x];
-            }
             csync(NC);
         }
         if (!ok) break;
         bar_target += gridDim.x;
-        const bool withhold = s == 0 && a.withhold > 0 && (int)blockIdx.x == a.withhold - 1;
-        if (!grid_sync(a.barrier, bar_target, a.err, a.timeout_ns, withhold, NC, &s_ok)) ok = false;
+        if (t0 >= t1) grid_arrive(a.barrier, false, NC);  // a CTA without tiles still takes part
+        if (!grid_wait(a.barrier, bar_target, a.err, a.timeout_ns, NC, &s_ok)) ok = false;
     }
 
     if (ok) {
