@@ -117,9 +117,9 @@ typedef struct {
     void *stream;               /* cudaStream_t, NULL = legacy default stream               */
     int32_t device;             /* CUDA device ordinal, -1 = current device                 */
     int32_t verbose;            /* 1: print the tiling / launch plan to stderr              */
-    int32_t debug_withhold_barrier; /* test hook: k > 0 makes CTA k-1 withhold its first grid-
-                                   barrier arrival in every launch, so the other CTAs' bounded
-                                   waits run out and the call returns FEDFEM_ERR_TIMEOUT; 0 = off */
+    int32_t debug_withhold_barrier; /* test hook: k > 0 makes CTA k-1 withhold the publication of
+                                   its completed steps, so its neighbours' bounded waits run out
+                                   and the call returns FEDFEM_ERR_TIMEOUT; 0 = off */
     int32_t reserved;
 } fedfem_options;
 

@@ -428,7 +428,7 @@ static fedfem_status batch_build(fedfem_batch *b, const fedfem_scenario *sc, int
             const int64_t k = std::min<int64_t>(spl, distinct[j] - n);
             a.n0 = n;
             a.nsteps = (int32_t)k;
-            cudaMemsetAsync(c->d_barrier, 0, 4, stm);
+            cudaMemsetAsync(c->d_tile_done, 0, c->til.n_tiles * sizeof(unsigned int), stm);
             launch_step(a, c->precision, c->kahan, c->npe, grids[j], c->block, c->smem, c->ts_cap, stm);
             n += k;
         }

@@ -40,6 +40,8 @@ struct fedfem_ctx {
     int32_t *d_sptr = nullptr;
     int2 *d_bnd = nullptr;
     int32_t *d_colptr = nullptr;
+    int32_t *d_nbr_ptr = nullptr, *d_nbr = nullptr;
+    unsigned int *d_tile_done = nullptr;
     fedfem::PhysParams *d_phys = nullptr;
     int32_t *d_cta_tile = nullptr;  // NULL: tiles_per_cta consecutive tiles per CTA
     void *d_T[2] = {nullptr, nullptr};
@@ -51,7 +53,6 @@ struct fedfem_ctx {
     uint8_t *d_isdir = nullptr;
     int32_t *d_dir_new = nullptr;
     double *d_dir_T = nullptr;
-    unsigned int *d_barrier = nullptr;
     int32_t *d_err = nullptr;
     unsigned long long *d_bad_elem = nullptr;
     // pre-computation inputs (original numbering for elements)

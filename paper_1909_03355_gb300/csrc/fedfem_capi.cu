@@ -358,6 +358,9 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
     CK(upload(c, (void **)&c->d_sptr, T.sptr.data(), T.sptr.size() * sizeof(int32_t)), "upload halo ptr");
     CK(upload(c, (void **)&c->d_bnd, T.bnd.data(), T.bnd.size() * sizeof(int2)), "upload boundary");
     CK(upload(c, (void **)&c->d_colptr, T.colptr.data(), T.colptr.size() * sizeof(int32_t)), "upload colours");
+    CK(upload(c, (void **)&c->d_nbr_ptr, T.nbr_ptr.data(), T.nbr_ptr.size() * sizeof(int32_t)), "upload neighbours");
+    CK(upload(c, (void **)&c->d_nbr, T.nbr.data(), T.nbr.size() * sizeof(int32_t)), "upload neighbours");
+    CK(dalloc(c, (void **)&c->d_tile_done, (T.n_tiles + 16) * sizeof(unsigned int)), "alloc tile progress");
     const size_t n_slots = T.sptr.empty() ? 0 : (size_t)T.sptr.back();
     for (int b = 0; b < 2; ++b) {
         CK(dalloc(c, &c->d_T[b], (nn + NODE_PAD) * rs), "alloc T");
@@ -392,7 +395,6 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
         CK(upload(c, (void **)&c->d_phys, &ph, sizeof(ph)), "upload physics");
         CK(cudaStreamSynchronize(c->stream), "synchronize");
     }
-    CK(dalloc(c, (void **)&c->d_barrier, 64), "alloc barrier");
     CK(dalloc(c, (void **)&c->d_err, 64), "alloc status");
     CK(cudaMemsetAsync(c->d_err, 0, 64, c->stream), "memset");
     CK(dalloc(c, (void **)&c->d_bad_elem, 8), "alloc");
@@ -698,7 +700,9 @@ StepArgs step_args(fedfem_ctx *c)
     a.Qext = c->d_Qext;
     a.Ac = c->d_Ac;
     a.Ar = c->d_Ar;
-    a.barrier = c->d_barrier;
+    a.tile_done = c->d_tile_done;
+    a.nbr_ptr = c->d_nbr_ptr;
+    a.nbr = c->d_nbr;
     a.err = c->d_err;
     a.phys = c->d_phys;
     a.cta_tile = c->d_cta_tile;
@@ -738,7 +742,7 @@ fedfem_status enqueue_steps(fedfem_ctx *c, int64_t n, void *rec, int64_t rec_str
         a.nsteps = (int32_t)k;
         a.rec = rec ? (uint8_t *)rec + (size_t)done * rec_stride * (c->precision == 64 ? 8 : 4) : nullptr;
         a.rec_stride = rec_stride;
-        CK(cudaMemsetAsync(c->d_barrier, 0, 4, c->stream), "reset barrier");
+        CK(cudaMemsetAsync(c->d_tile_done, 0, c->til.n_tiles * sizeof(unsigned int), c->stream), "reset tile progress");
         CK(launch_step(a, c->precision, c->kahan, c->npe, c->grid, c->block, c->smem, c->ts_cap, c->stream), "step launch");
         c->step += k;
         done += k;

@@ -57,6 +57,7 @@ struct Tiling {
     std::vector<int32_t> sptr;                     // [n_shared+1] halo slot ranges
     std::vector<int2> bnd;                         // {local, gid} owned boundary nodes
     std::vector<int32_t> colptr;                   // per tile: first chunk of each colour class
+    std::vector<int32_t> nbr_ptr, nbr;             // per tile: tiles sharing a node (CSR)
     // incidence (new node ids), ascending element / face order inside each list
     std::vector<int32_t> n2e_ptr;                  // [nn+1]
     std::vector<int64_t> n2e;                      // (e << 3) | k
@@ -106,7 +107,9 @@ struct StepArgs {
     const void *Ac;             // Real [nn]
     const void *Ar;             // Real [nn]
     void *part[2];              // Real [n_slots] halo partial sums, step parity
-    unsigned int *barrier;      // grid barrier counter (zeroed before each launch)
+    unsigned int *tile_done;    // [n_tiles] steps completed by each tile in this launch (zeroed per launch)
+    const int32_t *nbr_ptr;     // tile neighbours (CSR over tiles)
+    const int32_t *nbr;
     int32_t *err;               // device error word
     // physics: one table entry per scenario, selected by TileInfo::scenario
     const PhysParams *phys;

@@ -205,46 +205,57 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// Grid-wide barrier on a monotonically increasing counter, split into an arrival and a wait so
-// that work which touches only this CTA's own data can run in between.  Entered by the NC
-// consumer threads of every CTA.  `withhold` (test hook) skips this CTA's arrival.
-__device__ __forceinline__ void grid_arrive(unsigned int *bar, bool withhold, int nc)
+// Neighbour synchronisation (in place of a grid barrier).  A tile publishes how many steps of
+// this launch it has completed; before step s it waits until every tile it shares a node with
+// has completed step s - 1.  Neighbours therefore never drift apart by more than one step, which
+// is what the step-parity double buffers of T, the compensation and the halo partials allow.
+// Entered by the NC consumer threads; thread 0 does the memory operations.
+__device__ __forceinline__ void tile_publish(unsigned int *done, int t, unsigned int steps, bool withhold, int nc)
 {
-    csync(nc);  // every consumer's halo writes precede the arrival
+    csync(nc);  // every consumer's halo writes precede the release
     if (threadIdx.x == 0) {
         __threadfence();
-        if (!withhold) atomicAdd(bar, 1u);
+        if (!withhold) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(done + t), "r"(steps) : "memory");
     }
 }
 
-// Wait (with a deadline) until every CTA has arrived.  Returns false if the deadline passed or
-// another CTA raised an error (every CTA then leaves the kernel).
-__device__ bool grid_wait(unsigned int *bar, unsigned int target, int32_t *err, long long timeout_ns, int nc,
-                          int *s_ok)
+// Wait (with a deadline) until all neighbours of tile t have completed `steps` steps; the lanes
+// of warp 0 poll the neighbours' counters in parallel.  Returns false if the deadline passed or
+// another CTA raised an error (every CTA then leaves).
+__device__ bool tile_wait(const unsigned int *done, const int32_t *nbr_ptr, const int32_t *nbr, int t,
+                          unsigned int steps, int32_t *err, long long timeout_ns, int nc, int *s_ok)
 {
     fence_proxy_async_global();  // order this thread's global writes before later TMA reads
     csync(nc);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         int ok = 1;
         const unsigned long long t0 = global_ns();
-        for (unsigned spin = 0;; ++spin) {
-            unsigned int v;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
-            if (v >= target) break;
-            if (*(volatile int32_t *)err) {
-                ok = 0;
-                break;
+        unsigned spin = 0;
+        const int q1 = nbr_ptr[t + 1];
+        for (int q = nbr_ptr[t] + (int)threadIdx.x; q < q1 && ok; q += 32) {
+            const unsigned int *p = done + nbr[q];
+            for (;; ++spin) {
+                unsigned int v;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+                if (v >= steps) break;
+                if ((spin & 15u) == 15u) {
+                    if (*(volatile int32_t *)err) {
+                        ok = 0;
+                        break;
+                    }
+                    if ((long long)(global_ns() - t0) > timeout_ns) {
+                        atomicOr(err, ERRBIT_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+                __nanosleep(32);
             }
-            if ((spin & 31u) == 31u && (long long)(global_ns() - t0) > timeout_ns) {
-                atomicOr(err, ERRBIT_TIMEOUT);
-                ok = 0;
-                break;
-            }
-            __nanosleep(32);
         }
+        ok = __all_sync(0xffffffffu, ok);
         __threadfence();
         fence_proxy_async_global();
-        *s_ok = ok;
+        if (threadIdx.x == 0) *s_ok = ok;
     }
     csync(nc);
     return *s_ok != 0;
@@ -587,13 +598,16 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
     int kc = 0;           // chunks consumed (fits in 32 bits per launch)
     uint32_t tphase = 0;  // phase of the node-load barrier
     bool ok = true;
-    unsigned int bar_target = 0;
     for (int s = 0; s < a.nsteps && ok; ++s) {
         const long long n = a.n0 + s;
         const int cur = (int)(n & 1), nxt = cur ^ 1;
         R *Tc = reinterpret_cast<R *>(a.T[cur]);
         R *Tn = reinterpret_cast<R *>(a.T[nxt]);
         for (int t = t0; t < t1 && ok; ++t) {
+            if (s > 0 && !tile_wait(a.tile_done, a.nbr_ptr, a.nbr, t, (unsigned)s, a.err, a.timeout_ns, NC, &s_ok)) {
+                ok = false;
+                break;
+            }
             const TileInfo ti = a.tiles[t];
             const Phys<R> ph(a.phys[ti.scenario]);
             const int nb = ti.node_begin;
@@ -726,11 +740,10 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                 const int4 sh = a.sh[ti.sh_begin + q];
                 part[sh.z + (sh.w >> 16)] = Fs[sh.x];
             }
-            if (t == t1 - 1) {
-                // last tile of this CTA: arrive at the grid barrier now; the interior updates
-                // below touch only this CTA's own nodes and overlap the other CTAs' arrivals
-                const bool withhold = s == 0 && a.withhold > 0 && (int)blockIdx.x == a.withhold - 1;
-                grid_arrive(a.barrier, withhold, NC);
+            {
+                // publish the step: the interior updates below touch only this tile's own nodes
+                const bool withhold = a.withhold > 0 && (int)blockIdx.x == a.withhold - 1;
+                tile_publish(a.tile_done, t, (unsigned)(s + 1), withhold, NC);
             }
             // ---- update interior nodes: aligned groups of four consecutive nodes per thread
             //      (vector loads), two groups in flight; scalar head and tail
@@ -784,9 +797,6 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
             csync(NC);
         }
         if (!ok) break;
-        bar_target += gridDim.x;
-        if (t0 >= t1) grid_arrive(a.barrier, false, NC);  // a CTA without tiles still takes part
-        if (!grid_wait(a.barrier, bar_target, a.err, a.timeout_ns, NC, &s_ok)) ok = false;
     }
 
     if (ok) {
@@ -796,7 +806,11 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
         R *Tc = reinterpret_cast<R *>(a.T[cur]);
         const R *Tp = reinterpret_cast<const R *>(a.T[prv]);
         const R *part = reinterpret_cast<const R *>(a.part[prv]);
-        for (int t = t0; t < t1; ++t) {
+        for (int t = t0; t < t1 && ok; ++t) {
+            if (!tile_wait(a.tile_done, a.nbr_ptr, a.nbr, t, (unsigned)a.nsteps, a.err, a.timeout_ns, NC, &s_ok)) {
+                ok = false;
+                break;
+            }
             const TileInfo ti = a.tiles[t];
             const Phys<R> ph(a.phys[ti.scenario]);
             for (int q = tid; q < ti.sh_count; q += NC) {

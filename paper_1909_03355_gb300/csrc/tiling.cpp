@@ -177,6 +177,24 @@ std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *
         }
     }
 
+    // tile neighbours: tiles that share at least one node (CSR, ascending)
+    {
+        std::vector<std::vector<int32_t>> nb(n_tiles);
+        for (int64_t i = 0; i < nn; ++i) {
+            if (cnt[i] < 2) continue;
+            for (int64_t a = ntp[i]; a < ntp[i + 1]; ++a)
+                for (int64_t b = ntp[i]; b < ntp[i + 1]; ++b)
+                    if (a != b) nb[ntl[a]].push_back(ntl[b]);
+        }
+        T.nbr_ptr.assign(1, 0);
+        for (int t = 0; t < n_tiles; ++t) {
+            std::sort(nb[t].begin(), nb[t].end());
+            nb[t].erase(std::unique(nb[t].begin(), nb[t].end()), nb[t].end());
+            T.nbr.insert(T.nbr.end(), nb[t].begin(), nb[t].end());
+            T.nbr_ptr.push_back((int32_t)T.nbr.size());
+        }
+    }
+
     // 3./4. per tile: local numbering, colouring, chunks, shared and boundary entries
     std::vector<int32_t> loc(nn, -1);
     std::vector<uint64_t> mask;
@@ -351,6 +369,9 @@ std::string validate_tiling(const Tiling &T)
         }
     }
     if (chunks != T.n_chunks) return "chunk count";
+    if ((int)T.nbr_ptr.size() != T.n_tiles + 1) return "neighbour lists";
+    for (int32_t v : T.nbr)
+        if (v < 0 || v >= T.n_tiles) return "neighbour id out of range";
     for (int t = 0; t < T.n_tiles; ++t) {
         const TileInfo &ti = T.tiles[t];
         if (ti.n_colors < 1 || ti.col_begin < 0 || ti.col_begin + ti.n_colors >= (int)T.colptr.size() ||

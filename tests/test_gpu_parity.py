@@ -291,8 +291,8 @@ def test_watchdog_reports_divergence_and_context_recovers():
 
 
 def test_barrier_timeout_is_reported_not_hung():
-    """A CTA withholds its first grid-barrier arrival; the others' bounded waits run out, the
-    call returns ERR_TIMEOUT and the context stays usable."""
+    """A CTA withholds the publication of its completed steps; its neighbours' bounded waits run
+    out, the call returns ERR_TIMEOUT and the context stays usable."""
     from paper_1909_03355_gb300.capi import FedFemError
     p = fi.nonlinear_cube(12, "hex")
     f = FedFem(p, precision=32, barrier_timeout_s=0.05, debug_withhold_barrier=1)
