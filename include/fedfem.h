@@ -14,7 +14,7 @@
  *  - Node and element ids are 0-based int32; node coordinates are FP64 [n][3] row-major.
  *  - Every call returns a fedfem_status; no exception crosses the ABI.  After an error the
  *    context's message is available from fedfem_error_string().  A device-side failure
- *    (watchdog or barrier timeout) leaves the context usable: restore a state and continue.
+ *    (watchdog or wait timeout) leaves the context usable: restore a state and continue.
  *  - Work is enqueued on the stream given in fedfem_options.stream (a cudaStream_t, NULL for
  *    the legacy default stream).  Calls that return data to the host synchronise that stream.
  *  - Temperatures are in the unit of T_zero (deg C by default, T_zero = -273.15).
@@ -40,7 +40,7 @@ typedef enum {
     FEDFEM_ERR_MESH = 2,        /* element with det J <= 0 / V <= 0, or a node id out of range */
     FEDFEM_ERR_UNSTABLE = 3,    /* dt > dt_crit without force (Section 3.4, Eq. 29)           */
     FEDFEM_ERR_DIVERGED = 4,    /* watchdog: a temperature became non-finite or > T_guard     */
-    FEDFEM_ERR_TIMEOUT = 5,     /* a device-side wait (grid barrier, TMA) exceeded its limit  */
+    FEDFEM_ERR_TIMEOUT = 5,     /* a device-side wait (tile progress, TMA) exceeded its limit */
     FEDFEM_ERR_CUDA = 6,        /* CUDA runtime error                                         */
     FEDFEM_ERR_OOM = 7,         /* device allocation failed                                   */
     FEDFEM_ERR_STATE = 8,       /* call out of order (create -> precompute -> set_dt -> step) */
