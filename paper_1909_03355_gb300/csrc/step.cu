@@ -674,12 +674,19 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                 }
             }
             // halo nodes: values into Fs (free until the element phase) while the bulk copy is
-            // in flight; four entries per thread in flight
+            // in flight; HU entries per thread in flight, the next HU entries loaded meanwhile
+            const int4 *shp = a.sh + ti.sh_begin;
+            int4 shn[HU];
+#pragma unroll
+            for (int u = 0; u < HU; ++u)
+                if (tid + u * NC < ti.sh_count) shn[u] = __ldg(shp + tid + u * NC);
             for (int q0 = tid; q0 < ti.sh_count; q0 += HU * NC) {
                 int4 sh[HU];
 #pragma unroll
-                for (int u = 0; u < HU; ++u)
-                    if (q0 + u * NC < ti.sh_count) sh[u] = __ldg(a.sh + ti.sh_begin + q0 + u * NC);
+                for (int u = 0; u < HU; ++u) {
+                    sh[u] = shn[u];
+                    if (q0 + (HU + u) * NC < ti.sh_count) shn[u] = __ldg(shp + q0 + (HU + u) * NC);
+                }
                 const R *pprev = reinterpret_cast<const R *>(a.part[nxt]);
                 HaloIn<R> hin[HU];
                 if (s > 0) {
@@ -712,12 +719,12 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                     break;
                 }
             }
-            for (int q = tid; q < ti.sh_count; q += NC) {
-                const int l = a.sh[ti.sh_begin + q].x;
-                Ts[l] = Fs[l];
+            // halo values into Ts (the shared nodes are the local ids [n_interior, n_local)),
+            // accumulators cleared
+            for (int l = tid; l < ti.n_local; l += NC) {
+                if (l >= ti.n_interior) Ts[l] = Fs[l];
+                Fs[l] = (R)0;
             }
-            csync(NC);
-            for (int l = tid; l < ti.n_local; l += NC) Fs[l] = (R)0;
             if (a.rec) {
                 R *rec = reinterpret_cast<R *>(a.rec) + (size_t)s * a.rec_stride;
                 for (int l = tid; l < ti.n_owned; l += NC) rec[nb + l] = Ts[l];
@@ -781,7 +788,8 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                 Fs[b.x] += surface_outflow<R>(Ts[b.x], Ac[b.y], Ar[b.y], ph);
             }
             csync(NC);
-            // ---- halo partials (the only data other tiles read after the barrier)
+            // ---- halo partials (the only data other tiles read after the barrier): entry q is
+            //      local node n_interior + q; only its (first slot, count | rank) pair is read
             R *part = reinterpret_cast<R *>(a.part[cur]);
             for (int q = tid; q < ti.sh_count; q += NC) {
                 const int4 sh = a.sh[ti.sh_begin + q];

@@ -356,7 +356,7 @@ std::string validate_tiling(const Tiling &T)
         for (int q = 0; q < ti.sh_count; ++q) {
             const int4 h = T.sh[ti.sh_begin + q];
             const int cnt = h.w & 0xFFFF, rank = h.w >> 16;
-            if (h.x < ti.n_interior || h.x >= ti.n_local || h.y < 0 || h.y >= T.nn || cnt < 2 || rank >= cnt ||
+            if (h.x != ti.n_interior + q || h.y < 0 || h.y >= T.nn || cnt < 2 || rank >= cnt ||
                 h.z < 0 || h.z + (int64_t)cnt > n_slots)
                 return "halo entry out of range";
             if (h.x < ti.n_owned && (h.y != ti.node_begin + h.x || rank != 0)) return "owned halo entry";
