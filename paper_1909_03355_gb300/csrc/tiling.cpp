@@ -44,6 +44,9 @@ static void morton_sort(int npe, int64_t e0, int64_t e1, const int32_t *conn, co
                 lo[r] = std::min(lo[r], v);
                 hi[r] = std::max(hi[r], v);
             }
+    // one scale for all three axes (the largest span), so the curve, and the tiles cut from
+    // it, stay compact in physical space on elongated domains
+    const double span = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
     std::vector<std::pair<uint64_t, int64_t>> key(e1 - e0);
     const double q = (double)((1u << 21) - 1);
     for (int64_t e = e0; e < e1; ++e) {
@@ -52,7 +55,6 @@ static void morton_sort(int npe, int64_t e0, int64_t e1, const int32_t *conn, co
             for (int r = 0; r < 3; ++r) c[r] += xyz[3 * (int64_t)conn[npe * e + k] + r];
         uint64_t m = 0;
         for (int r = 0; r < 3; ++r) {
-            const double span = hi[r] - lo[r];
             double u = span > 0 ? (c[r] / npe - lo[r]) / span : 0.0;
             u = std::min(1.0, std::max(0.0, u));
             m |= spread3((uint64_t)(u * q)) << r;
