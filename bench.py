@@ -37,6 +37,14 @@ ELEM_BYTES_FP32 = 28 * 4 + 8 * 4
 NODE_BYTES_FP32 = 8 + 8 + 8 + 4
 ELEM_BYTES_FP64 = 28 * 8 + 8 * 4
 NODE_BYTES_FP64 = 16 + 8 + 8
+# the same per linear tetrahedron: 6 conductances + 4 int32 node ids
+TET_BYTES_FP32 = 6 * 4 + 4 * 4
+TET_BYTES_FP64 = 6 * 8 + 4 * 4
+L2_BYTES = 129e6
+
+# The paper's own timings (Section 4.3): C++ on one thread of an Intel i7-6700 @ 3.40 GHz,
+# 0.1 m cube with 40,021 tets / 7,872 nodes, dt = 0.005 s, 2000 steps
+PAPER_CUBE_MS = {"temperature_independent": 2.376, "temperature_dependent": 4.656}
 
 
 def peaks():
@@ -126,6 +134,89 @@ def src_hash():
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
+def algorithmic_bytes(p, precision):
+    """Bytes one explicit step must move on problem p (each array once)."""
+    hexa = p.conn.shape[1] == 8
+    if precision == 32:
+        eb = ELEM_BYTES_FP32 if hexa else TET_BYTES_FP32
+        nb = NODE_BYTES_FP32
+    else:
+        eb = ELEM_BYTES_FP64 if hexa else TET_BYTES_FP64
+        nb = NODE_BYTES_FP64
+    return eb * p.n_elems + nb * p.n_nodes
+
+
+def time_workload(p, precision, steps, stream, peak, dt=None, warm=20):
+    """Device-resident ms/step of `steps` explicit steps of problem p (CUDA events on the
+    launching stream, after `warm` untimed steps), with its algorithmic bandwidth."""
+    import torch
+    from paper_1909_03355_gb300.fedfem import FedFem
+    f = FedFem(p, precision=precision, stream=stream)
+    dtc = f.precompute()
+    dt = 0.9 * dtc if dt is None else dt
+    f.set_dt(dt)
+    f.set_T(p.initial_T())
+    f.step(warm)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        f.step_async(steps)
+        e1.record(stream)
+    f.sync()
+    ms = e0.elapsed_time(e1) / steps
+    info = f.info()
+    T = f.get_T()
+    f.close()
+    nbytes = algorithmic_bytes(p, precision)
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"precision": "f32+kahan" if precision == 32 else "f64", "steps": steps, "ms_per_step": ms,
+            "value": p.n_elems / (ms * 1e-3), "unit": UNIT, "dt": dt, "dt_crit": dtc,
+            "algorithmic_MB_per_step": nbytes / 1e6, "achieved_GBps": gbs, "hbm_frac": gbs / peak,
+            "working_set": "L2-resident" if nbytes < L2_BYTES else "larger than L2",
+            "grid": info["grid"], "block": info["block"], "finite": bool(np.all(np.isfinite(T)))}
+
+
+def extra_workloads(stream, peak):
+    """The paper-shaped cube, the 64^3 nonlinear hex and tet cubes, a long slab and the
+    jittered 128^3 cube, each in FP32 + Kahan and (where stated) FP64."""
+    import fedfem_inputs as fi
+    from oracle import oracle as O
+    out = {}
+    # paper's 0.1 m cube: 19^3 cells x 6 tets (41,154 tets, 8,000 nodes), dt = 0.005 s, 2000 steps
+    pc = fi.paper_cube("tet", 19)
+    pdt = 0.005
+    g32 = time_workload(pc, 32, 2000, stream, peak, dt=pdt)
+    g64 = time_workload(pc, 64, 2000, stream, peak, dt=pdt)
+    m = O.OracleModel(pc)
+    t0 = time.perf_counter()
+    m.run(pc.initial_T(), pdt, 400)
+    orc_ms = 1e3 * (time.perf_counter() - t0) / 400
+    out["paper_cube"] = {
+        "workload": "paper_cube_tet_19: 0.1 m cube, 19^3 cells x 6 tets = 41,154 tets, 8,000 nodes, k = 200 iso, "
+                    "rho = 1000, c = 2000, T0 = 37, back face held at 37, 0.2 W per node on front/top/sides, "
+                    "dt = 0.005 s, 2000 steps",
+        "elements": pc.n_elems, "nodes": pc.n_nodes, "gpu_fp32": g32, "gpu_fp64": g64,
+        "oracle_1core_ms_per_step": orc_ms, "oracle_sample": "400 steps, single-threaded FP64 C oracle",
+        "real_time_factor_fp32": pdt / (g32["ms_per_step"] * 1e-3),
+        "paper_ms_per_step": PAPER_CUBE_MS,
+        "paper_context": "C++, one thread of an Intel i7-6700 @ 3.40 GHz, 40,021 tets / 7,872 nodes (Section 4.3)",
+        "note": "k(T), c(T) are evaluated every step by the same kernel, so temperature-dependent laws cost the same"}
+    for kind in ("hex", "tet"):
+        q = fi.nonlinear_cube(64, kind)
+        out[f"nonlinear_{kind}_64"] = {"elements": q.n_elems, "nodes": q.n_nodes,
+                                        "gpu_fp32": time_workload(q, 32, 2000, stream, peak),
+                                        "gpu_fp64": time_workload(q, 64, 400, stream, peak)}
+    sl = fi.slab(2048, 32, 32, Lx=1.0, k=(1.0, 5.0, 20.0), k_lin=0.002, c0=500.0, c_lin=0.001, rho=2700.0,
+                 T0=20.0, T_s=100.0)
+    out["slab_2048x32x32"] = {"elements": sl.n_elems, "nodes": sl.n_nodes,
+                              "gpu_fp32": time_workload(sl, 32, 2000, stream, peak)}
+    jc = fi.large_cube(128, jitter=0.2)
+    out["large_hex_128_jitter"] = {"elements": jc.n_elems, "nodes": jc.n_nodes,
+                                   "note": "interior nodes jittered by +-0.2 h (seeded): every element differs",
+                                   "gpu_fp32": time_workload(jc, 32, 2000, stream, peak)}
+    return out
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -189,6 +280,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=400)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_setup(args)
@@ -352,6 +444,10 @@ def main():
                    "plan": best, "tuned": [[r[0], None if r[1] == float("inf") else r[1]] for r in tuned]}
         fb.close()
 
+    extras = None
+    if rank == 0 and not args.no_extras:
+        extras = extra_workloads(stream, peak)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -379,6 +475,7 @@ def main():
             "fp32_over_fp64": value / v64,
             "adjoint": adj,
             "batched": batched,
+            "extras": extras,
             "wall_s": wall,
         }
         print(json.dumps(line), flush=True)
