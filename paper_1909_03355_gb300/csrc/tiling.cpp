@@ -13,6 +13,7 @@
 //   4. give every (tile, shared node) pair a halo slot; the slots of one node are contiguous
 //      and ordered by tile, which fixes the order of the cross-tile sum.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -64,6 +65,9 @@ static void morton_sort(int npe, int64_t e0, int64_t e1, const int32_t *conn, co
     std::sort(key.begin(), key.end());
     for (const auto &kv : key) order.push_back(kv.second);
 }
+
+// Iterated-greedy passes of the per-tile element colouring.
+static constexpr int kColourPasses = 8;
 
 std::string build_tiling(int npe, int64_t ne, int64_t nn, const int32_t *conn, const double *xyz,
                          const uint8_t *is_bnd, int n_tiles, int CH, Tiling &T)
@@ -226,19 +230,104 @@ std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *
         if (ti.n_local > 65535) return "tile with more than 65535 nodes (use more tiles)";
         T.max_local = std::max(T.max_local, ti.n_local);
 
-        // greedy colouring in Morton order
+        // element colouring (every class costs the step kernel a barrier and a padded chunk):
+        // the parity pattern of the quantised centroids when it is proper (structured hex
+        // grids: 8 colours), else the best of greedy colourings from the Morton order, from a
+        // raster order, and iterated greedy (Culberson: recolouring class by class, classes in
+        // reverse order, never needs more colours)
         const int64_t m = tb[t + 1] - tb[t];
-        mask.assign(ti.n_local, 0);
         std::vector<uint8_t> col(m);
-        for (int64_t p = 0; p < m; ++p) {
-            const int64_t e = order[tb[t] + p];
-            uint64_t used = 0;
-            for (int k = 0; k < npe; ++k) used |= mask[loc[conn[npe * e + k]]];
-            if (~used == 0) return "more than 64 colours needed in a tile";
-            const int c = __builtin_ctzll(~used);
-            col[p] = (uint8_t)c;
-            for (int k = 0; k < npe; ++k) mask[loc[conn[npe * e + k]]] |= 1ULL << c;
-            T.max_colors = std::max(T.max_colors, c + 1);
+        int ncol_best = 0;
+        {
+            // raster order of the element centroids quantised to the mean element edge
+            std::vector<int64_t> raster(m);
+            std::vector<uint8_t> parity(m);  // candidate 8-colouring (validated below)
+            {
+                double lo[3] = {1e300, 1e300, 1e300};
+                std::vector<double> cen(3 * m);
+                double hsum = 0;  // sum of the elements' mean bounding-box edges
+                for (int64_t p = 0; p < m; ++p) {
+                    const int64_t e = order[tb[t] + p];
+                    double edge = 0;
+                    for (int r = 0; r < 3; ++r) {
+                        double c = 0, a = 1e300, b = -1e300;
+                        for (int k = 0; k < npe; ++k) {
+                            const double v = xyz[3 * (int64_t)conn[npe * e + k] + r];
+                            c += v;
+                            a = std::min(a, v);
+                            b = std::max(b, v);
+                        }
+                        cen[3 * p + r] = c / npe;
+                        lo[r] = std::min(lo[r], cen[3 * p + r]);
+                        edge += (b - a) / 3;
+                    }
+                    hsum += edge;
+                }
+                const double hsz = std::max(1e-300, hsum / (double)std::max<int64_t>(m, 1));
+                std::vector<std::array<int64_t, 3>> q(m);
+                for (int64_t p = 0; p < m; ++p)
+                    for (int r = 0; r < 3; ++r) q[p][2 - r] = (int64_t)std::floor((cen[3 * p + r] - lo[r]) / hsz + 0.5);
+                std::iota(raster.begin(), raster.end(), 0);
+                std::stable_sort(raster.begin(), raster.end(), [&](int64_t a, int64_t b) { return q[a] < q[b]; });
+                for (int64_t p = 0; p < m; ++p)
+                    parity[p] = (uint8_t)((q[p][2] & 1) | ((q[p][1] & 1) << 1) | ((q[p][0] & 1) << 2));
+            }
+            // the parity pattern of the quantised centroids is a proper colouring on structured
+            // hex grids; it is kept only if no two elements sharing a node got the same colour
+            {
+                mask.assign(ti.n_local, 0);
+                bool proper = true;
+                for (int64_t p = 0; p < m && proper; ++p) {
+                    const int64_t e = order[tb[t] + p];
+                    const uint64_t bit = 1ULL << parity[p];
+                    for (int k = 0; k < npe; ++k) {
+                        uint64_t &mk = mask[loc[conn[npe * e + k]]];
+                        if (mk & bit) proper = false;
+                        mk |= bit;
+                    }
+                }
+                if (proper) {
+                    col = parity;
+                    ncol_best = 0;
+                    for (int64_t p = 0; p < m; ++p) ncol_best = std::max(ncol_best, (int)parity[p] + 1);
+                }
+            }
+            std::vector<int64_t> seq(m);
+            std::iota(seq.begin(), seq.end(), 0);
+            std::vector<uint8_t> trial(m);
+            for (int pass = 0; pass < kColourPasses; ++pass) {
+                if (pass == 1) seq = raster;
+                mask.assign(ti.n_local, 0);
+                int nc = 0;
+                for (int64_t p : seq) {
+                    const int64_t e = order[tb[t] + p];
+                    uint64_t used = 0;
+                    for (int k = 0; k < npe; ++k) used |= mask[loc[conn[npe * e + k]]];
+                    if (~used == 0) return "more than 64 colours needed in a tile";
+                    const int c = __builtin_ctzll(~used);
+                    trial[p] = (uint8_t)c;
+                    nc = std::max(nc, c + 1);
+                    for (int k = 0; k < npe; ++k) mask[loc[conn[npe * e + k]]] |= 1ULL << c;
+                }
+                if (ncol_best == 0 || nc < ncol_best) {
+                    col = trial;
+                    ncol_best = nc;
+                }
+                // next order (after the two starting orders): the classes of the best colouring,
+                // last class first
+                if (pass >= 1)
+                    std::stable_sort(seq.begin(), seq.end(), [&](int64_t a, int64_t b) { return col[a] > col[b]; });
+            }
+            // number the colours in use 0, 1, ... (a candidate may leave a class empty)
+            int remap[64];
+            for (int c = 0; c < 64; ++c) remap[c] = -1;
+            for (int64_t p = 0; p < m; ++p) remap[col[p]] = 0;
+            int used = 0;
+            for (int c = 0; c < 64; ++c)
+                if (remap[c] == 0) remap[c] = used++;
+            for (int64_t p = 0; p < m; ++p) col[p] = (uint8_t)remap[col[p]];
+            ncol_best = used;
+            T.max_colors = std::max(T.max_colors, ncol_best);
         }
         std::vector<int64_t> perm(m);
         std::iota(perm.begin(), perm.end(), 0);
@@ -384,6 +473,28 @@ std::string validate_tiling(const Tiling &T)
             if (u1 <= u0) return "empty colour class";
             for (int64_t sl = ((int64_t)ti.chunk_begin + u0) * T.CH; sl < ((int64_t)ti.chunk_begin + u1) * T.CH; ++sl)
                 if (T.elem_col[sl] != c && T.elem_col[sl] != 0xFF) return "chunk with two colours";
+        }
+    }
+    // a colour class is a set of elements without a common node: the step kernel adds their
+    // loads into shared memory without atomics
+    {
+        std::vector<int64_t> stamp(T.max_local > 0 ? T.max_local : 1, -1);
+        int64_t cls = 0;
+        for (int t = 0; t < T.n_tiles; ++t) {
+            const TileInfo &ti = T.tiles[t];
+            for (int c = 0; c < ti.n_colors; ++c, ++cls) {
+                const int u0 = T.colptr[ti.col_begin + c], u1 = T.colptr[ti.col_begin + c + 1];
+                for (int64_t sl = ((int64_t)ti.chunk_begin + u0) * T.CH; sl < ((int64_t)ti.chunk_begin + u1) * T.CH;
+                     ++sl) {
+                    if (T.elem_col[sl] == 0xFF) continue;
+                    for (int k = 0; k < T.npe; ++k) {
+                        const int l = T.lconn[sl * T.npe + k];
+                        if (l >= (int)stamp.size()) return "local id out of range";
+                        if (stamp[l] == cls) return "two elements of one colour class share a node";
+                        stamp[l] = cls;
+                    }
+                }
+            }
         }
     }
     if (T.elem_col.size() != (size_t)T.n_chunks * T.CH || T.chunk_col.size() != (size_t)T.n_chunks * 2)
