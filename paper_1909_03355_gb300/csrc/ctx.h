@@ -72,7 +72,8 @@ struct fedfem_ctx {
     // state
     bool precomputed = false, has_dt = false, has_T = false;
     double dt = 0, dt_crit = 0, T_lo = 0, T_hi = 0, lambda_cond = 0;
-    int power_iters = 0, power_max_iter = 1000;
+    int power_iters = 0, power_max_iter = 1000;  // Lanczos steps for dt_crit: taken, limit
+    double *d_lz = nullptr;                      // [power_max_iter][4] alpha_j, -, beta_j^2, -
     double power_tol = 1e-10;
     int64_t step = 0;
     std::string err;

@@ -457,6 +457,7 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
     for (int i = 0; i < 4; ++i) CK(dalloc(c, (void **)&c->d_v[i], nn * 8), "alloc scratch");
     CK(dalloc(c, (void **)&c->d_Y, (size_t)ne * npe * 8), "alloc scratch");
     CK(dalloc(c, (void **)&c->d_red, 2 * 1024 * 8 + 64), "alloc scratch");
+    CK(dalloc(c, (void **)&c->d_lz, 4 * (size_t)c->power_max_iter * 8), "alloc Lanczos coefficients");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     return FEDFEM_OK;
 }
@@ -535,41 +536,82 @@ fedfem_status fedfem::run_precompute_arrays(fedfem_ctx *c)
     return FEDFEM_OK;
 }
 
+// Largest eigenvalue of the m x m symmetric tridiagonal matrix with diagonal a and squared
+// off-diagonal b2 (b2[i] couples rows i and i + 1) by bisection on the Sturm count of the
+// LDL^T pivots (number of eigenvalues below x).
+static double tridiag_max_eigenvalue(const std::vector<double> &a, const std::vector<double> &b2, int m)
+{
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < m; ++i) {
+        const double r = (i > 0 ? std::sqrt(b2[i - 1]) : 0.0) + (i + 1 < m ? std::sqrt(b2[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    const double pad = 1e-12 * std::max(std::fabs(lo), std::fabs(hi)) + 1e-300;
+    lo -= pad;
+    hi += pad;
+    auto below = [&](double x) {
+        int n = 0;
+        double d = 1.0;
+        for (int i = 0; i < m; ++i) {
+            d = (a[i] - x) - (i > 0 ? b2[i - 1] / d : 0.0);
+            if (d == 0.0) d = -1e-300;
+            if (d < 0.0) ++n;
+        }
+        return n;
+    };
+    for (int k = 0; k < 200 && hi - lo > 1e-15 * std::max(std::fabs(hi), std::fabs(lo)); ++k) {
+        const double mid = 0.5 * (lo + hi);
+        if (below(mid) >= m)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    return hi;
+}
+
 extern "C" fedfem_status fedfem_precompute(fedfem_ctx *c, double T_lo, double T_hi, double *dt_crit_out)
 {
     if (!c) return FEDFEM_ERR_ARG;
     if (!(T_lo <= T_hi)) return fail(c, FEDFEM_ERR_ARG, "T_lo must be <= T_hi");
     fedfem_status s = run_precompute_arrays(c);
     if (s != FEDFEM_OK) return s;
-    // critical time step (Section 3.4): power iteration on C0^-1/2 K0 C0^-1/2 (free nodes)
+    // critical time step (Section 3.4): largest eigenvalue of C0^-1/2 K0 C0^-1/2 on the free
+    // nodes by Lanczos.  The coefficients stay on the device; every 16 steps the host reads them
+    // and takes the largest eigenvalue of the tridiagonal matrix, and stops when it changes by
+    // < tol relative or the Krylov space is exhausted.
     const int64_t nn = c->nn;
-    double *x = c->d_v[0], *u = c->d_v[1], *F = c->d_v[2], *z = c->d_v[3];
-    double *partial = c->d_red, *sums = c->d_red + 2 * 1024;
-    launch_power_init(nn, c->d_isdir, x, c->stream);
-    double lam = 0.0;
-    int it = 0;
+    double *vcur = c->d_v[0], *vprev = c->d_v[1], *u = c->d_v[2], *F = c->d_v[3];
+    double *partial = c->d_red, *norm2 = c->d_red + 2 * 1024;
     const int max_iter = c->power_max_iter;
     const double tol = c->power_tol;
-    // x is normalised after the first iteration; the Rayleigh quotient x.z is read every
-    // 16 iterations and the iteration stops when it changes by < tol relative
+    launch_lanczos_start(nn, c->d_isdir, F, vcur, partial, norm2, c->stream);
+    double lam = 0.0;
+    int it = 0;
+    std::vector<double> coef, alpha, beta2;
     for (it = 0; it < max_iter; ++it) {
-        launch_scale_free(nn, x, c->d_C0, c->d_isdir, u, c->stream);
-        launch_apply(c->npe, c->ne, nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, u, nullptr, 0.0, c->d_Y, F,
-                     c->stream);
-        launch_power_dots(nn, x, F, c->d_C0, c->d_isdir, z, partial, sums, c->stream);
-        launch_normalize(nn, z, sums, x, c->stream);
+        launch_lanczos_step(c->npe, c->ne, nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, c->d_C0, c->d_isdir,
+                            vprev, vcur, u, F, c->d_Y, it ? c->d_lz + 4 * (it - 1) + 2 : nullptr, c->d_lz + 4 * it,
+                            partial, c->stream);
+        std::swap(vprev, vcur);  // v_{j+1} was written over v_{j-1}
         if ((it & 15) == 15 || it == max_iter - 1) {
-            double h2[2];
-            CK(cudaMemcpyAsync(h2, sums, 16, cudaMemcpyDeviceToHost, c->stream), "read");
+            coef.resize(4 * (size_t)(it + 1));
+            CK(cudaMemcpyAsync(coef.data(), c->d_lz, coef.size() * 8, cudaMemcpyDeviceToHost, c->stream), "read");
             CK(cudaStreamSynchronize(c->stream), "synchronize");
-            // Rayleigh quotient with a normalised x (x was normalised by the previous iteration)
-            const double rq = h2[0];
-            const bool done = it > 16 && std::fabs(rq - lam) <= tol * std::fabs(rq);
-            lam = rq;
+            alpha.resize(it + 1);
+            beta2.resize(it + 1);
+            for (int j = 0; j <= it; ++j) {
+                alpha[j] = coef[4 * j];
+                beta2[j] = coef[4 * j + 2];
+            }
+            const double theta = tridiag_max_eigenvalue(alpha, beta2, it + 1);
+            const bool exhausted = !(beta2[it] > 1e-28 * theta * theta);
+            const bool done = exhausted || (it > 16 && std::fabs(theta - lam) <= tol * std::fabs(theta));
+            lam = theta;
             if (done) break;
         }
     }
-    CK(cudaGetLastError(), "power iteration");
+    CK(cudaGetLastError(), "Lanczos");
     c->lambda_cond = lam;
     c->power_iters = it;
     const double fk_max = std::max(1.0 + c->k_lin * T_lo, 1.0 + c->k_lin * T_hi);

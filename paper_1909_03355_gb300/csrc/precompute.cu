@@ -370,6 +370,59 @@ __global__ void k_normalize(int64_t nn, const double *z, const double *sums, dou
         x[g] = z[g] * inv;
 }
 
+// Lanczos steps for the largest eigenvalue of M = C0^-1/2 K0 C0^-1/2 on the free nodes (the
+// vectors are zero on Dirichlet nodes).  Step j: w = M v_j - beta_{j-1} v_{j-1},
+// alpha_j = w . v_j, w -= alpha_j v_j, beta_j^2 = w . w, v_{j+1} = w / beta_j.  The
+// coefficients stay in device memory (read by the next kernels); the host reads them in batches.
+
+// w = C0^-1/2 F - beta_{j-1} v_{j-1} (free nodes), written over F; partial sums of w . v_j
+__global__ void __launch_bounds__(256) k_lz_w(int64_t nn, double *F, const double *C0, const uint8_t *isdir,
+                                              const double *vprev, const double *beta2_prev, const double *vcur,
+                                              double *partial)
+{
+    __shared__ double red[64];
+    const double b = beta2_prev ? sqrt(*beta2_prev) : 0.0;
+    double a = 0.0, z = 0.0;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
+        const double w = isdir[g] ? 0.0 : F[g] / sqrt(C0[g]) - (beta2_prev ? b * vprev[g] : 0.0);
+        F[g] = w;
+        a += w * vcur[g];
+    }
+    block_sum2<256>(a, z, red);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+// w -= alpha_j v_j; partial sums of w . w (alpha == NULL: plain squared norm)
+__global__ void __launch_bounds__(256) k_lz_orth(int64_t nn, double *w, const double *vcur, const double *alpha,
+                                                 double *partial)
+{
+    __shared__ double red[64];
+    const double al = alpha ? *alpha : 0.0;
+    double s = 0.0, z = 0.0;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
+        const double x = alpha ? w[g] - al * vcur[g] : w[g];
+        if (alpha) w[g] = x;
+        s += x * x;
+    }
+    block_sum2<256>(s, z, red);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = s;
+        partial[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+// v_{j+1} = w / beta_j (zero once beta_j underflows: the Krylov space is exhausted)
+__global__ void k_lz_next(int64_t nn, const double *w, const double *beta2, double *vnext)
+{
+    const double b2 = *beta2;
+    const double inv = b2 > 1e-280 ? 1.0 / sqrt(b2) : 0.0;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x)
+        vnext[g] = w[g] * inv;
+}
+
 __global__ void k_init_power(int64_t nn, const uint8_t *isdir, double *x)
 {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x)
@@ -525,6 +578,31 @@ void launch_power_dots(int64_t nn, const double *x, const double *F, const doubl
     const int nb = reduce_blocks(nn);
     k_power_dots<<<nb, 256, 0, st>>>(nn, x, F, C0, isdir, z, partial);
     k_sum_partials<<<1, 256, 0, st>>>(nb, partial, sums);
+}
+
+void launch_lanczos_start(int64_t nn, const uint8_t *isdir, double *x, double *v0, double *partial, double *norm2,
+                          cudaStream_t st)
+{
+    const int nb = reduce_blocks(nn);
+    k_init_power<<<nblk(nn), 256, 0, st>>>(nn, isdir, x);
+    k_lz_orth<<<nb, 256, 0, st>>>(nn, x, nullptr, nullptr, partial);
+    k_sum_partials<<<1, 256, 0, st>>>(nb, partial, norm2);
+    k_lz_next<<<nblk(nn), 256, 0, st>>>(nn, x, norm2, v0);
+}
+
+void launch_lanczos_step(int npe, int64_t ne, int64_t nn, const int32_t *gconn, const double *cond64,
+                         const int32_t *n2e_ptr, const int64_t *n2e, const double *C0, const uint8_t *isdir,
+                         double *vprev, const double *vcur, double *u, double *F, double *Y, const double *beta2_prev,
+                         double *coef, double *partial, cudaStream_t st)
+{
+    const int nb = reduce_blocks(nn);
+    k_scale_free<<<nblk(nn), 256, 0, st>>>(nn, vcur, C0, isdir, u);
+    launch_apply(npe, ne, nn, gconn, cond64, n2e_ptr, n2e, u, nullptr, 0.0, Y, F, st);
+    k_lz_w<<<nb, 256, 0, st>>>(nn, F, C0, isdir, vprev, beta2_prev, vcur, partial);
+    k_sum_partials<<<1, 256, 0, st>>>(nb, partial, coef);  // coef[0] = alpha_j
+    k_lz_orth<<<nb, 256, 0, st>>>(nn, F, vcur, coef, partial);
+    k_sum_partials<<<1, 256, 0, st>>>(nb, partial, coef + 2);  // coef[2] = beta_j^2
+    k_lz_next<<<nblk(nn), 256, 0, st>>>(nn, F, coef + 2, vprev);  // v_{j+1} over v_{j-1}
 }
 
 void launch_normalize(int64_t nn, const double *z, const double *sums, double *x, cudaStream_t st)

@@ -56,6 +56,15 @@ void launch_power_init(int64_t nn, const uint8_t *isdir, double *x, cudaStream_t
 void launch_scale_free(int64_t nn, const double *x, const double *C0, const uint8_t *isdir, double *u, cudaStream_t st);
 void launch_power_dots(int64_t nn, const double *x, const double *F, const double *C0, const uint8_t *isdir, double *z,
                        double *partial, double *sums, cudaStream_t st);
+// Lanczos for the largest eigenvalue of C0^-1/2 K0 C0^-1/2 (free nodes): start vector
+// v0 = x / |x| (norm2 receives |x|^2), then one step per call; coef receives alpha_j at [0] and
+// beta_j^2 at [2], and v_{j+1} is written over vprev.
+void launch_lanczos_start(int64_t nn, const uint8_t *isdir, double *x, double *v0, double *partial, double *norm2,
+                          cudaStream_t st);
+void launch_lanczos_step(int npe, int64_t ne, int64_t nn, const int32_t *gconn, const double *cond64,
+                         const int32_t *n2e_ptr, const int64_t *n2e, const double *C0, const uint8_t *isdir,
+                         double *vprev, const double *vcur, double *u, double *F, double *Y, const double *beta2_prev,
+                         double *coef, double *partial, cudaStream_t st);
 void launch_normalize(int64_t nn, const double *z, const double *sums, double *x, cudaStream_t st);
 int launch_surface_rate(int64_t nn, const double *Ac, const double *Ar, const double *C0, const uint8_t *isdir, double h,
                         double rad_coef, double fc_min, double *partial, cudaStream_t st);

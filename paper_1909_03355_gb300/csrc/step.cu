@@ -453,6 +453,29 @@ struct ACoef<double> {
 
 template <typename R>
 __device__ __forceinline__ ACoef<R> load_A(const StepArgs &a, int g);
+// A of the four nodes g .. g + 3 (g a multiple of 4: 16-byte aligned vector loads)
+template <typename R>
+__device__ __forceinline__ void load_A4(const StepArgs &a, int g, ACoef<R> *out);
+template <>
+__device__ __forceinline__ void load_A4<float>(const StepArgs &a, int g, ACoef<float> *out)
+{
+    const float4 x = __ldg(reinterpret_cast<const float4 *>(a.A2 + g));
+    const float4 y = __ldg(reinterpret_cast<const float4 *>(a.A2 + g) + 1);
+    out[0].v = make_float2(x.x, x.y);
+    out[1].v = make_float2(x.z, x.w);
+    out[2].v = make_float2(y.x, y.y);
+    out[3].v = make_float2(y.z, y.w);
+}
+template <>
+__device__ __forceinline__ void load_A4<double>(const StepArgs &a, int g, ACoef<double> *out)
+{
+    const double2 x = __ldg(reinterpret_cast<const double2 *>(a.A + g));
+    const double2 y = __ldg(reinterpret_cast<const double2 *>(a.A + g) + 1);
+    out[0].v = x.x;
+    out[1].v = x.y;
+    out[2].v = y.x;
+    out[3].v = y.y;
+}
 template <>
 __device__ __forceinline__ ACoef<float> load_A<float>(const StepArgs &a, int g)
 {
@@ -517,6 +540,10 @@ __device__ __forceinline__ R surface_outflow(R T, R Ac, R Ar, const Phys<R> &ph)
 // 3 -> 79.3 us, 4 -> 85.6 us, all spills going to local memory).
 #ifndef HALO_INFLIGHT
 #define HALO_INFLIGHT 2
+#endif
+// Groups of four interior nodes per consumer thread whose loads are in flight together.
+#ifndef UPD_INFLIGHT
+#define UPD_INFLIGHT 2
 #endif
 
 template <typename R>
@@ -801,27 +828,27 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                 tile_publish(a.tile_done, t, (unsigned)(s + 1), withhold, NC);
             }
             // ---- update interior nodes: aligned groups of four consecutive nodes per thread
-            //      (vector loads), two groups in flight; scalar head and tail
+            //      (vector loads), UG groups in flight; scalar head and tail
             {
+                constexpr int UG = UPD_INFLIGHT;
                 const int head = min(ti.n_interior, (4 - (nb & 3)) & 3);
                 const int ngrp = (ti.n_interior - head) >> 2;
                 const int tail0 = head + 4 * ngrp;
-                for (int j0 = tid; j0 < ngrp; j0 += 2 * NC) {
-                    Vec4<R> Qv[2], cpv[2];
-                    ACoef<R> Av[2][4];
+                for (int j0 = tid; j0 < ngrp; j0 += UG * NC) {
+                    Vec4<R> Qv[UG], cpv[UG];
+                    ACoef<R> Av[UG][4];
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
+                    for (int u = 0; u < UG; ++u) {
                         const int j = j0 + u * NC;
                         if (j < ngrp) {
                             const int g = nb + head + 4 * j;
                             Qv[u] = load4<R>(Qext + g);
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) Av[u][e] = load_A<R>(a, g + e);
+                            load_A4<R>(a, g, Av[u]);
                             if (KAHAN) cpv[u] = load4<R>(reinterpret_cast<const R *>(a.comp[cur] + g));
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
+                    for (int u = 0; u < UG; ++u) {
                         const int j = j0 + u * NC;
                         if (j < ngrp) {
                             const int l = head + 4 * j;
