@@ -136,6 +136,32 @@ def test_internal_loads_and_dt_crit(kind):
     f.close()
 
 
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+@pytest.mark.parametrize("n", [2, 3, 6])
+def test_dt_crit_vs_dense_eigensolver(kind, n):
+    """The GPU critical step (FP64 Lanczos) against scipy's dense generalized symmetric
+    eigensolver: without surface terms dt_crit = 2 / (lambda_max(K0, C0 on the free nodes)
+    max f_k / min f_c) (Section 3.4).  n = 2 has fewer free nodes than one convergence check
+    takes, so the Krylov space is exhausted."""
+    import scipy.linalg
+    p = fi.nonlinear_cube(n, kind, jitter=0.2 if n > 2 else 0.0)
+    p.conv_faces = None
+    p.rad_faces = None
+    p.dir_nodes = np.array([0, 1], np.int32)
+    p.dir_T = np.array([20.0, 20.0])
+    m = O.OracleModel(p)
+    free = p.free_mask()
+    Kd = brute.dense_assemble(p.conn, m.K, p.n_nodes)
+    lam = scipy.linalg.eigh(Kd[np.ix_(free, free)], np.diag(m.C0[free]), eigvals_only=True).max()
+    mat = p.mats[0]
+    fk = max(1 + mat.k_lin * p.T_lo, 1 + mat.k_lin * p.T_hi)
+    fc = min(1 + mat.c_lin * p.T_lo, 1 + mat.c_lin * p.T_hi)
+    f = FedFem(p, precision=64)
+    dtc = f.precompute()
+    f.close()
+    assert dtc == pytest.approx(2.0 / (lam * fk / fc), rel=1e-9)
+
+
 def test_inverted_element_reported():
     p = fi.plain_cube(3)
     p.conn = p.conn.copy()
