@@ -62,6 +62,8 @@ class Problem:
     steps: int = 1
     T_lo: float = 0.0                           # temperature range used for the critical step
     T_hi: float = 0.0
+    quadrature: int = 8                         # hexahedron conduction matrix: 8 = 2x2x2 Gauss,
+                                                # 1 = one centre point (Eq. 17)
 
     @property
     def npe(self) -> int:

@@ -120,7 +120,12 @@ typedef struct {
     int32_t debug_withhold_barrier; /* test hook: k > 0 makes CTA k-1 withhold the publication of
                                    its completed steps, so its neighbours' bounded waits run out
                                    and the call returns FEDFEM_ERR_TIMEOUT; 0 = off */
-    int32_t reserved;
+    int32_t quadrature;         /* conduction matrix of hexahedra: 0 or 8 = 2x2x2 Gauss points
+                                   (default), 1 = one point at the element centre with weight 8
+                                   (Eq. 17, reduced integration without hourglass control: the
+                                   element matrix has rank 3).  Lumped masses, source loads and
+                                   face areas keep their exact integration.  Ignored for tets;
+                                   other values give FEDFEM_ERR_ARG */
 } fedfem_options;
 
 /* Fill *opt with defaults (FP32 + Kahan, colour scatter, automatic launch plan). */

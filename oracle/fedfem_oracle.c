@@ -12,8 +12,10 @@
  *    semidefinite conduction load and the update is T += dt (Q - F) / C.  The paper's K of
  *    Eq. 2 is therefore -K0.
  *  - Convection (Eq. 4): heat leaves when T > T_a, nodal load -A^c_i h (T_i - T_a).
- *  - Hexahedra integrate Eq. 12 with 2x2x2 Gauss points (the one-point rule of Eq. 17 has
- *    hourglass modes on distorted meshes); tetrahedra use Eq. 18 exactly.
+ *  - Hexahedra integrate Eq. 12 with 2x2x2 Gauss points by default (the one-point rule of
+ *    Eq. 17 has hourglass modes); the one-point conduction matrix of Eq. 17 is available as an
+ *    option (orc_hex_matrix_centre), with masses, loads and areas integrated as by default.
+ *    Tetrahedra use Eq. 18 exactly.
  *  - Temperature-dependent conductivity is evaluated at the element nodes and averaged over
  *    the element (Section 4.2.2): f_k,e = mean_i f_k(T_i); c(T) is evaluated per node (Eq. 16).
  *  - Lumped (diagonal) thermal mass by row sums, M_i = sum_e rho_e int_e N_i dV (Section 3.1).
@@ -114,6 +116,41 @@ int orc_hex_matrices(const double *x, const double *k, double *K, double *w, dou
             w[i] += d * N[i];
         }
         *vol += d;
+    }
+    return 0;
+}
+
+/*
+ * One-point conduction matrix of the reduced-integration hexahedron (Eq. 17): the
+ * gradients B of the trilinear shape functions at the element centre (xi = eta = zeta = 0),
+ * K = 8 det J(0) B^T k B.  Returns -1 if det J(0) <= 0.
+ */
+int orc_hex_matrix_centre(const double *x, const double *k, double *K)
+{
+    double dN[8][3];
+    for (int i = 0; i < 8; ++i)
+        for (int s = 0; s < 3; ++s) dN[i][s] = HEX_NAT[i][s] / 8.0;
+    double J[3][3] = {{0}};
+    for (int i = 0; i < 8; ++i)
+        for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 3; ++s) J[r][s] += x[3 * i + r] * dN[i][s];
+    const double d = det3(J);
+    if (!(d > 0.0)) return -1;
+    double Ji[3][3];
+    inv3(J, d, Ji);
+    double B[8][3];
+    for (int i = 0; i < 8; ++i)
+        for (int r = 0; r < 3; ++r) {
+            B[i][r] = 0.0;
+            for (int s = 0; s < 3; ++s) B[i][r] += Ji[s][r] * dN[i][s];
+        }
+    for (int i = 0; i < 8; ++i) {
+        double kB[3];
+        for (int r = 0; r < 3; ++r) {
+            kB[r] = 0.0;
+            for (int s = 0; s < 3; ++s) kB[r] += k[3 * r + s] * B[i][s];
+        }
+        for (int j = 0; j < 8; ++j) K[8 * j + i] = 8.0 * d * (B[j][0] * kB[0] + B[j][1] * kB[1] + B[j][2] * kB[2]);
     }
     return 0;
 }

@@ -60,6 +60,7 @@ def lib():
             L = C.CDLL(build())
             P = C.c_void_p
             L.orc_hex_matrices.argtypes = [P, P, P, P, P]
+            L.orc_hex_matrix_centre.argtypes = [P, P, P]
             L.orc_tet_matrices.argtypes = [P, P, P, P, P]
             L.orc_face_area.argtypes = [P, C.c_int]
             L.orc_face_area.restype = C.c_double
@@ -96,6 +97,15 @@ def hex_matrices(x, k):
     if lib().orc_hex_matrices(_p(x), _p(k), _p(K), _p(w), _p(v)):
         raise ValueError("det J <= 0")
     return K, w, float(v[0])
+
+
+def hex_matrix_centre(x, k):
+    """K [8,8] of one hexahedron by the one-point centre rule of Eq. 17 (weight 8)."""
+    x, k = _f64(x), _f64(k)
+    K = np.zeros((8, 8))
+    if lib().orc_hex_matrix_centre(_p(x), _p(k), _p(K)):
+        raise ValueError("det J <= 0")
+    return K
 
 
 def tet_matrices(x, k):
@@ -155,6 +165,12 @@ class OracleModel:
                               _p(self.Ar), _p(self.isdir))
         if rc:
             raise ValueError(f"element {rc - 1} has det J <= 0")
+        if npe == 8 and getattr(p, "quadrature", 8) == 1:
+            # one-point conduction matrices (Eq. 17); masses, loads and areas stay as computed
+            for e in range(ne):
+                m = 0 if p.elem_mat is None else int(p.elem_mat[e])
+                if L.orc_hex_matrix_centre(_p(self.xyz[self.conn[e]]), _p(self.mat_k0[m]), _p(self.K[e])):
+                    raise ValueError(f"element {e} has det J(0) <= 0")
         self._keep = (conv, rad, dn)
         self.m = _Model(nn=nn, ne=ne, npe=npe, pad=0, conn=_p(self.conn), K=_p(self.K),
                         theta=_p(self.theta), W=_p(self.W), C0=_p(self.C0), Qext=_p(self.Qext),

@@ -43,7 +43,7 @@ class Options(C.Structure):
     _fields_ = [("precision", I32), ("kahan", I32), ("scatter", I32), ("block", I32),
                 ("steps_per_launch", I32), ("ctas_per_sm", I32), ("tiles_per_cta", I32), ("stages", I32),
                 ("chunk", I32), ("l2_policy", I32), ("barrier_timeout_s", F64), ("T_guard", F64), ("stream", P), ("device", I32),
-                ("verbose", I32), ("debug_withhold_barrier", I32), ("reserved", I32)]
+                ("verbose", I32), ("debug_withhold_barrier", I32), ("quadrature", I32)]
 
 
 class Info(C.Structure):

@@ -260,6 +260,11 @@ fedfem_status create_ctx(const fedfem_mesh *mesh, const fedfem_material *mats, i
         delete c;
         return FEDFEM_ERR_ARG;
     }
+    if (o.quadrature != 0 && o.quadrature != 1 && o.quadrature != 8) {
+        err = "quadrature must be 0, 1 or 8";
+        delete c;
+        return FEDFEM_ERR_ARG;
+    }
     c->opt = o;
     c->precision = o.precision;
     c->kahan = (o.precision == 32 && o.kahan) ? 1 : 0;
@@ -490,6 +495,7 @@ fedfem_status fedfem::run_precompute_arrays(fedfem_ctx *c)
     ea.chunks = c->d_chunks;
     ea.cond64 = c->d_cond64;
     ea.W = c->d_W;
+    ea.quad = c->opt.quadrature == 1 ? 1 : 8;
     ea.err = c->d_err;
     ea.bad_elem = c->d_bad_elem;
     launch_elem(npe, ea, c->stream);

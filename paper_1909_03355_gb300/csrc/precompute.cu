@@ -58,8 +58,13 @@ __global__ void k_elem_hex(ElemArgs a)
         for (int p = 0; p < 28; ++p) K[p] = 0.0;
         for (int i = 0; i < 8; ++i) w[i] = 0.0;
         bool bad = false;
-        for (int q = 0; q < 8; ++q) {
-            const double xi = g * c_hex_sign[q][0], et = g * c_hex_sign[q][1], ze = g * c_hex_sign[q][2];
+        // points 0-7: 2x2x2 Gauss (unit weights) for w and, by default, K; point 8: the centre
+        // with weight 8 for the one-point conduction matrix of Eq. 17
+        const bool centre = a.quad == 1;
+        for (int q = 0; q < (centre ? 9 : 8); ++q) {
+            const bool is_c = q == 8;
+            const double xi = is_c ? 0.0 : g * c_hex_sign[q][0], et = is_c ? 0.0 : g * c_hex_sign[q][1],
+                         ze = is_c ? 0.0 : g * c_hex_sign[q][2];
             double dN[8][3], N[8];
             for (int i = 0; i < 8; ++i) {
                 const double sx = c_hex_sign[i][0], sy = c_hex_sign[i][1], sz = c_hex_sign[i][2];
@@ -97,13 +102,16 @@ __global__ void k_elem_hex(ElemArgs a)
                 B[i][1] = (C10 * dN[i][0] + C11 * dN[i][1] + C12 * dN[i][2]) * id;
                 B[i][2] = (C20 * dN[i][0] + C21 * dN[i][1] + C22 * dN[i][2]) * id;
             }
+            const bool add_K = centre ? is_c : true;
+            const double wk = is_c ? 8.0 * det : det;
             int p = 0;
             for (int i = 0; i < 8; ++i) {
                 const double kb0 = k[0] * B[i][0] + k[1] * B[i][1] + k[2] * B[i][2];
                 const double kb1 = k[3] * B[i][0] + k[4] * B[i][1] + k[5] * B[i][2];
                 const double kb2 = k[6] * B[i][0] + k[7] * B[i][1] + k[8] * B[i][2];
-                for (int j = i + 1; j < 8; ++j) K[p++] += det * (B[j][0] * kb0 + B[j][1] * kb1 + B[j][2] * kb2);
-                w[i] += det * N[i];
+                if (add_K)
+                    for (int j = i + 1; j < 8; ++j) K[p++] += wk * (B[j][0] * kb0 + B[j][1] * kb1 + B[j][2] * kb2);
+                if (!is_c) w[i] += det * N[i];
             }
         }
         if (bad) {

@@ -18,6 +18,7 @@ struct ElemArgs {
     uint8_t *chunks;            // element stream (conductances written here)
     double *cond64;             // [ne][n_pairs] FP64 copy
     double *W;                  // [ne][npe] int_e N_i dV
+    int quad;                   // hexahedron conduction matrix: 8 = 2x2x2 Gauss, 1 = centre point
     int32_t *err;
     unsigned long long *bad_elem;
 };

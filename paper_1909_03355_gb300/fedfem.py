@@ -58,7 +58,7 @@ def problem_structs(p, keep):
 
 def make_options(precision=32, kahan=True, scatter=0, block=0, steps_per_launch=0, ctas_per_sm=0,
                  tiles_per_cta=0, stages=0, chunk=0, l2_policy=0, barrier_timeout_s=1.0, T_guard=1e6, stream=None, device=-1,
-                 verbose=False, debug_withhold_barrier=0):
+                 verbose=False, debug_withhold_barrier=0, quadrature=0):
     L = capi.load()
     o = capi.Options()
     L.fedfem_default_options(C.byref(o))
@@ -78,6 +78,7 @@ def make_options(precision=32, kahan=True, scatter=0, block=0, steps_per_launch=
     o.device = device
     o.verbose = 1 if verbose else 0
     o.debug_withhold_barrier = debug_withhold_barrier
+    o.quadrature = quadrature
     return o
 
 
@@ -98,6 +99,7 @@ class FedFem:
         self.p = problem
         keep = []
         mesh, mats, bcs = problem_structs(problem, keep)
+        plan.setdefault("quadrature", getattr(problem, "quadrature", 8))
         self.opt = make_options(precision=precision, kahan=kahan, stream=_stream_handle(stream), **plan)
         h = C.c_void_p()
         st = self.L.fedfem_create(C.byref(mesh), mats, len(problem.mats), C.byref(bcs), C.byref(self.opt),

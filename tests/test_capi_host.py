@@ -89,3 +89,6 @@ def test_create_rejects_bad_input_without_gpu(lib_path):
     with pytest.raises(capi.FedFemError) as ei:
         FedFem(p)
     assert "share k_lin" in str(ei.value)
+    with pytest.raises(capi.FedFemError) as ei:
+        FedFem(fi.plain_cube(2), quadrature=4)
+    assert ei.value.name == "ERR_ARG" and "quadrature" in str(ei.value)

@@ -162,6 +162,26 @@ def test_dt_crit_vs_dense_eigensolver(kind, n):
     assert dtc == pytest.approx(2.0 / (lam * fk / fc), rel=1e-9)
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_hex_centre_rule_vs_oracle(precision):
+    """The one-point conduction matrices of Eq. 17 (option quadrature = 1) on the jittered
+    nonlinear hex cube: GPU against the oracle after 300 steps, and the critical step."""
+    p = fi.nonlinear_cube(10, "hex", jitter=0.2)
+    p8 = fi.nonlinear_cube(10, "hex", jitter=0.2)
+    p.quadrature = 1
+    m = O.OracleModel(p)
+    dto = m.dt_crit()[0]
+    dt = 0.9 * min(dto, O.OracleModel(p8).dt_crit()[0])
+    T_ref = m.run(p.initial_T(), dt, 300)
+    # the 2x2x2 operator gives a clearly different field on this distorted mesh
+    assert rel(O.OracleModel(p8).run(p8.initial_T(), dt, 300), T_ref) > 1e-4
+    f = FedFem(p, precision=precision)
+    assert f.precompute() == pytest.approx(dto, rel=1e-6)
+    f.close()
+    T = run_gpu(p, dt, 300, precision)
+    assert rel(T, T_ref) <= TOL[precision]
+
+
 def test_inverted_element_reported():
     p = fi.plain_cube(3)
     p.conn = p.conn.copy()

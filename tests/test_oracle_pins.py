@@ -53,6 +53,55 @@ def test_tet_matches_face_vector_formula(seed):
     assert np.allclose(w, V / 4, rtol=1e-14)
 
 
+def _parallelepiped(rng):
+    """Corner nodes (VTK order) x0 + (s_x a + s_y b + s_z c) / 2 of a random parallelepiped
+    with edge vectors a, b, c (positively oriented), and the matrix [a b c]."""
+    E = rng.uniform(-0.3, 0.3, size=(3, 3)) + np.diag(rng.uniform(0.5, 2.0, size=3))
+    if np.linalg.det(E) < 0:
+        E[:, 0] *= -1
+    s = 2.0 * brute.VTK_CORNERS - 1.0
+    return rng.uniform(-1, 1, size=3) + 0.5 * s @ E.T, E, s
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_hex_centre_rule_closed_form_on_parallelepipeds(seed):
+    """Eq. 17 on a parallelepiped: the shape-function gradients at the centre are
+    grad N_i = [a b c]^-T s_i / 4 and 8 det J = V = det [a b c], so K = V G^T k G."""
+    rng = np.random.default_rng(300 + seed)
+    x, E, s = _parallelepiped(rng)
+    k = _rand_spd(rng)
+    G = np.linalg.solve(E.T, s.T) / 4.0          # [3, 8] gradients
+    Kc = np.linalg.det(E) * G.T @ k @ G
+    K = O.hex_matrix_centre(x, k)
+    assert np.max(np.abs(K - Kc)) <= 1e-13 * np.max(np.abs(Kc))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_hex_centre_rule_matches_gauss_on_linear_fields(seed):
+    """On a parallelepiped the gradient of a linear field is constant and the centre value of
+    grad N_i equals its element mean, so the one-point and 2x2x2 loads agree for linear T."""
+    rng = np.random.default_rng(400 + seed)
+    x, _, _ = _parallelepiped(rng)
+    k = _rand_spd(rng)
+    T = x @ rng.standard_normal(3) + rng.standard_normal()
+    K1 = O.hex_matrix_centre(x, k)
+    K8, _, _ = O.hex_matrices(x, k)
+    assert np.max(np.abs(K1 @ T - K8 @ T)) <= 1e-12 * np.max(np.abs(K8 @ T))
+    # ... but not for a general field (the one-point matrix has rank 3: hourglass modes)
+    assert np.linalg.matrix_rank(K1) == 3 and np.linalg.matrix_rank(K8) == 7
+
+
+def test_hex_centre_rule_invariants(patch_nodes):
+    """Distorted hexahedron of the patch: K 1 = 0, symmetry, rank 3."""
+    k = _rand_spd(np.random.default_rng(9))
+    p = fi.patch_problem(patch_nodes, "hex")
+    for e in range(p.n_elems):
+        K = O.hex_matrix_centre(p.xyz[p.conn[e]], k)
+        assert np.max(np.abs(K.sum(axis=1))) <= 1e-13 * np.max(np.abs(K))
+        assert np.max(np.abs(K - K.T)) <= 1e-14 * np.max(np.abs(K))
+        assert np.linalg.matrix_rank(K, tol=1e-10 * np.max(np.abs(K))) == 3
+
+
 def test_distorted_elements_invariants(patch_nodes):
     """K 1 = 0 (a constant field carries no heat), symmetry, sum_i w_i = volume."""
     k = _rand_spd(np.random.default_rng(7))
