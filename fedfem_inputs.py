@@ -28,14 +28,15 @@ SIDES = ("x0", "x1", "y0", "y1", "z0", "z1")
 
 @dataclasses.dataclass
 class Material:
-    """Thermal material: density rho, conductivity k(T) = k0 * (1 + k_lin*T) with k0 a 3x3
-    SPD tensor (Eq. 1, isotropic / orthotropic / anisotropic), and specific heat
-    c(T) = c0 * (1 + c_lin*T)."""
+    """Thermal material: density rho, conductivity k(T) = k0 * (1 + k_lin*(T - T_ref)) with k0
+    a 3x3 SPD tensor (Eq. 1, isotropic / orthotropic / anisotropic), and specific heat
+    c(T) = c0 * (1 + c_lin*(T - T_ref)); k0 and c0 are the values at T_ref."""
     rho: float
     k0: np.ndarray
     k_lin: float = 0.0
     c0: float = 1.0
     c_lin: float = 0.0
+    T_ref: float = 0.0
 
 
 @dataclasses.dataclass
@@ -427,11 +428,20 @@ def patch_problem(coords: np.ndarray, kind: str = "hex", field=(200.0, 100.0, 20
                    T_lo=0.0, T_hi=float(lin.max()))
 
 
-def paper_cube(kind: str = "tet", n: int = 19, L: float = 0.1, k="iso", steps: int = 2000) -> Problem:
+def two_point_law(T1: float, v1: float, T2: float, v2: float):
+    """(lin, T_ref) of the law v(T) = v1 (1 + lin (T - T_ref)) through (T1, v1) and (T2, v2):
+    linear interpolation between two tabulated points (Section 4.2.2)."""
+    return (v2 / v1 - 1.0) / (T2 - T1), T1
+
+
+def paper_cube(kind: str = "tet", n: int = 19, L: float = 0.1, k="iso", steps: int = 2000,
+               td: bool = False) -> Problem:
     """Stand-in for the paper's 0.1 m cube (Section 4.2.1): n^3 cells (x6 tets), k = 200
     (iso), 300/400/200 (ortho) or the anisotropic tensor of Section 4.2.1, rho = 1000,
     c = 2000, T0 = 37, T = 37 held on the back face (y = L), 0.2 W on every node of the front,
-    top and two side faces, bottom adiabatic."""
+    top and two side faces, bottom adiabatic.  td: the temperature-dependent laws the paper
+    tabulates in Section 4.2.2 (k = 200 at 37 and 2000 at 337, c = 2000 at 37 and 8000 at 337,
+    linear in between), with k scaled for the ortho / aniso tensors."""
     xyz, conn = cube_mesh(n, kind, L=L)
     if k == "iso":
         k0 = 200.0 * np.eye(3)
@@ -446,8 +456,11 @@ def paper_cube(kind: str = "tet", n: int = 19, L: float = 0.1, k="iso", steps: i
     nq = np.zeros(xyz.shape[0])
     nq[loaded] = 0.2
     nq[back] = 0.0
-    return Problem(name=f"paper_cube_{kind}_{n}", xyz=xyz, conn=conn,
-                   mats=[Material(rho=1000.0, k0=k0, c0=2000.0)], nodal_Q=nq,
+    k_lin, T_ref = two_point_law(37.0, 200.0, 337.0, 2000.0) if td else (0.0, 0.0)
+    c_lin, _ = two_point_law(37.0, 2000.0, 337.0, 8000.0) if td else (0.0, 0.0)
+    return Problem(name=f"paper_cube_{kind}_{n}{'_td' if td else ''}", xyz=xyz, conn=conn,
+                   mats=[Material(rho=1000.0, k0=k0, k_lin=k_lin, c0=2000.0, c_lin=c_lin, T_ref=T_ref)],
+                   nodal_Q=nq,
                    dir_nodes=back, dir_T=np.full(len(back), 37.0),
                    T0=np.full(xyz.shape[0], 37.0), steps=steps, T_lo=37.0, T_hi=100.0)
 
@@ -466,6 +479,7 @@ def save_npz(p: Problem, path: str) -> None:
     for i, m in enumerate(p.mats):
         d[f"mat{i}_rho"], d[f"mat{i}_k0"] = m.rho, m.k0
         d[f"mat{i}_k_lin"], d[f"mat{i}_c0"], d[f"mat{i}_c_lin"] = m.k_lin, m.c0, m.c_lin
+        d[f"mat{i}_T_ref"] = m.T_ref
     d["n_mats"] = len(p.mats)
     np.savez(path, **d)
 
@@ -473,7 +487,9 @@ def save_npz(p: Problem, path: str) -> None:
 def load_npz(path: str) -> Problem:
     z = np.load(path, allow_pickle=False)
     mats = [Material(float(z[f"mat{i}_rho"]), z[f"mat{i}_k0"], float(z[f"mat{i}_k_lin"]),
-                     float(z[f"mat{i}_c0"]), float(z[f"mat{i}_c_lin"])) for i in range(int(z["n_mats"]))]
+                     float(z[f"mat{i}_c0"]), float(z[f"mat{i}_c_lin"]),
+                     float(z[f"mat{i}_T_ref"]) if f"mat{i}_T_ref" in z.files else 0.0)
+            for i in range(int(z["n_mats"]))]
     kw = {}
     for f in dataclasses.fields(Problem):
         if f.name == "mats":

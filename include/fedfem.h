@@ -68,15 +68,18 @@ typedef struct {
     const double *elem_kscale;  /* [n_elems] conductivity scale theta_e > 0, or NULL (1)  */
 } fedfem_mesh;
 
-/* Material (Eq. 1): density rho, conductivity k_ij(T) = k0_ij (1 + k_lin T) with k0 3x3
- * symmetric positive definite (row-major), specific heat c(T) = c0 (1 + c_lin T).
- * All materials of one context must share k_lin and c_lin. */
+/* Material (Eq. 1): density rho, conductivity k_ij(T) = k0_ij (1 + k_lin (T - T_ref)) with k0
+ * 3x3 symmetric positive definite (row-major), specific heat c(T) = c0 (1 + c_lin (T - T_ref)):
+ * k0 and c0 are the values at the reference temperature T_ref, and the laws interpolate
+ * linearly between two tabulated points as in Section 4.2.2 (T_ref = 0: k0 (1 + k_lin T)).
+ * All materials of one context must share k_lin, c_lin and T_ref. */
 typedef struct {
     double rho;
     double k0[9];
     double k_lin;
     double c0;
     double c_lin;
+    double T_ref;
 } fedfem_material;
 
 /* Boundary conditions and loads (Eq. 3-7).  Faces are boundary faces listed by node ids
@@ -242,7 +245,7 @@ fedfem_status fedfem_adjoint(fedfem_ctx *ctx, const double *dL_dtrace, double *d
 
 /* Physical constants of the energy-balance terms (the context's values for fedfem_energy). */
 typedef struct {
-    double dt, c_lin, h, T_inf, eps, T_amb, T_zero;
+    double dt, c_lin, h, T_inf, eps, T_amb, T_zero, T_ref;
 } fedfem_energy_params;
 
 /*

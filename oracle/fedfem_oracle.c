@@ -266,8 +266,9 @@ typedef struct {
     const double *Ac;     /* [nn] convection area share */
     const double *Ar;     /* [nn] radiation area share */
     const int32_t *isdir; /* [nn] 1 on Gamma_E */
-    double k_lin, c_lin;  /* f_k(T) = 1 + k_lin T, f_c(T) = 1 + c_lin T */
+    double k_lin, c_lin;  /* f_k(T) = 1 + k_lin (T - T_ref), f_c(T) = 1 + c_lin (T - T_ref) */
     double h, T_inf, eps, T_amb, T_zero;
+    double T_ref;         /* temperature at which k0 and c0 are given */
 } orc_model;
 
 /*
@@ -341,7 +342,7 @@ void orc_internal_loads(const orc_model *m, const double *T, double *F)
         const int32_t *c = m->conn + npe * e;
         const double *Ke = m->K + (int64_t)npe * npe * e;
         double fk = 0.0;
-        for (int i = 0; i < npe; ++i) fk += 1.0 + m->k_lin * T[c[i]];
+        for (int i = 0; i < npe; ++i) fk += 1.0 + m->k_lin * (T[c[i]] - m->T_ref);
         fk /= npe;
         const double s = m->theta[e] * fk;
         for (int i = 0; i < npe; ++i) {
@@ -386,7 +387,7 @@ void orc_run(const orc_model *m, double dt, int64_t nsteps, double *T, double *e
                 continue;
             }
             const double Q = orc_nodal_Q(m, i, T[i]);
-            const double Ci = m->C0[i] * (1.0 + m->c_lin * T[i]);
+            const double Ci = m->C0[i] * (1.0 + m->c_lin * (T[i] - m->T_ref));
             const double Tn = T[i] + dt / Ci * (Q - F[i]);
             S += Ci * (Tn - T[i]);
             B += dt * Q;
@@ -444,8 +445,8 @@ void orc_dt_crit(const orc_model *m, double T_lo, double T_hi, double tol, int64
         lam = rq;
         if (done) break;
     }
-    const double fk_max = fmax(1.0 + m->k_lin * T_lo, 1.0 + m->k_lin * T_hi);
-    const double fc_min = fmin(1.0 + m->c_lin * T_lo, 1.0 + m->c_lin * T_hi);
+    const double fk_max = fmax(1.0 + m->k_lin * (T_lo - m->T_ref), 1.0 + m->k_lin * (T_hi - m->T_ref));
+    const double fc_min = fmin(1.0 + m->c_lin * (T_lo - m->T_ref), 1.0 + m->c_lin * (T_hi - m->T_ref));
     const double rl = fabs(T_lo - m->T_zero), rh = fabs(T_hi - m->T_zero);
     const double r3 = fmax(rl * rl * rl, rh * rh * rh);
     double surf = 0.0;
@@ -506,7 +507,7 @@ void orc_adjoint(const orc_model *m, double dt, int64_t nsteps, const double *T0
                 lnew[i] = lam[i];
                 continue;
             }
-            const double fc = 1.0 + m->c_lin * T[i];
+            const double fc = 1.0 + m->c_lin * (T[i] - m->T_ref);
             const double a = dt / (m->C0[i] * fc);
             const double R = orc_nodal_Q(m, i, T[i]) - F[i];
             const double da = -a * m->c_lin / fc;
@@ -518,7 +519,7 @@ void orc_adjoint(const orc_model *m, double dt, int64_t nsteps, const double *T0
             const int32_t *c = m->conn + npe * e;
             const double *Ke = m->K + (int64_t)npe * npe * e;
             double fk = 0.0;
-            for (int i = 0; i < npe; ++i) fk += 1.0 + m->k_lin * T[c[i]];
+            for (int i = 0; i < npe; ++i) fk += 1.0 + m->k_lin * (T[c[i]] - m->T_ref);
             fk /= npe;
             double muKT = 0.0;
             for (int i = 0; i < npe; ++i) {

@@ -50,7 +50,7 @@ class _Model(C.Structure):
                 ("C0", C.c_void_p), ("Qext", C.c_void_p), ("Ac", C.c_void_p), ("Ar", C.c_void_p),
                 ("isdir", C.c_void_p), ("k_lin", C.c_double), ("c_lin", C.c_double),
                 ("h", C.c_double), ("T_inf", C.c_double), ("eps", C.c_double),
-                ("T_amb", C.c_double), ("T_zero", C.c_double)]
+                ("T_amb", C.c_double), ("T_zero", C.c_double), ("T_ref", C.c_double)]
 
 
 def lib():
@@ -137,8 +137,9 @@ class OracleModel:
         self.mat_c0 = np.array([m.c0 for m in mats], float)
         k_lin = {m.k_lin for m in mats}
         c_lin = {m.c_lin for m in mats}
-        if len(k_lin) != 1 or len(c_lin) != 1:
-            raise ValueError("all materials must share k_lin and c_lin")
+        t_ref = {getattr(m, "T_ref", 0.0) for m in mats}
+        if len(k_lin) != 1 or len(c_lin) != 1 or len(t_ref) != 1:
+            raise ValueError("all materials must share k_lin, c_lin and T_ref")
         self.elem_mat = _i32(p.elem_mat)
         th = theta if theta is not None else p.elem_kscale
         self.theta = _f64(th) if th is not None else np.ones(ne)
@@ -177,7 +178,7 @@ class OracleModel:
                         Ac=_p(self.Ac), Ar=_p(self.Ar), isdir=_p(self.isdir),
                         k_lin=float(mats[0].k_lin), c_lin=float(mats[0].c_lin),
                         h=float(p.h), T_inf=float(p.T_inf), eps=float(p.eps), T_amb=float(p.T_amb),
-                        T_zero=float(p.T_zero))
+                        T_zero=float(p.T_zero), T_ref=float(getattr(mats[0], "T_ref", 0.0)))
         self.mref = C.byref(self.m)
 
     # lumped thermal mass at f_c = 1 (Section 3.1, Eq. 14 / 21)

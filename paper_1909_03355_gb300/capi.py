@@ -29,7 +29,7 @@ class Mesh(C.Structure):
 
 
 class Material(C.Structure):
-    _fields_ = [("rho", F64), ("k0", F64 * 9), ("k_lin", F64), ("c0", F64), ("c_lin", F64)]
+    _fields_ = [("rho", F64), ("k0", F64 * 9), ("k_lin", F64), ("c0", F64), ("c_lin", F64), ("T_ref", F64)]
 
 
 class Bcs(C.Structure):
@@ -60,7 +60,7 @@ class Scenario(C.Structure):
 
 class EnergyParams(C.Structure):
     _fields_ = [("dt", F64), ("c_lin", F64), ("h", F64), ("T_inf", F64), ("eps", F64), ("T_amb", F64),
-                ("T_zero", F64)]
+                ("T_zero", F64), ("T_ref", F64)]
 
 
 # exported names and their (restype, argtypes), as declared in include/fedfem.h

@@ -36,6 +36,7 @@ constexpr double kSigma = 5.67e-8;
 
 struct AdjPhys {
     double k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero;
+    double k_a, c_a;  // f_k = k_a + k_lin T, f_c = c_a + c_lin T
 };
 
 int nblk(int64_t n, int bs = 256)
@@ -56,12 +57,12 @@ __global__ void k_gather_sensors(int ns, const int32_t *sens, const R *T, const 
 
 // mu_i = a_i lambda_i, a_i = A_i / f_c(T_i) (A = 0 on Dirichlet nodes); musum += mu
 template <typename R>
-__global__ void k_adj_mu(int64_t nn, const R *Tn, const double *A, const double *lam, double c_lin, double *mu,
-                         double *musum)
+__global__ void k_adj_mu(int64_t nn, const R *Tn, const double *A, const double *lam, double c_a, double c_lin,
+                         double *mu, double *musum)
 {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
         const double t = (double)Tn[g];
-        const double m = A[g] / (1.0 + c_lin * t) * lam[g];
+        const double m = A[g] / (c_a + c_lin * t) * lam[g];
         mu[g] = m;
         musum[g] += m;
     }
@@ -71,7 +72,7 @@ __global__ void k_adj_mu(int64_t nn, const R *Tn, const double *A, const double 
 // G_e = f_k (c mu_e) + (mu_e . c T_e) k_lin / npe into per-element slots; theta gradient.
 template <int NPE, typename R>
 __global__ void k_adj_elem(int64_t ne, const int32_t *gconn, const double *cond64, const R *Tn, const double *mu,
-                           const double *theta, double k_lin, double *YF, double *YG, double *gtheta)
+                           const double *theta, double k_a, double k_lin, double *YF, double *YG, double *gtheta)
 {
     constexpr int NC = NPE * (NPE - 1) / 2;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
@@ -96,7 +97,7 @@ __global__ void k_adj_elem(int64_t ne, const int32_t *gconn, const double *cond6
                 cm[i] += gm;
                 cm[j] -= gm;
             }
-        const double fk = 1.0 + k_lin * (sum / NPE);
+        const double fk = k_a + k_lin * (sum / NPE);
         double mcT = 0.0;
         for (int k = 0; k < NPE; ++k) mcT += m[k] * cT[k];
         for (int k = 0; k < NPE; ++k) {
@@ -127,7 +128,7 @@ __global__ void k_adj_node(int64_t nn, int npe, const int32_t *n2e_ptr, const in
             continue;
         }
         const double t = (double)Tn[g];
-        const double fc = 1.0 + ph.c_lin * t;
+        const double fc = ph.c_a + ph.c_lin * t;
         const double a = A[g] / fc;
         const double u = t - ph.T_zero, b = ph.T_amb - ph.T_zero;
         const double Q = Qext[g] - Ac[g] * ph.h * (t - ph.T_inf) - Ar[g] * ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
@@ -296,7 +297,7 @@ extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, 
     CKR(cudaMemsetAsync(lam[0], 0, nn * 8, c->stream), "memset");
     CKR(cudaMemsetAsync(musum, 0, nn * 8, c->stream), "memset");
     CKR(cudaMemsetAsync(gth, 0, ne * 8, c->stream), "memset");
-    const AdjPhys ph{c->k_lin, c->c_lin, c->h, c->T_inf, c->eps * kSigma, c->T_amb, c->T_zero};
+    const AdjPhys ph{c->k_lin, c->c_lin, c->h, c->T_inf, c->eps * kSigma, c->T_amb, c->T_zero, c->k_a(), c->c_a()};
     int cur = 0;
     for (int64_t k = n_ckpt - 1; k >= 0; --k) {
         // recompute the segment from its checkpoint, recording T^n for every step
@@ -314,24 +315,24 @@ extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, 
                 k_adj_inject<<<nblk(ns), 256, 0, c->stream>>>(ns, c->d_sensors, d_dl + (rel / se - 1) * ns, lam[cur]);
             const void *Tn = (const uint8_t *)rec + (size_t)s * nn * rs;
             if (c->precision == 64) {
-                k_adj_mu<double><<<nblk(nn), 256, 0, c->stream>>>(nn, (const double *)Tn, c->d_A, lam[cur], c->c_lin, mu, musum);
+                k_adj_mu<double><<<nblk(nn), 256, 0, c->stream>>>(nn, (const double *)Tn, c->d_A, lam[cur], c->c_a(), c->c_lin, mu, musum);
                 if (npe == 8)
                     k_adj_elem<8, double><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const double *)Tn, mu,
-                                                                           c->d_kscale, c->k_lin, YF, YG, gth);
+                                                                           c->d_kscale, c->k_a(), c->k_lin, YF, YG, gth);
                 else
                     k_adj_elem<4, double><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const double *)Tn, mu,
-                                                                           c->d_kscale, c->k_lin, YF, YG, gth);
+                                                                           c->d_kscale, c->k_a(), c->k_lin, YF, YG, gth);
                 k_adj_node<double><<<nblk(nn), 256, 0, c->stream>>>(nn, npe, c->d_n2e_ptr, c->d_n2e, YF, YG, (const double *)Tn,
                                                                    lam[cur], mu, c->d_A, c->d_Qext64, c->d_Ac64, c->d_Ar64,
                                                                    c->d_isdir, ph, lam[cur ^ 1]);
             } else {
-                k_adj_mu<float><<<nblk(nn), 256, 0, c->stream>>>(nn, (const float *)Tn, c->d_A, lam[cur], c->c_lin, mu, musum);
+                k_adj_mu<float><<<nblk(nn), 256, 0, c->stream>>>(nn, (const float *)Tn, c->d_A, lam[cur], c->c_a(), c->c_lin, mu, musum);
                 if (npe == 8)
                     k_adj_elem<8, float><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const float *)Tn, mu,
-                                                                          c->d_kscale, c->k_lin, YF, YG, gth);
+                                                                          c->d_kscale, c->k_a(), c->k_lin, YF, YG, gth);
                 else
                     k_adj_elem<4, float><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const float *)Tn, mu,
-                                                                          c->d_kscale, c->k_lin, YF, YG, gth);
+                                                                          c->d_kscale, c->k_a(), c->k_lin, YF, YG, gth);
                 k_adj_node<float><<<nblk(nn), 256, 0, c->stream>>>(nn, npe, c->d_n2e_ptr, c->d_n2e, YF, YG, (const float *)Tn,
                                                                   lam[cur], mu, c->d_A, c->d_Qext64, c->d_Ac64, c->d_Ar64,
                                                                   c->d_isdir, ph, lam[cur ^ 1]);

@@ -279,7 +279,7 @@ static fedfem_status batch_build(fedfem_batch *b, const fedfem_scenario *sc, int
         const fedfem_scenario &q = sc[b->order[p]];
         const double Tz = (q.bcs.T_zero == 0.0 && q.bcs.n_rad_faces == 0) ? -273.15 : q.bcs.T_zero;
         phys[p] = PhysParams{q.mat.k_lin, q.mat.c_lin, q.bcs.h, q.bcs.T_inf, q.bcs.eps * 5.67e-8, q.bcs.T_amb, Tz,
-                             c->opt.T_guard};
+                             c->opt.T_guard, 1.0 - q.mat.k_lin * q.mat.T_ref, 1.0 - q.mat.c_lin * q.mat.T_ref};
     }
     BCK(balloc(b, (void **)&c->d_phys, S * sizeof(PhysParams)), "alloc physics");
     BCK(cudaMemcpy(c->d_phys, phys.data(), S * sizeof(PhysParams), cudaMemcpyHostToDevice), "upload physics");
@@ -318,7 +318,7 @@ static fedfem_status batch_build(fedfem_batch *b, const fedfem_scenario *sc, int
     const int max_iter = c->power_max_iter;
     for (int it = 0; it < max_iter; ++it) {
         launch_scale_free(nn, x, c->d_C0, c->d_isdir, u, stm);
-        launch_apply(c->npe, c->ne, nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, u, nullptr, 0.0, c->d_Y, F, stm);
+        launch_apply(c->npe, c->ne, nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, u, nullptr, 1.0, 0.0, c->d_Y, F, stm);
         k_seg_dots<<<S, 256, 0, stm>>>(d_nr, x, F, c->d_C0, c->d_isdir, z, sums);
         k_seg_normalize<<<S, 256, 0, stm>>>(d_nr, z, sums, x);
         if ((it & 15) == 15 || it == max_iter - 1) {
@@ -337,9 +337,12 @@ static fedfem_status batch_build(fedfem_batch *b, const fedfem_scenario *sc, int
     std::vector<double> h_coef(3 * S), fk_max(S), fc_min(S);
     for (int p = 0; p < S; ++p) {
         const fedfem_scenario &q = sc[b->order[p]];
-        fk_max[p] = std::max(1.0 + q.mat.k_lin * q.T_lo, 1.0 + q.mat.k_lin * q.T_hi);
-        fc_min[p] = std::min(1.0 + q.mat.c_lin * q.T_lo, 1.0 + q.mat.c_lin * q.T_hi);
-        if (!(fk_max[p] > 0) || !(fc_min[p] > 0)) return bfail(b, FEDFEM_ERR_ARG, "material law not positive on [T_lo, T_hi]");
+        const double r = q.mat.T_ref;
+        const double fk_lo = 1.0 + q.mat.k_lin * (q.T_lo - r), fk_hi = 1.0 + q.mat.k_lin * (q.T_hi - r);
+        fk_max[p] = std::max(fk_lo, fk_hi);
+        fc_min[p] = std::min(1.0 + q.mat.c_lin * (q.T_lo - r), 1.0 + q.mat.c_lin * (q.T_hi - r));
+        if (!(std::min(fk_lo, fk_hi) > 0) || !(fc_min[p] > 0))
+            return bfail(b, FEDFEM_ERR_ARG, "material law not positive on [T_lo, T_hi]");
         const double rl = std::fabs(q.T_lo - phys[p].T_zero), rh = std::fabs(q.T_hi - phys[p].T_zero);
         h_coef[3 * p] = q.bcs.h;
         h_coef[3 * p + 1] = 4.0 * 5.67e-8 * q.bcs.eps * std::max(rl * rl * rl, rh * rh * rh);

@@ -19,7 +19,11 @@ struct fedfem_ctx {
     int face_nv = 4;
     int64_t n_conv = 0, n_rad = 0;
     double h = 0, T_inf = 0, eps = 0, T_amb = 0, T_zero = -273.15;
-    double k_lin = 0, c_lin = 0;
+    double k_lin = 0, c_lin = 0, T_ref = 0;  // f_k = 1 + k_lin (T - T_ref), f_c likewise
+    double k_a() const { return 1.0 - k_lin * T_ref; }  // f_k = k_a + k_lin T
+    double c_a() const { return 1.0 - c_lin * T_ref; }
+    double fk(double T) const { return 1.0 + k_lin * (T - T_ref); }
+    double fc(double T) const { return 1.0 + c_lin * (T - T_ref); }
     fedfem_options opt;
     int precision = 32, kahan = 1;
 

@@ -123,8 +123,9 @@ static std::string validate(const fedfem_mesh *m, const fedfem_material *mats, i
             if (!(m->elem_kscale[e] > 0) || !std::isfinite(m->elem_kscale[e])) return "elem_kscale must be > 0";
     for (int i = 0; i < n_mats; ++i) {
         if (!(mats[i].rho > 0) || !(mats[i].c0 > 0)) return "rho and c0 must be > 0";
-        if (!per_material_laws && (mats[i].k_lin != mats[0].k_lin || mats[i].c_lin != mats[0].c_lin))
-            return "all materials must share k_lin and c_lin";
+        if (!per_material_laws &&
+            (mats[i].k_lin != mats[0].k_lin || mats[i].c_lin != mats[0].c_lin || mats[i].T_ref != mats[0].T_ref))
+            return "all materials must share k_lin, c_lin and T_ref";
         for (int r = 0; r < 3; ++r)
             for (int s = 0; s < 3; ++s)
                 if (mats[i].k0[3 * r + s] != mats[i].k0[3 * s + r]) return "k0 must be symmetric";
@@ -283,6 +284,7 @@ fedfem_status create_ctx(const fedfem_mesh *mesh, const fedfem_material *mats, i
     c->mats.assign(mats, mats + n_mats);
     c->k_lin = mats[0].k_lin;
     c->c_lin = mats[0].c_lin;
+    c->T_ref = mats[0].T_ref;
     c->dir_nodes.assign(bcs->dir_nodes, bcs->dir_nodes + bcs->n_dir);
     c->dir_T.assign(bcs->dir_T, bcs->dir_T + bcs->n_dir);
     c->face_nv = bcs->face_nv ? bcs->face_nv : (npe == 8 ? 4 : 3);
@@ -396,7 +398,8 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
         c->d_Ar = c->d_Ar64;
     }
     {
-        const PhysParams ph{c->k_lin, c->c_lin, c->h, c->T_inf, c->eps * 5.67e-8, c->T_amb, c->T_zero, c->opt.T_guard};
+        const PhysParams ph{c->k_lin, c->c_lin, c->h,      c->T_inf, c->eps * 5.67e-8, c->T_amb, c->T_zero,
+                            c->opt.T_guard, c->k_a(), c->c_a()};
         CK(upload(c, (void **)&c->d_phys, &ph, sizeof(ph)), "upload physics");
         CK(cudaStreamSynchronize(c->stream), "synchronize");
     }
@@ -620,9 +623,10 @@ extern "C" fedfem_status fedfem_precompute(fedfem_ctx *c, double T_lo, double T_
     CK(cudaGetLastError(), "Lanczos");
     c->lambda_cond = lam;
     c->power_iters = it;
-    const double fk_max = std::max(1.0 + c->k_lin * T_lo, 1.0 + c->k_lin * T_hi);
-    const double fc_min = std::min(1.0 + c->c_lin * T_lo, 1.0 + c->c_lin * T_hi);
-    if (!(fc_min > 0) || !(fk_max > 0)) return fail(c, FEDFEM_ERR_ARG, "conductivity or heat law not positive on [T_lo, T_hi]");
+    const double fk_max = std::max(c->fk(T_lo), c->fk(T_hi));
+    const double fk_min = std::min(c->fk(T_lo), c->fk(T_hi));
+    const double fc_min = std::min(c->fc(T_lo), c->fc(T_hi));
+    if (!(fc_min > 0) || !(fk_min > 0)) return fail(c, FEDFEM_ERR_ARG, "conductivity or heat law not positive on [T_lo, T_hi]");
     const double rl = std::fabs(T_lo - c->T_zero), rh = std::fabs(T_hi - c->T_zero);
     const double r3 = std::max(rl * rl * rl, rh * rh * rh);
     const int nb = launch_surface_rate(nn, c->d_Ac64, c->d_Ar64, c->d_C0, c->d_isdir, c->h,
@@ -832,7 +836,7 @@ extern "C" fedfem_status fedfem_internal_loads(fedfem_ctx *c, const double *T_ho
     if (!c->precomputed) return fail(c, FEDFEM_ERR_STATE, "call fedfem_precompute first");
     CK(cudaMemcpyAsync(c->d_v[0], T_host, c->nn * 8, cudaMemcpyHostToDevice, c->stream), "upload");
     launch_permute_old_to_new(c->nn, c->d_v[0], c->d_old_of_new, c->d_v[1], c->stream);
-    launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, c->d_v[1], c->d_v[1], c->k_lin,
+    launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, c->d_v[1], c->d_v[1], c->k_a(), c->k_lin,
                  c->d_Y, c->d_v[2], c->stream);
     launch_permute_new_to_old(c->nn, c->d_v[2], c->d_old_of_new, c->d_v[3], c->stream);
     CK(cudaGetLastError(), "internal loads");
@@ -850,9 +854,9 @@ extern "C" fedfem_status fedfem_energy(fedfem_ctx *c, double *stored_change, dou
     if (s != FEDFEM_OK) return s;
     s = state_f64_new(c, c->step, T1);
     if (s != FEDFEM_OK) return s;
-    launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, T0, T0, c->k_lin, c->d_Y, F,
+    launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, T0, T0, c->k_a(), c->k_lin, c->d_Y, F,
                  c->stream);
-    EnergyPhys ph{c->dt, c->c_lin, c->h, c->T_inf, c->eps * 5.67e-8, c->T_amb, c->T_zero};
+    EnergyPhys ph{c->dt, c->c_lin, c->h, c->T_inf, c->eps * 5.67e-8, c->T_amb, c->T_zero, c->c_a()};
     double *partial = c->d_red, *sums = c->d_red + 2 * 1024;
     launch_energy(c->nn, T0, T1, F, c->d_C0, c->d_Qext64, c->d_Ac64, c->d_Ar64, c->d_isdir, ph, partial, sums, c->stream);
     CK(cudaGetLastError(), "energy");

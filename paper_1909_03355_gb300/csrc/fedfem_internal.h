@@ -40,6 +40,7 @@ struct TileInfo {
 // Physical constants of one problem (one scenario of a batch).
 struct PhysParams {
     double k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero, T_guard;
+    double k_a, c_a;  // f_k = k_a + k_lin T, f_c = c_a + c_lin T (k_a = 1 - k_lin T_ref)
 };
 
 // Host-side result of the tiling pass.

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kThreads) k_energy_blocks(int64_t n, const dou
                                                              const double *Ac, const double *Ar, const uint8_t *isdir,
                                                              double dt, double c_lin, double h, double T_inf,
                                                              double eps_sigma, double T_amb, double T_zero,
-                                                             double *partials)
+                                                             double T_ref, double *partials)
 {
     __shared__ double red[2 * (kThreads / 32)];
     double S = 0.0, B = 0.0;
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kThreads) k_energy_blocks(int64_t n, const dou
         const double t = T0[g];
         const double u = t - T_zero, b = T_amb - T_zero;
         const double Q = Qext[g] - Ac[g] * h * (t - T_inf) - Ar[g] * eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
-        S += C0[g] * (1.0 + c_lin * t) * (T1[g] - t);
+        S += C0[g] * (1.0 + c_lin * (t - T_ref)) * (T1[g] - t);
         B += dt * Q;
     }
     warp_sum2(S, B);
@@ -149,7 +149,7 @@ extern "C" fedfem_status fedfem_energy_terms_noalloc(int64_t n_nodes, const doub
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     k_energy_blocks<<<nblocks, kThreads, 0, s>>>(n_nodes, T_prev, T_next, F, C0, Qext, Ac, Ar, is_dirichlet, ph->dt,
                                                  ph->c_lin, ph->h, ph->T_inf, ph->eps * 5.67e-8, ph->T_amb,
-                                                 ph->T_zero, partials);
+                                                 ph->T_zero, ph->T_ref, partials);
     k_energy_final<<<1, kThreads, 0, s>>>(nblocks, partials, out);
     return cudaGetLastError() == cudaSuccess ? FEDFEM_OK : FEDFEM_ERR_CUDA;
 }

@@ -42,6 +42,7 @@ struct NodeArgs {
 
 struct EnergyPhys {
     double dt, c_lin, h, T_inf, eps_sigma, T_amb, T_zero;
+    double c_a;  // f_c = c_a + c_lin T
 };
 
 void launch_elem(int npe, const ElemArgs &a, cudaStream_t st);
@@ -50,7 +51,7 @@ void launch_node_sums(const NodeArgs &a, cudaStream_t st);
 void launch_set_A(int64_t nn, double dt, const double *C0, const uint8_t *isdir, double *A, float2 *A2,
                   cudaStream_t st);
 void launch_apply(int npe, int64_t ne, int64_t nn, const int32_t *gconn, const double *cond64, const int32_t *n2e_ptr,
-                  const int64_t *n2e, const double *x, const double *Tk, double k_lin, double *Y, double *F,
+                  const int64_t *n2e, const double *x, const double *Tk, double k_a, double k_lin, double *Y, double *F,
                   cudaStream_t st);
 int reduce_blocks(int64_t nn);
 void launch_power_init(int64_t nn, const uint8_t *isdir, double *x, cudaStream_t st);

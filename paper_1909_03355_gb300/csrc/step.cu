@@ -389,9 +389,9 @@ __device__ __forceinline__ void store4<double>(double *p, const Vec4<double> &v)
 }
 
 // Element conduction loads of the element in lane `lane` of a staged chunk (Eq. 20):
-// F_i = f_k,e sum_{j != i} c_ij (T_i - T_j), f_k,e = 1 + k_lin mean_i T_i.
+// F_i = f_k,e sum_{j != i} c_ij (T_i - T_j), f_k,e = k_a + k_lin mean_i T_i.
 template <typename R, int NPE>
-__device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int lane, const R *Ts, R k_lin,
+__device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int lane, const R *Ts, R k_a, R k_lin,
                                               R *F, int *id)
 {
     using L = Layout<R, NPE>;
@@ -418,7 +418,7 @@ __device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int la
             F[i] += g;
             F[j] -= g;
         }
-    const R fk = (R)1 + k_lin * (sum * ((R)1 / (R)NPE));
+    const R fk = k_a + k_lin * (sum * ((R)1 / (R)NPE));
 #pragma unroll
     for (int k = 0; k < NPE; ++k) F[k] *= fk;
 }
@@ -426,11 +426,11 @@ __device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int la
 // Physical constants of the step in the working precision (converted once per launch).
 template <typename R>
 struct Phys {
-    R k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero, T_guard;
+    R k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero, T_guard, k_a, c_a;
     Phys() = default;
     __device__ explicit Phys(const PhysParams &p)
         : k_lin((R)p.k_lin), c_lin((R)p.c_lin), h((R)p.h), T_inf((R)p.T_inf), eps_sigma((R)p.eps_sigma),
-          T_amb((R)p.T_amb), T_zero((R)p.T_zero), T_guard((R)p.T_guard)
+          T_amb((R)p.T_amb), T_zero((R)p.T_zero), T_guard((R)p.T_guard), k_a((R)p.k_a), c_a((R)p.c_a)
     {
     }
 };
@@ -505,7 +505,7 @@ template <typename R, bool KAHAN>
 __device__ __forceinline__ R node_update(R T, float comp, ACoef<R> A, R Q, R F, const Phys<R> &ph, float &comp_out,
                                          int32_t *err)
 {
-    const R fc = (R)1 + ph.c_lin * T;
+    const R fc = ph.c_a + ph.c_lin * T;
     const R inc = A.mul((Q - F) / fc);
     R Tn;
     if constexpr (KAHAN) {
@@ -785,7 +785,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                             R F[NPE];
                             int id[NPE];
                             const int col = blk[col_off + lane32];
-                            element_loads<R, NPE>(blk, CH, lane32, Ts, ph.k_lin, F, id);
+                            element_loads<R, NPE>(blk, CH, lane32, Ts, ph.k_a, ph.k_lin, F, id);
                             __syncwarp();
                             if (lane32 == 0) mbar_arrive(&empty[slot]);  // stage back to the producer
                             if (col != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F, id);
@@ -793,8 +793,8 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                             R F0[NPE], F1[NPE];
                             int id0[NPE], id1[NPE];
                             const int col0 = blk[col_off + lane32], col1 = blk[col_off + lane32 + 32];
-                            element_loads<R, NPE>(blk, CH, lane32, Ts, ph.k_lin, F0, id0);
-                            element_loads<R, NPE>(blk, CH, lane32 + 32, Ts, ph.k_lin, F1, id1);
+                            element_loads<R, NPE>(blk, CH, lane32, Ts, ph.k_a, ph.k_lin, F0, id0);
+                            element_loads<R, NPE>(blk, CH, lane32 + 32, Ts, ph.k_a, ph.k_lin, F1, id1);
                             __syncwarp();
                             if (lane32 == 0) mbar_arrive(&empty[slot]);
                             if (col0 != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F0, id0);

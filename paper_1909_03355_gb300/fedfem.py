@@ -41,6 +41,7 @@ def problem_structs(p, keep):
         for r, v in enumerate(np.asarray(m.k0, float).reshape(9)):
             mats[i].k0[r] = v
         mats[i].k_lin, mats[i].c0, mats[i].c_lin = m.k_lin, m.c0, m.c_lin
+        mats[i].T_ref = getattr(m, "T_ref", 0.0)
     dn = _i32(p.dir_nodes) if p.dir_nodes is not None and len(p.dir_nodes) else None
     dT = _f64(p.dir_T) if dn is not None else None
     cf = _i32(p.conv_faces) if p.conv_faces is not None and len(p.conv_faces) else None

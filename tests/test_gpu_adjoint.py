@@ -26,9 +26,12 @@ def small_setup(kind="hex", n=4):
     return p, sensors
 
 
-@pytest.mark.parametrize("kind", ["hex", "tet"])
-def test_adjoint_matches_oracle_adjoint_fp64(kind):
+@pytest.mark.parametrize("kind,T_ref", [("hex", 0.0), ("tet", 0.0), ("hex", 60.0)])
+def test_adjoint_matches_oracle_adjoint_fp64(kind, T_ref):
     p, sensors = small_setup(kind)
+    if T_ref:  # laws given at a reference temperature (Section 4.2.2 form)
+        m0 = p.mats[0]
+        p.mats[0] = fi.Material(m0.rho, m0.k0, m0.k_lin, m0.c0, m0.c_lin, T_ref=T_ref)
     m = O.OracleModel(p)
     dt = 0.9 * m.dt_crit()[0]
     nsteps, se, ck = 60, 10, 20

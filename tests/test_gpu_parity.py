@@ -182,6 +182,22 @@ def test_hex_centre_rule_vs_oracle(precision):
     assert rel(T, T_ref) <= TOL[precision]
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_paper_cube_temperature_dependent_laws(precision):
+    """The paper's cube with the two-point laws of Section 4.2.2 (k and c given at 37 deg C,
+    T_ref = 37) at its own dt = 0.005 s: GPU against the oracle after 400 steps."""
+    p = fi.paper_cube("tet", 8, td=True)
+    m = O.OracleModel(p)
+    f = FedFem(p, precision=precision)
+    dtc = f.precompute()
+    f.close()
+    assert dtc == pytest.approx(m.dt_crit()[0], rel=1e-6)
+    assert 0.005 < dtc
+    T_ref = m.run(p.initial_T(), 0.005, 400)
+    assert T_ref.max() > 37.2  # the loads have heated it
+    assert rel(run_gpu(p, 0.005, 400, precision), T_ref) <= TOL[precision]
+
+
 def test_inverted_element_reported():
     p = fi.plain_cube(3)
     p.conn = p.conn.copy()

@@ -250,6 +250,37 @@ def test_critical_step_vs_dense_eigensolver(n):
         assert lam_o == pytest.approx(lam, rel=1e-8)
 
 
+def test_reference_temperature_law_is_a_rescaled_law():
+    """k0 (1 + k_lin (T - T_ref)) = k0 (1 - k_lin T_ref) (1 + k_lin / (1 - k_lin T_ref) T), and
+    the same for c: a law with a reference temperature gives the same run as the rescaled law
+    with T_ref = 0 (pinned elsewhere), including the critical step."""
+    p = fi.nonlinear_cube(4, "hex", jitter=0.2)
+    m0 = p.mats[0]
+    ref = fi.nonlinear_cube(4, "hex", jitter=0.2)
+    Tr = 60.0
+    p.mats[0] = fi.Material(m0.rho, m0.k0, 0.004, m0.c0, 0.002, T_ref=Tr)
+    sk, sc = 1.0 - 0.004 * Tr, 1.0 - 0.002 * Tr
+    ref.mats[0] = fi.Material(m0.rho, np.asarray(m0.k0) * sk, 0.004 / sk, m0.c0 * sc, 0.002 / sc)
+    a, b = O.OracleModel(p), O.OracleModel(ref)
+    assert a.dt_crit()[0] == pytest.approx(b.dt_crit()[0], rel=1e-9)
+    dt = 0.9 * b.dt_crit()[0]
+    Ta, Tb = a.run(p.initial_T(), dt, 200), b.run(ref.initial_T(), dt, 200)
+    assert np.max(np.abs(Ta - Tb)) <= 1e-11 * np.max(np.abs(Tb))
+    T = fi.random_state(p, 5)
+    assert np.max(np.abs(a.internal_loads(T) - b.internal_loads(T))) <= 1e-11 * np.max(np.abs(b.internal_loads(T)))
+
+
+def test_two_point_law_of_section_4_2_2():
+    """The tabulated laws of Section 4.2.2 (k = 200 / 2000, c = 2000 / 8000 at 37 / 337 deg C,
+    6 W/(m K) and 20 J/(kg K) per degree) as (lin, T_ref) laws."""
+    k_lin, Tr = fi.two_point_law(37.0, 200.0, 337.0, 2000.0)
+    c_lin, _ = fi.two_point_law(37.0, 2000.0, 337.0, 8000.0)
+    assert Tr == 37.0
+    assert 200.0 * (1 + k_lin * (337.0 - Tr)) == pytest.approx(2000.0, rel=1e-14)
+    assert 200.0 * k_lin == pytest.approx(6.0, rel=1e-14)
+    assert 2000.0 * c_lin == pytest.approx(20.0, rel=1e-14)
+
+
 # ------------------------------------------------------------------------------ slab ------
 
 @pytest.mark.parametrize("ny", [1, 2])

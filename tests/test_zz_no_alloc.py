@@ -48,7 +48,7 @@ def test_energy_terms_noalloc_matches_fedfem_energy():
     arrays = [torch.tensor(a, dtype=torch.float64, device=dev) for a in (m.C0, m.Qext, m.Ac, m.Ar)]
     isdir = torch.tensor(m.isdir.astype(np.uint8), device=dev)
     ph = capi.EnergyParams(dt=dt, c_lin=p.mats[0].c_lin, h=p.h, T_inf=p.T_inf, eps=p.eps, T_amb=p.T_amb,
-                           T_zero=p.T_zero)
+                           T_zero=p.T_zero, T_ref=p.mats[0].T_ref)
     out = torch.full((2,), float("nan"), dtype=torch.float64, device=dev)
     results = []
     for _ in range(2):
