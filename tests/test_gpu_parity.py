@@ -198,6 +198,16 @@ def test_paper_cube_temperature_dependent_laws(precision):
     assert rel(run_gpu(p, 0.005, 400, precision), T_ref) <= TOL[precision]
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_paper_cube_full_run(precision):
+    """The paper-shaped 0.1 m cube (41,154 tets) at the paper's dt = 0.005 s for all 2000 steps
+    of Section 4.3: GPU against the oracle."""
+    p = fi.paper_cube("tet", 19)
+    m = O.OracleModel(p)
+    T_ref = m.run(p.initial_T(), 0.005, 2000)
+    assert rel(run_gpu(p, 0.005, 2000, precision), T_ref) <= TOL[precision]
+
+
 def test_inverted_element_reported():
     p = fi.plain_cube(3)
     p.conn = p.conn.copy()
