@@ -65,6 +65,8 @@ class Problem:
     T_hi: float = 0.0
     quadrature: int = 8                         # hexahedron conduction matrix: 8 = 2x2x2 Gauss,
                                                 # 1 = one centre point (Eq. 17)
+    q_schedule: Optional[np.ndarray] = None     # [n] multiplier of the external loads at step n
+    Tinf_schedule: Optional[np.ndarray] = None  # [n] convection ambient temperature at step n
 
     @property
     def npe(self) -> int:

@@ -269,6 +269,12 @@ typedef struct {
     double k_lin, c_lin;  /* f_k(T) = 1 + k_lin (T - T_ref), f_c(T) = 1 + c_lin (T - T_ref) */
     double h, T_inf, eps, T_amb, T_zero;
     double T_ref;         /* temperature at which k0 and c0 are given */
+    /* time-dependent loads (optional): at step n the external loads are q_sched[n] Qext and
+     * the convection ambient temperature is Tinf_sched[n] (the last entry beyond the end);
+     * n counts from sched_step0 at the first step of a run */
+    const double *q_sched;
+    const double *Tinf_sched;
+    int64_t n_sched, sched_step0;
 } orc_model;
 
 /*
@@ -353,12 +359,31 @@ void orc_internal_loads(const orc_model *m, const double *T, double *F)
     }
 }
 
-/* Net external nodal heat flow Q_i (Eq. 4, 5, 7 lumped to nodes). */
-double orc_nodal_Q(const orc_model *m, int64_t i, double Ti)
+/* Load multiplier and convection ambient temperature at step n. */
+static double orc_q_scale(const orc_model *m, int64_t n)
+{
+    if (!m->q_sched || m->n_sched <= 0) return 1.0;
+    return m->q_sched[n < m->n_sched ? n : m->n_sched - 1];
+}
+
+static double orc_T_inf(const orc_model *m, int64_t n)
+{
+    if (!m->Tinf_sched || m->n_sched <= 0) return m->T_inf;
+    return m->Tinf_sched[n < m->n_sched ? n : m->n_sched - 1];
+}
+
+/* Net external nodal heat flow Q_i at step n (Eq. 4, 5, 7 lumped to nodes). */
+static double orc_nodal_Q_n(const orc_model *m, int64_t i, double Ti, int64_t n)
 {
     const double a = Ti - m->T_zero, b = m->T_amb - m->T_zero;
-    return m->Qext[i] - m->Ac[i] * m->h * (Ti - m->T_inf)
+    return orc_q_scale(m, n) * m->Qext[i] - m->Ac[i] * m->h * (Ti - orc_T_inf(m, n))
          - m->Ar[i] * ORC_SIGMA * m->eps * (a * a * a * a - b * b * b * b);
+}
+
+/* Net external nodal heat flow Q_i at the first step of a run. */
+double orc_nodal_Q(const orc_model *m, int64_t i, double Ti)
+{
+    return orc_nodal_Q_n(m, i, Ti, m->sched_step0);
 }
 
 /* dQ_i/dT_i */
@@ -386,7 +411,7 @@ void orc_run(const orc_model *m, double dt, int64_t nsteps, double *T, double *e
                 B += dt * F[i];
                 continue;
             }
-            const double Q = orc_nodal_Q(m, i, T[i]);
+            const double Q = orc_nodal_Q_n(m, i, T[i], m->sched_step0 + n);
             const double Ci = m->C0[i] * (1.0 + m->c_lin * (T[i] - m->T_ref));
             const double Tn = T[i] + dt / Ci * (Q - F[i]);
             S += Ci * (Tn - T[i]);
@@ -471,7 +496,8 @@ void orc_dt_crit(const orc_model *m, double T_lo, double T_hi, double tol, int64
  *   lambda_j^n = dL/dT_j^n + lambda_j^{n+1} (1 + a_j'(T_j) R_j) + mu_j dQ_j/dT_j
  *              - sum_{e∋j} theta_e [ f_k,e (K0_e mu_e)_j + (mu_e . K0_e T_e) k_lin / npe ],
  *   R_j = Q_j - F_j,  a_j' = -a_j c_lin / f_c(T_j),
- *   dL/dtheta_e = -sum_n f_k,e mu_e . K0_e T_e^n,   dL/ds_e = sum_n sum_{i in e} mu_i w_ie.
+ *   dL/dtheta_e = -sum_n f_k,e mu_e . K0_e T_e^n,
+ *   dL/ds_e = sum_n q_scale(n) sum_{i in e} mu_i w_ie (q_scale = 1 without a load schedule).
  * T0 [nn]: initial state (Dirichlet imposed); dLdtrace [n/sample_every][ns];
  * outputs g_theta [ne], g_source [ne] (overwritten); trace_out optional forward trace.
  */
@@ -485,7 +511,9 @@ void orc_adjoint(const orc_model *m, double dt, int64_t nsteps, const double *T0
     memcpy(states, T0, nn * sizeof(double));
     for (int64_t n = 0; n < nsteps; ++n) {
         memcpy(states + (n + 1) * nn, states + n * nn, nn * sizeof(double));
-        orc_run(m, dt, 1, states + (n + 1) * nn, NULL, NULL, 0, 0, NULL);
+        orc_model mn = *m;
+        mn.sched_step0 = m->sched_step0 + n;
+        orc_run(&mn, dt, 1, states + (n + 1) * nn, NULL, NULL, 0, 0, NULL);
     }
     double *lam = (double *)calloc(nn, sizeof(double));
     double *lnew = (double *)malloc(nn * sizeof(double));
@@ -509,11 +537,12 @@ void orc_adjoint(const orc_model *m, double dt, int64_t nsteps, const double *T0
             }
             const double fc = 1.0 + m->c_lin * (T[i] - m->T_ref);
             const double a = dt / (m->C0[i] * fc);
-            const double R = orc_nodal_Q(m, i, T[i]) - F[i];
+            const int64_t step = m->sched_step0 + n - 1;
+            const double R = orc_nodal_Q_n(m, i, T[i], step) - F[i];
             const double da = -a * m->c_lin / fc;
             mu[i] = a * lam[i];
             lnew[i] = lam[i] * (1.0 + da * R) + mu[i] * orc_nodal_dQ(m, i, T[i]);
-            musum[i] += mu[i];
+            musum[i] += orc_q_scale(m, step) * mu[i];  /* d Q_i / d s_e = q_scale w_ie */
         }
         for (int64_t e = 0; e < ne; ++e) {
             const int32_t *c = m->conn + npe * e;

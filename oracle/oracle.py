@@ -50,7 +50,9 @@ class _Model(C.Structure):
                 ("C0", C.c_void_p), ("Qext", C.c_void_p), ("Ac", C.c_void_p), ("Ar", C.c_void_p),
                 ("isdir", C.c_void_p), ("k_lin", C.c_double), ("c_lin", C.c_double),
                 ("h", C.c_double), ("T_inf", C.c_double), ("eps", C.c_double),
-                ("T_amb", C.c_double), ("T_zero", C.c_double), ("T_ref", C.c_double)]
+                ("T_amb", C.c_double), ("T_zero", C.c_double), ("T_ref", C.c_double),
+                ("q_sched", C.c_void_p), ("Tinf_sched", C.c_void_p), ("n_sched", C.c_int64),
+                ("sched_step0", C.c_int64)]
 
 
 def lib():
@@ -180,6 +182,22 @@ class OracleModel:
                         h=float(p.h), T_inf=float(p.T_inf), eps=float(p.eps), T_amb=float(p.T_amb),
                         T_zero=float(p.T_zero), T_ref=float(getattr(mats[0], "T_ref", 0.0)))
         self.mref = C.byref(self.m)
+        self._sched = (None, None)
+        if getattr(p, "q_schedule", None) is not None or getattr(p, "Tinf_schedule", None) is not None:
+            self.set_schedule(getattr(p, "q_schedule", None), getattr(p, "Tinf_schedule", None))
+
+    def set_schedule(self, q_scale=None, T_inf=None):
+        """Time-dependent loads: at step n the external loads are q_scale[n] Qext and the
+        convection ambient temperature is T_inf[n] (the last entry beyond the end)."""
+        q = _f64(q_scale)
+        t = _f64(T_inf)
+        lens = {len(a) for a in (q, t) if a is not None}
+        if len(lens) > 1:
+            raise ValueError("q_scale and T_inf must have the same length")
+        self._sched = (q, t)
+        self.m.q_sched = None if q is None else q.ctypes.data
+        self.m.Tinf_sched = None if t is None else t.ctypes.data
+        self.m.n_sched = lens.pop() if lens else 0
 
     # lumped thermal mass at f_c = 1 (Section 3.1, Eq. 14 / 21)
     @property
@@ -197,8 +215,10 @@ class OracleModel:
         L = lib()
         return np.array([L.orc_nodal_Q(self.mref, i, float(T[i])) for i in range(len(T))])
 
-    def run(self, T, dt, nsteps, energy=False, sensors=None, sample_every=0):
-        """n explicit steps from T (copied); returns T (and per-step energy [n,2], trace)."""
+    def run(self, T, dt, nsteps, energy=False, sensors=None, sample_every=0, step0=0):
+        """n explicit steps from T (copied), the first being step `step0` of the load schedule;
+        returns T (and per-step energy [n,2], trace)."""
+        self.m.sched_step0 = int(step0)
         T = np.array(T, dtype=np.float64, copy=True)
         E = np.zeros((nsteps, 2)) if energy else None
         sens = _i32(sensors)
@@ -224,6 +244,7 @@ class OracleModel:
 
     def adjoint(self, dt, nsteps, T0, sensors, sample_every, dLdtrace):
         """(dL/dtheta [E], dL/dsource [E]) for a loss of the sensor trace."""
+        self.m.sched_step0 = 0
         T0 = _f64(T0)
         sens = _i32(sensors)
         g = _f64(dLdtrace)

@@ -37,6 +37,7 @@ constexpr double kSigma = 5.67e-8;
 struct AdjPhys {
     double k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero;
     double k_a, c_a;  // f_k = k_a + k_lin T, f_c = c_a + c_lin T
+    double qs;        // external-load multiplier of the step (time-dependent loads)
 };
 
 int nblk(int64_t n, int bs = 256)
@@ -58,13 +59,13 @@ __global__ void k_gather_sensors(int ns, const int32_t *sens, const R *T, const 
 // mu_i = a_i lambda_i, a_i = A_i / f_c(T_i) (A = 0 on Dirichlet nodes); musum += mu
 template <typename R>
 __global__ void k_adj_mu(int64_t nn, const R *Tn, const double *A, const double *lam, double c_a, double c_lin,
-                         double *mu, double *musum)
+                         double qs, double *mu, double *musum)
 {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
         const double t = (double)Tn[g];
         const double m = A[g] / (c_a + c_lin * t) * lam[g];
         mu[g] = m;
-        musum[g] += m;
+        musum[g] += qs * m;  // d Q_g / d s_e = qs w_ge
     }
 }
 
@@ -131,7 +132,7 @@ __global__ void k_adj_node(int64_t nn, int npe, const int32_t *n2e_ptr, const in
         const double fc = ph.c_a + ph.c_lin * t;
         const double a = A[g] / fc;
         const double u = t - ph.T_zero, b = ph.T_amb - ph.T_zero;
-        const double Q = Qext[g] - Ac[g] * ph.h * (t - ph.T_inf) - Ar[g] * ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
+        const double Q = ph.qs * Qext[g] - Ac[g] * ph.h * (t - ph.T_inf) - Ar[g] * ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
         const double dQ = -Ac[g] * ph.h - Ar[g] * ph.eps_sigma * 4.0 * u * u * u;
         const double d = -a * ph.c_lin / fc * (Q - F);
         lam_out[g] = lam[g] * (1.0 + d) + mu[g] * dQ - G;
@@ -297,7 +298,7 @@ extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, 
     CKR(cudaMemsetAsync(lam[0], 0, nn * 8, c->stream), "memset");
     CKR(cudaMemsetAsync(musum, 0, nn * 8, c->stream), "memset");
     CKR(cudaMemsetAsync(gth, 0, ne * 8, c->stream), "memset");
-    const AdjPhys ph{c->k_lin, c->c_lin, c->h, c->T_inf, c->eps * kSigma, c->T_amb, c->T_zero, c->k_a(), c->c_a()};
+    AdjPhys ph{c->k_lin, c->c_lin, c->h, c->T_inf, c->eps * kSigma, c->T_amb, c->T_zero, c->k_a(), c->c_a(), 1.0};
     int cur = 0;
     for (int64_t k = n_ckpt - 1; k >= 0; --k) {
         // recompute the segment from its checkpoint, recording T^n for every step
@@ -314,8 +315,10 @@ extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, 
             if (rel % se == 0)
                 k_adj_inject<<<nblk(ns), 256, 0, c->stream>>>(ns, c->d_sensors, d_dl + (rel / se - 1) * ns, lam[cur]);
             const void *Tn = (const uint8_t *)rec + (size_t)s * nn * rs;
+            ph.T_inf = c->Tinf_at(step_k + s);  // loads of the step from T^n, n = step_k + s
+            ph.qs = c->qs_at(step_k + s);
             if (c->precision == 64) {
-                k_adj_mu<double><<<nblk(nn), 256, 0, c->stream>>>(nn, (const double *)Tn, c->d_A, lam[cur], c->c_a(), c->c_lin, mu, musum);
+                k_adj_mu<double><<<nblk(nn), 256, 0, c->stream>>>(nn, (const double *)Tn, c->d_A, lam[cur], c->c_a(), c->c_lin, ph.qs, mu, musum);
                 if (npe == 8)
                     k_adj_elem<8, double><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const double *)Tn, mu,
                                                                            c->d_kscale, c->k_a(), c->k_lin, YF, YG, gth);
@@ -326,7 +329,7 @@ extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, 
                                                                    lam[cur], mu, c->d_A, c->d_Qext64, c->d_Ac64, c->d_Ar64,
                                                                    c->d_isdir, ph, lam[cur ^ 1]);
             } else {
-                k_adj_mu<float><<<nblk(nn), 256, 0, c->stream>>>(nn, (const float *)Tn, c->d_A, lam[cur], c->c_a(), c->c_lin, mu, musum);
+                k_adj_mu<float><<<nblk(nn), 256, 0, c->stream>>>(nn, (const float *)Tn, c->d_A, lam[cur], c->c_a(), c->c_lin, ph.qs, mu, musum);
                 if (npe == 8)
                     k_adj_elem<8, float><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const float *)Tn, mu,
                                                                           c->d_kscale, c->k_a(), c->k_lin, YF, YG, gth);

@@ -24,6 +24,20 @@ struct fedfem_ctx {
     double c_a() const { return 1.0 - c_lin * T_ref; }
     double fk(double T) const { return 1.0 + k_lin * (T - T_ref); }
     double fc(double T) const { return 1.0 + c_lin * (T - T_ref); }
+    // time-dependent loads: at step n the external loads are sched_q[n] Q_ext and the
+    // convection ambient temperature is sched_Tinf[n] (last entry beyond the end)
+    std::vector<double> sched_q, sched_Tinf;
+    double *d_sched_q = nullptr, *d_sched_Tinf = nullptr;
+    int64_t sched_len = 0, sched_cap = 0;
+    double qs_at(int64_t n) const
+    {
+        return sched_q.empty() ? 1.0 : sched_q[(size_t)std::max<int64_t>(0, std::min<int64_t>(n, sched_len - 1))];
+    }
+    double Tinf_at(int64_t n) const
+    {
+        return sched_Tinf.empty() ? T_inf
+                                  : sched_Tinf[(size_t)std::max<int64_t>(0, std::min<int64_t>(n, sched_len - 1))];
+    }
     fedfem_options opt;
     int precision = 32, kahan = 1;
 

@@ -768,6 +768,9 @@ StepArgs step_args(fedfem_ctx *c)
     // smaller meshes keep it cached from step to step
     const bool big = (int64_t)c->til.n_chunks * c->chunk_bytes > (64LL << 20);
     a.l2_stream_policy = c->opt.l2_policy == 2 || (c->opt.l2_policy == 0 && big) ? 1 : 0;
+    a.sched_q = c->sched_q.empty() ? nullptr : c->d_sched_q;
+    a.sched_Tinf = c->sched_Tinf.empty() ? nullptr : c->d_sched_Tinf;
+    a.sched_len = c->sched_len;
     a.scatter = c->opt.scatter;
     a.withhold = c->opt.debug_withhold_barrier;
     a.timeout_ns = (long long)(c->opt.barrier_timeout_s * 1e9);
@@ -856,7 +859,9 @@ extern "C" fedfem_status fedfem_energy(fedfem_ctx *c, double *stored_change, dou
     if (s != FEDFEM_OK) return s;
     launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, T0, T0, c->k_a(), c->k_lin, c->d_Y, F,
                  c->stream);
-    EnergyPhys ph{c->dt, c->c_lin, c->h, c->T_inf, c->eps * 5.67e-8, c->T_amb, c->T_zero, c->c_a()};
+    // the step from T^(n-1) to T^n with the loads of step n - 1
+    EnergyPhys ph{c->dt, c->c_lin, c->h, c->Tinf_at(c->step - 1), c->eps * 5.67e-8, c->T_amb, c->T_zero, c->c_a(),
+                  c->qs_at(c->step - 1)};
     double *partial = c->d_red, *sums = c->d_red + 2 * 1024;
     launch_energy(c->nn, T0, T1, F, c->d_C0, c->d_Qext64, c->d_Ac64, c->d_Ar64, c->d_isdir, ph, partial, sums, c->stream);
     CK(cudaGetLastError(), "energy");
@@ -865,6 +870,39 @@ extern "C" fedfem_status fedfem_energy(fedfem_ctx *c, double *stored_change, dou
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     *stored_change = h2[0];
     *boundary_in = h2[1];
+    return FEDFEM_OK;
+}
+
+extern "C" fedfem_status fedfem_set_schedule(fedfem_ctx *c, int64_t n_entries, const double *q_scale,
+                                             const double *T_inf)
+{
+    if (!c) return FEDFEM_ERR_ARG;
+    if (n_entries < 0) return fail(c, FEDFEM_ERR_ARG, "n_entries < 0");
+    if (!c->group_elem.empty()) return fail(c, FEDFEM_ERR_UNSUPPORTED, "load schedules are not available for batches");
+    if (n_entries > 0 && !q_scale && !T_inf) return fail(c, FEDFEM_ERR_ARG, "no schedule array given");
+    for (int64_t i = 0; i < n_entries; ++i)
+        if ((q_scale && !std::isfinite(q_scale[i])) || (T_inf && !std::isfinite(T_inf[i])))
+            return fail(c, FEDFEM_ERR_ARG, "non-finite schedule entry");
+    c->sched_q.clear();
+    c->sched_Tinf.clear();
+    c->sched_len = 0;
+    if (n_entries == 0) return FEDFEM_OK;
+    if (n_entries > c->sched_cap) {
+        CK(dalloc(c, (void **)&c->d_sched_q, n_entries * 8), "alloc schedule");
+        CK(dalloc(c, (void **)&c->d_sched_Tinf, n_entries * 8), "alloc schedule");
+        c->sched_cap = n_entries;
+    }
+    // the stream may still run steps that read the previous schedule
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    if (q_scale) {
+        c->sched_q.assign(q_scale, q_scale + n_entries);
+        CK(cudaMemcpy(c->d_sched_q, q_scale, n_entries * 8, cudaMemcpyHostToDevice), "upload schedule");
+    }
+    if (T_inf) {
+        c->sched_Tinf.assign(T_inf, T_inf + n_entries);
+        CK(cudaMemcpy(c->d_sched_Tinf, T_inf, n_entries * 8, cudaMemcpyHostToDevice), "upload schedule");
+    }
+    c->sched_len = n_entries;
     return FEDFEM_OK;
 }
 

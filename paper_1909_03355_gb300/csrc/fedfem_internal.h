@@ -112,6 +112,10 @@ struct StepArgs {
     const int32_t *nbr_ptr;     // tile neighbours (CSR over tiles)
     const int32_t *nbr;
     int32_t *err;               // device error word
+    // time-dependent loads (NULL: constant): external-load multiplier and convection ambient
+    // temperature per global step, the last entry held beyond sched_len
+    const double *sched_q, *sched_Tinf;
+    int64_t sched_len;
     // physics: one table entry per scenario, selected by TileInfo::scenario
     const PhysParams *phys;
     // CTA c processes tiles [cta_tile[c], cta_tile[c + 1]) (NULL: tiles_per_cta consecutive tiles)

@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(256) k_energy_terms(int64_t nn, const double *
         }
         const double t = T0[g];
         const double u = t - ph.T_zero, b = ph.T_amb - ph.T_zero;
-        const double Q = Qext[g] - Ac[g] * ph.h * (t - ph.T_inf) - Ar[g] * ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
+        const double Q = ph.qs * Qext[g] - Ac[g] * ph.h * (t - ph.T_inf) - Ar[g] * ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
         S += C0[g] * (ph.c_a + ph.c_lin * t) * (T1[g] - t);
         B += ph.dt * Q;
     }

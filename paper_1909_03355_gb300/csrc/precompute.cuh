@@ -43,6 +43,7 @@ struct NodeArgs {
 struct EnergyPhys {
     double dt, c_lin, h, T_inf, eps_sigma, T_amb, T_zero;
     double c_a;  // f_c = c_a + c_lin T
+    double qs;   // multiplier of the external loads (time-dependent loads)
 };
 
 void launch_elem(int npe, const ElemArgs &a, cudaStream_t st);

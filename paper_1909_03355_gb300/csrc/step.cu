@@ -427,13 +427,31 @@ __device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int la
 template <typename R>
 struct Phys {
     R k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero, T_guard, k_a, c_a;
+    R qs, qs_prev;  // external-load multiplier of this step and of the previous one
     Phys() = default;
     __device__ explicit Phys(const PhysParams &p)
         : k_lin((R)p.k_lin), c_lin((R)p.c_lin), h((R)p.h), T_inf((R)p.T_inf), eps_sigma((R)p.eps_sigma),
-          T_amb((R)p.T_amb), T_zero((R)p.T_zero), T_guard((R)p.T_guard), k_a((R)p.k_a), c_a((R)p.c_a)
+          T_amb((R)p.T_amb), T_zero((R)p.T_zero), T_guard((R)p.T_guard), k_a((R)p.k_a), c_a((R)p.c_a), qs((R)1),
+          qs_prev((R)1)
     {
     }
 };
+
+// Time-dependent loads of global step n: the load multiplier of steps n and n - 1 (the halo
+// nodes are finished for step n - 1) and the convection ambient temperature of step n.
+template <typename R>
+__device__ __forceinline__ void apply_schedule(Phys<R> &ph, const StepArgs &a, long long n)
+{
+    if (a.sched_len <= 0) return;
+    const long long L = a.sched_len - 1;
+    const long long i = n < L ? n : L;
+    const long long ip = n - 1 < 0 ? 0 : (n - 1 < L ? n - 1 : L);
+    if (a.sched_q) {
+        ph.qs = (R)a.sched_q[i];
+        ph.qs_prev = (R)a.sched_q[ip];
+    }
+    if (a.sched_Tinf) ph.T_inf = (R)a.sched_Tinf[i];
+}
 
 // A_i = dt / C0_i: FP64 in the FP64 form; in the FP32 form the FP64 value is kept as an
 // unevaluated pair of floats (hi + lo, 48 significant bits) and A q is formed with one FMA and
@@ -579,7 +597,7 @@ __device__ __forceinline__ R halo_finish(const HaloIn<R> &h, const R *part, cons
     F += h.p[0];
     F += h.p[1];
     for (int q = 2; q < h.cnt; ++q) F += ld_cg(part + h.z + q);
-    return node_update<R, KAHAN>(h.T, h.cp, h.A, h.Q, F, ph, cn, err);
+    return node_update<R, KAHAN>(h.T, h.cp, h.A, h.Q * ph.qs_prev, F, ph, cn, err);
 }
 
 // Shared-memory layout: [stages][chunk_bytes] ring | MBAR_BYTES of mbarriers (full[S], empty[S],
@@ -677,6 +695,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
             if (tid == 0) {
                 s_ti = a.tiles[t];
                 s_ph = Phys<R>(a.phys[s_ti.scenario]);
+                apply_schedule(s_ph, a, a.n0 + s);
             }
             csync(NC);
             const TileInfo &ti = s_ti;
@@ -858,7 +877,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                             for (int e = 0; e < 4; ++e) {
                                 float cn;
                                 out.v[e] = node_update<R, KAHAN>(Ts[l + e], KAHAN ? (float)cpv[u].v[e] : 0.0f, Av[u][e],
-                                                                  Qv[u].v[e], Fs[l + e], ph, cn, a.err);
+                                                                  Qv[u].v[e] * ph.qs, Fs[l + e], ph, cn, a.err);
                                 cout.v[e] = (R)cn;
                             }
                             store4<R>(Tn + g, out);
@@ -871,7 +890,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                     const int g = nb + l;
                     float cn;
                     const R v = node_update<R, KAHAN>(Ts[l], KAHAN ? ld_cg(a.comp[cur] + g) : 0.0f, load_A<R>(a, g),
-                                                      Qext[g], Fs[l], ph, cn, a.err);
+                                                      Qext[g] * ph.qs, Fs[l], ph, cn, a.err);
                     Tn[g] = v;
                     if (KAHAN) a.comp[nxt][g] = cn;
                 }
@@ -894,7 +913,8 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                 break;
             }
             const TileInfo ti = a.tiles[t];
-            const Phys<R> ph(a.phys[ti.scenario]);
+            Phys<R> ph(a.phys[ti.scenario]);
+            apply_schedule(ph, a, n);  // qs_prev: the loads of step n - 1
             for (int q = tid; q < ti.sh_count; q += NC) {
                 const int4 sh = a.sh[ti.sh_begin + q];
                 if ((sh.w >> 16) != 0) continue;

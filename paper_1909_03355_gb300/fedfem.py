@@ -111,6 +111,19 @@ class FedFem:
         self.n_nodes = problem.n_nodes
         self.n_elems = problem.n_elems
         self.precision = precision
+        q, t = getattr(problem, "q_schedule", None), getattr(problem, "Tinf_schedule", None)
+        if q is not None or t is not None:
+            self.set_schedule(q, t)
+
+    def set_schedule(self, q_scale=None, T_inf=None):
+        """Time-dependent loads: at step n the external loads are q_scale[n] Q_ext and the
+        convection ambient temperature is T_inf[n] (the last entries hold beyond the end)."""
+        q, t = _f64(q_scale), _f64(T_inf)
+        n = len(q) if q is not None else (len(t) if t is not None else 0)
+        if q is not None and t is not None and len(t) != n:
+            raise ValueError("q_scale and T_inf must have the same length")
+        self._sched = (q, t)
+        self._ck(self.L.fedfem_set_schedule(self.h, n, _ptr(q), _ptr(t)))
 
     # -- errors
     def _ck(self, st):

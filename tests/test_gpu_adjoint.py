@@ -26,12 +26,17 @@ def small_setup(kind="hex", n=4):
     return p, sensors
 
 
-@pytest.mark.parametrize("kind,T_ref", [("hex", 0.0), ("tet", 0.0), ("hex", 60.0)])
-def test_adjoint_matches_oracle_adjoint_fp64(kind, T_ref):
+@pytest.mark.parametrize("kind,T_ref,scheduled", [("hex", 0.0, False), ("tet", 0.0, False), ("hex", 60.0, False),
+                                                   ("hex", 0.0, True)])
+def test_adjoint_matches_oracle_adjoint_fp64(kind, T_ref, scheduled):
     p, sensors = small_setup(kind)
     if T_ref:  # laws given at a reference temperature (Section 4.2.2 form)
         m0 = p.mats[0]
         p.mats[0] = fi.Material(m0.rho, m0.k0, m0.k_lin, m0.c0, m0.c_lin, T_ref=T_ref)
+    if scheduled:  # time-dependent loads: the source gradient carries q(n)
+        k = np.arange(45)
+        p.q_schedule = 1.0 + 0.6 * np.cos(0.2 * k)
+        p.Tinf_schedule = 20.0 + 3.0 * k
     m = O.OracleModel(p)
     dt = 0.9 * m.dt_crit()[0]
     nsteps, se, ck = 60, 10, 20

@@ -208,6 +208,45 @@ def test_paper_cube_full_run(precision):
     assert rel(run_gpu(p, 0.005, 2000, precision), T_ref) <= TOL[precision]
 
 
+def _scheduled_cube():
+    p = fi.nonlinear_cube(9, "hex", jitter=0.2)
+    n = 250
+    k = np.arange(n)
+    p.q_schedule = 1.0 + 0.7 * np.sin(0.05 * k) + k / n
+    p.Tinf_schedule = 20.0 + 200.0 * (k / n) ** 2
+    return p
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_time_dependent_loads(precision):
+    """Load multiplier and convection ambient temperature per step (last entries held beyond
+    the schedule): GPU against the oracle over 300 steps, with launches of 37 steps and the run
+    split across two calls, so the schedule is indexed by the global step everywhere."""
+    p = _scheduled_cube()
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    T_ref = m.run(p.initial_T(), dt, 300)
+    assert rel(T_ref, O.OracleModel(fi.nonlinear_cube(9, "hex", jitter=0.2)).run(p.initial_T(), dt, 300)) > 1e-3
+    f = FedFem(p, precision=precision, steps_per_launch=37)
+    f.precompute()
+    f.set_dt(dt, force=True)
+    f.set_T(p.initial_T())
+    f.step(123)
+    f.step(177)
+    assert rel(f.get_T(), T_ref) <= TOL[precision]
+    # energy terms of the last step use the loads of that step
+    _, E = m.run(p.initial_T(), dt, 300, energy=True)
+    S, B = f.energy()
+    if precision == 64:
+        assert S == pytest.approx(E[-1, 0], rel=1e-8) and B == pytest.approx(E[-1, 1], rel=1e-8)
+    f.set_schedule(None, None)  # removing the schedule restores constant loads
+    f.set_T(p.initial_T())
+    f.step(50)
+    T_c = O.OracleModel(fi.nonlinear_cube(9, "hex", jitter=0.2)).run(p.initial_T(), dt, 50)
+    assert rel(f.get_T(), T_c) <= TOL[precision]
+    f.close()
+
+
 def test_inverted_element_reported():
     p = fi.plain_cube(3)
     p.conn = p.conn.copy()

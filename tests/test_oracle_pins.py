@@ -360,6 +360,36 @@ def test_single_brick_nodal_loads():
     assert np.allclose(T, 5.0 + 7 * 0.01 * 0.7 / Cn, rtol=1e-14)
 
 
+def test_single_brick_time_dependent_loads():
+    """Load schedule on the single brick: a nodal heat flow scaled by q(n) and a convection
+    ambient temperature T_inf(n) at step n (the last entry held beyond the end) follow the
+    scalar forward-Euler recurrence with the same per-step values; a run split in two with
+    step0 continues the schedule."""
+    a, b, c = 0.3, 0.5, 0.7
+    rho, c0, cl = 800.0, 900.0, 0.002
+    hc = 40.0
+    p = fi.single_brick(a, b, c, rho, c0, cl, T0=100.0, conv=(hc, 15.0))
+    p.nodal_Q = np.full(8, 3.0)
+    n = 150
+    steps = np.arange(n)
+    p.q_schedule = 1.0 + 0.5 * np.sin(0.1 * steps)
+    p.Tinf_schedule = 15.0 + 30.0 * (steps / n)
+    m = O.OracleModel(p)
+    A = (a * b + b * c + c * a) / 4.0
+    Cn = rho * c0 * a * b * c / 8.0
+    dt = 0.5
+    T = m.run(p.initial_T(), dt, n + 40)
+    s = 100.0
+    for k in range(n + 40):
+        j = min(k, n - 1)
+        q = p.q_schedule[j] * 3.0 - A * hc * (s - p.Tinf_schedule[j])
+        s = s + dt / (Cn * (1 + cl * s)) * q
+    assert np.max(np.abs(T - s)) <= 1e-12 * abs(s)
+    T1 = m.run(p.initial_T(), dt, 70)
+    T2 = m.run(T1, dt, n + 40 - 70, step0=70)
+    assert np.max(np.abs(T2 - T)) <= 1e-13 * abs(s)
+
+
 @pytest.mark.parametrize("kind", ["hex", "tet"])
 def test_surface_area_shares_sum_to_face_areas(kind):
     """Nodal-quadrature lumping keeps the total area: sum A^c = 1 (top), sum A^r = 4 (sides)."""
@@ -424,9 +454,15 @@ def _adjoint_setup():
     return p, sensors
 
 
-def test_adjoint_matches_central_differences():
-    """Reverse-time adjoint vs central finite differences of the forward loop (FP64)."""
+@pytest.mark.parametrize("scheduled", [False, True])
+def test_adjoint_matches_central_differences(scheduled):
+    """Reverse-time adjoint vs central finite differences of the forward loop (FP64); also
+    with a load schedule (q(n) scales the sources, T_inf(n) moves)."""
     p, sensors = _adjoint_setup()
+    if scheduled:
+        k = np.arange(30)
+        p.q_schedule = 1.0 + 0.8 * np.cos(0.3 * k)
+        p.Tinf_schedule = 20.0 + 2.0 * k
     m0 = O.OracleModel(p)
     dt = 0.9 * m0.dt_crit()[0]
     nsteps, se = 30, 5
