@@ -8,7 +8,7 @@
 // kernel over that prefix, with CTA -> tile ranges balanced by element count.  Each tile
 // carries its scenario's physical constants (a per-scenario table) and each node its
 // scenario's time step (folded into A = dt / C0).  The critical step of every scenario comes
-// from an FP64 power iteration segmented by scenario.  The whole launch sequence is captured
+// from FP64 Lanczos segmented by scenario.  The whole launch sequence is captured
 // once in a CUDA graph and replayed by fedfem_batch_run; %globaltimer stamps at the phase ends
 // give each scenario's completion time.
 #include <cuda_runtime.h>
@@ -72,46 +72,63 @@ __global__ void k_set_A_nodes(int64_t nn, const double *dtn, const double *C0, c
     }
 }
 
-// Power iteration, one block per scenario over its contiguous node range: z = F / sqrt(C0)
-// on free nodes, sums (x . z, z . z).
-__global__ void __launch_bounds__(256) k_seg_dots(const int64_t *nr, const double *x, const double *F,
-                                                  const double *C0, const uint8_t *isdir, double *z, double *sums)
+// Fixed-order sum over a block of 256 threads; the result is valid in thread 0.
+__device__ double block_sum1(double a, double *red)
 {
-    __shared__ double red[16];
-    const int p = blockIdx.x;
-    double a = 0.0, b = 0.0;
-    for (int64_t g = nr[p] + threadIdx.x; g < nr[p + 1]; g += blockDim.x) {
-        const double v = isdir[g] ? 0.0 : F[g] / sqrt(C0[g]);
-        z[g] = v;
-        a += x[g] * v;
-        b += v * v;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        red[2 * (threadIdx.x >> 5)] = a;
-        red[2 * (threadIdx.x >> 5) + 1] = b;
-    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double sa = 0.0, sb = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            sa += red[2 * w];
-            sb += red[2 * w + 1];
-        }
-        sums[2 * p] = sa;
-        sums[2 * p + 1] = sb;
-    }
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    return s;
 }
 
-__global__ void __launch_bounds__(256) k_seg_normalize(const int64_t *nr, const double *z, const double *sums,
-                                                       double *x)
+// Lanczos steps for the largest eigenvalue of C0^-1/2 K0 C0^-1/2 of every scenario, one block
+// per scenario over its node range (vectors zero on Dirichlet nodes): w = C0^-1/2 F -
+// beta_{j-1} v_{j-1} written over F and alpha_j = w . v_j; then w -= alpha_j v_j and
+// beta_j^2 = w . w; then v_{j+1} = w / beta_j.  Coefficients per scenario: [p].
+__global__ void __launch_bounds__(256) k_seg_lz_w(const int64_t *nr, double *F, const double *C0, const uint8_t *isdir,
+                                                  const double *vprev, const double *beta2_prev, const double *vcur,
+                                                  double *alpha)
+{
+    __shared__ double red[8];
+    const int p = blockIdx.x;
+    const double b = beta2_prev ? sqrt(beta2_prev[p]) : 0.0;
+    double a = 0.0;
+    for (int64_t g = nr[p] + threadIdx.x; g < nr[p + 1]; g += blockDim.x) {
+        const double w = isdir[g] ? 0.0 : F[g] / sqrt(C0[g]) - (beta2_prev ? b * vprev[g] : 0.0);
+        F[g] = w;
+        a += w * vcur[g];
+    }
+    a = block_sum1(a, red);
+    if (threadIdx.x == 0) alpha[p] = a;
+}
+
+// w -= alpha_j v_j (alpha == NULL: w unchanged); beta2 = w . w
+__global__ void __launch_bounds__(256) k_seg_lz_orth(const int64_t *nr, double *w, const double *vcur,
+                                                     const double *alpha, double *beta2)
+{
+    __shared__ double red[8];
+    const int p = blockIdx.x;
+    const double al = alpha ? alpha[p] : 0.0;
+    double s = 0.0;
+    for (int64_t g = nr[p] + threadIdx.x; g < nr[p + 1]; g += blockDim.x) {
+        const double x = alpha ? w[g] - al * vcur[g] : w[g];
+        if (alpha) w[g] = x;
+        s += x * x;
+    }
+    s = block_sum1(s, red);
+    if (threadIdx.x == 0) beta2[p] = s;
+}
+
+// v_{j+1} = w / beta_j (zero once beta_j underflows: that scenario's Krylov space is exhausted)
+__global__ void __launch_bounds__(256) k_seg_lz_next(const int64_t *nr, const double *w, const double *beta2,
+                                                     double *vnext)
 {
     const int p = blockIdx.x;
-    const double inv = sums[2 * p + 1] > 0.0 ? 1.0 / sqrt(sums[2 * p + 1]) : 0.0;
-    for (int64_t g = nr[p] + threadIdx.x; g < nr[p + 1]; g += blockDim.x) x[g] = z[g] * inv;
+    const double inv = beta2[p] > 1e-280 ? 1.0 / sqrt(beta2[p]) : 0.0;
+    for (int64_t g = nr[p] + threadIdx.x; g < nr[p + 1]; g += blockDim.x) vnext[g] = w[g] * inv;
 }
 
 // Largest linearised surface rate per scenario (one block each).
@@ -306,34 +323,59 @@ static fedfem_status batch_build(fedfem_batch *b, const fedfem_scenario *sc, int
     BCK(balloc(b, (void **)&d_nr, (S + 1) * 8), "alloc");
     BCK(cudaMemcpy(d_nr, nr.data(), (S + 1) * 8, cudaMemcpyHostToDevice), "upload");
 
-    // ---- critical step of every scenario: power iteration segmented by scenario
-    double *x = c->d_v[0], *u = c->d_v[1], *F = c->d_v[2], *z = c->d_v[3];
-    double *sums = nullptr, *surf = nullptr, *coef = nullptr;
-    BCK(balloc(b, (void **)&sums, 2 * S * 8), "alloc");
+    // ---- critical step of every scenario: Lanczos segmented by scenario; the host takes each
+    //      scenario's largest tridiagonal eigenvalue every 16 steps until all have converged
+    //      (relative change < tol) or exhausted their Krylov space
+    double *vcur = c->d_v[0], *vprev = c->d_v[1], *u = c->d_v[2], *F = c->d_v[3];
+    double *surf = nullptr, *coef = nullptr, *lz_a = nullptr, *lz_b = nullptr, *norm2 = nullptr;
+    const int max_iter = c->power_max_iter;
     BCK(balloc(b, (void **)&surf, S * 8), "alloc");
     BCK(balloc(b, (void **)&coef, 3 * S * 8), "alloc");
+    BCK(balloc(b, (void **)&norm2, S * 8), "alloc");
+    BCK(balloc(b, (void **)&lz_a, (size_t)max_iter * S * 8), "alloc");
+    BCK(balloc(b, (void **)&lz_b, (size_t)max_iter * S * 8), "alloc");
     cudaStream_t stm = c->stream;
-    launch_power_init(nn, c->d_isdir, x, stm);
-    std::vector<double> h_sums(2 * S), lam(S, 0.0);
-    const int max_iter = c->power_max_iter;
+    launch_power_init(nn, c->d_isdir, F, stm);
+    k_seg_lz_orth<<<S, 256, 0, stm>>>(d_nr, F, nullptr, nullptr, norm2);
+    k_seg_lz_next<<<S, 256, 0, stm>>>(d_nr, F, norm2, vcur);
+    std::vector<double> lam(S, 0.0), ha, hb, al, b2;
+    std::vector<char> lz_done(S, 0);
     for (int it = 0; it < max_iter; ++it) {
-        launch_scale_free(nn, x, c->d_C0, c->d_isdir, u, stm);
+        launch_scale_free(nn, vcur, c->d_C0, c->d_isdir, u, stm);
         launch_apply(c->npe, c->ne, nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, u, nullptr, 1.0, 0.0, c->d_Y, F, stm);
-        k_seg_dots<<<S, 256, 0, stm>>>(d_nr, x, F, c->d_C0, c->d_isdir, z, sums);
-        k_seg_normalize<<<S, 256, 0, stm>>>(d_nr, z, sums, x);
+        k_seg_lz_w<<<S, 256, 0, stm>>>(d_nr, F, c->d_C0, c->d_isdir, vprev, it ? lz_b + (size_t)(it - 1) * S : nullptr,
+                                       vcur, lz_a + (size_t)it * S);
+        k_seg_lz_orth<<<S, 256, 0, stm>>>(d_nr, F, vcur, lz_a + (size_t)it * S, lz_b + (size_t)it * S);
+        k_seg_lz_next<<<S, 256, 0, stm>>>(d_nr, F, lz_b + (size_t)it * S, vprev);
+        std::swap(vprev, vcur);  // v_{j+1} was written over v_{j-1}
         if ((it & 15) == 15 || it == max_iter - 1) {
-            BCK(cudaMemcpyAsync(h_sums.data(), sums, 2 * S * 8, cudaMemcpyDeviceToHost, stm), "read");
+            const size_t m = (size_t)(it + 1);
+            ha.resize(m * S);
+            hb.resize(m * S);
+            BCK(cudaMemcpyAsync(ha.data(), lz_a, m * S * 8, cudaMemcpyDeviceToHost, stm), "read");
+            BCK(cudaMemcpyAsync(hb.data(), lz_b, m * S * 8, cudaMemcpyDeviceToHost, stm), "read");
             BCK(cudaStreamSynchronize(stm), "synchronize");
-            bool done = it > 16;
+            bool done = true;
+            al.resize(m);
+            b2.resize(m);
             for (int p = 0; p < S; ++p) {
-                const double rq = h_sums[2 * p];
-                if (!(std::fabs(rq - lam[p]) <= c->power_tol * std::fabs(rq))) done = false;
-                lam[p] = rq;
+                if (lz_done[p]) continue;
+                for (size_t j = 0; j < m; ++j) {
+                    al[j] = ha[j * S + p];
+                    b2[j] = hb[j * S + p];
+                }
+                const double theta = tridiag_max_eigenvalue(al, b2, (int)m);
+                const bool exhausted = !(b2[m - 1] > 1e-28 * theta * theta);
+                if (exhausted || (it > 16 && std::fabs(theta - lam[p]) <= c->power_tol * std::fabs(theta)))
+                    lz_done[p] = 1;
+                else
+                    done = false;
+                lam[p] = theta;
             }
             if (done) break;
         }
     }
-    BCK(cudaGetLastError(), "power iteration");
+    BCK(cudaGetLastError(), "Lanczos");
     std::vector<double> h_coef(3 * S), fk_max(S), fc_min(S);
     for (int p = 0; p < S; ++p) {
         const fedfem_scenario &q = sc[b->order[p]];

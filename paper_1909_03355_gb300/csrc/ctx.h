@@ -115,6 +115,9 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c);
 fedfem_status create_ctx(const fedfem_mesh *mesh, const fedfem_material *mats, int32_t n_mats, const fedfem_bcs *bcs,
                          const fedfem_options *opt_in, const std::vector<int64_t> *group_elem, fedfem_ctx **out,
                          std::string &err);
+// Largest eigenvalue of the m x m symmetric tridiagonal matrix with diagonal a and squared
+// off-diagonal b2 (Sturm bisection).
+double tridiag_max_eigenvalue(const std::vector<double> &a, const std::vector<double> &b2, int m);
 fedfem_status check_device(fedfem_ctx *c);
 fedfem_status run_precompute_arrays(fedfem_ctx *c);
 fedfem_status install_T(fedfem_ctx *c, const double *T0_dev_old);

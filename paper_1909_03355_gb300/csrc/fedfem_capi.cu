@@ -240,6 +240,44 @@ static fedfem_status make_plan(fedfem_ctx *c, const std::vector<uint8_t> &is_bnd
 
 namespace fedfem {
 
+// Largest eigenvalue of the m x m symmetric tridiagonal matrix with diagonal a and squared
+// off-diagonal b2 (b2[i] couples rows i and i + 1) by bisection on the Sturm count of the
+// LDL^T pivots (number of eigenvalues below x).
+double tridiag_max_eigenvalue(const std::vector<double> &a, const std::vector<double> &b2, int m)
+{
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < m; ++i) {
+        const double r = (i > 0 ? std::sqrt(b2[i - 1]) : 0.0) + (i + 1 < m ? std::sqrt(b2[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    const double pad = 1e-12 * std::max(std::fabs(lo), std::fabs(hi)) + 1e-300;
+    lo -= pad;
+    hi += pad;
+    auto below = [&](double x) {
+        int n = 0;
+        double d = 1.0;
+        for (int i = 0; i < m; ++i) {
+            d = (a[i] - x) - (i > 0 ? b2[i - 1] / d : 0.0);
+            if (d == 0.0) d = -1e-300;
+            if (d < 0.0) ++n;
+        }
+        return n;
+    };
+    for (int k = 0; k < 200 && hi - lo > 1e-15 * std::max(std::fabs(hi), std::fabs(lo)); ++k) {
+        const double mid = 0.5 * (lo + hi);
+        if (below(mid) >= m)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    return hi;
+}
+
+}  // namespace fedfem
+
+namespace fedfem {
+
 // Host copy of the problem and device set-up; group_elem (optional) packs independent meshes
 // (batched scenarios) whose tiles must not mix.
 fedfem_status create_ctx(const fedfem_mesh *mesh, const fedfem_material *mats, int32_t n_mats, const fedfem_bcs *bcs,
@@ -550,40 +588,6 @@ fedfem_status fedfem::run_precompute_arrays(fedfem_ctx *c)
     return FEDFEM_OK;
 }
 
-// Largest eigenvalue of the m x m symmetric tridiagonal matrix with diagonal a and squared
-// off-diagonal b2 (b2[i] couples rows i and i + 1) by bisection on the Sturm count of the
-// LDL^T pivots (number of eigenvalues below x).
-static double tridiag_max_eigenvalue(const std::vector<double> &a, const std::vector<double> &b2, int m)
-{
-    double lo = 1e300, hi = -1e300;
-    for (int i = 0; i < m; ++i) {
-        const double r = (i > 0 ? std::sqrt(b2[i - 1]) : 0.0) + (i + 1 < m ? std::sqrt(b2[i]) : 0.0);
-        lo = std::min(lo, a[i] - r);
-        hi = std::max(hi, a[i] + r);
-    }
-    const double pad = 1e-12 * std::max(std::fabs(lo), std::fabs(hi)) + 1e-300;
-    lo -= pad;
-    hi += pad;
-    auto below = [&](double x) {
-        int n = 0;
-        double d = 1.0;
-        for (int i = 0; i < m; ++i) {
-            d = (a[i] - x) - (i > 0 ? b2[i - 1] / d : 0.0);
-            if (d == 0.0) d = -1e-300;
-            if (d < 0.0) ++n;
-        }
-        return n;
-    };
-    for (int k = 0; k < 200 && hi - lo > 1e-15 * std::max(std::fabs(hi), std::fabs(lo)); ++k) {
-        const double mid = 0.5 * (lo + hi);
-        if (below(mid) >= m)
-            hi = mid;
-        else
-            lo = mid;
-    }
-    return hi;
-}
-
 extern "C" fedfem_status fedfem_precompute(fedfem_ctx *c, double T_lo, double T_hi, double *dt_crit_out)
 {
     if (!c) return FEDFEM_ERR_ARG;
@@ -618,7 +622,7 @@ extern "C" fedfem_status fedfem_precompute(fedfem_ctx *c, double T_lo, double T_
                 alpha[j] = coef[4 * j];
                 beta2[j] = coef[4 * j + 2];
             }
-            const double theta = tridiag_max_eigenvalue(alpha, beta2, it + 1);
+            const double theta = fedfem::tridiag_max_eigenvalue(alpha, beta2, it + 1);
             const bool exhausted = !(beta2[it] > 1e-28 * theta * theta);
             const bool done = exhausted || (it > 16 && std::fabs(theta - lam) <= tol * std::fabs(theta));
             lam = theta;
