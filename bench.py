@@ -449,7 +449,7 @@ def main():
         torch.cuda.synchronize()
         free_c = torch.cuda.mem_get_info()[0]
         nn_a, ne_a, npe_a = pi.n_nodes, pi.n_elems, pi.npe
-        sweep_tmp = (trc.size * 8 + 100 * nn_a * 4 + 4 * nn_a * 8 + 2 * ne_a * npe_a * 8 + 2 * ne_a * 8)
+        sweep_tmp = (trc.size * 8 + 100 * nn_a * 4 + 4 * nn_a * 8 + 2 * ne_a * npe_a * 8 + 2 * ne_a * 8 + nn_a * 4)
         adj = {"workload": "inverse_32: 32^3 hex, 2000 FP32 steps, 512 sensors every 10 steps, checkpoints every 100",
                "forward_ms": 1e3 * t_fwd, "adjoint_ms": 1e3 * t_adj, "adjoint_over_forward": t_adj / t_fwd,
                "context_device_MB": (free_a - free_b) / 1e6,
@@ -459,7 +459,7 @@ def main():
                "memory_note": "cudaMemGetInfo deltas (2 MB granularity) for the context after precompute and for "
                               "what forward_record + adjoint keep (checkpoints, trace); the reverse sweep's own "
                               "buffers (one segment of states, lambda pair, mu, sum mu, element F/G slots, two "
-                              "gradients, dL/dtrace) are freed on return and counted by size"}
+                              "gradients, dL/dtrace, sensor map) are freed on return and counted by size"}
         fa.close()
 
     # ---- batched scenarios: 256 independent cubes (n ~ U{8..48}, steps ~ U{500..5000}) in one

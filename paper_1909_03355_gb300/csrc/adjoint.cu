@@ -110,11 +110,16 @@ __global__ void k_adj_elem(int64_t ne, const int32_t *gconn, const double *cond6
 }
 
 // Node pass: gather F and G in fixed (ascending element) order and form lambda^n.
+// With Tprev (the state one step earlier) the pass also prepares the next reverse step, as
+// k_adj_inject and k_adj_mu would: lambda^n += dL/dT^n at the sensors (dl_next, sensor index per
+// node), mu = A / f_c(T^(n-1)) lambda^n written over mu (each thread touches only its node),
+// musum += qs_prev mu.
 template <typename R>
 __global__ void k_adj_node(int64_t nn, int npe, const int32_t *n2e_ptr, const int64_t *n2e, const double *YF,
-                           const double *YG, const R *Tn, const double *lam, const double *mu, const double *A,
+                           const double *YG, const R *Tn, const double *lam, double *mu, const double *A,
                            const double *Qext, const double *Ac, const double *Ar, const uint8_t *isdir, AdjPhys ph,
-                           double *lam_out)
+                           double *lam_out, const R *Tprev, const int32_t *sens_idx, const double *dl_next,
+                           double qs_prev, double *musum)
 {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
         double F = 0.0, G = 0.0;
@@ -124,19 +129,34 @@ __global__ void k_adj_node(int64_t nn, int npe, const int32_t *n2e_ptr, const in
             F += YF[s];
             G += YG[s];
         }
+        double l;
         if (isdir[g]) {
-            lam_out[g] = lam[g] - G;
-            continue;
+            l = lam[g] - G;
+        } else {
+            const double t = (double)Tn[g];
+            const double fc = ph.c_a + ph.c_lin * t;
+            const double a = A[g] / fc;
+            const double u = t - ph.T_zero, b = ph.T_amb - ph.T_zero;
+            const double Q = ph.qs * Qext[g] - Ac[g] * ph.h * (t - ph.T_inf) - Ar[g] * ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
+            const double dQ = -Ac[g] * ph.h - Ar[g] * ph.eps_sigma * 4.0 * u * u * u;
+            const double d = -a * ph.c_lin / fc * (Q - F);
+            l = lam[g] * (1.0 + d) + mu[g] * dQ - G;
         }
-        const double t = (double)Tn[g];
-        const double fc = ph.c_a + ph.c_lin * t;
-        const double a = A[g] / fc;
-        const double u = t - ph.T_zero, b = ph.T_amb - ph.T_zero;
-        const double Q = ph.qs * Qext[g] - Ac[g] * ph.h * (t - ph.T_inf) - Ar[g] * ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
-        const double dQ = -Ac[g] * ph.h - Ar[g] * ph.eps_sigma * 4.0 * u * u * u;
-        const double d = -a * ph.c_lin / fc * (Q - F);
-        lam_out[g] = lam[g] * (1.0 + d) + mu[g] * dQ - G;
+        if (Tprev) {
+            if (dl_next && sens_idx[g] >= 0) l += dl_next[sens_idx[g]];
+            const double m = A[g] / (ph.c_a + ph.c_lin * (double)Tprev[g]) * l;
+            mu[g] = m;
+            musum[g] += qs_prev * m;
+        }
+        lam_out[g] = l;
     }
+}
+
+// sens_idx[sensor node] = its index in the sensor list (the array is -1 elsewhere)
+__global__ void k_sensor_index(int ns, const int32_t *sens, int32_t *sens_idx)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < ns) sens_idx[sens[s]] = s;
 }
 
 __global__ void k_adj_inject(int ns, const int32_t *sens, const double *dl, double *lam)
@@ -186,6 +206,29 @@ fedfem_status copy_state(fedfem_ctx *c, int64_t step, uint8_t *dst, bool save)
         if (c->kahan) CK(cudaMemcpyAsync(c->d_comp[b], dst + tb, c->nn * 4, cudaMemcpyDeviceToDevice, c->stream), "restore");
     }
     return FEDFEM_OK;
+}
+
+// One reverse step: mu (only at the first step of a segment; later steps get it from the
+// previous node pass), the element pass and the node pass.
+template <typename R>
+void adj_step(fedfem_ctx *c, bool first, const void *Tn, const void *Tprev, const double *dl_next, double qs_prev,
+              const AdjPhys &ph, const double *lam_in, double *lam_out, double *mu, double *musum, double *YF,
+              double *YG, double *gth, const int32_t *sens_idx)
+{
+    const int64_t nn = c->nn, ne = c->ne;
+    const int npe = c->npe;
+    const R *T = static_cast<const R *>(Tn);
+    if (first)
+        k_adj_mu<R><<<nblk(nn), 256, 0, c->stream>>>(nn, T, c->d_A, lam_in, c->c_a(), c->c_lin, ph.qs, mu, musum);
+    if (npe == 8)
+        k_adj_elem<8, R><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, T, mu, c->d_kscale, c->k_a(),
+                                                         c->k_lin, YF, YG, gth);
+    else
+        k_adj_elem<4, R><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, T, mu, c->d_kscale, c->k_a(),
+                                                         c->k_lin, YF, YG, gth);
+    k_adj_node<R><<<nblk(nn), 256, 0, c->stream>>>(nn, npe, c->d_n2e_ptr, c->d_n2e, YF, YG, T, lam_in, mu, c->d_A,
+                                                   c->d_Qext64, c->d_Ac64, c->d_Ar64, c->d_isdir, ph, lam_out,
+                                                   static_cast<const R *>(Tprev), sens_idx, dl_next, qs_prev, musum);
 }
 
 }  // namespace
@@ -298,6 +341,11 @@ extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, 
     CKR(cudaMemsetAsync(lam[0], 0, nn * 8, c->stream), "memset");
     CKR(cudaMemsetAsync(musum, 0, nn * 8, c->stream), "memset");
     CKR(cudaMemsetAsync(gth, 0, ne * 8, c->stream), "memset");
+    // sensor index of every node (-1 elsewhere) for the injections fused into the node pass
+    int32_t *sens_idx = nullptr;
+    CKR(talloc((void **)&sens_idx, nn * 4), "adjoint buffers");
+    CKR(cudaMemsetAsync(sens_idx, 0xFF, nn * 4, c->stream), "memset");
+    k_sensor_index<<<nblk(ns), 256, 0, c->stream>>>(ns, c->d_sensors, sens_idx);
     AdjPhys ph{c->k_lin, c->c_lin, c->h, c->T_inf, c->eps * kSigma, c->T_amb, c->T_zero, c->k_a(), c->c_a(), 1.0};
     int cur = 0;
     for (int64_t k = n_ckpt - 1; k >= 0; --k) {
@@ -312,34 +360,23 @@ extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, 
         }
         for (int s = K - 1; s >= 0; --s) {
             const int64_t rel = k * K + s + 1;  // steps after the record start of the state T^{n+1}
-            if (rel % se == 0)
+            const int64_t n = step_k + s;       // the step from T^n
+            const bool first = s == K - 1;      // no earlier node pass prepared this step
+            if (first && rel % se == 0)
                 k_adj_inject<<<nblk(ns), 256, 0, c->stream>>>(ns, c->d_sensors, d_dl + (rel / se - 1) * ns, lam[cur]);
             const void *Tn = (const uint8_t *)rec + (size_t)s * nn * rs;
-            ph.T_inf = c->Tinf_at(step_k + s);  // loads of the step from T^n, n = step_k + s
-            ph.qs = c->qs_at(step_k + s);
-            if (c->precision == 64) {
-                k_adj_mu<double><<<nblk(nn), 256, 0, c->stream>>>(nn, (const double *)Tn, c->d_A, lam[cur], c->c_a(), c->c_lin, ph.qs, mu, musum);
-                if (npe == 8)
-                    k_adj_elem<8, double><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const double *)Tn, mu,
-                                                                           c->d_kscale, c->k_a(), c->k_lin, YF, YG, gth);
-                else
-                    k_adj_elem<4, double><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const double *)Tn, mu,
-                                                                           c->d_kscale, c->k_a(), c->k_lin, YF, YG, gth);
-                k_adj_node<double><<<nblk(nn), 256, 0, c->stream>>>(nn, npe, c->d_n2e_ptr, c->d_n2e, YF, YG, (const double *)Tn,
-                                                                   lam[cur], mu, c->d_A, c->d_Qext64, c->d_Ac64, c->d_Ar64,
-                                                                   c->d_isdir, ph, lam[cur ^ 1]);
-            } else {
-                k_adj_mu<float><<<nblk(nn), 256, 0, c->stream>>>(nn, (const float *)Tn, c->d_A, lam[cur], c->c_a(), c->c_lin, ph.qs, mu, musum);
-                if (npe == 8)
-                    k_adj_elem<8, float><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const float *)Tn, mu,
-                                                                          c->d_kscale, c->k_a(), c->k_lin, YF, YG, gth);
-                else
-                    k_adj_elem<4, float><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, (const float *)Tn, mu,
-                                                                          c->d_kscale, c->k_a(), c->k_lin, YF, YG, gth);
-                k_adj_node<float><<<nblk(nn), 256, 0, c->stream>>>(nn, npe, c->d_n2e_ptr, c->d_n2e, YF, YG, (const float *)Tn,
-                                                                  lam[cur], mu, c->d_A, c->d_Qext64, c->d_Ac64, c->d_Ar64,
-                                                                  c->d_isdir, ph, lam[cur ^ 1]);
-            }
+            ph.T_inf = c->Tinf_at(n);
+            ph.qs = c->qs_at(n);
+            // the node pass prepares the next reverse step (the step from T^(n-1)) of this segment
+            const void *Tprev = s > 0 ? (const uint8_t *)rec + (size_t)(s - 1) * nn * rs : nullptr;
+            const double *dl_next = (s > 0 && (rel - 1) % se == 0) ? d_dl + ((rel - 1) / se - 1) * ns : nullptr;
+            const double qs_prev = s > 0 ? c->qs_at(n - 1) : 0.0;
+            if (c->precision == 64)
+                adj_step<double>(c, first, Tn, Tprev, dl_next, qs_prev, ph, lam[cur], lam[cur ^ 1], mu, musum, YF, YG,
+                                 gth, sens_idx);
+            else
+                adj_step<float>(c, first, Tn, Tprev, dl_next, qs_prev, ph, lam[cur], lam[cur ^ 1], mu, musum, YF, YG,
+                                gth, sens_idx);
             cur ^= 1;
         }
         CKR(cudaGetLastError(), "adjoint sweep");
