@@ -209,7 +209,8 @@ fedfem_status copy_state(fedfem_ctx *c, int64_t step, uint8_t *dst, bool save)
 }
 
 // One reverse step: mu (only at the first step of a segment; later steps get it from the
-// previous node pass), the element pass and the node pass.
+// previous node pass), the element pass and the node pass.  Small blocks (64 / 128 threads)
+// spread the few warps of small meshes over all SMs (32^3: 94.7 -> 90.8 ms per adjoint).
 template <typename R>
 void adj_step(fedfem_ctx *c, bool first, const void *Tn, const void *Tprev, const double *dl_next, double qs_prev,
               const AdjPhys &ph, const double *lam_in, double *lam_out, double *mu, double *musum, double *YF,
@@ -219,14 +220,14 @@ void adj_step(fedfem_ctx *c, bool first, const void *Tn, const void *Tprev, cons
     const int npe = c->npe;
     const R *T = static_cast<const R *>(Tn);
     if (first)
-        k_adj_mu<R><<<nblk(nn), 256, 0, c->stream>>>(nn, T, c->d_A, lam_in, c->c_a(), c->c_lin, ph.qs, mu, musum);
+        k_adj_mu<R><<<nblk(nn, 128), 128, 0, c->stream>>>(nn, T, c->d_A, lam_in, c->c_a(), c->c_lin, ph.qs, mu, musum);
     if (npe == 8)
-        k_adj_elem<8, R><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, T, mu, c->d_kscale, c->k_a(),
+        k_adj_elem<8, R><<<nblk(ne, 64), 64, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, T, mu, c->d_kscale, c->k_a(),
                                                          c->k_lin, YF, YG, gth);
     else
-        k_adj_elem<4, R><<<nblk(ne), 128, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, T, mu, c->d_kscale, c->k_a(),
+        k_adj_elem<4, R><<<nblk(ne, 64), 64, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, T, mu, c->d_kscale, c->k_a(),
                                                          c->k_lin, YF, YG, gth);
-    k_adj_node<R><<<nblk(nn), 256, 0, c->stream>>>(nn, npe, c->d_n2e_ptr, c->d_n2e, YF, YG, T, lam_in, mu, c->d_A,
+    k_adj_node<R><<<nblk(nn, 128), 128, 0, c->stream>>>(nn, npe, c->d_n2e_ptr, c->d_n2e, YF, YG, T, lam_in, mu, c->d_A,
                                                    c->d_Qext64, c->d_Ac64, c->d_Ar64, c->d_isdir, ph, lam_out,
                                                    static_cast<const R *>(Tprev), sens_idx, dl_next, qs_prev, musum);
 }
