@@ -177,6 +177,19 @@ fedfem_status fedfem_set_T_device(fedfem_ctx *ctx, const double *T0_dev);
  */
 fedfem_status fedfem_step(fedfem_ctx *ctx, int64_t n_steps);
 
+/*
+ * n_steps explicit steps with the time step adapted per launch (Section 3.4 evaluated on the
+ * run): before every launch of up to steps_per_launch steps the current field's range
+ * [min T - margin, max T + margin] gives dt_crit (lambda_cond from fedfem_precompute, the
+ * f_k / f_c extrema and the surface rate over that range) and dt = safety dt_crit.  Nonlinear
+ * runs whose temperatures leave the range given to fedfem_precompute stay stable without a
+ * guessed upper bound.  *t_elapsed (may be NULL) receives the simulated time.  The context's dt
+ * is the last launch's.  0 < safety <= 1, margin >= 0 (deg C).
+ * Errors: ARG, STATE (no precompute / no T), DIVERGED, TIMEOUT, CUDA.
+ */
+fedfem_status fedfem_step_adaptive(fedfem_ctx *ctx, int64_t n_steps, double safety, double margin,
+                                   double *t_elapsed);
+
 /* Enqueue n_steps on the stream without synchronising; the device status is checked by the
  * next synchronising call (fedfem_sync, fedfem_get_T, fedfem_step).  Errors: STATE, CUDA. */
 fedfem_status fedfem_step_async(fedfem_ctx *ctx, int64_t n_steps);

@@ -438,6 +438,25 @@ void orc_run(const orc_model *m, double dt, int64_t nsteps, double *T, double *e
  *            / (C0_i min f_c),  extrema over [T_lo, T_hi];   dt_crit = 2 / lambda.
  * out[0] = dt_crit, out[1] = lambda_cond, out[2] = iterations used.
  */
+/*
+ * dt_crit = 2 / (lambda_cond max f_k / min f_c + max_i (A^c_i h + A^r_i 4 sigma eps max|T - T_z|^3)
+ * / (C0_i min f_c)) with the extrema over [T_lo, T_hi] (Section 3.4).
+ */
+double orc_dt_from_lambda(const orc_model *m, double lam, double T_lo, double T_hi)
+{
+    const double fk_max = fmax(1.0 + m->k_lin * (T_lo - m->T_ref), 1.0 + m->k_lin * (T_hi - m->T_ref));
+    const double fc_min = fmin(1.0 + m->c_lin * (T_lo - m->T_ref), 1.0 + m->c_lin * (T_hi - m->T_ref));
+    const double rl = fabs(T_lo - m->T_zero), rh = fabs(T_hi - m->T_zero);
+    const double r3 = fmax(rl * rl * rl, rh * rh * rh);
+    double surf = 0.0;
+    for (int64_t i = 0; i < m->nn; ++i) {
+        if (m->isdir[i]) continue;
+        const double s = (m->Ac[i] * m->h + m->Ar[i] * 4.0 * ORC_SIGMA * m->eps * r3) / (m->C0[i] * fc_min);
+        if (s > surf) surf = s;
+    }
+    return 2.0 / (lam * fk_max / fc_min + surf);
+}
+
 void orc_dt_crit(const orc_model *m, double T_lo, double T_hi, double tol, int64_t max_iter, double *out)
 {
     const int64_t nn = m->nn;
@@ -470,17 +489,7 @@ void orc_dt_crit(const orc_model *m, double T_lo, double T_hi, double tol, int64
         lam = rq;
         if (done) break;
     }
-    const double fk_max = fmax(1.0 + m->k_lin * (T_lo - m->T_ref), 1.0 + m->k_lin * (T_hi - m->T_ref));
-    const double fc_min = fmin(1.0 + m->c_lin * (T_lo - m->T_ref), 1.0 + m->c_lin * (T_hi - m->T_ref));
-    const double rl = fabs(T_lo - m->T_zero), rh = fabs(T_hi - m->T_zero);
-    const double r3 = fmax(rl * rl * rl, rh * rh * rh);
-    double surf = 0.0;
-    for (int64_t i = 0; i < nn; ++i) {
-        if (m->isdir[i]) continue;
-        const double s = (m->Ac[i] * m->h + m->Ar[i] * 4.0 * ORC_SIGMA * m->eps * r3) / (m->C0[i] * fc_min);
-        if (s > surf) surf = s;
-    }
-    out[0] = 2.0 / (lam * fk_max / fc_min + surf);
+    out[0] = orc_dt_from_lambda(m, lam, T_lo, T_hi);
     out[1] = lam;
     out[2] = (double)it;
     free(x);

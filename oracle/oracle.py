@@ -75,6 +75,8 @@ def lib():
             L.orc_nodal_Q.restype = C.c_double
             L.orc_run.argtypes = [P, C.c_double, C.c_int64, P, P, P, C.c_int32, C.c_int32, P]
             L.orc_dt_crit.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_int64, P]
+            L.orc_dt_from_lambda.argtypes = [P, C.c_double, C.c_double, C.c_double]
+            L.orc_dt_from_lambda.restype = C.c_double
             L.orc_adjoint.argtypes = [P, C.c_double, C.c_int64, P, P, C.c_int32, C.c_int32, P, P, P]
             _lib = L
     return _lib
@@ -241,6 +243,24 @@ class OracleModel:
         out = np.zeros(3)
         lib().orc_dt_crit(self.mref, float(T_lo), float(T_hi), float(tol), int(max_iter), _p(out))
         return float(out[0]), float(out[1]), int(out[2])
+
+    def dt_from_lambda(self, lam, T_lo, T_hi):
+        """dt_crit of Section 3.4 for a given lambda_cond and temperature range."""
+        return lib().orc_dt_from_lambda(self.mref, float(lam), float(T_lo), float(T_hi))
+
+    def run_adaptive(self, T, nsteps, steps_per_launch, safety, margin, lam=None):
+        """Steps in launches of `steps_per_launch`; before each launch dt = safety dt_crit over
+        [min T - margin, max T + margin] of the current field.  Returns (T, simulated time)."""
+        lam = self.dt_crit()[1] if lam is None else lam
+        T = np.array(T, dtype=np.float64, copy=True)
+        t, done = 0.0, 0
+        while done < nsteps:
+            k = min(steps_per_launch, nsteps - done)
+            dt = safety * self.dt_from_lambda(lam, T.min() - margin, T.max() + margin)
+            T = self.run(T, dt, k, step0=done)
+            t += k * dt
+            done += k
+        return T, t
 
     def adjoint(self, dt, nsteps, T0, sensors, sample_every, dLdtrace):
         """(dL/dtheta [E], dL/dsource [E]) for a loss of the sensor trace."""

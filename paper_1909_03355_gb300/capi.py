@@ -72,6 +72,7 @@ SIGNATURES = {
     "fedfem_set_T": (I32, [P, P]),
     "fedfem_set_T_device": (I32, [P, P]),
     "fedfem_step": (I32, [P, I64]),
+    "fedfem_step_adaptive": (I32, [P, I64, F64, F64, P]),
     "fedfem_step_async": (I32, [P, I64]),
     "fedfem_sync": (I32, [P]),
     "fedfem_get_T": (I32, [P, P]),

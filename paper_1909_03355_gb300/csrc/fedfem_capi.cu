@@ -588,6 +588,28 @@ fedfem_status fedfem::run_precompute_arrays(fedfem_ctx *c)
     return FEDFEM_OK;
 }
 
+// dt_crit of Section 3.4 over [T_lo, T_hi] from the pre-computed lambda_cond: 2 / (lambda_cond
+// max f_k / min f_c + the largest linearised surface rate).
+static fedfem_status crit_step(fedfem_ctx *c, double T_lo, double T_hi, double *dt_crit)
+{
+    const double fk_max = std::max(c->fk(T_lo), c->fk(T_hi));
+    const double fk_min = std::min(c->fk(T_lo), c->fk(T_hi));
+    const double fc_min = std::min(c->fc(T_lo), c->fc(T_hi));
+    if (!(fc_min > 0) || !(fk_min > 0)) return fail(c, FEDFEM_ERR_ARG, "conductivity or heat law not positive on [T_lo, T_hi]");
+    const double rl = std::fabs(T_lo - c->T_zero), rh = std::fabs(T_hi - c->T_zero);
+    const double r3 = std::max(rl * rl * rl, rh * rh * rh);
+    double *partial = c->d_red;
+    const int nb = launch_surface_rate(c->nn, c->d_Ac64, c->d_Ar64, c->d_C0, c->d_isdir, c->h,
+                                       4.0 * 5.67e-8 * c->eps * r3, fc_min, partial, c->stream);
+    std::vector<double> pr(2 * nb);
+    CK(cudaMemcpyAsync(pr.data(), partial, pr.size() * 8, cudaMemcpyDeviceToHost, c->stream), "read");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    double surf = 0.0;
+    for (int b = 0; b < nb; ++b) surf = std::max(surf, pr[2 * b]);
+    *dt_crit = 2.0 / (c->lambda_cond * fk_max / fc_min + surf);
+    return FEDFEM_OK;
+}
+
 extern "C" fedfem_status fedfem_precompute(fedfem_ctx *c, double T_lo, double T_hi, double *dt_crit_out)
 {
     if (!c) return FEDFEM_ERR_ARG;
@@ -632,20 +654,10 @@ extern "C" fedfem_status fedfem_precompute(fedfem_ctx *c, double T_lo, double T_
     CK(cudaGetLastError(), "Lanczos");
     c->lambda_cond = lam;
     c->power_iters = it;
-    const double fk_max = std::max(c->fk(T_lo), c->fk(T_hi));
-    const double fk_min = std::min(c->fk(T_lo), c->fk(T_hi));
-    const double fc_min = std::min(c->fc(T_lo), c->fc(T_hi));
-    if (!(fc_min > 0) || !(fk_min > 0)) return fail(c, FEDFEM_ERR_ARG, "conductivity or heat law not positive on [T_lo, T_hi]");
-    const double rl = std::fabs(T_lo - c->T_zero), rh = std::fabs(T_hi - c->T_zero);
-    const double r3 = std::max(rl * rl * rl, rh * rh * rh);
-    const int nb = launch_surface_rate(nn, c->d_Ac64, c->d_Ar64, c->d_C0, c->d_isdir, c->h,
-                                       4.0 * 5.67e-8 * c->eps * r3, fc_min, partial, c->stream);
-    std::vector<double> pr(2 * nb);
-    CK(cudaMemcpyAsync(pr.data(), partial, pr.size() * 8, cudaMemcpyDeviceToHost, c->stream), "read");
-    CK(cudaStreamSynchronize(c->stream), "synchronize");
-    double surf = 0.0;
-    for (int b = 0; b < nb; ++b) surf = std::max(surf, pr[2 * b]);
-    c->dt_crit = 2.0 / (lam * fk_max / fc_min + surf);
+    double dtc = 0.0;
+    s = crit_step(c, T_lo, T_hi, &dtc);
+    if (s != FEDFEM_OK) return s;
+    c->dt_crit = dtc;
     c->T_lo = T_lo;
     c->T_hi = T_hi;
     c->precomputed = true;
@@ -836,6 +848,45 @@ extern "C" fedfem_status fedfem_step(fedfem_ctx *c, int64_t n_steps)
 {
     fedfem_status s = fedfem_step_async(c, n_steps);
     if (s != FEDFEM_OK) return s;
+    return check_device(c);
+}
+
+extern "C" fedfem_status fedfem_step_adaptive(fedfem_ctx *c, int64_t n_steps, double safety, double margin,
+                                              double *t_elapsed)
+{
+    if (!c) return FEDFEM_ERR_ARG;
+    if (n_steps < 0 || !(safety > 0) || !(safety <= 1) || !(margin >= 0) || !std::isfinite(margin))
+        return fail(c, FEDFEM_ERR_ARG, "need n_steps >= 0, 0 < safety <= 1, margin >= 0");
+    if (!c->precomputed || !c->has_T) return fail(c, FEDFEM_ERR_STATE, "call fedfem_precompute and fedfem_set_T first");
+    const int64_t spl = c->opt.steps_per_launch > 0 ? c->opt.steps_per_launch : 200;
+    double t = 0.0;
+    for (int64_t done = 0; done < n_steps;) {
+        const int64_t k = std::min(spl, n_steps - done);
+        // temperature range of the current state -> dt_crit over it -> dt for this launch
+        fedfem_status s = state_f64_new(c, c->step, c->d_v[0]);
+        if (s != FEDFEM_OK) return s;
+        const int nb = launch_minmax(c->nn, c->d_v[0], c->d_red, c->stream);
+        std::vector<double> pr(2 * nb);
+        CK(cudaMemcpyAsync(pr.data(), c->d_red, pr.size() * 8, cudaMemcpyDeviceToHost, c->stream), "read");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        double lo = 1e300, hi = -1e300;
+        for (int b = 0; b < nb; ++b) {
+            lo = std::min(lo, pr[2 * b]);
+            hi = std::max(hi, pr[2 * b + 1]);
+        }
+        if (!std::isfinite(lo) || !std::isfinite(hi)) return fail(c, FEDFEM_ERR_DIVERGED, "non-finite temperature");
+        double dtc = 0.0;
+        s = crit_step(c, lo - margin, hi + margin, &dtc);
+        if (s != FEDFEM_OK) return s;
+        c->dt = safety * dtc;
+        c->has_dt = true;
+        launch_set_A(c->nn, c->dt, c->d_C0, c->d_isdir, c->d_A, c->d_A2, c->stream);
+        s = enqueue_steps(c, k, nullptr, 0);
+        if (s != FEDFEM_OK) return s;
+        t += (double)k * c->dt;
+        done += k;
+    }
+    if (t_elapsed) *t_elapsed = t;
     return check_device(c);
 }
 

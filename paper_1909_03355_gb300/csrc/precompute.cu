@@ -431,6 +431,34 @@ __global__ void k_lz_next(int64_t nn, const double *w, const double *beta2, doub
         vnext[g] = w[g] * inv;
 }
 
+// per-block (min, max) of x over all nodes
+__global__ void __launch_bounds__(256) k_minmax(int64_t nn, const double *x, double *partial)
+{
+    __shared__ double red[16];
+    double lo = 1e300, hi = -1e300;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
+        lo = fmin(lo, x[g]);
+        hi = fmax(hi, x[g]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[2 * (threadIdx.x >> 5)] = lo;
+        red[2 * (threadIdx.x >> 5) + 1] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            lo = fmin(lo, red[2 * w]);
+            hi = fmax(hi, red[2 * w + 1]);
+        }
+        partial[2 * blockIdx.x] = fmin(lo, red[0]);
+        partial[2 * blockIdx.x + 1] = fmax(hi, red[1]);
+    }
+}
+
 __global__ void k_init_power(int64_t nn, const uint8_t *isdir, double *x)
 {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x)
@@ -611,6 +639,13 @@ void launch_lanczos_step(int npe, int64_t ne, int64_t nn, const int32_t *gconn, 
     k_lz_orth<<<nb, 256, 0, st>>>(nn, F, vcur, coef, partial);
     k_sum_partials<<<1, 256, 0, st>>>(nb, partial, coef + 2);  // coef[2] = beta_j^2
     k_lz_next<<<nblk(nn), 256, 0, st>>>(nn, F, coef + 2, vprev);  // v_{j+1} over v_{j-1}
+}
+
+int launch_minmax(int64_t nn, const double *x, double *partial, cudaStream_t st)
+{
+    const int nb = reduce_blocks(nn);
+    k_minmax<<<nb, 256, 0, st>>>(nn, x, partial);
+    return nb;
 }
 
 void launch_normalize(int64_t nn, const double *z, const double *sums, double *x, cudaStream_t st)

@@ -68,6 +68,8 @@ void launch_lanczos_step(int npe, int64_t ne, int64_t nn, const int32_t *gconn, 
                          const int32_t *n2e_ptr, const int64_t *n2e, const double *C0, const uint8_t *isdir,
                          double *vprev, const double *vcur, double *u, double *F, double *Y, const double *beta2_prev,
                          double *coef, double *partial, cudaStream_t st);
+// per-block (min, max) of x[0..nn) into partial[2 b], partial[2 b + 1]; returns the block count
+int launch_minmax(int64_t nn, const double *x, double *partial, cudaStream_t st);
 void launch_normalize(int64_t nn, const double *z, const double *sums, double *x, cudaStream_t st);
 int launch_surface_rate(int64_t nn, const double *Ac, const double *Ar, const double *C0, const uint8_t *isdir, double h,
                         double rad_coef, double fc_min, double *partial, cudaStream_t st);

@@ -165,6 +165,13 @@ class FedFem:
     def step(self, n):
         self._ck(self.L.fedfem_step(self.h, int(n)))
 
+    def step_adaptive(self, n, safety=0.9, margin=0.0):
+        """n steps with dt = safety dt_crit over the current temperature range (+- margin),
+        re-evaluated before every launch; returns the simulated time."""
+        t = C.c_double()
+        self._ck(self.L.fedfem_step_adaptive(self.h, int(n), float(safety), float(margin), C.byref(t)))
+        return t.value
+
     def step_async(self, n):
         self._ck(self.L.fedfem_step_async(self.h, int(n)))
 

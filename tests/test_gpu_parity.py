@@ -247,6 +247,26 @@ def test_time_dependent_loads(precision):
     f.close()
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_adaptive_time_step(precision):
+    """dt re-evaluated before every launch from the current range: a heating cube precomputed for
+    [20, 40] deg C runs far beyond that range; GPU against the oracle's adaptive run (the two
+    lambda_cond estimates agree to ~1e-10, hence the FP64 bound of 1e-8)."""
+    p = fi.nonlinear_cube(8, "hex")
+    p.T_lo, p.T_hi = 20.0, 40.0
+    m = O.OracleModel(p)
+    T_ref, t_ref = m.run_adaptive(p.initial_T(), 600, 50, 0.9, 0.0)
+    assert T_ref.max() > 500.0
+    f = FedFem(p, precision=precision, steps_per_launch=50)
+    f.precompute()
+    f.set_T(p.initial_T())
+    t = f.step_adaptive(600, 0.9, 0.0)
+    tol = 1e-8 if precision == 64 else 2e-4
+    assert t == pytest.approx(t_ref, rel=tol)
+    assert rel(f.get_T(), T_ref) <= tol
+    f.close()
+
+
 def test_inverted_element_reported():
     p = fi.plain_cube(3)
     p.conn = p.conn.copy()

@@ -281,6 +281,38 @@ def test_two_point_law_of_section_4_2_2():
     assert 2000.0 * c_lin == pytest.approx(20.0, rel=1e-14)
 
 
+def test_adaptive_step_is_the_fixed_step_without_temperature_laws():
+    """Without k(T), c(T) and radiation dt_crit does not depend on the temperature range, so
+    the per-launch adaptive step is the fixed step: same field (bitwise) and time n dt."""
+    p = fi.nonlinear_cube(4, "hex")
+    m0 = p.mats[0]
+    p.mats[0] = fi.Material(m0.rho, m0.k0, 0.0, m0.c0, 0.0)
+    p.rad_faces = None
+    m = O.OracleModel(p)
+    lam = m.dt_crit()[1]
+    dt = 0.8 * m.dt_from_lambda(lam, -100.0, 5000.0)
+    T1, t = m.run_adaptive(p.initial_T(), 130, 40, 0.8, 7.0, lam)
+    assert np.array_equal(T1, m.run(p.initial_T(), dt, 130))
+    assert t == pytest.approx(130 * dt, rel=1e-15)
+
+
+def test_adaptive_step_follows_the_heating_range():
+    """Heating nonlinear cube: the critical step shrinks as the range grows (f_k and the
+    radiation rate grow with T), so the adaptive steps do not increase, and the run stays finite
+    far above the range a fixed step would have been chosen for."""
+    p = fi.nonlinear_cube(6, "hex")
+    m = O.OracleModel(p)
+    lam = m.dt_crit()[1]
+    assert m.dt_from_lambda(lam, 20.0, 400.0) < m.dt_from_lambda(lam, 20.0, 40.0)
+    T, dts, done = p.initial_T(), [], 0
+    while done < 400:
+        dts.append(0.9 * m.dt_from_lambda(lam, T.min(), T.max()))
+        T = m.run(T, dts[-1], 50, step0=done)
+        done += 50
+    assert np.all(np.isfinite(T)) and T.max() > 300.0
+    assert np.all(np.diff(dts) <= 1e-12 * dts[0])
+
+
 # ------------------------------------------------------------------------------ slab ------
 
 @pytest.mark.parametrize("ny", [1, 2])
