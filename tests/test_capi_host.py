@@ -92,3 +92,14 @@ def test_create_rejects_bad_input_without_gpu(lib_path):
     with pytest.raises(capi.FedFemError) as ei:
         FedFem(fi.plain_cube(2), quadrature=4)
     assert ei.value.name == "ERR_ARG" and "quadrature" in str(ei.value)
+    # empty inputs
+    p = fi.plain_cube(2)
+    p.conn = p.conn[:0]
+    with pytest.raises(capi.FedFemError) as ei:
+        FedFem(p)
+    assert ei.value.name == "ERR_ARG" and "empty" in str(ei.value)
+    p = fi.plain_cube(2)
+    p.mats = []
+    with pytest.raises(capi.FedFemError) as ei:
+        FedFem(p)
+    assert ei.value.name == "ERR_ARG"

@@ -267,6 +267,40 @@ def test_adaptive_time_step(precision):
     f.close()
 
 
+def _single_element(kind):
+    if kind == "hex":
+        return fi.single_brick(0.3, 0.5, 0.7, rho=800.0, c0=900.0, c_lin=0.002, T0=400.0, conv=(40.0, 15.0),
+                               rad=(0.7, -50.0), steps=200)
+    xyz = np.array([[0, 0, 0], [0.4, 0, 0], [0, 0.5, 0], [0.1, 0.1, 0.6]], float)
+    conn = np.array([[0, 1, 2, 3]], np.int32)
+    bf = fi.boundary_faces(conn)
+    return fi.Problem(name="tet1", xyz=xyz, conn=conn,
+                      mats=[fi.Material(800.0, np.diag([1.0, 2.0, 3.0]), 0.001, 900.0, 0.002)],
+                      conv_faces=bf, h=40.0, T_inf=15.0, rad_faces=bf, eps=0.7, T_amb=-50.0,
+                      nodal_Q=np.array([5.0, 0.0, 0.0, 1.0]), T0=np.array([400.0, 350.0, 300.0, 250.0]),
+                      steps=200, T_lo=-50.0, T_hi=400.0)
+
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+@pytest.mark.parametrize("precision", [64, 32])
+def test_single_element(kind, precision):
+    """Degenerate mesh: one element (one tile, one mostly padded chunk, no shared nodes) with
+    convection and radiation on every face: GPU against the oracle; zero steps leave the state
+    and the step counter unchanged."""
+    p = _single_element(kind)
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    f = FedFem(p, precision=precision)
+    f.precompute()
+    f.set_dt(dt, force=True)
+    f.set_T(p.initial_T())
+    f.step(0)
+    assert f.step_count == 0 and np.array_equal(f.get_T(), p.initial_T())
+    f.step(p.steps)
+    assert rel(f.get_T(), m.run(p.initial_T(), dt, p.steps)) <= TOL[precision]
+    f.close()
+
+
 def test_inverted_element_reported():
     p = fi.plain_cube(3)
     p.conn = p.conn.copy()
