@@ -383,9 +383,13 @@ def main():
 
     # roofline of the step kernel: algorithmic bytes per launch / average launch duration
     bytes_step = ELEM_BYTES_FP32 * E + NODE_BYTES_FP32 * N
-    full = [d for i, d in enumerate(durs) if min(spl, K - i * spl) == spl] or durs
-    avg_launch_ms = sum(full) / len(full)
-    achieved = bytes_step * spl / (avg_launch_ms * 1e-3) / 1e9
+    # per-launch step counts (the last launch may be partial); the roofline uses the full
+    # launches when there are any, else all launches, with their own step counts
+    steps_of = [min(spl, K - i * spl) for i in range(n_launch)]
+    sel = [i for i in range(n_launch) if steps_of[i] == spl] or list(range(n_launch))
+    launch_steps = sum(steps_of[i] for i in sel) / len(sel)
+    avg_launch_ms = sum(durs[i] for i in sel) / len(sel)
+    achieved = bytes_step * launch_steps / (avg_launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     tr = traffic_from_profile(src_hash())
 
@@ -509,8 +513,9 @@ def main():
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": None if tr is None else tr * E * spl,
-                         "algorithmic_bytes_per_launch": bytes_step * spl, "kernel": "fed_step_kernel<float,8,Kahan>",
+                         "traffic": None if tr is None else tr * E * launch_steps,
+                         "algorithmic_bytes_per_launch": bytes_step * launch_steps,
+                         "steps_per_timed_launch": launch_steps, "kernel": "fed_step_kernel<float,8,Kahan>",
                          "avg_launch_ms": avg_launch_ms},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 8 * N / K, "d2h_bytes_per_step": 8 * N / K,
