@@ -77,7 +77,7 @@ def test_adjoint_fp32_forward_close_to_oracle():
 
 def test_adjoint_vs_central_differences_fp64():
     """Gradient of a sensor-misfit loss against central differences (delta = 1e-4 relative) of
-    the GPU forward run on 20 random elements; spec bound 1e-5 relative."""
+    the GPU forward run on 20 random elements; bound 1e-5 relative."""
     p, sensors = small_setup("hex", 5)
     f = FedFem(p, precision=64)
     dt = 0.9 * f.precompute()
