@@ -406,7 +406,6 @@ def main():
     assert np.all(np.isfinite(Tout))
 
     # ---- FP64 form on the same workload
-    f.close()
     f64 = FedFem(p, precision=64, stream=stream)
     f64.precompute()
     f64.set_dt(dt)
@@ -424,7 +423,15 @@ def main():
     ms64 = max_over_ranks(ms64, world)
     v64 = whole_job_rate(E * K64, world, ms64 * 1e-3)
     bytes64 = ELEM_BYTES_FP64 * E + NODE_BYTES_FP64 * N
+    # precision policy: the FP32 + Kahan form against the FP64 form after the same steps (untimed)
+    T64 = f64.get_T()
     f64.close()
+    f.set_T(T0)
+    f.step(20 + K64)
+    T32 = f.get_T()
+    f.close()
+    prec = {"steps": 20 + K64, "rel_linf": float(np.max(np.abs(T32 - T64)) / np.max(np.abs(T64))),
+            "rel_linf_of_change": float(np.max(np.abs(T32 - T64)) / max(np.max(np.abs(T64 - T0)), 1e-300))}
 
     # ---- adjoint / forward on the 32^3 inverse problem (2000 FP32 steps, 512 sensors sampled
     #      every 10 steps, checkpoints every 100)
@@ -525,6 +532,7 @@ def main():
             "fp64": {"value": v64, "unit": UNIT, "ms_per_step": ms64 / K64, "steps": K64,
                      "achieved_GBps": bytes64 / (ms64 * 1e-3 / K64) / 1e9},
             "fp32_over_fp64": value / v64,
+            "fp32_vs_fp64": prec,
             "adjoint": adj,
             "batched": batched,
             "extras": extras,

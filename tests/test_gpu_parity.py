@@ -497,3 +497,23 @@ def test_full_size_large_cube_parity(precision):
     assert rel(T, ref) <= TOL[precision]
     # heat has started to flow: the field is not the initial one
     assert np.max(np.abs(ref - 20.0)) > 0
+
+
+def test_full_config_fp32_vs_fp64_20000_steps():
+    """The precision policy on the large-run configuration itself: 128^3, 20,000 steps, FP32 with
+    the Kahan-compensated accumulator against the FP64 form (pinned to the oracle at 1e-10
+    above), rel-L-infinity <= 2e-4."""
+    p = fi.large_cube(128)
+    out = {}
+    for prec in (64, 32):
+        f = FedFem(p, precision=prec)
+        dtc = f.precompute()
+        if prec == 64:
+            dt = 0.9 * dtc
+        f.set_dt(dt)
+        f.set_T(p.initial_T())
+        f.step(20000)
+        out[prec] = f.get_T()
+        f.close()
+    assert np.all(np.isfinite(out[64])) and np.max(out[64]) > 100.0  # the cube has heated up
+    assert rel(out[32], out[64]) <= TOL[32]
