@@ -67,6 +67,7 @@ class Problem:
                                                 # 1 = one centre point (Eq. 17)
     q_schedule: Optional[np.ndarray] = None     # [n] multiplier of the external loads at step n
     Tinf_schedule: Optional[np.ndarray] = None  # [n] convection ambient temperature at step n
+    Tdir_schedule: Optional[np.ndarray] = None  # [n] offset added to every dir_T at step n
 
     @property
     def npe(self) -> int:

@@ -275,6 +275,11 @@ typedef struct {
     const double *q_sched;
     const double *Tinf_sched;
     int64_t n_sched, sched_step0;
+    /* time-dependent Dirichlet values (optional): with Tdir_sched set, the value of Dirichlet
+     * node i at step n is Tdir[i] + Tdir_sched[n] (same length and end rule as the load
+     * schedule); Tdir [nn] holds the prescribed values of Gamma_E (read on Dirichlet nodes) */
+    const double *Tdir;
+    const double *Tdir_sched;
 } orc_model;
 
 /*
@@ -372,6 +377,22 @@ static double orc_T_inf(const orc_model *m, int64_t n)
     return m->Tinf_sched[n < m->n_sched ? n : m->n_sched - 1];
 }
 
+/* Offset of the prescribed temperatures at step n (0 without a Dirichlet schedule). */
+static double orc_T_dir_offset(const orc_model *m, int64_t n)
+{
+    if (!m->Tdir_sched || m->n_sched <= 0) return 0.0;
+    return m->Tdir_sched[n < m->n_sched ? n : m->n_sched - 1];
+}
+
+/* Dirichlet values of step n written into T (Gamma_E of Eq. 3 with a time-dependent value). */
+static void orc_impose_dirichlet(const orc_model *m, double *T, int64_t n)
+{
+    if (!m->Tdir_sched || !m->Tdir) return;
+    const double d = orc_T_dir_offset(m, n);
+    for (int64_t i = 0; i < m->nn; ++i)
+        if (m->isdir[i]) T[i] = m->Tdir[i] + d;
+}
+
 /* Net external nodal heat flow Q_i at step n (Eq. 4, 5, 7 lumped to nodes). */
 static double orc_nodal_Q_n(const orc_model *m, int64_t i, double Ti, int64_t n)
 {
@@ -394,7 +415,9 @@ static double orc_nodal_dQ(const orc_model *m, int64_t i, double Ti)
 }
 
 /*
- * n explicit steps (Eq. 15 / 16) from T (in/out, Dirichlet values already imposed).
+ * n explicit steps (Eq. 15 / 16) from T (in/out, Dirichlet values already imposed; with a
+ * Dirichlet schedule they are set to those of step sched_step0 first and to those of step
+ * n + 1 after step n).
  * energy (optional, [n][2]): per step S = sum_free C_i(T_i)(T_i' - T_i) and
  * B = dt (sum_free Q_i + sum_Dirichlet F_i).
  * trace (optional): T at the sensor nodes after every `sample_every`-th step, [n/sample_every][ns].
@@ -403,6 +426,7 @@ void orc_run(const orc_model *m, double dt, int64_t nsteps, double *T, double *e
              const int32_t *sensors, int32_t ns, int32_t sample_every, double *trace)
 {
     double *F = (double *)malloc(m->nn * sizeof(double));
+    orc_impose_dirichlet(m, T, m->sched_step0);
     for (int64_t n = 0; n < nsteps; ++n) {
         orc_internal_loads(m, T, F);
         double S = 0.0, B = 0.0;
@@ -418,6 +442,7 @@ void orc_run(const orc_model *m, double dt, int64_t nsteps, double *T, double *e
             B += dt * Q;
             T[i] = Tn;
         }
+        orc_impose_dirichlet(m, T, m->sched_step0 + n + 1);
         if (energy) {
             energy[2 * n] = S;
             energy[2 * n + 1] = B;
@@ -518,6 +543,7 @@ void orc_adjoint(const orc_model *m, double dt, int64_t nsteps, const double *T0
     const int npe = m->npe;
     double *states = (double *)malloc((size_t)(nsteps + 1) * nn * sizeof(double));
     memcpy(states, T0, nn * sizeof(double));
+    orc_impose_dirichlet(m, states, m->sched_step0);
     for (int64_t n = 0; n < nsteps; ++n) {
         memcpy(states + (n + 1) * nn, states + n * nn, nn * sizeof(double));
         orc_model mn = *m;

@@ -10,6 +10,7 @@ Function map (paper passages):
                               (Section 3.1), surface area shares (Eq. 4/7 lumped to nodes)
   OracleModel.internal_loads  Eq. 11/20 with the element-mean k(T) of Section 4.2.2
   OracleModel.run             time-stepping stage, Fig. 1 (iii): Eq. 15/16, Dirichlet re-imposed
+  OracleModel.set_schedule    time-dependent loads, convection temperature and Dirichlet values
   OracleModel.dt_crit         Section 3.4, Eq. 29
   OracleModel.adjoint         reverse-time discrete adjoint of Eq. 16/20 (derived, no paper
                               counterpart)
@@ -52,7 +53,7 @@ class _Model(C.Structure):
                 ("h", C.c_double), ("T_inf", C.c_double), ("eps", C.c_double),
                 ("T_amb", C.c_double), ("T_zero", C.c_double), ("T_ref", C.c_double),
                 ("q_sched", C.c_void_p), ("Tinf_sched", C.c_void_p), ("n_sched", C.c_int64),
-                ("sched_step0", C.c_int64)]
+                ("sched_step0", C.c_int64), ("Tdir", C.c_void_p), ("Tdir_sched", C.c_void_p)]
 
 
 def lib():
@@ -177,28 +178,36 @@ class OracleModel:
                 if L.orc_hex_matrix_centre(_p(self.xyz[self.conn[e]]), _p(self.mat_k0[m]), _p(self.K[e])):
                     raise ValueError(f"element {e} has det J(0) <= 0")
         self._keep = (conv, rad, dn)
+        self.Tdir = np.zeros(nn)
+        if dn is not None:
+            self.Tdir[dn] = _f64(p.dir_T)
         self.m = _Model(nn=nn, ne=ne, npe=npe, pad=0, conn=_p(self.conn), K=_p(self.K),
                         theta=_p(self.theta), W=_p(self.W), C0=_p(self.C0), Qext=_p(self.Qext),
                         Ac=_p(self.Ac), Ar=_p(self.Ar), isdir=_p(self.isdir),
                         k_lin=float(mats[0].k_lin), c_lin=float(mats[0].c_lin),
                         h=float(p.h), T_inf=float(p.T_inf), eps=float(p.eps), T_amb=float(p.T_amb),
-                        T_zero=float(p.T_zero), T_ref=float(getattr(mats[0], "T_ref", 0.0)))
+                        T_zero=float(p.T_zero), T_ref=float(getattr(mats[0], "T_ref", 0.0)),
+                        Tdir=_p(self.Tdir))
         self.mref = C.byref(self.m)
-        self._sched = (None, None)
-        if getattr(p, "q_schedule", None) is not None or getattr(p, "Tinf_schedule", None) is not None:
-            self.set_schedule(getattr(p, "q_schedule", None), getattr(p, "Tinf_schedule", None))
+        self._sched = (None, None, None)
+        sched = [getattr(p, f, None) for f in ("q_schedule", "Tinf_schedule", "Tdir_schedule")]
+        if any(s is not None for s in sched):
+            self.set_schedule(*sched)
 
-    def set_schedule(self, q_scale=None, T_inf=None):
-        """Time-dependent loads: at step n the external loads are q_scale[n] Qext and the
-        convection ambient temperature is T_inf[n] (the last entry beyond the end)."""
+    def set_schedule(self, q_scale=None, T_inf=None, T_dir=None):
+        """Time-dependent loads and Dirichlet values: at step n the external loads are
+        q_scale[n] Qext, the convection ambient temperature is T_inf[n] and every prescribed
+        temperature is its value in the problem plus T_dir[n] (the last entry beyond the end)."""
         q = _f64(q_scale)
         t = _f64(T_inf)
-        lens = {len(a) for a in (q, t) if a is not None}
+        d = _f64(T_dir)
+        lens = {len(a) for a in (q, t, d) if a is not None}
         if len(lens) > 1:
-            raise ValueError("q_scale and T_inf must have the same length")
-        self._sched = (q, t)
+            raise ValueError("q_scale, T_inf and T_dir must have the same length")
+        self._sched = (q, t, d)
         self.m.q_sched = None if q is None else q.ctypes.data
         self.m.Tinf_sched = None if t is None else t.ctypes.data
+        self.m.Tdir_sched = None if d is None else d.ctypes.data
         self.m.n_sched = lens.pop() if lens else 0
 
     # lumped thermal mass at f_c = 1 (Section 3.1, Eq. 14 / 21)

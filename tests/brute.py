@@ -103,16 +103,22 @@ def c1_closed_form(n, dt, nsteps, T0=100.0):
 
 
 def ftcs_slab(nx, h, dt, nsteps, T0, Ts, k, rho, c0, k_lin=0.0, c_lin=0.0, conv=None,
-              source=0.0):
+              source=0.0, Ts_offset=None):
     """1-D forward-Euler recurrence equivalent to a bar of bricks whose field is constant over
     each cross-section (consistent row sums = lumped mass):
       interior  T_j += dt k / (rho c(T_j) h^2) [f_R (T_{j+1}-T_j) + f_L (T_{j-1}-T_j)]
       x = L end T_n += 2 dt k / (rho c(T_n) h^2) f_L (T_{n-1}-T_n) - 2 dt hc/(rho c(T_n) h) (T_n - T_inf)
     with f on an element = 1 + k_lin (T_left + T_right)/2 and c(T) = c0 (1 + c_lin T); a
-    uniform volumetric source s adds dt s / (rho c(T_j)) to every free node."""
+    uniform volumetric source s adds dt s / (rho c(T_j)) to every free node.  With Ts_offset
+    the held end is Ts + Ts_offset[n] at step n (the last entry beyond the end)."""
+    def end_value(n):
+        if Ts_offset is None:
+            return Ts
+        return Ts + Ts_offset[min(n, len(Ts_offset) - 1)]
+
     T = np.full(nx + 1, float(T0))
-    T[0] = Ts
-    for _ in range(nsteps):
+    T[0] = end_value(0)
+    for n in range(nsteps):
         f = 1.0 + k_lin * 0.5 * (T[:-1] + T[1:])          # per element
         c = c0 * (1.0 + c_lin * T)
         Tn = T.copy()
@@ -123,5 +129,6 @@ def ftcs_slab(nx, h, dt, nsteps, T0, Ts, k, rho, c0, k_lin=0.0, c_lin=0.0, conv=
             hc, Tinf = conv
             Tn[-1] -= 2.0 * dt * hc / (rho * c[-1] * h) * (T[-1] - Tinf)
         Tn[1:] += dt * source / (rho * c[1:])
+        Tn[0] = end_value(n + 1)
         T = Tn
     return T

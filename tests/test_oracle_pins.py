@@ -337,6 +337,35 @@ def test_slab_reduces_to_1d_recurrence(ny, nonlinear):
     assert np.max(np.abs(T - ref[ix])) <= 1e-13 * 100.0
 
 
+@pytest.mark.parametrize("nonlinear", [False, True])
+def test_slab_time_dependent_dirichlet(nonlinear):
+    """A prescribed temperature that changes every step (T_s + d[n], the last entry held):
+    the bar still reduces exactly to the 1-D recurrence with the same end values; a run split
+    in two with step0 continues the schedule, and d = 0 is the constant-value run."""
+    nx, k, rho, c0 = 16, 2.0, 3.0, 1.5
+    kl, cl = (0.01, 0.004) if nonlinear else (0.0, 0.0)
+    p = fi.slab(nx, 2, 2, Lx=1.0, k=(k, 7.0, 9.0), rho=rho, c0=c0, k_lin=kl, c_lin=cl,
+                T0=20.0, T_s=20.0, conv_end=(4.0, 10.0))
+    n = 120
+    d = 60.0 * np.sin(0.05 * np.arange(n)) + 0.5 * np.arange(n)
+    h = 1.0 / nx
+    dt = 0.2 * rho * c0 * h * h / (k * 3.0)
+    ix = np.rint(p.xyz[:, 0] / h).astype(int)
+    m = O.OracleModel(p)
+    T_const = m.run(p.initial_T(), dt, 200)
+    m.set_schedule(T_dir=np.zeros(n))
+    assert np.array_equal(m.run(p.initial_T(), dt, 200), T_const)
+    m.set_schedule(T_dir=d)
+    T = m.run(p.initial_T(), dt, 200)
+    ref = brute.ftcs_slab(nx, h, dt, 200, 20.0, 20.0, k, rho, c0, kl, cl, conv=(4.0, 10.0),
+                          Ts_offset=d)
+    assert np.max(np.abs(T - ref[ix])) <= 1e-13 * 100.0
+    assert np.all(T[p.dir_nodes] == 20.0 + d[-1])
+    T1 = m.run(p.initial_T(), dt, 75)
+    T2 = m.run(T1, dt, 125, step0=75)
+    assert np.max(np.abs(T2 - T)) <= 1e-13 * 100.0
+
+
 def test_slab_erfc_convergence():
     """Semi-infinite-slab closed form T0 + (Ts - T0) erfc(x / 2 sqrt(alpha t)): the error
     shrinks as the mesh is refined (O(h^2) with dt ~ h^2)."""
