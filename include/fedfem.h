@@ -229,16 +229,22 @@ fedfem_status fedfem_internal_loads(fedfem_ctx *ctx, const double *T_host, doubl
 fedfem_status fedfem_set_params(fedfem_ctx *ctx, const double *kscale, const double *source);
 
 /*
- * Time-dependent loads (the paper's loads are constant; Eq. 4-7 with time-varying data): at
- * step n (the global step counter, 0 after fedfem_set_T) the constant external loads Q_ext
- * (sources and nodal heat flows) are multiplied by q_scale[n] and the convection ambient
- * temperature is T_inf[n]; beyond n_entries - 1 the last entries hold.  Step n is the step
- * from T^n to T^(n+1).  Either array may be NULL (that term stays constant); n_entries = 0
- * removes the schedule.  The adjoint and fedfem_energy use the same per-step values.  Arrays:
- * [n_entries] FP64 host, copied.  Synchronises the context's stream.
- * Errors: ARG (n_entries < 0, both arrays NULL, non-finite entries), UNSUPPORTED (batches), CUDA.
+ * Time-dependent loads and prescribed temperatures (the paper's boundary data are constant;
+ * Eq. 3-7 with time-varying data): at step n (the global step counter, 0 after fedfem_set_T)
+ * the constant external loads Q_ext (sources and nodal heat flows) are multiplied by
+ * q_scale[n], the convection ambient temperature is T_inf[n], and every Dirichlet node holds
+ * its dir_T value plus T_dir[n]; beyond n_entries - 1 the last entries hold.  Step n is the
+ * step from T^n to T^(n+1).  Any array may be NULL (that term stays constant); n_entries = 0
+ * removes the schedule.  fedfem_set_T imposes the Dirichlet values of step 0; when a field is
+ * already installed and the Dirichlet offsets change, this call sets them to those of the
+ * current step.  During the steps a Dirichlet node moves by T_dir[n+1] - T_dir[n] each step, so
+ * it follows T_dir up to the rounding of the working precision.  The adjoint and fedfem_energy
+ * use the same per-step values.  Arrays: [n_entries] FP64 host, copied.  Synchronises the
+ * context's stream.
+ * Errors: ARG (n_entries < 0, all arrays NULL, non-finite entries), UNSUPPORTED (batches), CUDA.
  */
-fedfem_status fedfem_set_schedule(fedfem_ctx *ctx, int64_t n_entries, const double *q_scale, const double *T_inf);
+fedfem_status fedfem_set_schedule(fedfem_ctx *ctx, int64_t n_entries, const double *q_scale, const double *T_inf,
+                                  const double *T_dir);
 
 /* Checkpoint / resume: the state is (T, Kahan compensation, step counter).  state_bytes
  * returns the size of the opaque blob; get/set copy it to/from a host buffer. */

@@ -63,7 +63,7 @@ __global__ void k_set_A_nodes(int64_t nn, const double *dtn, const double *C0, c
                               float2 *A2)
 {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
-        const double v = isdir[g] ? 0.0 : dtn[g] / C0[g];
+        const double v = isdir[g] ? -0.0 : dtn[g] / C0[g];
         A[g] = v;
         if (A2) {
             const float hi = (float)v;
@@ -464,7 +464,7 @@ static fedfem_status batch_build(fedfem_batch *b, const fedfem_scenario *sc, int
     BCK(cudaStreamBeginCapture(stm, cudaStreamCaptureModeThreadLocal), "begin capture");
     k_stamp<<<1, 1, 0, stm>>>(b->d_stamp);
     cudaMemcpyAsync(c->d_v[0], b->d_T0, nn * 8, cudaMemcpyDeviceToDevice, stm);
-    launch_impose_dirichlet((int64_t)c->dir_nodes.size(), c->d_dir_new, c->d_dir_T, c->d_v[0], c->d_old_of_new, stm);
+    launch_impose_dirichlet((int64_t)c->dir_nodes.size(), c->d_dir_new, c->d_dir_T, 0.0, c->d_v[0], c->d_old_of_new, stm);
     launch_set_state(c->precision, nn, c->d_v[0], c->d_old_of_new, c->d_T[0], c->kahan ? c->d_comp[0] : nullptr, stm);
     int64_t n = 0;
     for (int j = 0; j < J; ++j) {

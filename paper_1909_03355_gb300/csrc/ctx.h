@@ -24,11 +24,17 @@ struct fedfem_ctx {
     double c_a() const { return 1.0 - c_lin * T_ref; }
     double fk(double T) const { return 1.0 + k_lin * (T - T_ref); }
     double fc(double T) const { return 1.0 + c_lin * (T - T_ref); }
-    // time-dependent loads: at step n the external loads are sched_q[n] Q_ext and the
-    // convection ambient temperature is sched_Tinf[n] (last entry beyond the end)
-    std::vector<double> sched_q, sched_Tinf;
-    double *d_sched_q = nullptr, *d_sched_Tinf = nullptr;
+    // time-dependent loads: at step n the external loads are sched_q[n] Q_ext, the convection
+    // ambient temperature is sched_Tinf[n] and the prescribed temperatures are dir_T +
+    // sched_Tdir[n] (last entry beyond the end)
+    std::vector<double> sched_q, sched_Tinf, sched_Tdir;
+    double *d_sched_q = nullptr, *d_sched_Tinf = nullptr, *d_sched_Tdir = nullptr;
     int64_t sched_len = 0, sched_cap = 0;
+    double Tdir_at(int64_t n) const
+    {
+        return sched_Tdir.empty() ? 0.0
+                                  : sched_Tdir[(size_t)std::max<int64_t>(0, std::min<int64_t>(n, sched_len - 1))];
+    }
     double qs_at(int64_t n) const
     {
         return sched_q.empty() ? 1.0 : sched_q[(size_t)std::max<int64_t>(0, std::min<int64_t>(n, sched_len - 1))];

@@ -689,7 +689,8 @@ fedfem_status install_T(fedfem_ctx *c, const double *T0_dev_old)
 {
     double *tmp = c->d_v[0];
     CK(cudaMemcpyAsync(tmp, T0_dev_old, c->nn * 8, cudaMemcpyDeviceToDevice, c->stream), "copy T0");
-    launch_impose_dirichlet((int64_t)c->dir_nodes.size(), c->d_dir_new, c->d_dir_T, tmp, c->d_old_of_new, c->stream);
+    launch_impose_dirichlet((int64_t)c->dir_nodes.size(), c->d_dir_new, c->d_dir_T, c->Tdir_at(0), tmp, c->d_old_of_new,
+                            c->stream);
     launch_set_state(c->precision, c->nn, tmp, c->d_old_of_new, c->d_T[0], c->kahan ? c->d_comp[0] : nullptr, c->stream);
     CK(cudaGetLastError(), "set T");
     c->step = 0;
@@ -791,6 +792,7 @@ StepArgs step_args(fedfem_ctx *c)
     a.l2_stream_policy = c->opt.l2_policy == 2 || (c->opt.l2_policy == 0 && big) ? 1 : 0;
     a.sched_q = c->sched_q.empty() ? nullptr : c->d_sched_q;
     a.sched_Tinf = c->sched_Tinf.empty() ? nullptr : c->d_sched_Tinf;
+    a.sched_Tdir = c->sched_Tdir.empty() ? nullptr : c->d_sched_Tdir;
     a.sched_len = c->sched_len;
     a.scatter = c->opt.scatter;
     a.withhold = c->opt.debug_withhold_barrier;
@@ -934,35 +936,51 @@ extern "C" fedfem_status fedfem_energy(fedfem_ctx *c, double *stored_change, dou
 }
 
 extern "C" fedfem_status fedfem_set_schedule(fedfem_ctx *c, int64_t n_entries, const double *q_scale,
-                                             const double *T_inf)
+                                             const double *T_inf, const double *T_dir)
 {
     if (!c) return FEDFEM_ERR_ARG;
     if (n_entries < 0) return fail(c, FEDFEM_ERR_ARG, "n_entries < 0");
     if (!c->group_elem.empty()) return fail(c, FEDFEM_ERR_UNSUPPORTED, "load schedules are not available for batches");
-    if (n_entries > 0 && !q_scale && !T_inf) return fail(c, FEDFEM_ERR_ARG, "no schedule array given");
+    if (n_entries > 0 && !q_scale && !T_inf && !T_dir) return fail(c, FEDFEM_ERR_ARG, "no schedule array given");
     for (int64_t i = 0; i < n_entries; ++i)
-        if ((q_scale && !std::isfinite(q_scale[i])) || (T_inf && !std::isfinite(T_inf[i])))
+        if ((q_scale && !std::isfinite(q_scale[i])) || (T_inf && !std::isfinite(T_inf[i])) ||
+            (T_dir && !std::isfinite(T_dir[i])))
             return fail(c, FEDFEM_ERR_ARG, "non-finite schedule entry");
-    c->sched_q.clear();
-    c->sched_Tinf.clear();
-    c->sched_len = 0;
-    if (n_entries == 0) return FEDFEM_OK;
+    const bool had_Tdir = !c->sched_Tdir.empty();
     if (n_entries > c->sched_cap) {
         CK(dalloc(c, (void **)&c->d_sched_q, n_entries * 8), "alloc schedule");
         CK(dalloc(c, (void **)&c->d_sched_Tinf, n_entries * 8), "alloc schedule");
+        CK(dalloc(c, (void **)&c->d_sched_Tdir, n_entries * 8), "alloc schedule");
         c->sched_cap = n_entries;
     }
     // the stream may still run steps that read the previous schedule
     CK(cudaStreamSynchronize(c->stream), "synchronize");
-    if (q_scale) {
-        c->sched_q.assign(q_scale, q_scale + n_entries);
-        CK(cudaMemcpy(c->d_sched_q, q_scale, n_entries * 8, cudaMemcpyHostToDevice), "upload schedule");
+    c->sched_q.clear();
+    c->sched_Tinf.clear();
+    c->sched_Tdir.clear();
+    c->sched_len = 0;
+    if (n_entries > 0) {
+        if (q_scale) {
+            c->sched_q.assign(q_scale, q_scale + n_entries);
+            CK(cudaMemcpy(c->d_sched_q, q_scale, n_entries * 8, cudaMemcpyHostToDevice), "upload schedule");
+        }
+        if (T_inf) {
+            c->sched_Tinf.assign(T_inf, T_inf + n_entries);
+            CK(cudaMemcpy(c->d_sched_Tinf, T_inf, n_entries * 8, cudaMemcpyHostToDevice), "upload schedule");
+        }
+        if (T_dir) {
+            c->sched_Tdir.assign(T_dir, T_dir + n_entries);
+            CK(cudaMemcpy(c->d_sched_Tdir, T_dir, n_entries * 8, cudaMemcpyHostToDevice), "upload schedule");
+        }
+        c->sched_len = n_entries;
     }
-    if (T_inf) {
-        c->sched_Tinf.assign(T_inf, T_inf + n_entries);
-        CK(cudaMemcpy(c->d_sched_Tinf, T_inf, n_entries * 8, cudaMemcpyHostToDevice), "upload schedule");
+    // a field already installed takes the prescribed values of the current step
+    if (c->has_T && (had_Tdir || !c->sched_Tdir.empty())) {
+        const int b = (int)(c->step & 1);
+        launch_impose_dirichlet_state(c->precision, (int64_t)c->dir_nodes.size(), c->d_dir_new, c->d_dir_T,
+                                      c->Tdir_at(c->step), c->d_T[b], c->kahan ? c->d_comp[b] : nullptr, c->stream);
+        CK(cudaGetLastError(), "impose Dirichlet values");
     }
-    c->sched_len = n_entries;
     return FEDFEM_OK;
 }
 

@@ -102,7 +102,7 @@ struct StepArgs {
     const int32_t *colptr;      // tile-relative chunk offsets of the colour classes
     void *T[2];                 // Real [nn]
     float *comp[2];             // [nn] (FP32 + Kahan)
-    const double *A;            // [nn] dt / C0 (0 on Dirichlet nodes), FP64 form
+    const double *A;            // [nn] dt / C0 (-0.0 on Dirichlet nodes: the sign bit marks them), FP64 form
     const float2 *A2;           // [nn] the same as a float pair (hi, lo), FP32 form
     const void *Qext;           // Real [nn]
     const void *Ac;             // Real [nn]
@@ -112,9 +112,10 @@ struct StepArgs {
     const int32_t *nbr_ptr;     // tile neighbours (CSR over tiles)
     const int32_t *nbr;
     int32_t *err;               // device error word
-    // time-dependent loads (NULL: constant): external-load multiplier and convection ambient
-    // temperature per global step, the last entry held beyond sched_len
-    const double *sched_q, *sched_Tinf;
+    // time-dependent loads (NULL: constant): external-load multiplier, convection ambient
+    // temperature and offset of the prescribed temperatures per global step, the last entry
+    // held beyond sched_len
+    const double *sched_q, *sched_Tinf, *sched_Tdir;
     int64_t sched_len;
     // physics: one table entry per scenario, selected by TileInfo::scenario
     const PhysParams *phys;

@@ -252,12 +252,14 @@ __global__ void k_node_sums(NodeArgs a)
     }
 }
 
-// A_i = dt / C0_i (Eq. 14 / 21) in FP64, 0 on Dirichlet nodes; optionally also as the float
-// pair (hi, lo) with hi = fl32(A), lo = fl32(A - hi) used by the FP32 form.
+// A_i = dt / C0_i (Eq. 14 / 21) in FP64, -0.0 on Dirichlet nodes (a zero whose sign bit tells
+// the step kernel that the node's value follows the prescribed-temperature schedule);
+// optionally also as the float pair (hi, lo) with hi = fl32(A), lo = fl32(A - hi) used by the
+// FP32 form.
 __global__ void k_set_A(int64_t nn, double dt, const double *C0, const uint8_t *isdir, double *A, float2 *A2)
 {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
-        const double v = isdir[g] ? 0.0 : dt / C0[g];
+        const double v = isdir[g] ? -0.0 : dt / C0[g];
         A[g] = v;
         if (A2) {
             const float hi = (float)v;
@@ -509,11 +511,26 @@ __global__ void k_set_state(int64_t nn, const double *T0_old, const int32_t *old
 template __global__ void k_set_state<float>(int64_t, const double *, const int32_t *, float *, float *);
 template __global__ void k_set_state<double>(int64_t, const double *, const int32_t *, double *, float *);
 
-__global__ void k_impose_dirichlet(int64_t nd, const int32_t *dir_new, const double *dir_T, double *T0_old,
-                                   const int32_t *old_of_new)
+__global__ void k_impose_dirichlet(int64_t nd, const int32_t *dir_new, const double *dir_T, double offset,
+                                   double *T0_old, const int32_t *old_of_new)
 {
     for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < nd; d += (int64_t)gridDim.x * blockDim.x)
-        T0_old[old_of_new[dir_new[d]]] = dir_T[d];
+        T0_old[old_of_new[dir_new[d]]] = dir_T[d] + offset;
+}
+
+// prescribed values dir_T + offset written into the working state (new order), with the
+// compensation of k_set_state
+template <typename R>
+__global__ void k_impose_dirichlet_state(int64_t nd, const int32_t *dir_new, const double *dir_T, double offset, R *T,
+                                         float *comp)
+{
+    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < nd; d += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = dir_new[d];
+        const double v = dir_T[d] + offset;
+        const R r = (R)v;
+        T[g] = r;
+        if (comp) comp[g] = (float)((double)r - v);
+    }
 }
 
 __global__ void k_permute_new_to_old(int64_t nn, const double *x_new, const int32_t *old_of_new, double *x_old)
@@ -678,10 +695,20 @@ void launch_set_state(int precision, int64_t nn, const double *T0_old, const int
         k_set_state<float><<<nblk(nn), 256, 0, st>>>(nn, T0_old, old_of_new, (float *)T, comp);
 }
 
-void launch_impose_dirichlet(int64_t nd, const int32_t *dir_new, const double *dir_T, double *T0_old,
+void launch_impose_dirichlet(int64_t nd, const int32_t *dir_new, const double *dir_T, double offset, double *T0_old,
                              const int32_t *old_of_new, cudaStream_t st)
 {
-    if (nd > 0) k_impose_dirichlet<<<nblk(nd), 256, 0, st>>>(nd, dir_new, dir_T, T0_old, old_of_new);
+    if (nd > 0) k_impose_dirichlet<<<nblk(nd), 256, 0, st>>>(nd, dir_new, dir_T, offset, T0_old, old_of_new);
+}
+
+void launch_impose_dirichlet_state(int precision, int64_t nd, const int32_t *dir_new, const double *dir_T,
+                                   double offset, void *T, float *comp, cudaStream_t st)
+{
+    if (nd <= 0) return;
+    if (precision == 64)
+        k_impose_dirichlet_state<double><<<nblk(nd), 256, 0, st>>>(nd, dir_new, dir_T, offset, (double *)T, nullptr);
+    else
+        k_impose_dirichlet_state<float><<<nblk(nd), 256, 0, st>>>(nd, dir_new, dir_T, offset, (float *)T, comp);
 }
 
 void launch_permute_new_to_old(int64_t nn, const double *x_new, const int32_t *old_of_new, double *x_old, cudaStream_t st)

@@ -76,8 +76,12 @@ int launch_surface_rate(int64_t nn, const double *Ac, const double *Ar, const do
 void launch_state_to_f64(int precision, int64_t nn, const void *T, const float *comp, double *out, cudaStream_t st);
 void launch_set_state(int precision, int64_t nn, const double *T0_old, const int32_t *old_of_new, void *T, float *comp,
                       cudaStream_t st);
-void launch_impose_dirichlet(int64_t nd, const int32_t *dir_new, const double *dir_T, double *T0_old,
+// prescribed values dir_T + offset into an old-order FP64 field
+void launch_impose_dirichlet(int64_t nd, const int32_t *dir_new, const double *dir_T, double offset, double *T0_old,
                              const int32_t *old_of_new, cudaStream_t st);
+// prescribed values dir_T + offset into the working state (new order; comp may be NULL)
+void launch_impose_dirichlet_state(int precision, int64_t nd, const int32_t *dir_new, const double *dir_T,
+                                   double offset, void *T, float *comp, cudaStream_t st);
 void launch_permute_new_to_old(int64_t nn, const double *x_new, const int32_t *old_of_new, double *x_old, cudaStream_t st);
 void launch_permute_old_to_new(int64_t nn, const double *x_old, const int32_t *old_of_new, double *x_new, cudaStream_t st);
 void launch_energy(int64_t nn, const double *T0, const double *T1, const double *F, const double *C0, const double *Qext,

@@ -428,17 +428,20 @@ template <typename R>
 struct Phys {
     R k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero, T_guard, k_a, c_a;
     R qs, qs_prev;  // external-load multiplier of this step and of the previous one
+    R dD, dD_prev;  // change of the prescribed temperatures over this step and the previous one
     Phys() = default;
     __device__ explicit Phys(const PhysParams &p)
         : k_lin((R)p.k_lin), c_lin((R)p.c_lin), h((R)p.h), T_inf((R)p.T_inf), eps_sigma((R)p.eps_sigma),
           T_amb((R)p.T_amb), T_zero((R)p.T_zero), T_guard((R)p.T_guard), k_a((R)p.k_a), c_a((R)p.c_a), qs((R)1),
-          qs_prev((R)1)
+          qs_prev((R)1), dD((R)0), dD_prev((R)0)
     {
     }
 };
 
 // Time-dependent loads of global step n: the load multiplier of steps n and n - 1 (the halo
-// nodes are finished for step n - 1) and the convection ambient temperature of step n.
+// nodes are finished for step n - 1), the convection ambient temperature of step n and the
+// changes d(n + 1) - d(n), d(n) - d(n - 1) of the prescribed-temperature offset d (formed in
+// FP64, so the Dirichlet values follow d up to the rounding of the working precision).
 template <typename R>
 __device__ __forceinline__ void apply_schedule(Phys<R> &ph, const StepArgs &a, long long n)
 {
@@ -446,27 +449,34 @@ __device__ __forceinline__ void apply_schedule(Phys<R> &ph, const StepArgs &a, l
     const long long L = a.sched_len - 1;
     const long long i = n < L ? n : L;
     const long long ip = n - 1 < 0 ? 0 : (n - 1 < L ? n - 1 : L);
+    const long long in = n + 1 < L ? n + 1 : L;
     if (a.sched_q) {
         ph.qs = (R)a.sched_q[i];
         ph.qs_prev = (R)a.sched_q[ip];
     }
     if (a.sched_Tinf) ph.T_inf = (R)a.sched_Tinf[i];
+    if (a.sched_Tdir) {
+        ph.dD = (R)(a.sched_Tdir[in] - a.sched_Tdir[i]);
+        ph.dD_prev = (R)(a.sched_Tdir[i] - a.sched_Tdir[ip]);
+    }
 }
 
 // A_i = dt / C0_i: FP64 in the FP64 form; in the FP32 form the FP64 value is kept as an
 // unevaluated pair of floats (hi + lo, 48 significant bits) and A q is formed with one FMA and
-// rounded once.
+// rounded once.  Dirichlet nodes carry A = -0.0 (dir() reads the sign bit).
 template <typename R>
 struct ACoef;
 template <>
 struct ACoef<float> {
     float2 v;
     __device__ __forceinline__ float mul(float q) const { return fmaf(v.x, q, v.y * q); }
+    __device__ __forceinline__ bool dir() const { return (__float_as_uint(v.x) >> 31) != 0u; }
 };
 template <>
 struct ACoef<double> {
     double v;
     __device__ __forceinline__ double mul(double q) const { return v * q; }
+    __device__ __forceinline__ bool dir() const { return __double_as_longlong(v) < 0; }
 };
 
 template <typename R>
@@ -518,13 +528,14 @@ __device__ __forceinline__ void add_loads(R *Fs, const R *F, const int *id)
     }
 }
 
-// Explicit nodal update (Eq. 16): T' = T + A / f_c(T) (Q - F), Kahan-compensated in FP32.
+// Explicit nodal update (Eq. 16): T' = T + A / f_c(T) (Q - F), Kahan-compensated in FP32; a
+// Dirichlet node moves by dD, the change of its prescribed value over the step.
 template <typename R, bool KAHAN>
-__device__ __forceinline__ R node_update(R T, float comp, ACoef<R> A, R Q, R F, const Phys<R> &ph, float &comp_out,
-                                         int32_t *err)
+__device__ __forceinline__ R node_update(R T, float comp, ACoef<R> A, R Q, R F, R dD, const Phys<R> &ph,
+                                         float &comp_out, int32_t *err)
 {
     const R fc = ph.c_a + ph.c_lin * T;
-    const R inc = A.mul((Q - F) / fc);
+    const R inc = A.dir() ? dD : A.mul((Q - F) / fc);
     R Tn;
     if constexpr (KAHAN) {
         const float y = inc - comp;
@@ -597,7 +608,7 @@ __device__ __forceinline__ R halo_finish(const HaloIn<R> &h, const R *part, cons
     F += h.p[0];
     F += h.p[1];
     for (int q = 2; q < h.cnt; ++q) F += ld_cg(part + h.z + q);
-    return node_update<R, KAHAN>(h.T, h.cp, h.A, h.Q * ph.qs_prev, F, ph, cn, err);
+    return node_update<R, KAHAN>(h.T, h.cp, h.A, h.Q * ph.qs_prev, F, ph.dD_prev, ph, cn, err);
 }
 
 // Shared-memory layout: [stages][chunk_bytes] ring | MBAR_BYTES of mbarriers (full[S], empty[S],
@@ -877,7 +888,8 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                             for (int e = 0; e < 4; ++e) {
                                 float cn;
                                 out.v[e] = node_update<R, KAHAN>(Ts[l + e], KAHAN ? (float)cpv[u].v[e] : 0.0f, Av[u][e],
-                                                                  Qv[u].v[e] * ph.qs, Fs[l + e], ph, cn, a.err);
+                                                                  Qv[u].v[e] * ph.qs, Fs[l + e], ph.dD, ph, cn,
+                                                                  a.err);
                                 cout.v[e] = (R)cn;
                             }
                             store4<R>(Tn + g, out);
@@ -890,7 +902,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                     const int g = nb + l;
                     float cn;
                     const R v = node_update<R, KAHAN>(Ts[l], KAHAN ? ld_cg(a.comp[cur] + g) : 0.0f, load_A<R>(a, g),
-                                                      Qext[g] * ph.qs, Fs[l], ph, cn, a.err);
+                                                      Qext[g] * ph.qs, Fs[l], ph.dD, ph, cn, a.err);
                     Tn[g] = v;
                     if (KAHAN) a.comp[nxt][g] = cn;
                 }

@@ -111,19 +111,20 @@ class FedFem:
         self.n_nodes = problem.n_nodes
         self.n_elems = problem.n_elems
         self.precision = precision
-        q, t = getattr(problem, "q_schedule", None), getattr(problem, "Tinf_schedule", None)
-        if q is not None or t is not None:
-            self.set_schedule(q, t)
+        sched = [getattr(problem, f, None) for f in ("q_schedule", "Tinf_schedule", "Tdir_schedule")]
+        if any(s is not None for s in sched):
+            self.set_schedule(*sched)
 
-    def set_schedule(self, q_scale=None, T_inf=None):
-        """Time-dependent loads: at step n the external loads are q_scale[n] Q_ext and the
-        convection ambient temperature is T_inf[n] (the last entries hold beyond the end)."""
-        q, t = _f64(q_scale), _f64(T_inf)
-        n = len(q) if q is not None else (len(t) if t is not None else 0)
-        if q is not None and t is not None and len(t) != n:
-            raise ValueError("q_scale and T_inf must have the same length")
-        self._sched = (q, t)
-        self._ck(self.L.fedfem_set_schedule(self.h, n, _ptr(q), _ptr(t)))
+    def set_schedule(self, q_scale=None, T_inf=None, T_dir=None):
+        """Time-dependent loads and prescribed temperatures: at step n the external loads are
+        q_scale[n] Q_ext, the convection ambient temperature is T_inf[n] and every Dirichlet
+        node holds its prescribed value plus T_dir[n] (the last entries hold beyond the end)."""
+        arrs = [_f64(a) for a in (q_scale, T_inf, T_dir)]
+        lens = {len(a) for a in arrs if a is not None}
+        if len(lens) > 1:
+            raise ValueError("q_scale, T_inf and T_dir must have the same length")
+        self._sched = tuple(arrs)
+        self._ck(self.L.fedfem_set_schedule(self.h, lens.pop() if lens else 0, *[_ptr(a) for a in arrs]))
 
     # -- errors
     def _ck(self, st):

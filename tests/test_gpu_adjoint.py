@@ -33,10 +33,13 @@ def test_adjoint_matches_oracle_adjoint_fp64(kind, T_ref, scheduled):
     if T_ref:  # laws given at a reference temperature (Section 4.2.2 form)
         m0 = p.mats[0]
         p.mats[0] = fi.Material(m0.rho, m0.k0, m0.k_lin, m0.c0, m0.c_lin, T_ref=T_ref)
-    if scheduled:  # time-dependent loads: the source gradient carries q(n)
+    if scheduled:  # time-dependent loads (the source gradient carries q(n)) and Dirichlet values
         k = np.arange(45)
         p.q_schedule = 1.0 + 0.6 * np.cos(0.2 * k)
         p.Tinf_schedule = 20.0 + 3.0 * k
+        bottom = np.flatnonzero(np.abs(p.xyz[:, 2]) < 1e-9).astype(np.int32)
+        p.dir_nodes, p.dir_T = bottom, np.full(len(bottom), 20.0)
+        p.Tdir_schedule = 15.0 * np.sin(0.3 * k)
     m = O.OracleModel(p)
     dt = 0.9 * m.dt_crit()[0]
     nsteps, se, ck = 60, 10, 20

@@ -217,6 +217,52 @@ def _scheduled_cube():
     return p
 
 
+def _dirichlet_cube(kind):
+    """Nonlinear cube with its bottom face held at 100 + 50 x plus an offset that moves every
+    step (a ramp with a sine on it, 250 entries, the last one held)."""
+    p = fi.nonlinear_cube(9, kind, jitter=0.2 if kind == "hex" else 0.0)
+    bottom = np.flatnonzero(np.abs(p.xyz[:, 2]) < 1e-9).astype(np.int32)
+    p.dir_nodes = bottom
+    p.dir_T = 100.0 + 50.0 * p.xyz[bottom, 0]
+    k = np.arange(250)
+    p.Tdir_schedule = 80.0 * np.sin(0.04 * k) + 0.4 * k
+    p.T_hi = max(p.T_hi, 400.0)
+    return p
+
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+@pytest.mark.parametrize("precision", [64, 32])
+def test_time_dependent_dirichlet(kind, precision):
+    """Prescribed temperatures that move every step (dir_T + d[n]): GPU against the oracle over
+    300 steps in launches of 37 steps with the run split across two calls; the energy terms of
+    the last step; a new offset schedule set at step 300 moves the Dirichlet values to those of
+    that step and the run continues with it."""
+    p = _dirichlet_cube(kind)
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    T_ref, E = m.run(p.initial_T(), dt, 300, energy=True)
+    f = FedFem(p, precision=precision, steps_per_launch=37)
+    f.precompute()
+    f.set_dt(dt, force=True)
+    f.set_T(p.initial_T())
+    f.step(123)
+    f.step(177)
+    T = f.get_T()
+    scale = np.max(np.abs(T_ref))
+    assert rel(T, T_ref) <= TOL[precision]
+    assert np.max(np.abs(T[p.dir_nodes] - (p.dir_T + p.Tdir_schedule[-1]))) <= TOL[precision] * scale
+    if precision == 64:
+        S, B = f.energy()
+        assert S == pytest.approx(E[-1, 0], rel=1e-8) and B == pytest.approx(E[-1, 1], rel=1e-8)
+    d2 = 30.0 * np.cos(0.03 * np.arange(400))
+    f.set_schedule(T_dir=d2)
+    m.set_schedule(T_dir=d2)
+    f.step(100)
+    T2 = m.run(T_ref, dt, 100, step0=300)
+    assert rel(f.get_T(), T2) <= TOL[precision]
+    f.close()
+
+
 @pytest.mark.parametrize("precision", [64, 32])
 def test_time_dependent_loads(precision):
     """Load multiplier and convection ambient temperature per step (last entries held beyond

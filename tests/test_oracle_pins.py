@@ -488,13 +488,15 @@ def test_stefan_law_spot_value():
 
 # -------------------------------------------------------------------------- energy ---------
 
-@pytest.mark.parametrize("kind", ["hex", "tet"])
-def test_energy_balance(kind):
+@pytest.mark.parametrize("kind,moving", [("hex", False), ("tet", False), ("hex", True)])
+def test_energy_balance(kind, moving):
     """Internal loads sum to zero, so the stored heat changes only by the boundary and source
-    flows: S^n = B^n every step (FP64)."""
+    flows: S^n = B^n every step (FP64), also when the prescribed temperatures move."""
     p = fi.nonlinear_cube(5, kind)
     p.dir_nodes = np.arange(0, 6, dtype=np.int32)
     p.dir_T = np.full(6, 60.0)
+    if moving:
+        p.Tdir_schedule = 40.0 * np.sin(0.2 * np.arange(60))
     m = O.OracleModel(p)
     dt = 0.9 * m.dt_crit()[0]
     T, E = m.run(p.initial_T(), dt, 60, energy=True)
@@ -518,12 +520,16 @@ def _adjoint_setup():
 @pytest.mark.parametrize("scheduled", [False, True])
 def test_adjoint_matches_central_differences(scheduled):
     """Reverse-time adjoint vs central finite differences of the forward loop (FP64); also
-    with a load schedule (q(n) scales the sources, T_inf(n) moves)."""
+    with a schedule (q(n) scales the sources, T_inf(n) moves, the bottom face is held at a
+    temperature that moves every step)."""
     p, sensors = _adjoint_setup()
     if scheduled:
         k = np.arange(30)
         p.q_schedule = 1.0 + 0.8 * np.cos(0.3 * k)
         p.Tinf_schedule = 20.0 + 2.0 * k
+        bottom = np.flatnonzero(np.abs(p.xyz[:, 2]) < 1e-9).astype(np.int32)
+        p.dir_nodes, p.dir_T = bottom, np.full(len(bottom), 20.0)
+        p.Tdir_schedule = 25.0 * np.sin(0.4 * k)
     m0 = O.OracleModel(p)
     dt = 0.9 * m0.dt_crit()[0]
     nsteps, se = 30, 5
