@@ -68,6 +68,11 @@ class Problem:
     q_schedule: Optional[np.ndarray] = None     # [n] multiplier of the external loads at step n
     Tinf_schedule: Optional[np.ndarray] = None  # [n] convection ambient temperature at step n
     Tdir_schedule: Optional[np.ndarray] = None  # [n] offset added to every dir_T at step n
+    # tabulated property factors (replace the materials' linear laws): f_k, f_c of k0, c0 at the
+    # increasing temperatures table_T, linear between points, end values held outside
+    table_T: Optional[np.ndarray] = None
+    table_fk: Optional[np.ndarray] = None
+    table_fc: Optional[np.ndarray] = None
 
     @property
     def npe(self) -> int:

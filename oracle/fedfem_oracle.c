@@ -280,7 +280,71 @@ typedef struct {
      * schedule); Tdir [nn] holds the prescribed values of Gamma_E (read on Dirichlet nodes) */
     const double *Tdir;
     const double *Tdir_sched;
+    /* tabulated property factors (optional, n_tab >= 2; they replace the linear laws above):
+     * f_k and f_c given at the increasing temperatures tab_T, interpolated linearly between
+     * neighbouring points and held at the end values outside [tab_T[0], tab_T[n_tab - 1]] */
+    int64_t n_tab;
+    const double *tab_T, *tab_fk, *tab_fc;
 } orc_model;
+
+/* Value of a tabulated factor v at T: linear between the two table points around T. */
+static double orc_table(const orc_model *m, const double *v, double T)
+{
+    const double *t = m->tab_T;
+    const int64_t n = m->n_tab;
+    if (T <= t[0]) return v[0];
+    if (T >= t[n - 1]) return v[n - 1];
+    int64_t j = 0;
+    while (T > t[j + 1]) ++j; /* t[j] < T <= t[j + 1] */
+    return v[j] + (v[j + 1] - v[j]) * (T - t[j]) / (t[j + 1] - t[j]);
+}
+
+/* Slope of a tabulated factor at T (0 where the end values are held). */
+static double orc_table_slope(const orc_model *m, const double *v, double T)
+{
+    const double *t = m->tab_T;
+    const int64_t n = m->n_tab;
+    if (T <= t[0] || T >= t[n - 1]) return 0.0;
+    int64_t j = 0;
+    while (T > t[j + 1]) ++j;
+    return (v[j + 1] - v[j]) / (t[j + 1] - t[j]);
+}
+
+/* Conductivity and capacity factors at a nodal temperature (Section 4.2.2) and their slopes. */
+static double orc_fk(const orc_model *m, double T)
+{
+    return m->n_tab >= 2 ? orc_table(m, m->tab_fk, T) : 1.0 + m->k_lin * (T - m->T_ref);
+}
+
+static double orc_fc(const orc_model *m, double T)
+{
+    return m->n_tab >= 2 ? orc_table(m, m->tab_fc, T) : 1.0 + m->c_lin * (T - m->T_ref);
+}
+
+static double orc_dfk(const orc_model *m, double T)
+{
+    return m->n_tab >= 2 ? orc_table_slope(m, m->tab_fk, T) : m->k_lin;
+}
+
+static double orc_dfc(const orc_model *m, double T)
+{
+    return m->n_tab >= 2 ? orc_table_slope(m, m->tab_fc, T) : m->c_lin;
+}
+
+/* Largest f_k and smallest f_c over [T_lo, T_hi]: a piecewise-linear factor takes its extrema
+ * at the interval ends or at table points inside it. */
+static void orc_factor_extrema(const orc_model *m, double T_lo, double T_hi, double *fk_max, double *fc_min)
+{
+    double kmax = fmax(orc_fk(m, T_lo), orc_fk(m, T_hi));
+    double cmin = fmin(orc_fc(m, T_lo), orc_fc(m, T_hi));
+    for (int64_t j = 0; m->n_tab >= 2 && j < m->n_tab; ++j)
+        if (m->tab_T[j] > T_lo && m->tab_T[j] < T_hi) {
+            kmax = fmax(kmax, m->tab_fk[j]);
+            cmin = fmin(cmin, m->tab_fc[j]);
+        }
+    *fk_max = kmax;
+    *fc_min = cmin;
+}
 
 /*
  * Pre-computation (Fig. 1 (i)): element matrices K0_e and shape-function integrals, lumped
@@ -353,7 +417,7 @@ void orc_internal_loads(const orc_model *m, const double *T, double *F)
         const int32_t *c = m->conn + npe * e;
         const double *Ke = m->K + (int64_t)npe * npe * e;
         double fk = 0.0;
-        for (int i = 0; i < npe; ++i) fk += 1.0 + m->k_lin * (T[c[i]] - m->T_ref);
+        for (int i = 0; i < npe; ++i) fk += orc_fk(m, T[c[i]]);
         fk /= npe;
         const double s = m->theta[e] * fk;
         for (int i = 0; i < npe; ++i) {
@@ -436,7 +500,7 @@ void orc_run(const orc_model *m, double dt, int64_t nsteps, double *T, double *e
                 continue;
             }
             const double Q = orc_nodal_Q_n(m, i, T[i], m->sched_step0 + n);
-            const double Ci = m->C0[i] * (1.0 + m->c_lin * (T[i] - m->T_ref));
+            const double Ci = m->C0[i] * orc_fc(m, T[i]);
             const double Tn = T[i] + dt / Ci * (Q - F[i]);
             S += Ci * (Tn - T[i]);
             B += dt * Q;
@@ -469,8 +533,8 @@ void orc_run(const orc_model *m, double dt, int64_t nsteps, double *T, double *e
  */
 double orc_dt_from_lambda(const orc_model *m, double lam, double T_lo, double T_hi)
 {
-    const double fk_max = fmax(1.0 + m->k_lin * (T_lo - m->T_ref), 1.0 + m->k_lin * (T_hi - m->T_ref));
-    const double fc_min = fmin(1.0 + m->c_lin * (T_lo - m->T_ref), 1.0 + m->c_lin * (T_hi - m->T_ref));
+    double fk_max, fc_min;
+    orc_factor_extrema(m, T_lo, T_hi, &fk_max, &fc_min);
     const double rl = fabs(T_lo - m->T_zero), rh = fabs(T_hi - m->T_zero);
     const double r3 = fmax(rl * rl * rl, rh * rh * rh);
     double surf = 0.0;
@@ -490,6 +554,7 @@ void orc_dt_crit(const orc_model *m, double T_lo, double T_hi, double tol, int64
     double *F = (double *)malloc(nn * sizeof(double));
     orc_model lin = *m;
     lin.k_lin = 0.0;
+    lin.n_tab = 0;
     double nrm = 0.0;
     for (int64_t i = 0; i < nn; ++i) {
         x[i] = m->isdir[i] ? 0.0 : 1.0 + 0.5 * sin(0.7 * (double)i + 0.3);
@@ -528,8 +593,8 @@ void orc_dt_crit(const orc_model *m, double T_lo, double T_hi, double tol, int64
  * kept (no checkpointing).  With a_i = dt / (C0_i f_c(T_i)) on free nodes (0 on Dirichlet),
  * mu_i = a_i lambda_i^{n+1}:
  *   lambda_j^n = dL/dT_j^n + lambda_j^{n+1} (1 + a_j'(T_j) R_j) + mu_j dQ_j/dT_j
- *              - sum_{e∋j} theta_e [ f_k,e (K0_e mu_e)_j + (mu_e . K0_e T_e) k_lin / npe ],
- *   R_j = Q_j - F_j,  a_j' = -a_j c_lin / f_c(T_j),
+ *              - sum_{e∋j} theta_e [ f_k,e (K0_e mu_e)_j + (mu_e . K0_e T_e) f_k'(T_j) / npe ],
+ *   R_j = Q_j - F_j,  a_j' = -a_j f_c'(T_j) / f_c(T_j),
  *   dL/dtheta_e = -sum_n f_k,e mu_e . K0_e T_e^n,
  *   dL/ds_e = sum_n q_scale(n) sum_{i in e} mu_i w_ie (q_scale = 1 without a load schedule).
  * T0 [nn]: initial state (Dirichlet imposed); dLdtrace [n/sample_every][ns];
@@ -570,11 +635,11 @@ void orc_adjoint(const orc_model *m, double dt, int64_t nsteps, const double *T0
                 lnew[i] = lam[i];
                 continue;
             }
-            const double fc = 1.0 + m->c_lin * (T[i] - m->T_ref);
+            const double fc = orc_fc(m, T[i]);
             const double a = dt / (m->C0[i] * fc);
             const int64_t step = m->sched_step0 + n - 1;
             const double R = orc_nodal_Q_n(m, i, T[i], step) - F[i];
-            const double da = -a * m->c_lin / fc;
+            const double da = -a * orc_dfc(m, T[i]) / fc;
             mu[i] = a * lam[i];
             lnew[i] = lam[i] * (1.0 + da * R) + mu[i] * orc_nodal_dQ(m, i, T[i]);
             musum[i] += orc_q_scale(m, step) * mu[i];  /* d Q_i / d s_e = q_scale w_ie */
@@ -583,7 +648,7 @@ void orc_adjoint(const orc_model *m, double dt, int64_t nsteps, const double *T0
             const int32_t *c = m->conn + npe * e;
             const double *Ke = m->K + (int64_t)npe * npe * e;
             double fk = 0.0;
-            for (int i = 0; i < npe; ++i) fk += 1.0 + m->k_lin * (T[c[i]] - m->T_ref);
+            for (int i = 0; i < npe; ++i) fk += orc_fk(m, T[c[i]]);
             fk /= npe;
             double muKT = 0.0;
             for (int i = 0; i < npe; ++i) {
@@ -594,7 +659,7 @@ void orc_adjoint(const orc_model *m, double dt, int64_t nsteps, const double *T0
             for (int j = 0; j < npe; ++j) {
                 double kmu = 0.0;
                 for (int i = 0; i < npe; ++i) kmu += Ke[npe * i + j] * mu[c[i]];
-                lnew[c[j]] -= m->theta[e] * (fk * kmu + muKT * m->k_lin / npe);
+                lnew[c[j]] -= m->theta[e] * (fk * kmu + muKT * orc_dfk(m, T[c[j]]) / npe);
             }
             g_theta[e] -= fk * muKT;
         }

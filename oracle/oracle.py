@@ -11,6 +11,7 @@ Function map (paper passages):
   OracleModel.internal_loads  Eq. 11/20 with the element-mean k(T) of Section 4.2.2
   OracleModel.run             time-stepping stage, Fig. 1 (iii): Eq. 15/16, Dirichlet re-imposed
   OracleModel.set_schedule    time-dependent loads, convection temperature and Dirichlet values
+  OracleModel.set_table       tabulated k(T), c(T) factors, linear between points (Section 4.2.2)
   OracleModel.dt_crit         Section 3.4, Eq. 29
   OracleModel.adjoint         reverse-time discrete adjoint of Eq. 16/20 (derived, no paper
                               counterpart)
@@ -53,7 +54,8 @@ class _Model(C.Structure):
                 ("h", C.c_double), ("T_inf", C.c_double), ("eps", C.c_double),
                 ("T_amb", C.c_double), ("T_zero", C.c_double), ("T_ref", C.c_double),
                 ("q_sched", C.c_void_p), ("Tinf_sched", C.c_void_p), ("n_sched", C.c_int64),
-                ("sched_step0", C.c_int64), ("Tdir", C.c_void_p), ("Tdir_sched", C.c_void_p)]
+                ("sched_step0", C.c_int64), ("Tdir", C.c_void_p), ("Tdir_sched", C.c_void_p),
+                ("n_tab", C.c_int64), ("tab_T", C.c_void_p), ("tab_fk", C.c_void_p), ("tab_fc", C.c_void_p)]
 
 
 def lib():
@@ -189,6 +191,8 @@ class OracleModel:
                         T_zero=float(p.T_zero), T_ref=float(getattr(mats[0], "T_ref", 0.0)),
                         Tdir=_p(self.Tdir))
         self.mref = C.byref(self.m)
+        if getattr(p, "table_T", None) is not None:
+            self.set_table(p.table_T, p.table_fk, p.table_fc)
         self._sched = (None, None, None)
         sched = [getattr(p, f, None) for f in ("q_schedule", "Tinf_schedule", "Tdir_schedule")]
         if any(s is not None for s in sched):
@@ -209,6 +213,20 @@ class OracleModel:
         self.m.Tinf_sched = None if t is None else t.ctypes.data
         self.m.Tdir_sched = None if d is None else d.ctypes.data
         self.m.n_sched = lens.pop() if lens else 0
+
+    def set_table(self, T, fk, fc):
+        """Tabulated factors of k0 and c0 at the temperatures T (increasing; linear between
+        points, end values held outside); None removes the table."""
+        if T is None:
+            self._tab = None
+            self.m.n_tab, self.m.tab_T, self.m.tab_fk, self.m.tab_fc = 0, None, None, None
+            return
+        self._tab = tuple(_f64(a) for a in (T, fk, fc))
+        n = len(self._tab[0])
+        if n < 2 or any(len(a) != n for a in self._tab) or np.any(np.diff(self._tab[0]) <= 0):
+            raise ValueError("a table needs >= 2 increasing temperatures and one factor of each kind per point")
+        self.m.n_tab = n
+        self.m.tab_T, self.m.tab_fk, self.m.tab_fc = (a.ctypes.data for a in self._tab)
 
     # lumped thermal mass at f_c = 1 (Section 3.1, Eq. 14 / 21)
     @property

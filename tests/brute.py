@@ -103,14 +103,16 @@ def c1_closed_form(n, dt, nsteps, T0=100.0):
 
 
 def ftcs_slab(nx, h, dt, nsteps, T0, Ts, k, rho, c0, k_lin=0.0, c_lin=0.0, conv=None,
-              source=0.0, Ts_offset=None):
+              source=0.0, Ts_offset=None, fk_fn=None, fc_fn=None):
     """1-D forward-Euler recurrence equivalent to a bar of bricks whose field is constant over
     each cross-section (consistent row sums = lumped mass):
       interior  T_j += dt k / (rho c(T_j) h^2) [f_R (T_{j+1}-T_j) + f_L (T_{j-1}-T_j)]
       x = L end T_n += 2 dt k / (rho c(T_n) h^2) f_L (T_{n-1}-T_n) - 2 dt hc/(rho c(T_n) h) (T_n - T_inf)
     with f on an element = 1 + k_lin (T_left + T_right)/2 and c(T) = c0 (1 + c_lin T); a
     uniform volumetric source s adds dt s / (rho c(T_j)) to every free node.  With Ts_offset
-    the held end is Ts + Ts_offset[n] at step n (the last entry beyond the end)."""
+    the held end is Ts + Ts_offset[n] at step n (the last entry beyond the end).  With fk_fn /
+    fc_fn (callables of the nodal temperature) the element factor is the mean of fk_fn over
+    its two end temperatures and c(T) = c0 fc_fn(T)."""
     def end_value(n):
         if Ts_offset is None:
             return Ts
@@ -119,8 +121,12 @@ def ftcs_slab(nx, h, dt, nsteps, T0, Ts, k, rho, c0, k_lin=0.0, c_lin=0.0, conv=
     T = np.full(nx + 1, float(T0))
     T[0] = end_value(0)
     for n in range(nsteps):
-        f = 1.0 + k_lin * 0.5 * (T[:-1] + T[1:])          # per element
-        c = c0 * (1.0 + c_lin * T)
+        if fk_fn is None:
+            f = 1.0 + k_lin * 0.5 * (T[:-1] + T[1:])      # per element
+        else:
+            fn = fk_fn(T)
+            f = 0.5 * (fn[:-1] + fn[1:])
+        c = c0 * (1.0 + c_lin * T) if fc_fn is None else c0 * fc_fn(T)
         Tn = T.copy()
         Tn[1:-1] = T[1:-1] + dt * k / (rho * c[1:-1] * h * h) * (
             f[1:] * (T[2:] - T[1:-1]) + f[:-1] * (T[:-2] - T[1:-1]))

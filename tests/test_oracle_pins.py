@@ -281,6 +281,83 @@ def test_two_point_law_of_section_4_2_2():
     assert 2000.0 * c_lin == pytest.approx(20.0, rel=1e-14)
 
 
+def test_two_point_table_is_the_linear_law():
+    """A two-point table through a linear law, spanning every temperature of the run, is that
+    law (run and dt_crit); extra collinear points change nothing."""
+    p = fi.nonlinear_cube(5, "hex")
+    m_lin = O.OracleModel(p)
+    kl, cl = p.mats[0].k_lin, p.mats[0].c_lin
+    dt = 0.9 * m_lin.dt_crit()[0]
+    T_lin = m_lin.run(p.initial_T(), dt, 200)
+    lo, hi = p.T_lo - 50.0, max(p.T_hi, T_lin.max()) + 50.0
+    for pts in (np.array([lo, hi]), np.array([lo, 0.7 * lo + 0.3 * hi, 0.5 * (lo + hi), hi])):
+        q = fi.nonlinear_cube(5, "hex")
+        q.table_T, q.table_fk, q.table_fc = pts, 1.0 + kl * pts, 1.0 + cl * pts
+        m = O.OracleModel(q)
+        assert np.max(np.abs(m.run(q.initial_T(), dt, 200) - T_lin)) <= 1e-12 * np.abs(T_lin).max()
+        assert m.dt_crit()[0] == pytest.approx(m_lin.dt_crit()[0], rel=1e-12)
+
+
+@pytest.mark.parametrize("ny", [1, 2])
+def test_slab_table_law_reduces_to_1d_recurrence(ny):
+    """Tabulated k(T), c(T) (linear between points, end values held; Section 4.2.2 with more
+    points): the bar reduces exactly to the 1-D recurrence whose element factor is the mean of
+    the two nodal values from numpy's interpolation; the hot end lies past the last point."""
+    nx, k, rho, c0 = 20, 2.0, 3.0, 1.5
+    tT = np.array([10.0, 30.0, 55.0, 80.0])
+    tk = np.array([1.0, 2.5, 1.8, 3.0])
+    tc = np.array([1.0, 0.7, 1.6, 1.2])
+    p = fi.slab(nx, ny, ny, Lx=1.0, k=(k, 7.0, 9.0), rho=rho, c0=c0, T0=0.0, T_s=100.0,
+                conv_end=(4.0, 10.0))
+    p.table_T, p.table_fk, p.table_fc = tT, tk, tc
+    m = O.OracleModel(p)
+    h = 1.0 / nx
+    dt = 0.2 * rho * c0 * 0.7 * h * h / (k * 3.0 * 3.0)
+    T = m.run(p.initial_T(), dt, 400)
+    ref = brute.ftcs_slab(nx, h, dt, 400, 0.0, 100.0, k, rho, c0, conv=(4.0, 10.0),
+                          fk_fn=lambda t: np.interp(t, tT, tk), fc_fn=lambda t: np.interp(t, tT, tc))
+    ix = np.rint(p.xyz[:, 0] / h).astype(int)
+    assert np.max(np.abs(T - ref[ix])) <= 1e-13 * 100.0
+    assert ref.min() < tT[0] and ref.max() > tT[-1] and np.sum((ref > tT[1]) & (ref < tT[2])) > 0
+
+
+def test_single_brick_table_capacity():
+    """A uniform brick cooling by convection from above the table to below it: every node
+    follows the scalar recurrence with c(T) from numpy's interpolation (end values held)."""
+    a, b, c = 0.3, 0.5, 0.7
+    rho, c0, hc, Tinf = 800.0, 900.0, 40.0, 15.0
+    tT = np.array([50.0, 150.0, 300.0])
+    tc = np.array([0.8, 1.5, 1.1])
+    p = fi.single_brick(a, b, c, rho, c0, 0.0, T0=400.0, conv=(hc, Tinf))
+    p.table_T, p.table_fk, p.table_fc = tT, np.array([1.0, 3.0, 2.0]), tc
+    m = O.OracleModel(p)
+    A = (a * b + b * c + c * a) / 4.0
+    Cn = rho * c0 * a * b * c / 8.0
+    dt, n = 20.0, 400
+    T = m.run(p.initial_T(), dt, n)
+    s = 400.0
+    for _ in range(n):
+        s = s + dt / (Cn * np.interp(s, tT, tc)) * (-A * hc * (s - Tinf))
+    assert s < tT[0]
+    assert np.max(np.abs(T - s)) <= 1e-12 * 400.0
+
+
+def test_table_critical_step_extrema():
+    """dt_crit with a table: 2 min f_c / (lambda max f_k) with the extrema of the interpolated
+    factors taken by brute force on a fine grid over [T_lo, T_hi] (no surface terms)."""
+    p = fi.nonlinear_cube(3, "hex")
+    p.h, p.eps = 0.0, 0.0
+    p.conv_faces, p.rad_faces = None, None
+    tT = np.array([-100.0, 137.0, 512.0, 2000.0])
+    p.table_T, p.table_fk, p.table_fc = tT, np.array([1.0, 4.0, 2.0, 3.5]), np.array([2.0, 2.5, 0.6, 0.9])
+    m = O.OracleModel(p)
+    lam = 7.0
+    for lo, hi in ((0.0, 1000.0), (200.0, 400.0), (-500.0, 3000.0)):
+        g = np.linspace(lo, hi, 1_000_001)
+        fk, fc = np.interp(g, tT, p.table_fk), np.interp(g, tT, p.table_fc)
+        assert m.dt_from_lambda(lam, lo, hi) == pytest.approx(2.0 * fc.min() / (lam * fk.max()), rel=1e-6)
+
+
 def test_adaptive_step_is_the_fixed_step_without_temperature_laws():
     """Without k(T), c(T) and radiation dt_crit does not depend on the temperature range, so
     the per-launch adaptive step is the fixed step: same field (bitwise) and time n dt."""
@@ -517,7 +594,7 @@ def _adjoint_setup():
     return p, sensors
 
 
-@pytest.mark.parametrize("scheduled", [False, True])
+@pytest.mark.parametrize("scheduled", [False, True, "table"])
 def test_adjoint_matches_central_differences(scheduled):
     """Reverse-time adjoint vs central finite differences of the forward loop (FP64); also
     with a schedule (q(n) scales the sources, T_inf(n) moves, the bottom face is held at a
@@ -530,6 +607,11 @@ def test_adjoint_matches_central_differences(scheduled):
         bottom = np.flatnonzero(np.abs(p.xyz[:, 2]) < 1e-9).astype(np.int32)
         p.dir_nodes, p.dir_T = bottom, np.full(len(bottom), 20.0)
         p.Tdir_schedule = 25.0 * np.sin(0.4 * k)
+    if scheduled == "table":  # tabulated k(T), c(T): the adjoint carries the segment slopes
+        p.q_schedule = p.Tinf_schedule = p.Tdir_schedule = None
+        p.table_T = np.array([0.0, 150.0, 300.0, 450.0, 1000.0])
+        p.table_fk = np.array([0.8, 1.0, 1.6, 1.3, 2.0])
+        p.table_fc = np.array([1.1, 1.0, 0.8, 1.4, 1.2])
     m0 = O.OracleModel(p)
     dt = 0.9 * m0.dt_crit()[0]
     nsteps, se = 30, 5
