@@ -246,6 +246,22 @@ fedfem_status fedfem_set_params(fedfem_ctx *ctx, const double *kscale, const dou
 fedfem_status fedfem_set_schedule(fedfem_ctx *ctx, int64_t n_entries, const double *q_scale, const double *T_inf,
                                   const double *T_dir);
 
+/*
+ * Tabulated property factors (Section 4.2.2 interpolates k and c linearly between the
+ * temperatures at which they are given): f_k = k / k0 and f_c = c / c0 at the n_points
+ * increasing temperatures T, linear between neighbouring points and held at the end values
+ * outside the table.  As in Section 4.2.2, k enters an element as the mean of its nodal
+ * factors f_k(T_i); c enters each node's lumped capacity as f_c(T_i).  The table replaces the
+ * materials' linear laws (k_lin, c_lin, T_ref) in the time steps, dt_crit (extrema of the
+ * factors over [T_lo, T_hi]: at the ends or at table points inside), fedfem_step_adaptive,
+ * fedfem_energy, fedfem_internal_loads and the adjoint.  n_points = 0 removes it.  Arrays:
+ * [n_points] FP64 host, copied.  Must precede fedfem_precompute.
+ * Errors: ARG (n_points not 0 or 2..8, NULL arrays, temperatures not finite and increasing,
+ * factors not finite and > 0), STATE (after fedfem_precompute), UNSUPPORTED (batches).
+ */
+fedfem_status fedfem_set_property_table(fedfem_ctx *ctx, int32_t n_points, const double *T, const double *fk,
+                                        const double *fc);
+
 /* Checkpoint / resume: the state is (T, Kahan compensation, step counter).  state_bytes
  * returns the size of the opaque blob; get/set copy it to/from a host buffer. */
 fedfem_status fedfem_state_bytes(fedfem_ctx *ctx, size_t *bytes);
@@ -293,6 +309,8 @@ typedef struct {
  *   f_c = 1), Qext, Ac, Ar (constant nodal loads and convection / radiation area shares) and
  *   is_dirichlet (1 on Gamma_E);  out: DEVICE array of 2 doubles receiving
  *   (stored_change, boundary_in);  stream: cudaStream_t or NULL.  Asynchronous on `stream`.
+ * The capacity factor is the linear law of params (c_lin, T_ref); a context with a property
+ * table gets its sums from fedfem_energy.
  * All calls on a device share the scratch array: calls that overlap on the GPU race.  Each call
  * overwrites every partial it reads, so nothing needs clearing between calls.  The first call
  * on a device looks the array's address up (cudaGetSymbolAddress) with that device current:

@@ -82,6 +82,7 @@ SIGNATURES = {
     "fedfem_internal_loads": (I32, [P, P, P]),
     "fedfem_set_params": (I32, [P, P, P]),
     "fedfem_set_schedule": (I32, [P, I64, P, P, P]),
+    "fedfem_set_property_table": (I32, [P, I32, P, P, P]),
     "fedfem_state_bytes": (I32, [P, P]),
     "fedfem_get_state": (I32, [P, P]),
     "fedfem_set_state": (I32, [P, P]),

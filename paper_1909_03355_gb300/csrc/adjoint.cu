@@ -6,8 +6,10 @@
 // With a_i = A_i / f_c(T_i^n) (0 on Dirichlet nodes), mu_i = a_i lambda_i^{n+1},
 // R_i = Q_i - F_i and c_e = theta_e K0_e (the stored pair conductances):
 //   lambda_j^n = dL/dT_j^n + lambda_j^{n+1} (1 + d_j) + mu_j dQ_j/dT_j - G_j,
-//   d_j = -a_j c_lin / f_c(T_j) R_j,
-//   G_j = sum_{e∋j} [ f_k,e (c_e mu_e)_j + (mu_e . c_e T_e) k_lin / npe ],
+//   d_j = -a_j f_c'(T_j) / f_c(T_j) R_j,
+//   G_j = sum_{e∋j} [ f_k,e (c_e mu_e)_j + (mu_e . c_e T_e) f_k'(T_j) / npe ],
+// (f' = k_lin, c_lin for the linear laws; the segment slope, 0 where the end values are held,
+// for tabulated factors)
 //   dL/dtheta_e = -sum_n f_k,e (mu_e . c_e T_e) / theta_e,
 //   dL/ds_e     =  sum_{i in e} w_ie sum_n mu_i^n.
 // The forward run keeps checkpoints of the state every K steps; each segment is recomputed
@@ -38,7 +40,19 @@ struct AdjPhys {
     double k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero;
     double k_a, c_a;  // f_k = k_a + k_lin T, f_c = c_a + c_lin T
     double qs;        // external-load multiplier of the step (time-dependent loads)
+    int tab;          // 1: tabulated f_k = tk, f_c = tc instead of the linear laws
+    HingeLaw<double> tk, tc;
 };
+
+__device__ __forceinline__ double adj_fc(const AdjPhys &ph, double t)
+{
+    return ph.tab ? hinge_value(ph.tc, t) : ph.c_a + ph.c_lin * t;
+}
+
+__device__ __forceinline__ double adj_dfc(const AdjPhys &ph, double t)
+{
+    return ph.tab ? hinge_slope(ph.tc, t) : ph.c_lin;
+}
 
 int nblk(int64_t n, int bs = 256)
 {
@@ -58,22 +72,22 @@ __global__ void k_gather_sensors(int ns, const int32_t *sens, const R *T, const 
 
 // mu_i = a_i lambda_i, a_i = A_i / f_c(T_i) (A = 0 on Dirichlet nodes); musum += mu
 template <typename R>
-__global__ void k_adj_mu(int64_t nn, const R *Tn, const double *A, const double *lam, double c_a, double c_lin,
-                         double qs, double *mu, double *musum)
+__global__ void k_adj_mu(int64_t nn, const R *Tn, const double *A, const double *lam, AdjPhys ph, double qs,
+                         double *mu, double *musum)
 {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
         const double t = (double)Tn[g];
-        const double m = A[g] / (c_a + c_lin * t) * lam[g];
+        const double m = A[g] / adj_fc(ph, t) * lam[g];
         mu[g] = m;
         musum[g] += qs * m;  // d Q_g / d s_e = qs w_ge
     }
 }
 
 // Element pass: forward loads F_e = f_k (c T_e) and adjoint loads
-// G_e = f_k (c mu_e) + (mu_e . c T_e) k_lin / npe into per-element slots; theta gradient.
+// G_e = f_k (c mu_e) + (mu_e . c T_e) f_k'(T_j) / npe into per-element slots; theta gradient.
 template <int NPE, typename R>
 __global__ void k_adj_elem(int64_t ne, const int32_t *gconn, const double *cond64, const R *Tn, const double *mu,
-                           const double *theta, double k_a, double k_lin, double *YF, double *YG, double *gtheta)
+                           const double *theta, AdjPhys ph, double *YF, double *YG, double *gtheta)
 {
     constexpr int NC = NPE * (NPE - 1) / 2;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
@@ -83,7 +97,7 @@ __global__ void k_adj_elem(int64_t ne, const int32_t *gconn, const double *cond6
             const int g = gconn[NPE * e + k];
             T[k] = (double)Tn[g];
             m[k] = mu[g];
-            sum += T[k];
+            sum += ph.tab ? hinge_value(ph.tk, T[k]) : T[k];
             cT[k] = 0.0;
             cm[k] = 0.0;
         }
@@ -98,12 +112,12 @@ __global__ void k_adj_elem(int64_t ne, const int32_t *gconn, const double *cond6
                 cm[i] += gm;
                 cm[j] -= gm;
             }
-        const double fk = k_a + k_lin * (sum / NPE);
+        const double fk = ph.tab ? sum / NPE : ph.k_a + ph.k_lin * (sum / NPE);
         double mcT = 0.0;
         for (int k = 0; k < NPE; ++k) mcT += m[k] * cT[k];
         for (int k = 0; k < NPE; ++k) {
             YF[NPE * e + k] = fk * cT[k];
-            YG[NPE * e + k] = fk * cm[k] + mcT * k_lin / NPE;
+            YG[NPE * e + k] = fk * cm[k] + mcT * (ph.tab ? hinge_slope(ph.tk, T[k]) : ph.k_lin) / NPE;
         }
         gtheta[e] -= fk * mcT / theta[e];
     }
@@ -134,17 +148,17 @@ __global__ void k_adj_node(int64_t nn, int npe, const int32_t *n2e_ptr, const in
             l = lam[g] - G;
         } else {
             const double t = (double)Tn[g];
-            const double fc = ph.c_a + ph.c_lin * t;
+            const double fc = adj_fc(ph, t);
             const double a = A[g] / fc;
             const double u = t - ph.T_zero, b = ph.T_amb - ph.T_zero;
             const double Q = ph.qs * Qext[g] - Ac[g] * ph.h * (t - ph.T_inf) - Ar[g] * ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
             const double dQ = -Ac[g] * ph.h - Ar[g] * ph.eps_sigma * 4.0 * u * u * u;
-            const double d = -a * ph.c_lin / fc * (Q - F);
+            const double d = -a * adj_dfc(ph, t) / fc * (Q - F);
             l = lam[g] * (1.0 + d) + mu[g] * dQ - G;
         }
         if (Tprev) {
             if (dl_next && sens_idx[g] >= 0) l += dl_next[sens_idx[g]];
-            const double m = A[g] / (ph.c_a + ph.c_lin * (double)Tprev[g]) * l;
+            const double m = A[g] / adj_fc(ph, (double)Tprev[g]) * l;
             mu[g] = m;
             musum[g] += qs_prev * m;
         }
@@ -220,13 +234,13 @@ void adj_step(fedfem_ctx *c, bool first, const void *Tn, const void *Tprev, cons
     const int npe = c->npe;
     const R *T = static_cast<const R *>(Tn);
     if (first)
-        k_adj_mu<R><<<nblk(nn, 128), 128, 0, c->stream>>>(nn, T, c->d_A, lam_in, c->c_a(), c->c_lin, ph.qs, mu, musum);
+        k_adj_mu<R><<<nblk(nn, 128), 128, 0, c->stream>>>(nn, T, c->d_A, lam_in, ph, ph.qs, mu, musum);
     if (npe == 8)
-        k_adj_elem<8, R><<<nblk(ne, 64), 64, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, T, mu, c->d_kscale, c->k_a(),
-                                                         c->k_lin, YF, YG, gth);
+        k_adj_elem<8, R><<<nblk(ne, 64), 64, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, T, mu, c->d_kscale, ph, YF, YG,
+                                                         gth);
     else
-        k_adj_elem<4, R><<<nblk(ne, 64), 64, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, T, mu, c->d_kscale, c->k_a(),
-                                                         c->k_lin, YF, YG, gth);
+        k_adj_elem<4, R><<<nblk(ne, 64), 64, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, T, mu, c->d_kscale, ph, YF, YG,
+                                                         gth);
     k_adj_node<R><<<nblk(nn, 128), 128, 0, c->stream>>>(nn, npe, c->d_n2e_ptr, c->d_n2e, YF, YG, T, lam_in, mu, c->d_A,
                                                    c->d_Qext64, c->d_Ac64, c->d_Ar64, c->d_isdir, ph, lam_out,
                                                    static_cast<const R *>(Tprev), sens_idx, dl_next, qs_prev, musum);
@@ -347,7 +361,8 @@ extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, 
     CKR(talloc((void **)&sens_idx, nn * 4), "adjoint buffers");
     CKR(cudaMemsetAsync(sens_idx, 0xFF, nn * 4, c->stream), "memset");
     k_sensor_index<<<nblk(ns), 256, 0, c->stream>>>(ns, c->d_sensors, sens_idx);
-    AdjPhys ph{c->k_lin, c->c_lin, c->h, c->T_inf, c->eps * kSigma, c->T_amb, c->T_zero, c->k_a(), c->c_a(), 1.0};
+    AdjPhys ph{c->k_lin, c->c_lin, c->h,   c->T_inf, c->eps * kSigma, c->T_amb, c->T_zero, c->k_a(), c->c_a(), 1.0,
+               c->n_tab > 0, c->hk,    c->hc};
     int cur = 0;
     for (int64_t k = n_ckpt - 1; k >= 0; --k) {
         // recompute the segment from its checkpoint, recording T^n for every step

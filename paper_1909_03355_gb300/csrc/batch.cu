@@ -342,7 +342,8 @@ static fedfem_status batch_build(fedfem_batch *b, const fedfem_scenario *sc, int
     std::vector<char> lz_done(S, 0);
     for (int it = 0; it < max_iter; ++it) {
         launch_scale_free(nn, vcur, c->d_C0, c->d_isdir, u, stm);
-        launch_apply(c->npe, c->ne, nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, u, nullptr, 1.0, 0.0, c->d_Y, F, stm);
+        launch_apply(c->npe, c->ne, nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, u, nullptr, 1.0, 0.0, nullptr, c->d_Y,
+                     F, stm);
         k_seg_lz_w<<<S, 256, 0, stm>>>(d_nr, F, c->d_C0, c->d_isdir, vprev, it ? lz_b + (size_t)(it - 1) * S : nullptr,
                                        vcur, lz_a + (size_t)it * S);
         k_seg_lz_orth<<<S, 256, 0, stm>>>(d_nr, F, vcur, lz_a + (size_t)it * S, lz_b + (size_t)it * S);
@@ -451,7 +452,7 @@ static fedfem_status batch_build(fedfem_batch *b, const fedfem_scenario *sc, int
     }
 
     // ---- capture the whole run in a CUDA graph
-    BCK(prepare_step(c->precision, c->kahan, c->npe, c->opt.scatter, c->smem), "kernel attributes");
+    BCK(prepare_step(c->precision, c->kahan, c->npe, c->opt.scatter, 0, c->smem), "kernel attributes");
     StepArgs a = step_args(c);
     const int64_t spl = c->opt.steps_per_launch > 0 ? c->opt.steps_per_launch : 200;
     // capture on a private stream (the legacy default stream cannot be captured); the graph is
@@ -474,7 +475,7 @@ static fedfem_status batch_build(fedfem_batch *b, const fedfem_scenario *sc, int
             a.n0 = n;
             a.nsteps = (int32_t)k;
             cudaMemsetAsync(c->d_tile_done, 0, c->til.n_tiles * sizeof(unsigned int), stm);
-            launch_step(a, c->precision, c->kahan, c->npe, grids[j], c->block, c->smem, c->ts_cap, stm);
+            launch_step(a, c->precision, c->kahan, c->npe, 0, grids[j], c->block, c->smem, c->ts_cap, stm);
             n += k;
         }
         k_stamp<<<1, 1, 0, stm>>>(b->d_stamp + 1 + j);

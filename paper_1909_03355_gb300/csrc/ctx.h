@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -22,8 +23,27 @@ struct fedfem_ctx {
     double k_lin = 0, c_lin = 0, T_ref = 0;  // f_k = 1 + k_lin (T - T_ref), f_c likewise
     double k_a() const { return 1.0 - k_lin * T_ref; }  // f_k = k_a + k_lin T
     double c_a() const { return 1.0 - c_lin * T_ref; }
-    double fk(double T) const { return 1.0 + k_lin * (T - T_ref); }
-    double fc(double T) const { return 1.0 + c_lin * (T - T_ref); }
+    // tabulated factors (fedfem_set_property_table): replace the linear laws when n_tab > 0
+    int n_tab = 0;
+    std::vector<double> tab_T, tab_fk, tab_fc;
+    fedfem::HingeLaw<double> hk{}, hc{};
+    const fedfem::HingeLaw<double> *tk_ptr() const { return n_tab ? &hk : nullptr; }
+    double fk(double T) const { return n_tab ? fedfem::hinge_value(hk, T) : 1.0 + k_lin * (T - T_ref); }
+    double fc(double T) const { return n_tab ? fedfem::hinge_value(hc, T) : 1.0 + c_lin * (T - T_ref); }
+    // extrema of f_k and f_c over [lo, hi]: at the ends or at table points inside
+    void law_extrema(double lo, double hi, double *fk_max, double *fk_min, double *fc_min) const
+    {
+        double kx = std::max(fk(lo), fk(hi)), kn = std::min(fk(lo), fk(hi)), cn = std::min(fc(lo), fc(hi));
+        for (int j = 0; j < n_tab; ++j)
+            if (tab_T[j] > lo && tab_T[j] < hi) {
+                kx = std::max(kx, tab_fk[j]);
+                kn = std::min(kn, tab_fk[j]);
+                cn = std::min(cn, tab_fc[j]);
+            }
+        *fk_max = kx;
+        *fk_min = kn;
+        *fc_min = cn;
+    }
     // time-dependent loads: at step n the external loads are sched_q[n] Q_ext, the convection
     // ambient temperature is sched_Tinf[n] and the prescribed temperatures are dir_T +
     // sched_Tdir[n] (last entry beyond the end)

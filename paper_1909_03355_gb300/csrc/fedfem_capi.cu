@@ -592,9 +592,8 @@ fedfem_status fedfem::run_precompute_arrays(fedfem_ctx *c)
 // max f_k / min f_c + the largest linearised surface rate).
 static fedfem_status crit_step(fedfem_ctx *c, double T_lo, double T_hi, double *dt_crit)
 {
-    const double fk_max = std::max(c->fk(T_lo), c->fk(T_hi));
-    const double fk_min = std::min(c->fk(T_lo), c->fk(T_hi));
-    const double fc_min = std::min(c->fc(T_lo), c->fc(T_hi));
+    double fk_max, fk_min, fc_min;
+    c->law_extrema(T_lo, T_hi, &fk_max, &fk_min, &fc_min);
     if (!(fc_min > 0) || !(fk_min > 0)) return fail(c, FEDFEM_ERR_ARG, "conductivity or heat law not positive on [T_lo, T_hi]");
     const double rl = std::fabs(T_lo - c->T_zero), rh = std::fabs(T_hi - c->T_zero);
     const double r3 = std::max(rl * rl * rl, rh * rh * rh);
@@ -794,6 +793,12 @@ StepArgs step_args(fedfem_ctx *c)
     a.sched_Tinf = c->sched_Tinf.empty() ? nullptr : c->d_sched_Tinf;
     a.sched_Tdir = c->sched_Tdir.empty() ? nullptr : c->d_sched_Tdir;
     a.sched_len = c->sched_len;
+    if (c->n_tab) {
+        a.tk64 = c->hk;
+        a.tc64 = c->hc;
+        a.tk32 = hinge_law_f32(c->hk);
+        a.tc32 = hinge_law_f32(c->hc);
+    }
     a.scatter = c->opt.scatter;
     a.withhold = c->opt.debug_withhold_barrier;
     a.timeout_ns = (long long)(c->opt.barrier_timeout_s * 1e9);
@@ -821,7 +826,8 @@ fedfem_status enqueue_steps(fedfem_ctx *c, int64_t n, void *rec, int64_t rec_str
         a.rec = rec ? (uint8_t *)rec + (size_t)done * rec_stride * (c->precision == 64 ? 8 : 4) : nullptr;
         a.rec_stride = rec_stride;
         CK(cudaMemsetAsync(c->d_tile_done, 0, c->til.n_tiles * sizeof(unsigned int), c->stream), "reset tile progress");
-        CK(launch_step(a, c->precision, c->kahan, c->npe, c->grid, c->block, c->smem, c->ts_cap, c->stream), "step launch");
+        CK(launch_step(a, c->precision, c->kahan, c->npe, c->n_tab > 0, c->grid, c->block, c->smem, c->ts_cap, c->stream),
+           "step launch");
         c->step += k;
         done += k;
     }
@@ -902,7 +908,7 @@ extern "C" fedfem_status fedfem_internal_loads(fedfem_ctx *c, const double *T_ho
     CK(cudaMemcpyAsync(c->d_v[0], T_host, c->nn * 8, cudaMemcpyHostToDevice, c->stream), "upload");
     launch_permute_old_to_new(c->nn, c->d_v[0], c->d_old_of_new, c->d_v[1], c->stream);
     launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, c->d_v[1], c->d_v[1], c->k_a(), c->k_lin,
-                 c->d_Y, c->d_v[2], c->stream);
+                 c->tk_ptr(), c->d_Y, c->d_v[2], c->stream);
     launch_permute_new_to_old(c->nn, c->d_v[2], c->d_old_of_new, c->d_v[3], c->stream);
     CK(cudaGetLastError(), "internal loads");
     CK(cudaMemcpyAsync(F_host, c->d_v[3], c->nn * 8, cudaMemcpyDeviceToHost, c->stream), "download");
@@ -919,11 +925,11 @@ extern "C" fedfem_status fedfem_energy(fedfem_ctx *c, double *stored_change, dou
     if (s != FEDFEM_OK) return s;
     s = state_f64_new(c, c->step, T1);
     if (s != FEDFEM_OK) return s;
-    launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, T0, T0, c->k_a(), c->k_lin, c->d_Y, F,
-                 c->stream);
+    launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, T0, T0, c->k_a(), c->k_lin,
+                 c->tk_ptr(), c->d_Y, F, c->stream);
     // the step from T^(n-1) to T^n with the loads of step n - 1
-    EnergyPhys ph{c->dt, c->c_lin, c->h, c->Tinf_at(c->step - 1), c->eps * 5.67e-8, c->T_amb, c->T_zero, c->c_a(),
-                  c->qs_at(c->step - 1)};
+    EnergyPhys ph{c->dt,     c->c_lin,  c->h,   c->Tinf_at(c->step - 1), c->eps * 5.67e-8, c->T_amb, c->T_zero, c->c_a(),
+                  c->qs_at(c->step - 1), c->n_tab > 0, c->hc};
     double *partial = c->d_red, *sums = c->d_red + 2 * 1024;
     launch_energy(c->nn, T0, T1, F, c->d_C0, c->d_Qext64, c->d_Ac64, c->d_Ar64, c->d_isdir, ph, partial, sums, c->stream);
     CK(cudaGetLastError(), "energy");
@@ -981,6 +987,36 @@ extern "C" fedfem_status fedfem_set_schedule(fedfem_ctx *c, int64_t n_entries, c
                                       c->Tdir_at(c->step), c->d_T[b], c->kahan ? c->d_comp[b] : nullptr, c->stream);
         CK(cudaGetLastError(), "impose Dirichlet values");
     }
+    return FEDFEM_OK;
+}
+
+extern "C" fedfem_status fedfem_set_property_table(fedfem_ctx *c, int32_t n_points, const double *T, const double *fk,
+                                                   const double *fc)
+{
+    if (!c) return FEDFEM_ERR_ARG;
+    if (!c->group_elem.empty()) return fail(c, FEDFEM_ERR_UNSUPPORTED, "property tables are not available for batches");
+    if (c->precomputed) return fail(c, FEDFEM_ERR_STATE, "set the property table before fedfem_precompute");
+    if (n_points == 0) {
+        c->n_tab = 0;
+        c->tab_T.clear();
+        c->tab_fk.clear();
+        c->tab_fc.clear();
+        return FEDFEM_OK;
+    }
+    if (n_points < 2 || n_points > kMaxTablePoints) return fail(c, FEDFEM_ERR_ARG, "a table has 2 to 8 points");
+    if (!T || !fk || !fc) return fail(c, FEDFEM_ERR_ARG, "NULL table array");
+    for (int j = 0; j < n_points; ++j) {
+        if (!std::isfinite(T[j]) || (j > 0 && !(T[j] > T[j - 1])))
+            return fail(c, FEDFEM_ERR_ARG, "table temperatures must be finite and increasing");
+        if (!(fk[j] > 0) || !(fc[j] > 0) || !std::isfinite(fk[j]) || !std::isfinite(fc[j]))
+            return fail(c, FEDFEM_ERR_ARG, "table factors must be finite and > 0");
+    }
+    c->n_tab = n_points;
+    c->tab_T.assign(T, T + n_points);
+    c->tab_fk.assign(fk, fk + n_points);
+    c->tab_fc.assign(fc, fc + n_points);
+    c->hk = make_hinge_law(n_points, T, fk);
+    c->hc = make_hinge_law(n_points, T, fc);
     return FEDFEM_OK;
 }
 

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/fedfem.h"
+#include "law.cuh"
 
 namespace fedfem {
 
@@ -117,6 +118,10 @@ struct StepArgs {
     // held beyond sched_len
     const double *sched_q, *sched_Tinf, *sched_Tdir;
     int64_t sched_len;
+    // tabulated f_k, f_c (used by the kernels instantiated for tables instead of the linear
+    // laws of PhysParams): working-precision copies for the FP32 and FP64 forms
+    HingeLaw<float> tk32, tc32;
+    HingeLaw<double> tk64, tc64;
     // physics: one table entry per scenario, selected by TileInfo::scenario
     const PhysParams *phys;
     // CTA c processes tiles [cta_tile[c], cta_tile[c + 1]) (NULL: tiles_per_cta consecutive tiles)
@@ -136,9 +141,9 @@ struct StepArgs {
 };
 
 // Launchers (step.cu).  Return cudaError_t of the launch.
-cudaError_t launch_step(const StepArgs &a, int precision, int kahan, int npe, int grid, int block,
+cudaError_t launch_step(const StepArgs &a, int precision, int kahan, int npe, int table, int grid, int block,
                         size_t smem, int ts_cap, cudaStream_t st);
-cudaError_t prepare_step(int precision, int kahan, int npe, int scatter, size_t smem);
+cudaError_t prepare_step(int precision, int kahan, int npe, int scatter, int table, size_t smem);
 size_t step_smem_bytes(int precision, int npe, int chunk, int stages, int max_local);
 int step_ts_cap(int precision, int max_local);
 int step_max_blocks_per_sm(int precision, int kahan, int npe, int block, size_t smem);

@@ -272,7 +272,7 @@ __global__ void k_set_A(int64_t nn, double dt, const double *C0, const uint8_t *
 // element mean of `Tk` (or 1 when Tk == NULL).
 template <int NPE>
 __global__ void k_apply(int64_t ne, const int32_t *gconn, const double *cond64, const double *x, const double *Tk,
-                        double k_a, double k_lin, double *Y)
+                        double k_a, double k_lin, int tab, HingeLaw<double> tk, double *Y)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
         double xv[NPE], F[NPE];
@@ -280,7 +280,7 @@ __global__ void k_apply(int64_t ne, const int32_t *gconn, const double *cond64, 
         for (int k = 0; k < NPE; ++k) {
             const int g = gconn[NPE * e + k];
             xv[k] = x[g];
-            if (Tk) s += Tk[g];
+            if (Tk) s += tab ? hinge_value(tk, Tk[g]) : Tk[g];
             F[k] = 0.0;
         }
         int p = 0;
@@ -290,7 +290,7 @@ __global__ void k_apply(int64_t ne, const int32_t *gconn, const double *cond64, 
                 F[i] += gg;
                 F[j] -= gg;
             }
-        const double fk = Tk ? k_a + k_lin * (s / NPE) : 1.0;
+        const double fk = Tk ? (tab ? s / NPE : k_a + k_lin * (s / NPE)) : 1.0;
         for (int k = 0; k < NPE; ++k) Y[NPE * e + k] = fk * F[k];
     }
 }
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(256) k_energy_terms(int64_t nn, const double *
         const double t = T0[g];
         const double u = t - ph.T_zero, b = ph.T_amb - ph.T_zero;
         const double Q = ph.qs * Qext[g] - Ac[g] * ph.h * (t - ph.T_inf) - Ar[g] * ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
-        S += C0[g] * (ph.c_a + ph.c_lin * t) * (T1[g] - t);
+        S += C0[g] * (ph.tab ? hinge_value(ph.tc, t) : ph.c_a + ph.c_lin * t) * (T1[g] - t);
         B += ph.dt * Q;
     }
     block_sum2<256>(S, B, red);
@@ -603,13 +603,15 @@ void launch_set_A(int64_t nn, double dt, const double *C0, const uint8_t *isdir,
 }
 
 void launch_apply(int npe, int64_t ne, int64_t nn, const int32_t *gconn, const double *cond64, const int32_t *n2e_ptr,
-                  const int64_t *n2e, const double *x, const double *Tk, double k_a, double k_lin, double *Y, double *F,
-                  cudaStream_t st)
+                  const int64_t *n2e, const double *x, const double *Tk, double k_a, double k_lin,
+                  const HingeLaw<double> *tk, double *Y, double *F, cudaStream_t st)
 {
+    const int tab = tk != nullptr;
+    const HingeLaw<double> law = tk ? *tk : HingeLaw<double>{};
     if (npe == 8)
-        k_apply<8><<<nblk(ne), 256, 0, st>>>(ne, gconn, cond64, x, Tk, k_a, k_lin, Y);
+        k_apply<8><<<nblk(ne), 256, 0, st>>>(ne, gconn, cond64, x, Tk, k_a, k_lin, tab, law, Y);
     else
-        k_apply<4><<<nblk(ne), 256, 0, st>>>(ne, gconn, cond64, x, Tk, k_a, k_lin, Y);
+        k_apply<4><<<nblk(ne), 256, 0, st>>>(ne, gconn, cond64, x, Tk, k_a, k_lin, tab, law, Y);
     k_gather<<<nblk(nn), 256, 0, st>>>(nn, npe, n2e_ptr, n2e, Y, F);
 }
 
@@ -650,7 +652,7 @@ void launch_lanczos_step(int npe, int64_t ne, int64_t nn, const int32_t *gconn, 
 {
     const int nb = reduce_blocks(nn);
     k_scale_free<<<nblk(nn), 256, 0, st>>>(nn, vcur, C0, isdir, u);
-    launch_apply(npe, ne, nn, gconn, cond64, n2e_ptr, n2e, u, nullptr, 1.0, 0.0, Y, F, st);
+    launch_apply(npe, ne, nn, gconn, cond64, n2e_ptr, n2e, u, nullptr, 1.0, 0.0, nullptr, Y, F, st);
     k_lz_w<<<nb, 256, 0, st>>>(nn, F, C0, isdir, vprev, beta2_prev, vcur, partial);
     k_sum_partials<<<1, 256, 0, st>>>(nb, partial, coef);  // coef[0] = alpha_j
     k_lz_orth<<<nb, 256, 0, st>>>(nn, F, vcur, coef, partial);

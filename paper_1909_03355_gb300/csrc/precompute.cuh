@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "law.cuh"
+
 namespace fedfem {
 
 struct ElemArgs {
@@ -44,6 +46,8 @@ struct EnergyPhys {
     double dt, c_lin, h, T_inf, eps_sigma, T_amb, T_zero;
     double c_a;  // f_c = c_a + c_lin T
     double qs;   // multiplier of the external loads (time-dependent loads)
+    int tab;     // 1: f_c from the table tc instead of the linear law
+    HingeLaw<double> tc;
 };
 
 void launch_elem(int npe, const ElemArgs &a, cudaStream_t st);
@@ -51,9 +55,11 @@ void launch_face_share(int64_t nf, int nv, const int32_t *faces, const double *x
 void launch_node_sums(const NodeArgs &a, cudaStream_t st);
 void launch_set_A(int64_t nn, double dt, const double *C0, const uint8_t *isdir, double *A, float2 *A2,
                   cudaStream_t st);
+// F = sum_e f_k,e K0_e x_e (fixed-order gather); f_k,e from the nodal Tk: k_a + k_lin mean T,
+// or with tk the mean of the tabulated nodal factors (Tk == NULL: f_k,e = 1)
 void launch_apply(int npe, int64_t ne, int64_t nn, const int32_t *gconn, const double *cond64, const int32_t *n2e_ptr,
-                  const int64_t *n2e, const double *x, const double *Tk, double k_a, double k_lin, double *Y, double *F,
-                  cudaStream_t st);
+                  const int64_t *n2e, const double *x, const double *Tk, double k_a, double k_lin,
+                  const HingeLaw<double> *tk, double *Y, double *F, cudaStream_t st);
 int reduce_blocks(int64_t nn);
 void launch_power_init(int64_t nn, const uint8_t *isdir, double *x, cudaStream_t st);
 void launch_scale_free(int64_t nn, const double *x, const double *C0, const uint8_t *isdir, double *u, cudaStream_t st);

@@ -389,10 +389,11 @@ __device__ __forceinline__ void store4<double>(double *p, const Vec4<double> &v)
 }
 
 // Element conduction loads of the element in lane `lane` of a staged chunk (Eq. 20):
-// F_i = f_k,e sum_{j != i} c_ij (T_i - T_j), f_k,e = k_a + k_lin mean_i T_i.
-template <typename R, int NPE>
+// F_i = f_k,e sum_{j != i} c_ij (T_i - T_j), f_k,e = k_a + k_lin mean_i T_i, or with a table
+// (TAB) the mean of the tabulated nodal factors (Section 4.2.2).
+template <typename R, int NPE, bool TAB>
 __device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int lane, const R *Ts, R k_a, R k_lin,
-                                              R *F, int *id)
+                                              const HingeLaw<R> &tk, R *F, int *id)
 {
     using L = Layout<R, NPE>;
     const typename L::V *cv = reinterpret_cast<const typename L::V *>(blk);
@@ -406,7 +407,7 @@ __device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int la
 #pragma unroll
     for (int k = 0; k < NPE; ++k) {
         T[k] = Ts[id[k]];
-        sum += T[k];
+        if (!TAB) sum += T[k];
         F[k] = 0;
     }
     int p = 0;
@@ -418,7 +419,11 @@ __device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int la
             F[i] += g;
             F[j] -= g;
         }
-    const R fk = k_a + k_lin * (sum * ((R)1 / (R)NPE));
+    if (TAB) {  // after the pair loop, when the conductances are no longer live
+#pragma unroll
+        for (int k = 0; k < NPE; ++k) sum += hinge_value(tk, T[k]);
+    }
+    const R fk = TAB ? sum * ((R)1 / (R)NPE) : k_a + k_lin * (sum * ((R)1 / (R)NPE));
 #pragma unroll
     for (int k = 0; k < NPE; ++k) F[k] *= fk;
 }
@@ -528,13 +533,40 @@ __device__ __forceinline__ void add_loads(R *Fs, const R *F, const int *id)
     }
 }
 
-// Explicit nodal update (Eq. 16): T' = T + A / f_c(T) (Q - F), Kahan-compensated in FP32; a
-// Dirichlet node moves by dD, the change of its prescribed value over the step.
-template <typename R, bool KAHAN>
-__device__ __forceinline__ R node_update(R T, float comp, ACoef<R> A, R Q, R F, R dD, const Phys<R> &ph,
-                                         float &comp_out, int32_t *err)
+// Tabulated f_k and f_c in the working precision (kernel parameters).
+template <typename R>
+__device__ __forceinline__ const HingeLaw<R> &law_k(const StepArgs &a);
+template <typename R>
+__device__ __forceinline__ const HingeLaw<R> &law_c(const StepArgs &a);
+template <>
+__device__ __forceinline__ const HingeLaw<float> &law_k<float>(const StepArgs &a)
 {
-    const R fc = ph.c_a + ph.c_lin * T;
+    return a.tk32;
+}
+template <>
+__device__ __forceinline__ const HingeLaw<double> &law_k<double>(const StepArgs &a)
+{
+    return a.tk64;
+}
+template <>
+__device__ __forceinline__ const HingeLaw<float> &law_c<float>(const StepArgs &a)
+{
+    return a.tc32;
+}
+template <>
+__device__ __forceinline__ const HingeLaw<double> &law_c<double>(const StepArgs &a)
+{
+    return a.tc64;
+}
+
+// Explicit nodal update (Eq. 16): T' = T + A / f_c(T) (Q - F), Kahan-compensated in FP32; a
+// Dirichlet node moves by dD, the change of its prescribed value over the step.  f_c is the
+// linear law of ph or (TAB) the table tc.
+template <typename R, bool KAHAN, bool TAB>
+__device__ __forceinline__ R node_update(R T, float comp, ACoef<R> A, R Q, R F, R dD, const Phys<R> &ph,
+                                         const HingeLaw<R> &tc, float &comp_out, int32_t *err)
+{
+    const R fc = TAB ? hinge_value(tc, T) : ph.c_a + ph.c_lin * T;
     const R inc = A.dir() ? dD : A.mul((Q - F) / fc);
     R Tn;
     if constexpr (KAHAN) {
@@ -600,22 +632,22 @@ __device__ __forceinline__ void halo_load(HaloIn<R> &h, const int4 sh, const R *
 
 // T^n of a halo node from T^{n-1}, its compensation and the fixed-order sum of the halo
 // partials of step n-1.
-template <typename R, bool KAHAN>
-__device__ __forceinline__ R halo_finish(const HaloIn<R> &h, const R *part, const Phys<R> &ph, float &cn,
-                                         int32_t *err)
+template <typename R, bool KAHAN, bool TAB>
+__device__ __forceinline__ R halo_finish(const HaloIn<R> &h, const R *part, const Phys<R> &ph,
+                                         const HingeLaw<R> &tc, float &cn, int32_t *err)
 {
     R F = 0;
     F += h.p[0];
     F += h.p[1];
     for (int q = 2; q < h.cnt; ++q) F += ld_cg(part + h.z + q);
-    return node_update<R, KAHAN>(h.T, h.cp, h.A, h.Q * ph.qs_prev, F, ph.dD_prev, ph, cn, err);
+    return node_update<R, KAHAN, TAB>(h.T, h.cp, h.A, h.Q * ph.qs_prev, F, ph.dD_prev, ph, tc, cn, err);
 }
 
 // Shared-memory layout: [stages][chunk_bytes] ring | MBAR_BYTES of mbarriers (full[S], empty[S],
 // node) | Ts[ts_cap] | Fs[ts_cap].  Threads [0, NC) are consumers; the last warp is the
 // producer of the element ring.  With at most 15 consumer warps + 1 producer warp every SM
 // sub-partition holds at most 4 warps, which leaves 128 registers per thread.
-template <typename R, int NPE, bool KAHAN, int SCATTER>
+template <typename R, int NPE, bool KAHAN, int SCATTER, bool TAB>
 __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -760,7 +792,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                         continue;
                     }
                     float cn;
-                    const R v = halo_finish<R, KAHAN>(hin[u], pprev, ph, cn, a.err);
+                    const R v = halo_finish<R, KAHAN, TAB>(hin[u], pprev, ph, law_c<R>(a), cn, a.err);
                     if ((sh[u].w >> 16) == 0) {  // owner writes T^n back
                         Tc[sh[u].y] = v;
                         if (KAHAN) a.comp[cur][sh[u].y] = cn;
@@ -815,7 +847,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                             R F[NPE];
                             int id[NPE];
                             const int col = blk[col_off + lane32];
-                            element_loads<R, NPE>(blk, CH, lane32, Ts, ph.k_a, ph.k_lin, F, id);
+                            element_loads<R, NPE, TAB>(blk, CH, lane32, Ts, ph.k_a, ph.k_lin, law_k<R>(a), F, id);
                             __syncwarp();
                             if (lane32 == 0) mbar_arrive(&empty[slot]);  // stage back to the producer
                             if (col != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F, id);
@@ -823,8 +855,9 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                             R F0[NPE], F1[NPE];
                             int id0[NPE], id1[NPE];
                             const int col0 = blk[col_off + lane32], col1 = blk[col_off + lane32 + 32];
-                            element_loads<R, NPE>(blk, CH, lane32, Ts, ph.k_a, ph.k_lin, F0, id0);
-                            element_loads<R, NPE>(blk, CH, lane32 + 32, Ts, ph.k_a, ph.k_lin, F1, id1);
+                            element_loads<R, NPE, TAB>(blk, CH, lane32, Ts, ph.k_a, ph.k_lin, law_k<R>(a), F0, id0);
+                            element_loads<R, NPE, TAB>(blk, CH, lane32 + 32, Ts, ph.k_a, ph.k_lin, law_k<R>(a), F1,
+                                                       id1);
                             __syncwarp();
                             if (lane32 == 0) mbar_arrive(&empty[slot]);
                             if (col0 != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F0, id0);
@@ -887,9 +920,9 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 float cn;
-                                out.v[e] = node_update<R, KAHAN>(Ts[l + e], KAHAN ? (float)cpv[u].v[e] : 0.0f, Av[u][e],
-                                                                  Qv[u].v[e] * ph.qs, Fs[l + e], ph.dD, ph, cn,
-                                                                  a.err);
+                                out.v[e] = node_update<R, KAHAN, TAB>(Ts[l + e], KAHAN ? (float)cpv[u].v[e] : 0.0f,
+                                                                       Av[u][e], Qv[u].v[e] * ph.qs, Fs[l + e], ph.dD,
+                                                                       ph, law_c<R>(a), cn, a.err);
                                 cout.v[e] = (R)cn;
                             }
                             store4<R>(Tn + g, out);
@@ -901,8 +934,9 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                     if (l >= head && l < tail0) continue;
                     const int g = nb + l;
                     float cn;
-                    const R v = node_update<R, KAHAN>(Ts[l], KAHAN ? ld_cg(a.comp[cur] + g) : 0.0f, load_A<R>(a, g),
-                                                      Qext[g] * ph.qs, Fs[l], ph.dD, ph, cn, a.err);
+                    const R v = node_update<R, KAHAN, TAB>(Ts[l], KAHAN ? ld_cg(a.comp[cur] + g) : 0.0f,
+                                                           load_A<R>(a, g), Qext[g] * ph.qs, Fs[l], ph.dD, ph,
+                                                           law_c<R>(a), cn, a.err);
                     Tn[g] = v;
                     if (KAHAN) a.comp[nxt][g] = cn;
                 }
@@ -933,7 +967,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                 float cn;
                 HaloIn<R> h;
                 halo_load<R, KAHAN>(h, sh, Tp, KAHAN ? a.comp[prv] : nullptr, part, Qext, a);
-                const R v = halo_finish<R, KAHAN>(h, part, ph, cn, a.err);
+                const R v = halo_finish<R, KAHAN, TAB>(h, part, ph, law_c<R>(a), cn, a.err);
                 Tc[sh.y] = v;
                 if (KAHAN) a.comp[cur][sh.y] = cn;
             }
@@ -955,16 +989,17 @@ size_t step_smem_bytes(int precision, int npe, int chunk, int stages, int max_lo
 }
 
 template <typename R, int NPE, bool KAHAN, int SCATTER>
-static void *kernel_ptr()
+static void *kernel_ptr(int table)
 {
-    return (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER>;
+    return table ? (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER, true>
+                 : (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER, false>;
 }
 
-static void *select_kernel(int precision, int kahan, int npe, int scatter)
+static void *select_kernel(int precision, int kahan, int npe, int scatter, int table)
 {
 #define FEDFEM_SEL(R, N, K)                                                                        \
-    return scatter == FEDFEM_SCATTER_ATOMIC ? kernel_ptr<R, N, K, FEDFEM_SCATTER_ATOMIC>()         \
-                                            : kernel_ptr<R, N, K, FEDFEM_SCATTER_COLOR>()
+    return scatter == FEDFEM_SCATTER_ATOMIC ? kernel_ptr<R, N, K, FEDFEM_SCATTER_ATOMIC>(table)    \
+                                            : kernel_ptr<R, N, K, FEDFEM_SCATTER_COLOR>(table)
     if (precision == 64) {
         if (npe == 8) FEDFEM_SEL(double, 8, false);
         FEDFEM_SEL(double, 4, false);
@@ -980,23 +1015,23 @@ static void *select_kernel(int precision, int kahan, int npe, int scatter)
 
 int step_max_blocks_per_sm(int precision, int kahan, int npe, int block, size_t smem)
 {
-    void *k = select_kernel(precision, kahan, npe, FEDFEM_SCATTER_COLOR);
+    void *k = select_kernel(precision, kahan, npe, FEDFEM_SCATTER_COLOR, 0);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block + 32, smem) != cudaSuccess) return 0;
     return nb;
 }
 
-cudaError_t prepare_step(int precision, int kahan, int npe, int scatter, size_t smem)
+cudaError_t prepare_step(int precision, int kahan, int npe, int scatter, int table, size_t smem)
 {
-    return cudaFuncSetAttribute(select_kernel(precision, kahan, npe, scatter), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    return cudaFuncSetAttribute(select_kernel(precision, kahan, npe, scatter, table),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t launch_step(const StepArgs &a, int precision, int kahan, int npe, int grid, int block, size_t smem,
-                        int ts_cap, cudaStream_t st)
+cudaError_t launch_step(const StepArgs &a, int precision, int kahan, int npe, int table, int grid, int block,
+                        size_t smem, int ts_cap, cudaStream_t st)
 {
-    void *k = select_kernel(precision, kahan, npe, a.scatter);
+    void *k = select_kernel(precision, kahan, npe, a.scatter, table);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(st, &cs);
     if (e != cudaSuccess) return e;

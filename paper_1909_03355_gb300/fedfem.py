@@ -114,6 +114,22 @@ class FedFem:
         sched = [getattr(problem, f, None) for f in ("q_schedule", "Tinf_schedule", "Tdir_schedule")]
         if any(s is not None for s in sched):
             self.set_schedule(*sched)
+        if getattr(problem, "table_T", None) is not None:
+            self.set_table(problem.table_T, problem.table_fk, problem.table_fc)
+
+    def set_table(self, T=None, fk=None, fc=None):
+        """Tabulated factors of k0 and c0 at the increasing temperatures T (2 to 8 points,
+        linear between points, end values held outside; nodal values averaged per element for
+        k as in Section 4.2.2); they replace the materials' linear laws.  Call before
+        precompute(); T=None removes the table."""
+        if T is None:
+            self._ck(self.L.fedfem_set_property_table(self.h, 0, None, None, None))
+            return
+        arrs = [_f64(a) for a in (T, fk, fc)]
+        if len({len(a) for a in arrs}) != 1:
+            raise ValueError("T, fk and fc must have the same length")
+        self._table = tuple(arrs)
+        self._ck(self.L.fedfem_set_property_table(self.h, len(arrs[0]), *[_ptr(a) for a in arrs]))
 
     def set_schedule(self, q_scale=None, T_inf=None, T_dir=None):
         """Time-dependent loads and prescribed temperatures: at step n the external loads are

@@ -27,9 +27,14 @@ def small_setup(kind="hex", n=4):
 
 
 @pytest.mark.parametrize("kind,T_ref,scheduled", [("hex", 0.0, False), ("tet", 0.0, False), ("hex", 60.0, False),
-                                                   ("hex", 0.0, True)])
+                                                   ("hex", 0.0, True), ("hex", 0.0, "table"), ("tet", 0.0, "table")])
 def test_adjoint_matches_oracle_adjoint_fp64(kind, T_ref, scheduled):
     p, sensors = small_setup(kind)
+    if scheduled == "table":  # tabulated k(T), c(T): the sweep carries the segment slopes
+        scheduled = False
+        p.table_T = np.array([0.0, 60.0, 150.0, 300.0, 600.0])
+        p.table_fk = np.array([0.8, 1.0, 1.6, 1.3, 2.0])
+        p.table_fc = np.array([1.1, 1.0, 0.8, 1.4, 1.2])
     if T_ref:  # laws given at a reference temperature (Section 4.2.2 form)
         m0 = p.mats[0]
         p.mats[0] = fi.Material(m0.rho, m0.k0, m0.k_lin, m0.c0, m0.c_lin, T_ref=T_ref)

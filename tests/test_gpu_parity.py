@@ -263,6 +263,61 @@ def test_time_dependent_dirichlet(kind, precision):
     f.close()
 
 
+def _table_cube(kind):
+    """Nonlinear cube with tabulated k(T), c(T): five points across the 20-820 degree range of
+    the run, the hottest nodes past the last point (held end values)."""
+    p = fi.nonlinear_cube(9, kind, jitter=0.2 if kind == "hex" else 0.0)
+    p.table_T = np.array([0.0, 100.0, 250.0, 450.0, 650.0])
+    p.table_fk = np.array([1.0, 1.6, 1.2, 2.5, 2.0])
+    p.table_fc = np.array([1.0, 0.8, 1.4, 1.1, 1.6])
+    return p
+
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+@pytest.mark.parametrize("precision", [64, 32])
+def test_property_table(kind, precision):
+    """Tabulated factors (linear between points, end values held, nodal k averaged per element):
+    dt_crit and internal loads at a random state against the oracle, then 300 steps in launches
+    of 37 with the run split across two calls, and the energy terms of the last step."""
+    p = _table_cube(kind)
+    m = O.OracleModel(p)
+    f = FedFem(p, precision=precision, steps_per_launch=37)
+    dtc = f.precompute()
+    assert dtc == pytest.approx(m.dt_crit()[0], rel=1e-6)
+    Tr = fi.random_state(p, 3, lo=-50.0, hi=900.0)
+    assert rel(f.internal_loads(Tr), m.internal_loads(Tr)) <= 1e-12
+    dt = 0.9 * m.dt_crit()[0]
+    T_ref, E = m.run(p.initial_T(), dt, 300, energy=True)
+    assert np.sum(T_ref > p.table_T[-1]) > 0 and np.sum(T_ref < p.table_T[1]) > 0
+    f.set_dt(dt, force=True)
+    f.set_T(p.initial_T())
+    f.step(123)
+    f.step(177)
+    assert rel(f.get_T(), T_ref) <= TOL[precision]
+    if precision == 64:
+        S, B = f.energy()
+        assert S == pytest.approx(E[-1, 0], rel=1e-8) and B == pytest.approx(E[-1, 1], rel=1e-8)
+    f.close()
+
+
+def test_property_table_errors():
+    from paper_1909_03355_gb300.fedfem import FedFemError
+    p = _table_cube("hex")
+    f = FedFem(fi.nonlinear_cube(3, "hex"), precision=64)
+    for T, fk, fc in (([1.0], [1.0], [1.0]), ([0.0, 0.0], [1.0, 1.0], [1.0, 1.0]),
+                      ([0.0, 1.0], [1.0, -1.0], [1.0, 1.0]), ([0.0, 1.0], [1.0, 1.0], [0.0, 1.0]),
+                      (np.arange(9.0), np.ones(9), np.ones(9))):
+        with pytest.raises(FedFemError):
+            f.set_table(T, fk, fc)
+    f.set_table(p.table_T, p.table_fk, p.table_fc)
+    f.set_table(None)  # removing the table restores the linear laws
+    m = O.OracleModel(fi.nonlinear_cube(3, "hex"))
+    assert f.precompute() == pytest.approx(m.dt_crit()[0], rel=1e-6)
+    with pytest.raises(FedFemError):
+        f.set_table(p.table_T, p.table_fk, p.table_fc)
+    f.close()
+
+
 @pytest.mark.parametrize("precision", [64, 32])
 def test_time_dependent_loads(precision):
     """Load multiplier and convection ambient temperature per step (last entries held beyond
