@@ -192,6 +192,10 @@ def extra_workloads(stream, peak):
     g32 = time_workload(pc, 32, 2000, stream, peak, dt=pdt)
     g64 = time_workload(pc, 64, 2000, stream, peak, dt=pdt)
     g32td = time_workload(fi.paper_cube("tet", 19, td=True), 32, 2000, stream, peak, dt=pdt)
+    # the same laws given as a two-point table (linear between 37 and 337 deg C, held outside)
+    pt = fi.paper_cube("tet", 19)
+    pt.table_T, pt.table_fk, pt.table_fc = np.array([37.0, 337.0]), np.array([1.0, 10.0]), np.array([1.0, 4.0])
+    g32tab = time_workload(pt, 32, 2000, stream, peak, dt=pdt)
     m = O.OracleModel(pc)
     t0 = time.perf_counter()
     m.run(pc.initial_T(), pdt, 400)
@@ -202,6 +206,7 @@ def extra_workloads(stream, peak):
                     "dt = 0.005 s, 2000 steps",
         "elements": pc.n_elems, "nodes": pc.n_nodes, "gpu_fp32": g32, "gpu_fp64": g64,
         "gpu_fp32_temperature_dependent": g32td,
+        "gpu_fp32_temperature_dependent_table": g32tab,
         "oracle_1core_ms_per_step": orc_ms, "oracle_sample": "400 steps, single-threaded FP64 C oracle",
         "real_time_factor_fp32": pdt / (g32["ms_per_step"] * 1e-3),
         "paper_ms_per_step": PAPER_CUBE_MS,
@@ -217,6 +222,14 @@ def extra_workloads(stream, peak):
                  T0=20.0, T_s=100.0)
     out["slab_2048x32x32"] = {"elements": sl.n_elems, "nodes": sl.n_nodes,
                               "gpu_fp32": time_workload(sl, 32, 2000, stream, peak)}
+    tc = fi.large_cube(128)
+    tc.table_T = np.array([0.0, 100.0, 250.0, 450.0, 650.0])
+    tc.table_fk = np.array([1.0, 1.6, 1.2, 2.5, 2.0])
+    tc.table_fc = np.array([1.0, 0.8, 1.4, 1.1, 1.6])
+    out["large_hex_128_table"] = {"elements": tc.n_elems, "nodes": tc.n_nodes,
+                                  "note": "the 128^3 cube with a five-point table for k(T), c(T) instead of the "
+                                          "linear laws (nodal factors averaged per element)",
+                                  "gpu_fp32": time_workload(tc, 32, 2000, stream, peak)}
     jc = fi.large_cube(128, jitter=0.2)
     out["large_hex_128_jitter"] = {"elements": jc.n_elems, "nodes": jc.n_nodes,
                                    "note": "interior nodes jittered by +-0.2 h (seeded): every element differs",
