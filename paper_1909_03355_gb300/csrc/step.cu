@@ -731,10 +731,6 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
         R *Tc = reinterpret_cast<R *>(a.T[cur]);
         R *Tn = reinterpret_cast<R *>(a.T[nxt]);
         for (int t = t0; t < t1 && ok; ++t) {
-            if (s > 0 && !tile_wait(a.tile_done, a.nbr_ptr, a.nbr, t, (unsigned)s, a.err, a.timeout_ns, NC, &s_ok)) {
-                ok = false;
-                break;
-            }
             if (tid == 0) {
                 s_ti = a.tiles[t];
                 s_ph = Phys<R>(a.phys[s_ti.scenario]);
@@ -747,10 +743,16 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
             const int a0 = nb & ~(ALN - 1);
             const int a1 = (nb + ti.n_owned + ALN - 1) & ~(ALN - 1);
             R *Ts = Ts_raw + (nb - a0);
-            // ---- load T^n: owned range by one bulk copy; L2 prefetch of the update operands
+            // ---- T^n of the interior nodes: a CTA with one tile keeps them in shared memory
+            //      from its own update of the previous step; at the first step of a launch, and
+            //      when a CTA takes several tiles, the owned range arrives by one bulk copy.
+            //      L2 prefetch of the update operands.
+            const bool bulk = s == 0 || t1 - t0 > 1;
             if (tid == 0) {
-                mbar_arrive_expect_tx(tbar, (uint32_t)((a1 - a0) * sizeof(R)));
-                tma_bulk_g2s(Ts_raw, Tc + a0, (uint32_t)((a1 - a0) * sizeof(R)), tbar, policy_evict_normal());
+                if (bulk) {
+                    mbar_arrive_expect_tx(tbar, (uint32_t)((a1 - a0) * sizeof(R)));
+                    tma_bulk_g2s(Ts_raw, Tc + a0, (uint32_t)((a1 - a0) * sizeof(R)), tbar, policy_evict_normal());
+                }
                 const int i0 = nb & ~3, i1 = (nb + ti.n_interior + 3) & ~3;
                 if (i1 > i0) {
                     const uint64_t pk = a.l2_stream_policy == 1 ? policy_evict_last() : policy_evict_normal();
@@ -762,8 +764,15 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                     if (KAHAN) l2_prefetch_bulk(a.comp[cur] + i0, (uint32_t)((i1 - i0) * 4), pk);
                 }
             }
-            // halo nodes: values into Fs (free until the element phase) while the bulk copy is
-            // in flight; HU entries per thread in flight, the next HU entries loaded meanwhile
+            if (s > 0 && !tile_wait(a.tile_done, a.nbr_ptr, a.nbr, t, (unsigned)s, a.err, a.timeout_ns, NC, &s_ok)) {
+                ok = false;
+                break;
+            }
+            // ---- halo nodes (local ids [n_interior, n_local)): T^n from T^(n-1) and the halo
+            //      partials of step n-1 (the owner writes it back); HU entries per thread in
+            //      flight, the next HU entries loaded meanwhile.  The values go straight into Ts,
+            //      or into Fs (free until the element phase) while a bulk copy is in flight.
+            R *Hs = bulk ? Fs : Ts;
             const int4 *shp = a.sh + ti.sh_begin;
             int4 shn[HU];
 #pragma unroll
@@ -788,7 +797,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                 for (int u = 0; u < HU; ++u) {
                     if (q0 + u * NC >= ti.sh_count) continue;
                     if (s == 0) {
-                        Fs[sh[u].x] = ld_cg(Tc + sh[u].y);
+                        Hs[sh[u].x] = ld_cg(Tc + sh[u].y);
                         continue;
                     }
                     float cn;
@@ -797,10 +806,10 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                         Tc[sh[u].y] = v;
                         if (KAHAN) a.comp[cur][sh[u].y] = cn;
                     }
-                    Fs[sh[u].x] = v;
+                    Hs[sh[u].x] = v;
                 }
             }
-            {
+            if (bulk) {
                 const int bad = mbar_wait_or_abort(tbar, tphase, a.timeout_ns, a.err) ? 0 : 1;
                 tphase ^= 1;
                 if (csync_or(NC, bad)) {
@@ -808,13 +817,13 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                     break;
                 }
             }
-            // halo values into Ts (the shared nodes are the local ids [n_interior, n_local)),
-            // accumulators cleared
+            // halo values into Ts after a bulk copy; accumulators cleared
             for (int l = tid; l < ti.n_local; l += NC) {
-                if (l >= ti.n_interior) Ts[l] = Fs[l];
+                if (bulk && l >= ti.n_interior) Ts[l] = Fs[l];
                 Fs[l] = (R)0;
             }
             if (a.rec) {
+                if (!bulk) csync(NC);  // the halo values were written by other threads
                 R *rec = reinterpret_cast<R *>(a.rec) + (size_t)s * a.rec_stride;
                 for (int l = tid; l < ti.n_owned; l += NC) rec[nb + l] = Ts[l];
             }
@@ -924,6 +933,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                                                                        Av[u][e], Qv[u].v[e] * ph.qs, Fs[l + e], ph.dD,
                                                                        ph, law_c<R>(a), cn, a.err);
                                 cout.v[e] = (R)cn;
+                                Ts[l + e] = out.v[e];  // kept for the next step
                             }
                             store4<R>(Tn + g, out);
                             if (KAHAN) store4<R>(reinterpret_cast<R *>(a.comp[nxt] + g), cout);
@@ -938,8 +948,15 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                                                            load_A<R>(a, g), Qext[g] * ph.qs, Fs[l], ph.dD, ph,
                                                            law_c<R>(a), cn, a.err);
                     Tn[g] = v;
+                    Ts[l] = v;
                     if (KAHAN) a.comp[nxt][g] = cn;
                 }
+            }
+            if (t1 - t0 > 1) {
+                // the next tile's bulk copy (async proxy) reads T written here and overwrites
+                // the shared memory written here
+                fence_proxy_async_global();
+                fence_proxy_async_smem();
             }
             csync(NC);
         }
