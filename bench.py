@@ -114,7 +114,7 @@ class ClockSampler:
 
 def traffic_from_profile(kernel_src_hash):
     """DRAM bytes per step of the step kernel from the committed ncu summary, or None when the
-    kernel source changed since the counters were taken."""
+    kernel's code changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "fed_step_kernel_large_hex.md")
     if not os.path.exists(path):
         return None
@@ -124,7 +124,7 @@ def traffic_from_profile(kernel_src_hash):
             if line.startswith("- ") and ":" in line:
                 k, v = line[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
-    if vals.get("step.cu sha256") != kernel_src_hash:
+    if vals.get("step.cu code sha256 (comments and whitespace removed)") != kernel_src_hash:
         return None
     try:
         return float(vals["dram bytes per element-step"])
@@ -133,9 +133,16 @@ def traffic_from_profile(kernel_src_hash):
 
 
 def src_hash():
+    """Hash of the step kernel's code: step.cu with its comments and whitespace removed, so that
+    a comment edit does not mark the committed counters stale but any code change does."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_1909_03355_gb300", "csrc", "step.cu"), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    import re
+    with open(os.path.join(ROOT, "paper_1909_03355_gb300", "csrc", "step.cu")) as fh:
+        src = fh.read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    code = " ".join(src.split())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def algorithmic_bytes(p, precision):

@@ -62,7 +62,7 @@ static std::string status_message(int32_t bits)
 {
     std::string m;
     if (bits & ERRBIT_DIVERGED) m += "watchdog: a temperature became non-finite or exceeded T_guard; ";
-    if (bits & ERRBIT_TIMEOUT) m += "device wait exceeded its limit (grid barrier or TMA stage); ";
+    if (bits & ERRBIT_TIMEOUT) m += "device wait exceeded its limit (neighbouring tiles' progress or a TMA stage); ";
     if (bits & ERRBIT_MESH) m += "element with non-positive Jacobian; ";
     if (bits & ERRBIT_BOUNDS) m += "index out of bounds; ";
     return m;

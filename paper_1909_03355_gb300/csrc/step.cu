@@ -2,10 +2,13 @@
 //
 // One cooperative launch advances the mesh by `nsteps` explicit steps.  Each CTA owns a fixed
 // contiguous run of element tiles.  Per step and tile:
-//   load     T^n of the tile's owned nodes arrives by one TMA bulk copy (cp.async.bulk) into
-//            shared memory; for halo (shared) nodes T^n is finished here from T^{n-1} and the
-//            fixed-order sum of last step's halo partials (the owner tile writes it back), so
-//            one grid barrier per step suffices;
+//   load     T^n of the tile's interior nodes stays in shared memory from the CTA's own update
+//            of the previous step (a TMA bulk copy, cp.async.bulk, brings the owned range at a
+//            launch's first step or when a CTA takes several tiles); the tile waits until the
+//            tiles it shares nodes with have finished the previous step (per-tile progress
+//            counters, no grid barrier), then finishes T^n of its halo (shared) nodes from
+//            T^{n-1} and the fixed-order sum of last step's halo partials (the owner tile writes
+//            it back);
 //   elements the element stream (pair conductances, tile-local node ids, colours) arrives by
 //            TMA bulk copies through a ring of shared-memory stages; each thread forms
 //            F_e = f_k,e sum_j c_ij (T_i - T_j) for one element (Eq. 20 with the element-mean
@@ -13,12 +16,12 @@
 //            the element loads into shared-memory accumulators colour by colour, so the
 //            per-node summation order is fixed (deterministic);
 //   surface  convection and radiation loads of the tile's owned boundary nodes (Eq. 4, 7);
+//   halo     write the tile's partial loads of its shared nodes and publish the step;
 //   update   T^{n+1} = T^n + A / f_c(T^n) (Q - F) for interior nodes (Eq. 16), with a Kahan
-//            compensated FP32 accumulator or in FP64; A = dt / C0 is FP64 and 0 on Dirichlet
-//            nodes, which therefore stay fixed (Fig. 1 (iii) 2.3);
-//   halo     write the tile's partial loads of its shared nodes.
-// Then a grid barrier with a deadline.  Every device wait is bounded: on timeout the kernel
-// sets an error bit, drains its own copies in flight and returns.
+//            compensated FP32 accumulator or in FP64; A = dt / C0 is FP64 and -0.0 on Dirichlet
+//            nodes, which move only by the change of their prescribed value (Fig. 1 (iii) 2.3).
+// Every device wait is bounded: on timeout the kernel sets an error bit, drains its own copies
+// in flight and returns.
 //
 // Element chunk layout (CH elements, chunk_bytes = CH (NC rs + 2 npe + 1) + 16):
 //   [NV][CH] vectors of conductances | [CH] id vectors (npe x u16) | [CH] u8 colours |
@@ -1059,7 +1062,7 @@ cudaError_t launch_step(const StepArgs &a, int precision, int kahan, int npe, in
     StepArgs args = a;
     void *params[] = {(void *)&args, (void *)&ts_cap};
     // block consumer threads plus one producer warp for the element ring; a cooperative launch
-    // (all CTAs co-resident for the grid barrier) that can also be captured in a CUDA graph
+    // (all CTAs co-resident, since tiles wait for their neighbours) that can also be captured in a CUDA graph
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block + 32);
