@@ -14,6 +14,11 @@ from .fedfem import _f64, _ptr, make_options, problem_structs, _stream_handle
 
 class FedFemBatch:
     def __init__(self, problems, dt_scale=0.9, precision=32, kahan=True, stream=None, **plan):
+        # per-step schedules and property tables belong to single-problem contexts
+        for p in problems:
+            for f in ("q_schedule", "Tinf_schedule", "Tdir_schedule", "table_T"):
+                if getattr(p, f, None) is not None:
+                    raise ValueError(f"{f} is not available for batched scenarios")
         self.L = capi.load()
         keep = []
         S = len(problems)

@@ -103,3 +103,18 @@ def test_create_rejects_bad_input_without_gpu(lib_path):
     with pytest.raises(capi.FedFemError) as ei:
         FedFem(p)
     assert ei.value.name == "ERR_ARG"
+
+
+def test_batch_rejects_schedules_and_tables_without_gpu():
+    """Batched scenarios carry constant loads and the linear laws: a problem with a schedule or a
+    property table is refused before any library call."""
+    import numpy as np
+
+    import fedfem_inputs as fi
+    from paper_1909_03355_gb300.batch import FedFemBatch
+    for field, value in (("q_schedule", np.ones(3)), ("Tinf_schedule", np.ones(3)),
+                         ("Tdir_schedule", np.zeros(3)), ("table_T", np.array([0.0, 1.0]))):
+        p = fi.nonlinear_cube(2, "hex")
+        setattr(p, field, value)
+        with pytest.raises(ValueError, match=field):
+            FedFemBatch([fi.nonlinear_cube(2, "hex"), p])
