@@ -12,6 +12,12 @@
 
 #include <cuda_runtime.h>
 
+#if defined(__CUDACC__)
+#define FEDFEM_UNROLL _Pragma("unroll")
+#else
+#define FEDFEM_UNROLL
+#endif
+
 namespace fedfem {
 
 constexpr int kMaxTablePoints = 8;
@@ -30,7 +36,7 @@ __host__ __device__ __forceinline__ R hinge_value(const HingeLaw<R> &t, R T)
     const R x = T - t.lo;
     const R u = x < (R)0 ? (R)0 : (x > t.span ? t.span : x);
     R f = t.v0 + t.s0 * u;
-#pragma unroll
+FEDFEM_UNROLL
     for (int j = 0; j < kHinges; ++j) {
         const R h = u - t.u[j];
         f += t.d[j] * (h > (R)0 ? h : (R)0);
@@ -46,7 +52,7 @@ __host__ __device__ __forceinline__ R hinge_slope(const HingeLaw<R> &t, R T)
     const R x = T - t.lo;
     if (!(x > (R)0) || !(x < t.span)) return (R)0;
     R s = t.s0;
-#pragma unroll
+FEDFEM_UNROLL
     for (int j = 0; j < kHinges; ++j)
         if (x > t.u[j]) s += t.d[j];
     return s;
