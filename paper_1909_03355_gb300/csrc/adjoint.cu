@@ -3,7 +3,7 @@
 // the discrete update of Eq. 16 with the element loads of Eq. 20 (element-mean k(T), Section
 // 4.2.2), the nodal c(T) of Eq. 16 and the surface loads of Eq. 4 and 7.
 //
-// With a_i = A_i / f_c(T_i^n) (0 on Dirichlet nodes), mu_i = a_i lambda_i^{n+1},
+// With a_i = A_i / f_c(T_i^n) (zero on Dirichlet nodes, whose A is -0.0), mu_i = a_i lambda_i^{n+1},
 // R_i = Q_i - F_i and c_e = theta_e K0_e (the stored pair conductances):
 //   lambda_j^n = dL/dT_j^n + lambda_j^{n+1} (1 + d_j) + mu_j dQ_j/dT_j - G_j,
 //   d_j = -a_j f_c'(T_j) / f_c(T_j) R_j,
@@ -70,7 +70,7 @@ __global__ void k_gather_sensors(int ns, const int32_t *sens, const R *T, const 
     }
 }
 
-// mu_i = a_i lambda_i, a_i = A_i / f_c(T_i) (A = 0 on Dirichlet nodes); musum += mu
+// mu_i = a_i lambda_i, a_i = A_i / f_c(T_i) (A = -0.0 on Dirichlet nodes); musum += mu
 template <typename R>
 __global__ void k_adj_mu(int64_t nn, const R *Tn, const double *A, const double *lam, AdjPhys ph, double qs,
                          double *mu, double *musum)

@@ -58,7 +58,7 @@ __global__ void k_stamp(unsigned long long *t)
     *t = v;
 }
 
-// A_i = dt_i / C0_i with a per-node time step (0 on Dirichlet nodes), plus the float pair.
+// A_i = dt_i / C0_i with a per-node time step (-0.0 on Dirichlet nodes), plus the float pair.
 __global__ void k_set_A_nodes(int64_t nn, const double *dtn, const double *C0, const uint8_t *isdir, double *A,
                               float2 *A2)
 {
