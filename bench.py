@@ -449,9 +449,15 @@ def main():
     f.set_T(T0)
     f.step(20 + K64)
     T32 = f.get_T()
+    # energy balance of the FP32 run's last step (stored heat change vs boundary and source
+    # input, both summed in FP64 from the FP32 states)
+    S_e, B_e = f.energy()
     f.close()
     prec = {"steps": 20 + K64, "rel_linf": float(np.max(np.abs(T32 - T64)) / np.max(np.abs(T64))),
-            "rel_linf_of_change": float(np.max(np.abs(T32 - T64)) / max(np.max(np.abs(T64 - T0)), 1e-300))}
+            "rel_linf_of_change": float(np.max(np.abs(T32 - T64)) / max(np.max(np.abs(T64 - T0)), 1e-300)),
+            "rel_l2_eq30": float(np.linalg.norm(T32 - T64) / np.linalg.norm(T64)),
+            "energy_last_step": {"stored_change_J": S_e, "boundary_and_source_in_J": B_e,
+                                 "rel_residual": abs(S_e - B_e) / max(abs(B_e), 1e-300)}}
 
     # ---- adjoint / forward on the 32^3 inverse problem (2000 FP32 steps, 512 sensors sampled
     #      every 10 steps, checkpoints every 100)
