@@ -332,6 +332,26 @@ typedef struct {
 } fedfem_info;
 fedfem_status fedfem_get_info(fedfem_ctx *ctx, fedfem_info *info);
 
+/*
+ * Host-only check of the element tiling the step kernel would use (no device call, no GPU
+ * needed): validates the mesh as fedfem_create does, cuts it into n_tiles tiles (Morton order,
+ * equal element counts) of `chunk`-element chunks (32 or 64), colours every tile and checks
+ * every index the kernel would read: tile node ranges, tile-local element ids, halo entries and
+ * their partial-load slots, boundary entries, and colour classes whose elements share no node.
+ * For checking a mesh before it goes to a GPU, and for host-side tests of the tiling.
+ *   mesh: as for fedfem_create (elem_mat and elem_kscale are not used);
+ *   boundary_nodes [n_boundary] (nodes with surface loads) or NULL;  stats: out, or NULL.
+ * Errors: ARG (bad mesh, sizes or boundary ids), MESH (the tiling or its check failed); the
+ * message is fedfem_create_error().
+ */
+typedef struct {
+    int32_t n_tiles, n_chunks, max_tile_nodes, n_colors_max;
+    int64_t n_shared_nodes, n_halo_slots;  /* shared nodes, and their (tile, node) partial slots */
+    int64_t n_padding_slots;               /* element slots of the chunks left empty            */
+} fedfem_tiling_stats;
+fedfem_status fedfem_check_tiling(const fedfem_mesh *mesh, int64_t n_boundary, const int32_t *boundary_nodes,
+                                  int32_t n_tiles, int32_t chunk, fedfem_tiling_stats *stats);
+
 /* Message of the last error on this context ("" if none).  Valid until the next call. */
 const char *fedfem_error_string(fedfem_ctx *ctx);
 /* Message of the last fedfem_create failure on this thread. */

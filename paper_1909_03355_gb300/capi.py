@@ -53,6 +53,11 @@ class Info(C.Structure):
                 ("dt", F64), ("dt_crit", F64)]
 
 
+class TilingStats(C.Structure):
+    _fields_ = [("n_tiles", I32), ("n_chunks", I32), ("max_tile_nodes", I32), ("n_colors_max", I32),
+                ("n_shared_nodes", I64), ("n_halo_slots", I64), ("n_padding_slots", I64)]
+
+
 class Scenario(C.Structure):
     _fields_ = [("mesh", Mesh), ("mat", Material), ("bcs", Bcs), ("T0", P), ("n_steps", I64),
                 ("T_lo", F64), ("T_hi", F64), ("dt_scale", F64)]
@@ -89,6 +94,7 @@ SIGNATURES = {
     "fedfem_forward_record": (I32, [P, I64, P, I32, I32, I32, P]),
     "fedfem_adjoint": (I32, [P, P, P, P]),
     "fedfem_get_info": (I32, [P, P]),
+    "fedfem_check_tiling": (I32, [P, I64, P, I32, I32, P]),
     "fedfem_energy_terms_noalloc": (I32, [I64, P, P, P, P, P, P, P, P, P, P, P]),
     "fedfem_error_string": (C.c_char_p, [P]),
     "fedfem_create_error": (C.c_char_p, []),

@@ -1100,6 +1100,52 @@ extern "C" const char *fedfem_error_string(fedfem_ctx *c) { return c ? c->err.c_
 
 extern "C" const char *fedfem_create_error(void) { return g_create_error.c_str(); }
 
+extern "C" fedfem_status fedfem_check_tiling(const fedfem_mesh *mesh, int64_t n_boundary, const int32_t *boundary_nodes,
+                                             int32_t n_tiles, int32_t chunk, fedfem_tiling_stats *stats)
+{
+    g_create_error.clear();
+    // the mesh checks of fedfem_create, with a neutral material and no boundary data
+    fedfem_material mat;
+    std::memset(&mat, 0, sizeof(mat));
+    mat.rho = mat.c0 = 1.0;
+    mat.k0[0] = mat.k0[4] = mat.k0[8] = 1.0;
+    fedfem_bcs bcs;
+    std::memset(&bcs, 0, sizeof(bcs));
+    std::string e = validate(mesh, &mat, 1, &bcs, false);
+    if (e.empty() && (n_tiles < 1 || (chunk != 32 && chunk != 64))) e = "n_tiles must be >= 1 and chunk 32 or 64";
+    if (e.empty() && (n_boundary < 0 || (n_boundary > 0 && !boundary_nodes))) e = "bad boundary node list";
+    std::vector<uint8_t> is_bnd;
+    if (e.empty()) {
+        is_bnd.assign(mesh->n_nodes, 0);
+        for (int64_t i = 0; i < n_boundary && e.empty(); ++i) {
+            if (boundary_nodes[i] < 0 || boundary_nodes[i] >= mesh->n_nodes) e = "boundary node out of range";
+            else is_bnd[boundary_nodes[i]] = 1;
+        }
+    }
+    if (!e.empty()) {
+        g_create_error = e;
+        return FEDFEM_ERR_ARG;
+    }
+    Tiling T;
+    e = build_tiling(mesh->nodes_per_elem, mesh->n_elems, mesh->n_nodes, mesh->conn, mesh->xyz, is_bnd.data(), n_tiles,
+                     chunk, T);
+    if (e.empty()) e = validate_tiling(T);
+    if (!e.empty()) {
+        g_create_error = "tiling: " + e;
+        return FEDFEM_ERR_MESH;
+    }
+    if (stats) {
+        stats->n_tiles = T.n_tiles;
+        stats->n_chunks = T.n_chunks;
+        stats->max_tile_nodes = T.max_local;
+        stats->n_colors_max = T.max_colors;
+        stats->n_shared_nodes = T.sptr.empty() ? 0 : (int64_t)T.sptr.size() - 1;
+        stats->n_halo_slots = T.sptr.empty() ? 0 : T.sptr.back();
+        stats->n_padding_slots = (int64_t)T.n_chunks * chunk - mesh->n_elems;
+    }
+    return FEDFEM_OK;
+}
+
 extern "C" void fedfem_destroy(fedfem_ctx *c)
 {
     if (!c) return;

@@ -8,8 +8,9 @@
 //      tiles of near-equal element counts;
 //   2. give every node an owner tile (the lowest tile touching it) and renumber nodes so that
 //      each tile owns a contiguous range [interior | owned-shared];
-//   3. colour each tile's elements greedily so that elements of one colour share no node
-//      (the deterministic shared-memory accumulation runs colour by colour);
+//   3. colour each tile's elements so that elements of one colour share no node (the
+//      deterministic shared-memory accumulation runs colour by colour): the lattice parity of
+//      structured hexahedral grids (8 colours) where a check proves it proper, else greedy;
 //   4. give every (tile, shared node) pair a halo slot; the slots of one node are contiguous
 //      and ordered by tile, which fixes the order of the cross-tile sum.
 #include <algorithm>
@@ -68,6 +69,58 @@ static void morton_sort(int npe, int64_t e0, int64_t e1, const int32_t *conn, co
 
 // Iterated-greedy passes of the per-tile element colouring.
 static constexpr int kColourPasses = 8;
+
+// Lattice parity of the hexahedra of a structured grid, from the connectivity alone (any node
+// jitter or anisotropy): crossing a face of local face pair d (VTK order: d = 0 for the faces
+// (0,3,7,4) / (1,2,6,5), 1 for (0,1,5,4) / (3,2,6,7), 2 for (0,1,2,3) / (4,5,6,7)) flips bit d,
+// assigned breadth-first over face neighbours (two hexahedra share a face when they share two
+// opposite corners of it).  Face-connected parts start at 0.  Returns false (bits unusable)
+// when the propagation contradicts itself, i.e. the mesh is not a consistently oriented grid.
+static bool hex_lattice_parity(int64_t ne, int64_t nn, const int32_t *conn, std::vector<int8_t> &bits)
+{
+    static const int F[6][4] = {{0, 3, 7, 4}, {1, 2, 6, 5}, {0, 1, 5, 4}, {3, 2, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}};
+    std::vector<int64_t> ptr(nn + 1, 0);
+    for (int64_t i = 0; i < ne * 8; ++i) ++ptr[conn[i] + 1];
+    for (int64_t i = 0; i < nn; ++i) ptr[i + 1] += ptr[i];
+    std::vector<int32_t> inc(ptr[nn]);
+    {
+        std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+        for (int64_t e = 0; e < ne; ++e)
+            for (int k = 0; k < 8; ++k) inc[fill[conn[8 * e + k]]++] = (int32_t)e;
+    }
+    auto has = [&](int64_t e, int32_t n) {
+        for (int k = 0; k < 8; ++k)
+            if (conn[8 * e + k] == n) return true;
+        return false;
+    };
+    bits.assign(ne, -1);
+    std::vector<int64_t> queue;
+    queue.reserve(ne);
+    for (int64_t s = 0; s < ne; ++s) {
+        if (bits[s] >= 0) continue;
+        bits[s] = 0;
+        queue.clear();
+        queue.push_back(s);
+        for (size_t qi = 0; qi < queue.size(); ++qi) {
+            const int64_t e = queue[qi];
+            for (int f = 0; f < 6; ++f) {
+                const int32_t a = conn[8 * e + F[f][0]], c = conn[8 * e + F[f][2]];
+                for (int64_t q = ptr[a]; q < ptr[a + 1]; ++q) {
+                    const int64_t o = inc[q];
+                    if (o == e || !has(o, c)) continue;
+                    const int8_t want = (int8_t)(bits[e] ^ (1 << (f >> 1)));
+                    if (bits[o] < 0) {
+                        bits[o] = want;
+                        queue.push_back(o);
+                    } else if (bits[o] != want) {
+                        return false;
+                    }
+                }
+            }
+        }
+    }
+    return true;
+}
 
 std::string build_tiling(int npe, int64_t ne, int64_t nn, const int32_t *conn, const double *xyz,
                          const uint8_t *is_bnd, int n_tiles, int CH, Tiling &T)
@@ -201,6 +254,10 @@ std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *
         }
     }
 
+    // lattice parity of structured hexahedral grids (a colouring candidate for every tile)
+    std::vector<int8_t> lattice;
+    const bool have_lattice = npe == 8 && hex_lattice_parity(ne, nn, conn, lattice);
+
     // 3./4. per tile: local numbering, colouring, chunks, shared and boundary entries
     std::vector<int32_t> loc(nn, -1);
     std::vector<uint64_t> mask;
@@ -231,10 +288,11 @@ std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *
         T.max_local = std::max(T.max_local, ti.n_local);
 
         // element colouring (every class costs the step kernel a barrier and a padded chunk):
-        // the parity pattern of the quantised centroids when it is proper (structured hex
-        // grids: 8 colours), else the best of greedy colourings from the Morton order, from a
-        // raster order, and iterated greedy (Culberson: recolouring class by class, classes in
-        // reverse order, never needs more colours)
+        // the lattice parity of the connectivity, else the parity pattern of the quantised
+        // centroids, when proper (structured hex grids: 8 colours), else the best of greedy
+        // colourings from the Morton order, from a raster order, and iterated greedy
+        // (Culberson: recolouring class by class, classes in reverse order, never needs more
+        // colours)
         const int64_t m = tb[t + 1] - tb[t];
         std::vector<uint8_t> col(m);
         int ncol_best = 0;
@@ -272,14 +330,22 @@ std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *
                 for (int64_t p = 0; p < m; ++p)
                     parity[p] = (uint8_t)((q[p][2] & 1) | ((q[p][1] & 1) << 1) | ((q[p][0] & 1) << 2));
             }
-            // the parity pattern of the quantised centroids is a proper colouring on structured
-            // hex grids; it is kept only if no two elements sharing a node got the same colour
-            {
+            // the lattice parity of the connectivity and the parity pattern of the quantised
+            // centroids are proper colourings on structured hex grids (the latter only while
+            // node jitter leaves the centroids on their lattice); a candidate is kept only if no
+            // two elements sharing a node got the same colour
+            std::vector<uint8_t> lat;
+            if (have_lattice) {
+                lat.resize(m);
+                for (int64_t p = 0; p < m; ++p) lat[p] = (uint8_t)lattice[order[tb[t] + p]];
+            }
+            for (int cand = have_lattice ? 0 : 1; cand < 2 && ncol_best == 0; ++cand) {
+                const std::vector<uint8_t> &cv = cand == 0 ? lat : parity;
                 mask.assign(ti.n_local, 0);
                 bool proper = true;
                 for (int64_t p = 0; p < m && proper; ++p) {
                     const int64_t e = order[tb[t] + p];
-                    const uint64_t bit = 1ULL << parity[p];
+                    const uint64_t bit = 1ULL << cv[p];
                     for (int k = 0; k < npe; ++k) {
                         uint64_t &mk = mask[loc[conn[npe * e + k]]];
                         if (mk & bit) proper = false;
@@ -287,15 +353,22 @@ std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *
                     }
                 }
                 if (proper) {
-                    col = parity;
-                    ncol_best = 0;
-                    for (int64_t p = 0; p < m; ++p) ncol_best = std::max(ncol_best, (int)parity[p] + 1);
+                    col = cv;
+                    for (int64_t p = 0; p < m; ++p) ncol_best = std::max(ncol_best, (int)cv[p] + 1);
                 }
+            }
+            // no colouring needs fewer colours than the most elements of the tile on one node
+            int deg_max = 0;
+            {
+                std::vector<int> deg(ti.n_local, 0);
+                for (int64_t p = 0; p < m; ++p)
+                    for (int k = 0; k < npe; ++k)
+                        deg_max = std::max(deg_max, ++deg[loc[conn[npe * order[tb[t] + p] + k]]]);
             }
             std::vector<int64_t> seq(m);
             std::iota(seq.begin(), seq.end(), 0);
             std::vector<uint8_t> trial(m);
-            for (int pass = 0; pass < kColourPasses; ++pass) {
+            for (int pass = 0; pass < kColourPasses && ncol_best != deg_max; ++pass) {
                 if (pass == 1) seq = raster;
                 mask.assign(ti.n_local, 0);
                 int nc = 0;

@@ -83,6 +83,23 @@ def make_options(precision=32, kahan=True, scatter=0, block=0, steps_per_launch=
     return o
 
 
+def check_tiling(problem, n_tiles, chunk=32):
+    """Host-only check of the tiling the step kernel would use for `problem` (no GPU needed):
+    returns its statistics, or raises FedFemError with the reason.  The nodes of the problem's
+    convection and radiation faces are the boundary nodes, as in fedfem_create."""
+    L = capi.load()
+    keep = []
+    mesh, _, bcs = problem_structs(problem, keep)
+    faces = [f for f in (problem.conv_faces, problem.rad_faces) if f is not None and len(f)]
+    bnd = _i32(np.unique(np.concatenate([np.asarray(f).ravel() for f in faces]))) if faces else None
+    st = capi.TilingStats()
+    rc = L.fedfem_check_tiling(C.byref(mesh), 0 if bnd is None else len(bnd), _ptr(bnd), int(n_tiles), int(chunk),
+                               C.byref(st))
+    if rc != capi.OK:
+        raise FedFemError(rc, L.fedfem_create_error().decode())
+    return {f: getattr(st, f) for f, _ in capi.TilingStats._fields_}
+
+
 def _stream_handle(stream):
     """cudaStream_t of a torch.cuda.Stream (or an int handle, or None for the legacy default)."""
     if stream is None:
