@@ -169,6 +169,16 @@ def test_element_loop_matches_dense_assembly(which, patch_nodes):
     assert np.max(np.abs(Fc)) <= 1e-13 * 37.0 * np.max(np.abs(Kd))
     # internal loads sum to zero (conservation, Eq. 11)
     assert abs(got.sum()) <= 1e-13 * np.abs(got).sum()
+    # a property table: the element factor is the mean of the nodal factors from numpy's
+    # interpolation (end values held), not the factor of the mean temperature
+    tT, tk = np.array([20.0, 90.0, 150.0, 260.0]), np.array([1.0, 2.2, 0.7, 1.5])
+    m.set_table(tT, tk, np.ones(4))
+    fk_tab = np.array([np.mean(np.interp(T[c], tT, tk)) for c in conn])
+    ref_tab = brute.dense_assemble(conn, Ke, len(xyz), theta * fk_tab) @ T
+    got_tab = m.internal_loads(T)
+    assert np.max(np.abs(got_tab - ref_tab)) <= 1e-13 * np.max(np.abs(ref_tab))
+    fk_mean = np.array([np.interp(np.mean(T[c]), tT, tk) for c in conn])
+    assert np.max(np.abs(fk_mean - fk_tab)) > 1e-3  # the two readings differ on this field
 
 
 # -------------------------------------------------------------------------- patch tests -----
