@@ -53,6 +53,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(fedfem_bcs, face_nv), offsetof(fedfem_bcs, elem_source),
          offsetof(fedfem_options, stream), offsetof(fedfem_options, debug_withhold_barrier));
   printf("%zu %zu\n", offsetof(fedfem_info, dt), offsetof(fedfem_scenario, dt_scale));
+  printf("%zu %zu %zu %zu\n", sizeof(fedfem_energy_params), sizeof(fedfem_tiling_stats),
+         offsetof(fedfem_tiling_stats, n_shared_nodes), offsetof(fedfem_options, quadrature));
   return 0;
 }
 '''
@@ -67,7 +69,9 @@ int main(void) {
     want = [C.sizeof(capi.Mesh), C.sizeof(capi.Material), C.sizeof(capi.Bcs), C.sizeof(capi.Options),
             C.sizeof(capi.Info), C.sizeof(capi.Scenario),
             capi.Bcs.face_nv.offset, capi.Bcs.elem_source.offset, capi.Options.stream.offset,
-            capi.Options.debug_withhold_barrier.offset, capi.Info.dt.offset, capi.Scenario.dt_scale.offset]
+            capi.Options.debug_withhold_barrier.offset, capi.Info.dt.offset, capi.Scenario.dt_scale.offset,
+            C.sizeof(capi.EnergyParams), C.sizeof(capi.TilingStats), capi.TilingStats.n_shared_nodes.offset,
+            capi.Options.quadrature.offset]
     assert got == want
 
 
