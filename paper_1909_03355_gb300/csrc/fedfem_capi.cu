@@ -1062,6 +1062,7 @@ extern "C" fedfem_status fedfem_set_state(fedfem_ctx *c, const void *buf)
     std::memcpy(hdr, buf, 32);
     if (hdr[1] != c->nn || hdr[2] != c->precision || hdr[3] != c->kahan)
         return fail(c, FEDFEM_ERR_ARG, "state blob does not match this context");
+    if (hdr[0] < 0) return fail(c, FEDFEM_ERR_ARG, "state blob with a negative step counter");
     const size_t rs = c->precision == 64 ? 8 : 4;
     c->step = hdr[0];
     const int b = (int)(c->step & 1);

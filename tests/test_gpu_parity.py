@@ -500,6 +500,14 @@ def test_checkpoint_resume_bitwise():
     assert f.step_count == 103
     f.step(97)
     assert np.array_equal(a, f.get_T())
+    # blobs that do not belong to this context are refused on the host, the state untouched
+    from paper_1909_03355_gb300.capi import FedFemError
+    for field, value in ((0, -5), (1, p.n_nodes + 1)):
+        bad = st.copy()
+        bad[8 * field:8 * field + 8] = np.frombuffer(np.int64(value).tobytes(), np.uint8)
+        with pytest.raises(FedFemError):
+            f.set_state(bad)
+    assert f.step_count == 200 and np.array_equal(a, f.get_T())
     f.close()
 
 
