@@ -138,3 +138,54 @@ def ftcs_slab(nx, h, dt, nsteps, T0, Ts, k, rho, c0, k_lin=0.0, c_lin=0.0, conv=
         Tn[0] = end_value(n + 1)
         T = Tn
     return T
+
+
+def hex_shape_integrals_gauss3(x):
+    """w_i = int_Ve N_i dV of a trilinear hexahedron (VTK order) by 3x3x3 Gauss-Legendre points
+    (numpy's leggauss), with the shape functions written as products of 1-D linear functions
+    of the corner index bits.  N_i det J has degree <= 3 in each natural coordinate, so both
+    this rule (exact to degree 5) and the 2x2x2 rule (exact to degree 3) integrate it exactly;
+    the two share no code.  Returns (w [8], volume)."""
+    x = np.asarray(x, float)
+    g, gw = np.polynomial.legendre.leggauss(3)
+    sgn = 2.0 * VTK_CORNERS - 1.0                      # [8, 3] corner signs
+    w = np.zeros(8)
+    vol = 0.0
+    for a, wa in zip(g, gw):
+        for b, wb in zip(g, gw):
+            for c, wc in zip(g, gw):
+                p = np.array([a, b, c])
+                lin = 0.5 * (1.0 + sgn * p)             # [8, 3] 1-D factors
+                N = np.prod(lin, axis=1)
+                dN = np.empty((8, 3))
+                for d in range(3):
+                    o = [q for q in range(3) if q != d]
+                    dN[:, d] = 0.5 * sgn[:, d] * lin[:, o[0]] * lin[:, o[1]]
+                J = x.T @ dN                            # dx_r / dxi_s
+                dj = np.linalg.det(J)
+                w += wa * wb * wc * dj * N
+                vol += wa * wb * wc * dj
+    return w, vol
+
+
+def hex_shape_integrals_exact(x):
+    """Exact w_i = int N_i det J over [-1,1]^3 as a polynomial integral in rational arithmetic
+    (sympy), for coordinates given as decimals.  Returns (w [8] as floats, volume)."""
+    import sympy as sp
+    xi = sp.symbols("xi0:3")
+    X = [[sp.Rational(str(float(v))) for v in row] for row in np.asarray(x, float)]
+    N = []
+    for ci in VTK_CORNERS:
+        f = sp.Integer(1)
+        for d in range(3):
+            f *= (1 + (2 * int(ci[d]) - 1) * xi[d]) / 2
+        N.append(sp.expand(f))
+    J = sp.Matrix(3, 3, lambda r, s: sum(X[i][r] * sp.diff(N[i], xi[s]) for i in range(8)))
+    dj = sp.expand(J.det())
+
+    def integ(f):
+        for v in xi:
+            f = sp.integrate(f, (v, -1, 1))
+        return f
+    w = [integ(sp.expand(Ni * dj)) for Ni in N]
+    return np.array([float(v) for v in w]), float(integ(dj))

@@ -119,6 +119,47 @@ def test_distorted_elements_invariants(patch_nodes):
         assert tot == pytest.approx(1.0, rel=1e-12)
 
 
+def test_hex_shape_integrals_on_distorted_elements(patch_nodes):
+    """w_i = int_Ve N_i dV (lumped masses and source loads, Section 3.1) on non-parallelepiped
+    hexahedra: the oracle's 2x2x2 values against an independent 3x3x3 Gauss-Legendre
+    integration on every element of the distorted patch and of a jittered cube, and against
+    exact rational integration (sympy) on the patch's inner element.  A centre-point det J or a
+    permuted node order in N_i fails this; sum_i w_i = V alone would not."""
+    k = np.eye(3)
+    xyz, conn = fi.cube_mesh(4, "hex", jitter=0.3, seed=11)
+    elems = [fi.patch_problem(patch_nodes, "hex")]
+    cases = [(e.xyz, e.conn) for e in elems] + [(xyz, conn)]
+    worst = 0.0
+    for X, Cn in cases:
+        for c in Cn:
+            _, w, vol = O.hex_matrices(X[c], k)
+            w3, v3 = brute.hex_shape_integrals_gauss3(X[c])
+            worst = max(worst, np.max(np.abs(w - w3)) / np.max(np.abs(w3)))
+            assert vol == pytest.approx(v3, rel=1e-14)
+            # distorted: the shares are not all equal
+            assert np.ptp(w3) > 1e-3 * np.max(w3) or X is xyz
+    assert worst <= 1e-14
+    # the lumped thermal mass and source loads of the jittered cube assemble those w_i
+    p = fi.Problem("j", xyz, conn, [fi.Material(2.0, k, 0.0, 3.0, 0.0)], T0=np.zeros(len(xyz)),
+                   elem_source=np.linspace(1.0, 2.0, len(conn)))
+    m = O.OracleModel(p)
+    M = np.zeros(len(xyz))
+    Q = np.zeros(len(xyz))
+    for e, c in enumerate(conn):
+        w3, _ = brute.hex_shape_integrals_gauss3(xyz[c])
+        np.add.at(M, c, 6.0 * w3)
+        np.add.at(Q, c, p.elem_source[e] * w3)
+    assert np.max(np.abs(m.C0 - M)) <= 1e-14 * np.max(M)
+    assert np.max(np.abs(m.Qext - Q)) <= 1e-14 * np.max(Q)
+    pytest.importorskip("sympy")
+    pe = fi.patch_problem(patch_nodes, "hex")
+    x = pe.xyz[pe.conn[0]]
+    we, ve = brute.hex_shape_integrals_exact(x)
+    _, w, vol = O.hex_matrices(x, k)
+    assert np.max(np.abs(w - we)) <= 1e-14 * np.max(we)
+    assert vol == pytest.approx(ve, rel=1e-14)
+
+
 def test_face_areas():
     """Quad area by bilinear-patch quadrature and triangle area vs closed forms."""
     sq = np.array([[0, 0, 0], [2, 0, 0], [2, 3, 0], [0, 3, 0]], float)
