@@ -1,11 +1,13 @@
 /*
  * FED-FEM oracle: TEST INFRASTRUCTURE ONLY.
  *
- * A plain, slow, single-threaded FP64 CPU implementation of the fast explicit dynamics finite
+ * A plain, slow FP64 CPU implementation of the fast explicit dynamics finite
  * element method (FED-FEM) for transient heat conduction (Zhang & Chauhan, arXiv:1909.03355).
  * Only the test suite, the smoke check and the CPU-baseline leg of bench.py may load it.  It
  * shares no code with the CUDA library: it follows the paper's equations in their textbook
  * form (full 8x8 / 4x4 element matrices, element loop and scatter, literal Eq. 7 radiation).
+ * Everything runs on one thread except orc_run_mt, the same time stepping over all host cores
+ * with a result bitwise equal to the single-threaded orc_run.
  *
  * Readings of the paper used here (where it is silent, garbled or at odds with itself):
  *  - Sign (Eq. 2, 11-13): the element load F_e = theta_e f_k,e K0_e T_e is the positive
@@ -31,6 +33,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_SIGMA 5.67e-8 /* Stefan-Boltzmann constant as printed with Eq. 7 */
 
@@ -678,4 +683,118 @@ void orc_adjoint(const orc_model *m, double dt, int64_t nsteps, const double *T0
     free(mu);
     free(F);
     free(musum);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* the same time stepping over all host cores (OpenMP)                                          */
+/* ------------------------------------------------------------------------------------------ */
+
+/*
+ * Incidence of the mesh: for every node the (element, local index) pairs that touch it, in
+ * increasing element order (ptr [nn + 1], ent [ne * npe] = e * npe + i).
+ */
+static void orc_node_incidence(const orc_model *m, int64_t *ptr, int64_t *ent)
+{
+    const int npe = m->npe;
+    memset(ptr, 0, (m->nn + 1) * sizeof(int64_t));
+    for (int64_t e = 0; e < m->ne; ++e)
+        for (int i = 0; i < npe; ++i) ++ptr[m->conn[npe * e + i] + 1];
+    for (int64_t n = 0; n < m->nn; ++n) ptr[n + 1] += ptr[n];
+    int64_t *fill = (int64_t *)malloc(m->nn * sizeof(int64_t));
+    memcpy(fill, ptr, m->nn * sizeof(int64_t));
+    for (int64_t e = 0; e < m->ne; ++e)
+        for (int i = 0; i < npe; ++i) ent[fill[m->conn[npe * e + i]]++] = e * npe + i;
+    free(fill);
+}
+
+/*
+ * orc_run over nthreads host threads.  The element loop of Eq. 11 / 20 is split in two passes:
+ * every element forms its load vector F_e = theta_e f_k,e K0_e T_e (elements in parallel),
+ * then every node adds the loads of its elements in increasing element order (nodes in
+ * parallel).  Each node therefore receives the same terms in the same order as in the serial
+ * element loop with scatter, so the result is bitwise that of orc_run.  The nodal update is
+ * independent per node (Eq. 16); the energy sums are added in node order afterwards.
+ * Same arguments as orc_run; nthreads <= 0 uses the OpenMP default.
+ */
+void orc_run_mt(const orc_model *m, double dt, int64_t nsteps, double *T, double *energy,
+                const int32_t *sensors, int32_t ns, int32_t sample_every, double *trace, int32_t nthreads)
+{
+    const int64_t nn = m->nn, ne = m->ne;
+    const int npe = m->npe;
+#ifdef _OPENMP
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+    const int nt = 1;
+    (void)nthreads;
+#endif
+    int64_t *ptr = (int64_t *)malloc((nn + 1) * sizeof(int64_t));
+    int64_t *ent = (int64_t *)malloc((size_t)ne * npe * sizeof(int64_t));
+    double *Fe = (double *)malloc((size_t)ne * npe * sizeof(double));
+    double *Tn = (double *)malloc(nn * sizeof(double));
+    double *Sn = energy ? (double *)malloc(nn * sizeof(double)) : NULL;
+    double *Bn = energy ? (double *)malloc(nn * sizeof(double)) : NULL;
+    orc_node_incidence(m, ptr, ent);
+    orc_impose_dirichlet(m, T, m->sched_step0);
+    for (int64_t n = 0; n < nsteps; ++n) {
+        const int64_t step = m->sched_step0 + n;
+#pragma omp parallel num_threads(nt)
+        {
+#pragma omp for schedule(static)
+            for (int64_t e = 0; e < ne; ++e) {
+                const int32_t *c = m->conn + npe * e;
+                const double *Ke = m->K + (int64_t)npe * npe * e;
+                double fk = 0.0;
+                for (int i = 0; i < npe; ++i) fk += orc_fk(m, T[c[i]]);
+                fk /= npe;
+                const double s = m->theta[e] * fk;
+                for (int i = 0; i < npe; ++i) {
+                    double acc = 0.0;
+                    for (int j = 0; j < npe; ++j) acc += Ke[npe * i + j] * T[c[j]];
+                    Fe[npe * e + i] = s * acc;
+                }
+            }
+#pragma omp for schedule(static)
+            for (int64_t i = 0; i < nn; ++i) {
+                double F = 0.0;
+                for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) F += Fe[ent[q]];
+                if (m->isdir[i]) {
+                    Tn[i] = T[i];
+                    if (energy) {
+                        Sn[i] = 0.0;
+                        Bn[i] = dt * F;
+                    }
+                    continue;
+                }
+                const double Q = orc_nodal_Q_n(m, i, T[i], step);
+                const double Ci = m->C0[i] * orc_fc(m, T[i]);
+                const double t = T[i] + dt / Ci * (Q - F);
+                if (energy) {
+                    Sn[i] = Ci * (t - T[i]);
+                    Bn[i] = dt * Q;
+                }
+                Tn[i] = t;
+            }
+        }
+        memcpy(T, Tn, nn * sizeof(double));
+        orc_impose_dirichlet(m, T, step + 1);
+        if (energy) {
+            double S = 0.0, B = 0.0;
+            for (int64_t i = 0; i < nn; ++i) {
+                S += Sn[i];
+                B += Bn[i];
+            }
+            energy[2 * n] = S;
+            energy[2 * n + 1] = B;
+        }
+        if (trace && sample_every > 0 && (n + 1) % sample_every == 0) {
+            const int64_t k = (n + 1) / sample_every - 1;
+            for (int s = 0; s < ns; ++s) trace[k * ns + s] = T[sensors[s]];
+        }
+    }
+    free(ptr);
+    free(ent);
+    free(Fe);
+    free(Tn);
+    free(Sn);
+    free(Bn);
 }

@@ -1,6 +1,8 @@
 """FED-FEM oracle (Python side): TEST INFRASTRUCTURE ONLY.
 
-Builds and loads ``fedfem_oracle.c`` (plain single-threaded FP64 C) and wraps it with numpy.
+Builds and loads ``fedfem_oracle.c`` (plain FP64 C; single-threaded, except the time stepping
+``run(..., threads=n)`` over n host threads, bitwise equal to the single-threaded run) and wraps
+it with numpy.
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
 import this module.  It shares no code with the CUDA library ``paper_1909_03355_gb300``; the
 only common input is the problem statement built by ``fedfem_inputs``.
@@ -10,6 +12,7 @@ Function map (paper passages):
                               (Section 3.1), surface area shares (Eq. 4/7 lumped to nodes)
   OracleModel.internal_loads  Eq. 11/20 with the element-mean k(T) of Section 4.2.2
   OracleModel.run             time-stepping stage, Fig. 1 (iii): Eq. 15/16, Dirichlet re-imposed
+                              (threads > 1: element pass and node gather in element order)
   OracleModel.set_schedule    time-dependent loads, convection temperature and Dirichlet values
   OracleModel.set_table       tabulated k(T), c(T) factors, linear between points (Section 4.2.2)
   OracleModel.dt_crit         Section 3.4, Eq. 29
@@ -40,7 +43,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
                                "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -77,12 +80,21 @@ def lib():
             L.orc_nodal_Q.argtypes = [P, C.c_int64, C.c_double]
             L.orc_nodal_Q.restype = C.c_double
             L.orc_run.argtypes = [P, C.c_double, C.c_int64, P, P, P, C.c_int32, C.c_int32, P]
+            L.orc_run_mt.argtypes = [P, C.c_double, C.c_int64, P, P, P, C.c_int32, C.c_int32, P, C.c_int32]
             L.orc_dt_crit.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_int64, P]
             L.orc_dt_from_lambda.argtypes = [P, C.c_double, C.c_double, C.c_double]
             L.orc_dt_from_lambda.restype = C.c_double
             L.orc_adjoint.argtypes = [P, C.c_double, C.c_int64, P, P, C.c_int32, C.c_int32, P, P, P]
             _lib = L
     return _lib
+
+
+def host_threads() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def _p(a):
@@ -244,9 +256,10 @@ class OracleModel:
         L = lib()
         return np.array([L.orc_nodal_Q(self.mref, i, float(T[i])) for i in range(len(T))])
 
-    def run(self, T, dt, nsteps, energy=False, sensors=None, sample_every=0, step0=0):
+    def run(self, T, dt, nsteps, energy=False, sensors=None, sample_every=0, step0=0, threads=1):
         """n explicit steps from T (copied), the first being step `step0` of the load schedule;
-        returns T (and per-step energy [n,2], trace)."""
+        returns T (and per-step energy [n,2], trace).  threads > 1 (or 0: all host cores) runs
+        the same steps over that many threads, with a bitwise equal result."""
         self.m.sched_step0 = int(step0)
         T = np.array(T, dtype=np.float64, copy=True)
         E = np.zeros((nsteps, 2)) if energy else None
@@ -254,8 +267,13 @@ class OracleModel:
         trace = None
         if sens is not None and sample_every > 0:
             trace = np.zeros((nsteps // sample_every, len(sens)))
-        lib().orc_run(self.mref, float(dt), int(nsteps), _p(T), _p(E), _p(sens),
-                      0 if sens is None else len(sens), int(sample_every), _p(trace))
+        if threads == 1:
+            lib().orc_run(self.mref, float(dt), int(nsteps), _p(T), _p(E), _p(sens),
+                          0 if sens is None else len(sens), int(sample_every), _p(trace))
+        else:
+            lib().orc_run_mt(self.mref, float(dt), int(nsteps), _p(T), _p(E), _p(sens),
+                             0 if sens is None else len(sens), int(sample_every), _p(trace),
+                             int(threads if threads > 0 else host_threads()))
         out = [T]
         if energy:
             out.append(E)

@@ -710,3 +710,38 @@ def test_adjoint_dot_product_linear():
     Jv = tr1 - tr0
     _, gs = m.adjoint(dt, 20, p.initial_T(), sensors, 5, w)
     assert np.sum(Jv * w) == pytest.approx(np.dot(v, gs), rel=1e-10)
+
+
+# ------------------------------------------------------------ multi-threaded time stepping --
+
+@pytest.mark.parametrize("case", ["hex_jitter", "tet", "moving_boundary_table", "sensors_schedule"])
+def test_threaded_run_is_bitwise_the_serial_run(case):
+    """The time stepping over several host threads (element pass, then a node gather in element
+    order) gives bitwise the serial element loop's result: states, per-step energy terms and
+    sensor traces, with Dirichlet nodes, schedules and property tables."""
+    sensors, every = None, 0
+    if case == "hex_jitter":
+        p = fi.nonlinear_cube(9, "hex", jitter=0.2)
+    elif case == "tet":
+        p = fi.nonlinear_cube(6, "tet")
+    elif case == "moving_boundary_table":
+        p = fi.nonlinear_cube(7, "hex", jitter=0.1)
+        bot = np.nonzero(p.xyz[:, 2] < 1e-12)[0].astype(np.int32)
+        p.dir_nodes, p.dir_T = bot, 100.0 + 50.0 * p.xyz[bot, 0]
+        p.Tdir_schedule = 80.0 * np.sin(0.04 * np.arange(120))
+        p.table_T = np.array([0.0, 100.0, 250.0, 450.0])
+        p.table_fk = np.array([1.0, 1.6, 1.2, 2.5])
+        p.table_fc = np.array([1.0, 0.8, 1.4, 1.1])
+    else:
+        p = fi.large_cube(8)
+        p.q_schedule = 1.0 + 0.5 * np.sin(0.1 * np.arange(90))
+        p.Tinf_schedule = 20.0 + np.arange(90) * 0.3
+        sensors, every = np.array([5, 77, 300, 601], np.int32), 7
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit(T_hi=900.0)[0]
+    for threads in (2, 3, 0):
+        a = m.run(p.initial_T(), dt, 150, energy=True, sensors=sensors, sample_every=every, step0=4)
+        b = m.run(p.initial_T(), dt, 150, energy=True, sensors=sensors, sample_every=every, step0=4,
+                  threads=threads)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
