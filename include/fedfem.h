@@ -310,11 +310,15 @@ typedef struct {
  *   is_dirichlet (1 on Gamma_E);  out: DEVICE array of 2 doubles receiving
  *   (stored_change, boundary_in);  stream: cudaStream_t or NULL.  Asynchronous on `stream`.
  * The capacity factor is the linear law of params (c_lin, T_ref); a context with a property
- * table gets its sums from fedfem_energy.
+ * table gets its sums from fedfem_energy.  With a load schedule, pass the data of the step the
+ * sums describe: Qext already multiplied by that step's load factor and T_inf that step's
+ * convection temperature.
  * All calls on a device share the scratch array: calls that overlap on the GPU race.  Each call
  * overwrites every partial it reads, so nothing needs clearing between calls.  The first call
  * on a device looks the array's address up (cudaGetSymbolAddress) with that device current:
- * make it before any stream capture.
+ * make it before any stream capture.  That address is kept for the life of the process, so
+ * the entry point must not be used on a device after cudaDeviceReset (a reset primary context
+ * reloads the library's device code).  Launch errors are those of this call's own launches.
  * Errors: ARG (NULL pointer, n_nodes out of range), CUDA.
  */
 fedfem_status fedfem_energy_terms_noalloc(int64_t n_nodes, const double *T_prev, const double *T_next,

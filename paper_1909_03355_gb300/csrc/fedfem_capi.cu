@@ -1064,12 +1064,15 @@ extern "C" fedfem_status fedfem_set_state(fedfem_ctx *c, const void *buf)
         return fail(c, FEDFEM_ERR_ARG, "state blob does not match this context");
     if (hdr[0] < 0) return fail(c, FEDFEM_ERR_ARG, "state blob with a negative step counter");
     const size_t rs = c->precision == 64 ? 8 : 4;
-    c->step = hdr[0];
-    const int b = (int)(c->step & 1);
+    // the step counter (which selects the ping-pong buffer and indexes the schedules) changes
+    // only once the state it describes has arrived
+    const int64_t step = hdr[0];
+    const int b = (int)(step & 1);
     const uint8_t *p = (const uint8_t *)buf + 32;
     CK(cudaMemcpyAsync(c->d_T[b], p, c->nn * rs, cudaMemcpyHostToDevice, c->stream), "upload state");
     if (c->kahan) CK(cudaMemcpyAsync(c->d_comp[b], p + c->nn * rs, c->nn * 4, cudaMemcpyHostToDevice, c->stream), "upload");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
+    c->step = step;
     c->has_T = true;
     return FEDFEM_OK;
 }

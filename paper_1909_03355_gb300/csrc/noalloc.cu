@@ -17,7 +17,12 @@
 //    overwrites all the partial sums it reads, so nothing has to be cleared between calls;
 //  - the first call on each device looks the array's device address up with
 //    cudaGetSymbolAddress (with that device current); make that first call before any stream
-//    capture begins.
+//    capture begins.  The address is kept for the life of the process: do not use this entry
+//    point on a device after cudaDeviceReset (or any other reset of its primary context),
+//    which reloads the library's device code at a possibly different address;
+//  - the sums are those of fedfem_energy for the step whose data the caller passes: with a
+//    load schedule, Qext must already carry that step's load multiplier and T_inf must be
+//    that step's convection temperature.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -147,9 +152,17 @@ extern "C" fedfem_status fedfem_energy_terms_noalloc(int64_t n_nodes, const doub
     if (st != FEDFEM_OK) return st;
     const int nblocks = (int)((n_nodes + kItemsPerBlock - 1) / kItemsPerBlock);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    k_energy_blocks<<<nblocks, kThreads, 0, s>>>(n_nodes, T_prev, T_next, F, C0, Qext, Ac, Ar, is_dirichlet, ph->dt,
-                                                 ph->c_lin, ph->h, ph->T_inf, ph->eps * 5.67e-8, ph->T_amb,
-                                                 ph->T_zero, ph->T_ref, partials);
-    k_energy_final<<<1, kThreads, 0, s>>>(nblocks, partials, out);
-    return cudaGetLastError() == cudaSuccess ? FEDFEM_OK : FEDFEM_ERR_CUDA;
+    // each launch's own return code: an error left behind by unrelated earlier work is neither
+    // reported here nor cleared
+    double dt = ph->dt, c_lin = ph->c_lin, h = ph->h, T_inf = ph->T_inf, eps_sigma = ph->eps * 5.67e-8,
+           T_amb = ph->T_amb, T_zero = ph->T_zero, T_ref = ph->T_ref;
+    void *args1[] = {&n_nodes, &T_prev, &T_next, &F, &C0, &Qext, &Ac, &Ar, &is_dirichlet, &dt, &c_lin,
+                     &h, &T_inf, &eps_sigma, &T_amb, &T_zero, &T_ref, &partials};
+    if (cudaLaunchKernel((const void *)k_energy_blocks, dim3(nblocks), dim3(kThreads), args1, 0, s) != cudaSuccess)
+        return FEDFEM_ERR_CUDA;
+    int nb = nblocks;
+    void *args2[] = {&nb, &partials, &out};
+    if (cudaLaunchKernel((const void *)k_energy_final, dim3(1), dim3(kThreads), args2, 0, s) != cudaSuccess)
+        return FEDFEM_ERR_CUDA;
+    return FEDFEM_OK;
 }
