@@ -397,6 +397,67 @@ fedfem_status fedfem_batch_get_T(fedfem_batch *b, int32_t s, double *T_host);
 const char *fedfem_batch_error_string(fedfem_batch *b);
 void fedfem_batch_destroy(fedfem_batch *b);
 
+/* ---------------------------------------------------------------------------------------
+ * Domain decomposition of one mesh (Section 3, Eq. 15-16: with the lumped capacitance every
+ * nodal equation is independent once its element loads are known, which permits a parallel
+ * implementation).  The elements are cut into n_sub slabs of equal element count along the
+ * longest axis of the bounding box (by element centroid; a coordinate bisection that also
+ * serves unstructured meshes).  A node is owned by the lowest-numbered slab among its
+ * elements.  Sub-domain s holds the elements of slab s plus every element touching a node it
+ * owns (one ghost layer), so each owned node receives all its element loads locally; the other
+ * nodes of those elements are its ghosts.  Each sub-domain is a context of its own.  One step
+ * = one step of every sub-domain (ghosts held fixed, like Dirichlet nodes), then the halo
+ * exchange: each owner packs the new values of its nodes that neighbours hold as ghosts into
+ * a send buffer, one message per sub-domain pair moves send buffer to receive buffer, and the
+ * receivers unpack into their ghost slots.  In FP32 + Kahan a message entry carries the value
+ * and its compensation (8 bytes), in FP64 the value (8 bytes).  All sub-domains run on the
+ * device and stream of `opt`; the field equals the undecomposed run's up to the order of the
+ * floating-point sums.  Not available with schedules or property tables.
+ * ------------------------------------------------------------------------------------- */
+typedef struct fedfem_dd fedfem_dd;
+typedef struct {
+    int32_t n_sub, axis;          /* sub-domains, slab axis (0 = x, 1 = y, 2 = z)            */
+    int32_t n_messages, reserved; /* sub-domain pairs that exchange ghost values each step   */
+    int64_t halo_entries;         /* ghost values sent per step (all messages)               */
+    int64_t halo_bytes_per_step;  /* bytes of those values                                   */
+    int64_t ghost_elements;       /* elements held by a sub-domain other than their slab's   */
+    int64_t step;                 /* steps since fedfem_dd_set_T                             */
+    double dt_crit;               /* as returned by fedfem_dd_precompute                     */
+} fedfem_dd_info;
+/* Partition the mesh and create one context per sub-domain (arguments as fedfem_create; the
+ * sub-domains' launch plans follow opt).  On failure *out is NULL and
+ * fedfem_dd_error_string(NULL) explains it.  Errors: ARG, MESH, CUDA, OOM. */
+fedfem_status fedfem_dd_create(const fedfem_mesh *mesh, const fedfem_material *mats, int32_t n_mats,
+                               const fedfem_bcs *bcs, const fedfem_options *opt, int32_t n_sub,
+                               fedfem_dd **out);
+/* Pre-computation of every sub-domain (fedfem_precompute).  *dt_crit_out = the smallest
+ * critical step over the sub-domains.  Each sub-domain's operator on its owned nodes is a
+ * principal sub-matrix of the whole mesh's, so this is at least the whole mesh's dt_crit (equal
+ * up to how much the highest mode is cut by the ghost boundaries; on the structured cubes
+ * tested, within 1e-3): choose dt with a safety factor.  Errors: as fedfem_precompute. */
+fedfem_status fedfem_dd_precompute(fedfem_dd *dd, double T_lo, double T_hi, double *dt_crit_out);
+/* Time step of all sub-domains; UNSTABLE if dt > dt_crit and force == 0. */
+fedfem_status fedfem_dd_set_dt(fedfem_dd *dd, double dt, int32_t force);
+/* Initial field [n_nodes] (host, the mesh's node order); Dirichlet values re-imposed, ghosts
+ * filled from their owners. */
+fedfem_status fedfem_dd_set_T(fedfem_dd *dd, const double *T0_host);
+/* n_steps explicit steps (one launch per sub-domain and step, then the halo exchange);
+ * synchronises and reports device-side errors as fedfem_step. */
+fedfem_status fedfem_dd_step(fedfem_dd *dd, int64_t n_steps);
+/* Current field [n_nodes] (host, FP64, the mesh's node order), each node from its owner. */
+fedfem_status fedfem_dd_get_T(fedfem_dd *dd, double *T_host);
+fedfem_status fedfem_dd_get_info(fedfem_dd *dd, fedfem_dd_info *info);
+/* Host-only query of the partition (no device call): sub-domain s of n_sub for this mesh, its
+ * elements (ascending global ids, core and ghost layer) and nodes (ascending global ids) and,
+ * per node, the owning sub-domain of a ghost (-1 for an owned node).  Pass NULL arrays to get
+ * the counts first.  Errors: ARG, MESH (node id out of range). */
+fedfem_status fedfem_dd_subdomain(const fedfem_mesh *mesh, int32_t n_sub, int32_t s, int64_t *n_elems,
+                                  int32_t *elems, int64_t *n_nodes, int32_t *nodes, int32_t *ghost_owner);
+/* Message of the last error on dd; with NULL, of the last fedfem_dd_create on this thread. */
+const char *fedfem_dd_error_string(fedfem_dd *dd);
+/* Release all sub-domains.  NULL is ignored. */
+void fedfem_dd_destroy(fedfem_dd *dd);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,6 +63,11 @@ class Scenario(C.Structure):
                 ("T_lo", F64), ("T_hi", F64), ("dt_scale", F64)]
 
 
+class DDInfo(C.Structure):
+    _fields_ = [("n_sub", I32), ("axis", I32), ("n_messages", I32), ("reserved", I32), ("halo_entries", I64),
+                ("halo_bytes_per_step", I64), ("ghost_elements", I64), ("step", I64), ("dt_crit", F64)]
+
+
 class EnergyParams(C.Structure):
     _fields_ = [("dt", F64), ("c_lin", F64), ("h", F64), ("T_inf", F64), ("eps", F64), ("T_amb", F64),
                 ("T_zero", F64), ("T_ref", F64)]
@@ -105,6 +110,16 @@ SIGNATURES = {
     "fedfem_batch_get_T": (I32, [P, I32, P]),
     "fedfem_batch_error_string": (C.c_char_p, [P]),
     "fedfem_batch_destroy": (None, [P]),
+    "fedfem_dd_create": (I32, [P, P, I32, P, P, I32, P]),
+    "fedfem_dd_precompute": (I32, [P, F64, F64, P]),
+    "fedfem_dd_set_dt": (I32, [P, F64, I32]),
+    "fedfem_dd_set_T": (I32, [P, P]),
+    "fedfem_dd_step": (I32, [P, I64]),
+    "fedfem_dd_get_T": (I32, [P, P]),
+    "fedfem_dd_get_info": (I32, [P, P]),
+    "fedfem_dd_subdomain": (I32, [P, I32, I32, P, P, P, P, P]),
+    "fedfem_dd_error_string": (C.c_char_p, [P]),
+    "fedfem_dd_destroy": (None, [P]),
 }
 
 _lib = None

@@ -55,6 +55,8 @@ int main(void) {
   printf("%zu %zu\n", offsetof(fedfem_info, dt), offsetof(fedfem_scenario, dt_scale));
   printf("%zu %zu %zu %zu\n", sizeof(fedfem_energy_params), sizeof(fedfem_tiling_stats),
          offsetof(fedfem_tiling_stats, n_shared_nodes), offsetof(fedfem_options, quadrature));
+  printf("%zu %zu %zu\n", sizeof(fedfem_dd_info), offsetof(fedfem_dd_info, halo_entries),
+         offsetof(fedfem_dd_info, dt_crit));
   return 0;
 }
 '''
@@ -71,7 +73,8 @@ int main(void) {
             capi.Bcs.face_nv.offset, capi.Bcs.elem_source.offset, capi.Options.stream.offset,
             capi.Options.debug_withhold_barrier.offset, capi.Info.dt.offset, capi.Scenario.dt_scale.offset,
             C.sizeof(capi.EnergyParams), C.sizeof(capi.TilingStats), capi.TilingStats.n_shared_nodes.offset,
-            capi.Options.quadrature.offset]
+            capi.Options.quadrature.offset,
+            C.sizeof(capi.DDInfo), capi.DDInfo.halo_entries.offset, capi.DDInfo.dt_crit.offset]
     assert got == want
 
 
@@ -122,3 +125,29 @@ def test_batch_rejects_schedules_and_tables_without_gpu():
         setattr(p, field, value)
         with pytest.raises(ValueError, match=field):
             FedFemBatch([fi.nonlinear_cube(2, "hex"), p])
+
+
+def test_decomposition_rejects_bad_input_without_gpu(lib_path):
+    """The domain decomposition validates its arguments on the host, and refuses schedules and
+    property tables in the binding."""
+    import numpy as np
+
+    import fedfem_inputs as fi
+    from paper_1909_03355_gb300 import capi, dd
+    p = fi.plain_cube(2)
+    for n_sub in (0, 9, 65):
+        with pytest.raises(capi.FedFemError) as ei:
+            dd.FedFemDD(p, n_sub)
+        assert ei.value.name == "ERR_ARG"
+    with pytest.raises(capi.FedFemError):
+        dd.subdomain(p, 2, 2)
+    q = fi.plain_cube(2)
+    q.conn = q.conn.copy()
+    q.conn[0, 0] = -1
+    with pytest.raises(capi.FedFemError) as ei:
+        dd.FedFemDD(q, 2)
+    assert ei.value.name == "ERR_MESH"
+    r = fi.nonlinear_cube(2, "hex")
+    r.q_schedule = np.ones(3)
+    with pytest.raises(ValueError, match="q_schedule"):
+        dd.FedFemDD(r, 2)
