@@ -65,6 +65,10 @@ class Problem:
     T_hi: float = 0.0
     quadrature: int = 8                         # hexahedron conduction matrix: 8 = 2x2x2 Gauss,
                                                 # 1 = one centre point (Eq. 17)
+    kT_eval: int = 0                            # conductivity law: 0 = element mean of the nodal
+                                                # factors (Section 4.2.2), 1 = at the quadrature points
+    face_quadrature: int = 0                    # surface loads: 0 = nodal lumping of the face areas,
+                                                # 1 = consistent integration over each face
     q_schedule: Optional[np.ndarray] = None     # [n] multiplier of the external loads at step n
     Tinf_schedule: Optional[np.ndarray] = None  # [n] convection ambient temperature at step n
     Tdir_schedule: Optional[np.ndarray] = None  # [n] offset added to every dir_T at step n

@@ -73,6 +73,52 @@ static const double HEX_NAT[8][3] = {
     {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
 
 /*
+ * The integrand of Eq. 12 for the trilinear hexahedron at Gauss point q of the 2x2x2 rule
+ * (points +-1/sqrt(3), unit weights): Kq_ij = det J (grad N_i)^T k (grad N_j) (row-major 8x8)
+ * and the shape function values N [8] at the point; *detJ = det J.  Returns -1 when
+ * det J <= 0 (inverted or degenerate element).
+ */
+static int orc_hex_point(const double *x, const double *k, int q, double *Kq, double *N, double *detJ)
+{
+    const double g = 1.0 / sqrt(3.0);
+    const double xi = HEX_NAT[q][0] * g, eta = HEX_NAT[q][1] * g, zeta = HEX_NAT[q][2] * g;
+    double dN[8][3];
+    for (int i = 0; i < 8; ++i) {
+        const double a = 1.0 + xi * HEX_NAT[i][0];
+        const double b = 1.0 + eta * HEX_NAT[i][1];
+        const double c = 1.0 + zeta * HEX_NAT[i][2];
+        N[i] = a * b * c / 8.0;
+        dN[i][0] = HEX_NAT[i][0] * b * c / 8.0;
+        dN[i][1] = a * HEX_NAT[i][1] * c / 8.0;
+        dN[i][2] = a * b * HEX_NAT[i][2] / 8.0;
+    }
+    double J[3][3] = {{0}};
+    for (int i = 0; i < 8; ++i)
+        for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 3; ++s) J[r][s] += x[3 * i + r] * dN[i][s];
+    const double d = det3(J);
+    if (!(d > 0.0)) return -1;
+    double Ji[3][3];
+    inv3(J, d, Ji);
+    double B[8][3]; /* grad_x N_i = J^-T grad_xi N_i */
+    for (int i = 0; i < 8; ++i)
+        for (int r = 0; r < 3; ++r) {
+            B[i][r] = 0.0;
+            for (int s = 0; s < 3; ++s) B[i][r] += Ji[s][r] * dN[i][s];
+        }
+    for (int i = 0; i < 8; ++i) {
+        double kB[3];
+        for (int r = 0; r < 3; ++r) {
+            kB[r] = 0.0;
+            for (int s = 0; s < 3; ++s) kB[r] += k[3 * r + s] * B[i][s];
+        }
+        for (int j = 0; j < 8; ++j) Kq[8 * j + i] = d * (B[j][0] * kB[0] + B[j][1] * kB[1] + B[j][2] * kB[2]);
+    }
+    *detJ = d;
+    return 0;
+}
+
+/*
  * Eq. 12 for the trilinear hexahedron: K_ij = int_Ve (grad N_i)^T k (grad N_j) dV, evaluated by
  * 2x2x2 Gauss quadrature (points +-1/sqrt(3), unit weights), together with w_i = int_Ve N_i dV
  * and the element volume.  x: [8][3] node coordinates; k: 3x3 conductivity (row-major).
@@ -80,47 +126,29 @@ static const double HEX_NAT[8][3] = {
  */
 int orc_hex_matrices(const double *x, const double *k, double *K, double *w, double *vol)
 {
-    const double g = 1.0 / sqrt(3.0);
     memset(K, 0, 64 * sizeof(double));
     memset(w, 0, 8 * sizeof(double));
     *vol = 0.0;
     for (int q = 0; q < 8; ++q) {
-        const double xi = HEX_NAT[q][0] * g, eta = HEX_NAT[q][1] * g, zeta = HEX_NAT[q][2] * g;
-        double N[8], dN[8][3];
-        for (int i = 0; i < 8; ++i) {
-            const double a = 1.0 + xi * HEX_NAT[i][0];
-            const double b = 1.0 + eta * HEX_NAT[i][1];
-            const double c = 1.0 + zeta * HEX_NAT[i][2];
-            N[i] = a * b * c / 8.0;
-            dN[i][0] = HEX_NAT[i][0] * b * c / 8.0;
-            dN[i][1] = a * HEX_NAT[i][1] * c / 8.0;
-            dN[i][2] = a * b * HEX_NAT[i][2] / 8.0;
-        }
-        double J[3][3] = {{0}};
-        for (int i = 0; i < 8; ++i)
-            for (int r = 0; r < 3; ++r)
-                for (int s = 0; s < 3; ++s) J[r][s] += x[3 * i + r] * dN[i][s];
-        const double d = det3(J);
-        if (!(d > 0.0)) return -1;
-        double Ji[3][3];
-        inv3(J, d, Ji);
-        double B[8][3]; /* grad_x N_i = J^-T grad_xi N_i */
-        for (int i = 0; i < 8; ++i)
-            for (int r = 0; r < 3; ++r) {
-                B[i][r] = 0.0;
-                for (int s = 0; s < 3; ++s) B[i][r] += Ji[s][r] * dN[i][s];
-            }
-        for (int i = 0; i < 8; ++i) {
-            double kB[3];
-            for (int r = 0; r < 3; ++r) {
-                kB[r] = 0.0;
-                for (int s = 0; s < 3; ++s) kB[r] += k[3 * r + s] * B[i][s];
-            }
-            for (int j = 0; j < 8; ++j)
-                K[8 * j + i] += d * (B[j][0] * kB[0] + B[j][1] * kB[1] + B[j][2] * kB[2]);
-            w[i] += d * N[i];
-        }
+        double Kq[64], N[8], d;
+        if (orc_hex_point(x, k, q, Kq, N, &d)) return -1;
+        for (int i = 0; i < 64; ++i) K[i] += Kq[i];
+        for (int i = 0; i < 8; ++i) w[i] += d * N[i];
         *vol += d;
+    }
+    return 0;
+}
+
+/*
+ * The 2x2x2 Gauss-point matrices of Eq. 12 for conductivity evaluated at the points (Eq. 20
+ * with D(T) inside the integral): Kq [8][8][8] (point, row, column) and the shape function
+ * values Nq [8][8] (point, node).  Returns -1 when det J <= 0 at a point.
+ */
+int orc_hex_matrices_qp(const double *x, const double *k, double *Kq, double *Nq)
+{
+    for (int q = 0; q < 8; ++q) {
+        double d;
+        if (orc_hex_point(x, k, q, Kq + 64 * q, Nq + 8 * q, &d)) return -1;
     }
     return 0;
 }
@@ -290,6 +318,22 @@ typedef struct {
      * neighbouring points and held at the end values outside [tab_T[0], tab_T[n_tab - 1]] */
     int64_t n_tab;
     const double *tab_T, *tab_fk, *tab_fc;
+    /* conductivity evaluated at quadrature points (Eq. 20 with D(T) inside the integral; nq > 0
+     * replaces the element mean of the nodal factors): F_e = theta_e sum_q f_k(T_q) Kq_{e,q} T_e
+     * with T_q = sum_i Nq[q][i] T_i */
+    int64_t nq;
+    const double *Kq; /* [ne][nq][npe][npe] */
+    const double *Nq; /* [nq][npe] */
+    /* consistent integration of the surface loads of Eq. 4 and Eq. 7 over the boundary faces
+     * (nfq > 0 replaces the nodal lumping of the areas Ac, Ar):
+     *   Q_i -= h sum_j Mf_ij (T_j - T_inf) over convection faces,
+     *   Q_i -= eps sigma sum_p Wf_p Nf_pi ((T_p - T_z)^4 - (T_amb - T_z)^4) over radiation faces */
+    int64_t n_cf, n_rf;
+    int32_t nvf, nfq;
+    const int32_t *cfaces, *rfaces; /* [n][nvf] */
+    const double *Mf;               /* [n_cf][nvf][nvf] int_f N_i N_j dA */
+    const double *Wf;               /* [n_rf][nfq] quadrature weight x area Jacobian */
+    const double *Nf;               /* [nfq][nvf] shape function values at the face points */
 } orc_model;
 
 /* Value of a tabulated factor v at T: linear between the two table points around T. */
@@ -414,21 +458,80 @@ int64_t orc_precompute(int64_t nn, int64_t ne, int32_t npe, const double *xyz, c
 
 /* Eq. 11 / 20: F = sum_e F_e, F_e = theta_e f_k,e K0_e T_e with f_k,e the element mean of the
  * nodal f_k(T_i) (Section 4.2.2).  F [nn] is overwritten. */
+/* Load vector of element e (Eq. 20): Fe[i] = theta_e f_k,e (K0_e T_e)_i with the element mean
+ * f_k,e of the nodal factors (Section 4.2.2), or with nq > 0 the sum over the quadrature points
+ * theta_e sum_q f_k(T_q) (Kq T_e)_i. */
+static void orc_element_loads(const orc_model *m, int64_t e, const double *T, double *Fe)
+{
+    const int npe = m->npe;
+    const int32_t *c = m->conn + npe * e;
+    if (m->nq > 0) {
+        double acc[8] = {0};
+        for (int64_t q = 0; q < m->nq; ++q) {
+            const double *Kq = m->Kq + ((int64_t)m->nq * e + q) * npe * npe;
+            double Tq = 0.0;
+            for (int i = 0; i < npe; ++i) Tq += m->Nq[npe * q + i] * T[c[i]];
+            const double f = orc_fk(m, Tq);
+            for (int i = 0; i < npe; ++i) {
+                double kt = 0.0;
+                for (int j = 0; j < npe; ++j) kt += Kq[npe * i + j] * T[c[j]];
+                acc[i] += f * kt;
+            }
+        }
+        for (int i = 0; i < npe; ++i) Fe[i] = m->theta[e] * acc[i];
+        return;
+    }
+    const double *Ke = m->K + (int64_t)npe * npe * e;
+    double fk = 0.0;
+    for (int i = 0; i < npe; ++i) fk += orc_fk(m, T[c[i]]);
+    fk /= npe;
+    const double s = m->theta[e] * fk;
+    for (int i = 0; i < npe; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < npe; ++j) acc += Ke[npe * i + j] * T[c[j]];
+        Fe[i] = s * acc;
+    }
+}
+
 void orc_internal_loads(const orc_model *m, const double *T, double *F)
 {
     const int npe = m->npe;
     memset(F, 0, m->nn * sizeof(double));
+    double Fe[8];
     for (int64_t e = 0; e < m->ne; ++e) {
-        const int32_t *c = m->conn + npe * e;
-        const double *Ke = m->K + (int64_t)npe * npe * e;
-        double fk = 0.0;
-        for (int i = 0; i < npe; ++i) fk += orc_fk(m, T[c[i]]);
-        fk /= npe;
-        const double s = m->theta[e] * fk;
-        for (int i = 0; i < npe; ++i) {
+        orc_element_loads(m, e, T, Fe);
+        for (int i = 0; i < npe; ++i) F[m->conn[npe * e + i]] += Fe[i];
+    }
+}
+
+/* Consistent surface loads (Eq. 4 and Eq. 7 integrated with the face shape functions) of the
+ * field T at step n into Qs [nn] (overwritten): convection faces by their face mass matrices,
+ * radiation faces by the face quadrature rule with the quartic of the interpolated temperature. */
+static double orc_T_inf(const orc_model *m, int64_t n);
+void orc_surface_loads(const orc_model *m, const double *T, int64_t n, double *Qs)
+{
+    const int nv = m->nvf;
+    memset(Qs, 0, m->nn * sizeof(double));
+    const double Tinf = orc_T_inf(m, n);
+    for (int64_t f = 0; f < m->n_cf; ++f) {
+        const int32_t *v = m->cfaces + (int64_t)nv * f;
+        const double *M = m->Mf + (int64_t)nv * nv * f;
+        for (int i = 0; i < nv; ++i) {
             double acc = 0.0;
-            for (int j = 0; j < npe; ++j) acc += Ke[npe * i + j] * T[c[j]];
-            F[c[i]] += s * acc;
+            for (int j = 0; j < nv; ++j) acc += M[nv * i + j] * (T[v[j]] - Tinf);
+            Qs[v[i]] -= m->h * acc;
+        }
+    }
+    const double b = m->T_amb - m->T_zero;
+    for (int64_t f = 0; f < m->n_rf; ++f) {
+        const int32_t *v = m->rfaces + (int64_t)nv * f;
+        const double *W = m->Wf + (int64_t)m->nfq * f;
+        for (int p = 0; p < m->nfq; ++p) {
+            double Tp = 0.0;
+            for (int j = 0; j < nv; ++j) Tp += m->Nf[nv * p + j] * T[v[j]];
+            const double a = Tp - m->T_zero;
+            const double flux = ORC_SIGMA * m->eps * (a * a * a * a - b * b * b * b);
+            for (int i = 0; i < nv; ++i) Qs[v[i]] -= W[p] * m->Nf[nv * p + i] * flux;
         }
     }
 }
@@ -495,16 +598,19 @@ void orc_run(const orc_model *m, double dt, int64_t nsteps, double *T, double *e
              const int32_t *sensors, int32_t ns, int32_t sample_every, double *trace)
 {
     double *F = (double *)malloc(m->nn * sizeof(double));
+    double *Qs = m->nfq > 0 ? (double *)malloc(m->nn * sizeof(double)) : NULL;
     orc_impose_dirichlet(m, T, m->sched_step0);
     for (int64_t n = 0; n < nsteps; ++n) {
         orc_internal_loads(m, T, F);
+        if (Qs) orc_surface_loads(m, T, m->sched_step0 + n, Qs);
         double S = 0.0, B = 0.0;
         for (int64_t i = 0; i < m->nn; ++i) {
             if (m->isdir[i]) {
                 B += dt * F[i];
                 continue;
             }
-            const double Q = orc_nodal_Q_n(m, i, T[i], m->sched_step0 + n);
+            const double Q = Qs ? orc_q_scale(m, m->sched_step0 + n) * m->Qext[i] + Qs[i]
+                                : orc_nodal_Q_n(m, i, T[i], m->sched_step0 + n);
             const double Ci = m->C0[i] * orc_fc(m, T[i]);
             const double Tn = T[i] + dt / Ci * (Q - F[i]);
             S += Ci * (Tn - T[i]);
@@ -522,6 +628,7 @@ void orc_run(const orc_model *m, double dt, int64_t nsteps, double *T, double *e
         }
     }
     free(F);
+    free(Qs);
 }
 
 /*
@@ -551,7 +658,24 @@ double orc_dt_from_lambda(const orc_model *m, double lam, double T_lo, double T_
     return 2.0 / (lam * fk_max / fc_min + surf);
 }
 
+typedef void (*orc_loads_fn)(const orc_model *m, const double *T, double *F, void *aux);
+
+static void orc_loads_serial(const orc_model *m, const double *T, double *F, void *aux)
+{
+    (void)aux;
+    orc_internal_loads(m, T, F);
+}
+
+static void orc_dt_crit_with(const orc_model *m, double T_lo, double T_hi, double tol, int64_t max_iter,
+                             double *out, orc_loads_fn loads, void *aux);
+
 void orc_dt_crit(const orc_model *m, double T_lo, double T_hi, double tol, int64_t max_iter, double *out)
+{
+    orc_dt_crit_with(m, T_lo, T_hi, tol, max_iter, out, orc_loads_serial, NULL);
+}
+
+static void orc_dt_crit_with(const orc_model *m, double T_lo, double T_hi, double tol, int64_t max_iter,
+                             double *out, orc_loads_fn loads, void *aux)
 {
     const int64_t nn = m->nn;
     double *x = (double *)malloc(nn * sizeof(double));
@@ -560,6 +684,7 @@ void orc_dt_crit(const orc_model *m, double T_lo, double T_hi, double tol, int64
     orc_model lin = *m;
     lin.k_lin = 0.0;
     lin.n_tab = 0;
+    lin.nq = 0; /* K0 itself (the sum of the point matrices) */
     double nrm = 0.0;
     for (int64_t i = 0; i < nn; ++i) {
         x[i] = m->isdir[i] ? 0.0 : 1.0 + 0.5 * sin(0.7 * (double)i + 0.3);
@@ -571,7 +696,7 @@ void orc_dt_crit(const orc_model *m, double T_lo, double T_hi, double tol, int64
     int64_t it;
     for (it = 0; it < max_iter; ++it) {
         for (int64_t i = 0; i < nn; ++i) y[i] = m->isdir[i] ? 0.0 : x[i] / sqrt(m->C0[i]);
-        orc_internal_loads(&lin, y, F);
+        loads(&lin, y, F, aux);
         double rq = 0.0, yy = 0.0;
         for (int64_t i = 0; i < nn; ++i) {
             y[i] = m->isdir[i] ? 0.0 : F[i] / sqrt(m->C0[i]);
@@ -733,26 +858,16 @@ void orc_run_mt(const orc_model *m, double dt, int64_t nsteps, double *T, double
     double *Tn = (double *)malloc(nn * sizeof(double));
     double *Sn = energy ? (double *)malloc(nn * sizeof(double)) : NULL;
     double *Bn = energy ? (double *)malloc(nn * sizeof(double)) : NULL;
+    double *Qs = m->nfq > 0 ? (double *)malloc(nn * sizeof(double)) : NULL;
     orc_node_incidence(m, ptr, ent);
     orc_impose_dirichlet(m, T, m->sched_step0);
     for (int64_t n = 0; n < nsteps; ++n) {
         const int64_t step = m->sched_step0 + n;
+        if (Qs) orc_surface_loads(m, T, step, Qs);
 #pragma omp parallel num_threads(nt)
         {
 #pragma omp for schedule(static)
-            for (int64_t e = 0; e < ne; ++e) {
-                const int32_t *c = m->conn + npe * e;
-                const double *Ke = m->K + (int64_t)npe * npe * e;
-                double fk = 0.0;
-                for (int i = 0; i < npe; ++i) fk += orc_fk(m, T[c[i]]);
-                fk /= npe;
-                const double s = m->theta[e] * fk;
-                for (int i = 0; i < npe; ++i) {
-                    double acc = 0.0;
-                    for (int j = 0; j < npe; ++j) acc += Ke[npe * i + j] * T[c[j]];
-                    Fe[npe * e + i] = s * acc;
-                }
-            }
+            for (int64_t e = 0; e < ne; ++e) orc_element_loads(m, e, T, Fe + npe * e);
 #pragma omp for schedule(static)
             for (int64_t i = 0; i < nn; ++i) {
                 double F = 0.0;
@@ -765,7 +880,7 @@ void orc_run_mt(const orc_model *m, double dt, int64_t nsteps, double *T, double
                     }
                     continue;
                 }
-                const double Q = orc_nodal_Q_n(m, i, T[i], step);
+                const double Q = Qs ? orc_q_scale(m, step) * m->Qext[i] + Qs[i] : orc_nodal_Q_n(m, i, T[i], step);
                 const double Ci = m->C0[i] * orc_fc(m, T[i]);
                 const double t = T[i] + dt / Ci * (Q - F);
                 if (energy) {
@@ -797,4 +912,178 @@ void orc_run_mt(const orc_model *m, double dt, int64_t nsteps, double *T, double
     free(Tn);
     free(Sn);
     free(Bn);
+    free(Qs);
+}
+
+/* Eq. 11 / 20 over nthreads threads: element pass, then node gather in element order (bitwise
+ * orc_internal_loads).  aux: the incidence and scratch of orc_loads_mt_ctx. */
+typedef struct {
+    int64_t *ptr, *ent;
+    double *Fe;
+    int nt;
+} orc_loads_mt_ctx;
+
+static void orc_loads_mt(const orc_model *m, const double *T, double *F, void *aux)
+{
+    const orc_loads_mt_ctx *x = (const orc_loads_mt_ctx *)aux;
+    const int npe = m->npe;
+    const int64_t ne = m->ne, nn = m->nn;
+#pragma omp parallel num_threads(x->nt)
+    {
+#pragma omp for schedule(static)
+        for (int64_t e = 0; e < ne; ++e) orc_element_loads(m, e, T, x->Fe + npe * e);
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < nn; ++i) {
+            double f = 0.0;
+            for (int64_t q = x->ptr[i]; q < x->ptr[i + 1]; ++q) f += x->Fe[x->ent[q]];
+            F[i] = f;
+        }
+    }
+}
+
+/* orc_dt_crit with the internal loads over nthreads threads (bitwise the same result). */
+void orc_dt_crit_mt(const orc_model *m, double T_lo, double T_hi, double tol, int64_t max_iter, double *out,
+                    int32_t nthreads)
+{
+    orc_loads_mt_ctx x;
+#ifdef _OPENMP
+    x.nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+    x.nt = 1;
+    (void)nthreads;
+#endif
+    x.ptr = (int64_t *)malloc((m->nn + 1) * sizeof(int64_t));
+    x.ent = (int64_t *)malloc((size_t)m->ne * m->npe * sizeof(int64_t));
+    x.Fe = (double *)malloc((size_t)m->ne * m->npe * sizeof(double));
+    orc_node_incidence(m, x.ptr, x.ent);
+    orc_dt_crit_with(m, T_lo, T_hi, tol, max_iter, out, orc_loads_mt, &x);
+    free(x.ptr);
+    free(x.ent);
+    free(x.Fe);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* method variants: conductivity at quadrature points, consistent face integration            */
+/* ------------------------------------------------------------------------------------------ */
+
+/*
+ * Quadrature rule of a boundary face: quadrilaterals (bilinear, corners (-1,-1), (1,-1), (1,1),
+ * (-1,1)) by 3x3 Gauss-Legendre points (0, +-sqrt(3/5); weights 8/9, 5/9), exact for degree 5 in
+ * each coordinate; triangles by Radon's 7-point rule of degree 5 (centroid, and two orbits of
+ * three points with barycentric coordinates (a, a, 1 - 2a), a = (6 -+ sqrt 15) / 21), weights
+ * normalised to sum 1.  Nf [nfq][nv] shape values, wref [nfq] reference weights.  Returns nfq.
+ */
+int orc_face_rule(int nv, double *Nf, double *wref)
+{
+    if (nv == 4) {
+        const double g = sqrt(0.6);
+        const double pt[3] = {-g, 0.0, g}, wt[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+        static const double S[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+        int p = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b, ++p) {
+                for (int i = 0; i < 4; ++i) Nf[4 * p + i] = (1.0 + pt[a] * S[i][0]) * (1.0 + pt[b] * S[i][1]) / 4.0;
+                wref[p] = wt[a] * wt[b];
+            }
+        return 9;
+    }
+    const double r = sqrt(15.0);
+    const double a1 = (6.0 - r) / 21.0, a2 = (6.0 + r) / 21.0;
+    const double w0 = 9.0 / 40.0, w1 = (155.0 - r) / 1200.0, w2 = (155.0 + r) / 1200.0;
+    double L[7][3] = {{1.0 / 3, 1.0 / 3, 1.0 / 3},
+                      {a1, a1, 1 - 2 * a1}, {a1, 1 - 2 * a1, a1}, {1 - 2 * a1, a1, a1},
+                      {a2, a2, 1 - 2 * a2}, {a2, 1 - 2 * a2, a2}, {1 - 2 * a2, a2, a2}};
+    const double W[7] = {w0, w1, w1, w1, w2, w2, w2};
+    for (int p = 0; p < 7; ++p) {
+        for (int i = 0; i < 3; ++i) Nf[3 * p + i] = L[p][i];
+        wref[p] = W[p];
+    }
+    return 7;
+}
+
+/*
+ * Consistent face data of nf faces (node ids [nf][nv] into xyz): the face mass matrices
+ * Mf [nf][nv][nv] = int_f N_i N_j dA and the quadrature weights times the area Jacobian
+ * Wf [nf][nfq] of the rule of orc_face_rule (quadrilateral: |x_s x x_t| at the point, reference
+ * area 4; triangle: the area, weights summing to 1).
+ */
+void orc_face_consistent(int64_t nf, int32_t nv, const int32_t *faces, const double *xyz, double *Mf, double *Wf)
+{
+    double Nf[9 * 4], wref[9];
+    const int nfq = orc_face_rule(nv, Nf, wref);
+    static const double S[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+    for (int64_t f = 0; f < nf; ++f) {
+        double x[4][3];
+        for (int i = 0; i < nv; ++i)
+            for (int r = 0; r < 3; ++r) x[i][r] = xyz[3 * (int64_t)faces[nv * f + i] + r];
+        double *W = Wf + (int64_t)nfq * f;
+        if (nv == 3) {
+            double a[3], b[3];
+            for (int r = 0; r < 3; ++r) {
+                a[r] = x[1][r] - x[0][r];
+                b[r] = x[2][r] - x[0][r];
+            }
+            const double c0 = a[1] * b[2] - a[2] * b[1], c1 = a[2] * b[0] - a[0] * b[2], c2 = a[0] * b[1] - a[1] * b[0];
+            const double A = 0.5 * sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+            for (int p = 0; p < nfq; ++p) W[p] = A * wref[p];
+        } else {
+            const double g = sqrt(0.6);
+            const double pt[3] = {-g, 0.0, g};
+            int p = 0;
+            for (int ia = 0; ia < 3; ++ia)
+                for (int ib = 0; ib < 3; ++ib, ++p) {
+                    const double s = pt[ia], t = pt[ib];
+                    double xs[3] = {0, 0, 0}, xt[3] = {0, 0, 0};
+                    for (int i = 0; i < 4; ++i)
+                        for (int r = 0; r < 3; ++r) {
+                            xs[r] += x[i][r] * S[i][0] * (1.0 + t * S[i][1]) / 4.0;
+                            xt[r] += x[i][r] * (1.0 + s * S[i][0]) * S[i][1] / 4.0;
+                        }
+                    const double c0 = xs[1] * xt[2] - xs[2] * xt[1];
+                    const double c1 = xs[2] * xt[0] - xs[0] * xt[2];
+                    const double c2 = xs[0] * xt[1] - xs[1] * xt[0];
+                    W[p] = wref[p] * sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+                }
+        }
+        double *M = Mf + (int64_t)nv * nv * f;
+        for (int i = 0; i < nv; ++i)
+            for (int j = 0; j < nv; ++j) {
+                double acc = 0.0;
+                for (int p = 0; p < nfq; ++p) acc += W[p] * Nf[nv * p + i] * Nf[nv * p + j];
+                M[nv * i + j] = acc;
+            }
+    }
+}
+
+/*
+ * Quadrature-point matrices of every element for conductivity evaluated at the points:
+ * hexahedra with the 2x2x2 rule (nq = 8, orc_hex_matrices_qp), or with one_point = 1 the single
+ * centre point of Eq. 17 (nq = 1, N_i = 1/8); tetrahedra one point at the centroid (nq = 1,
+ * N_i = 1/4, the exact matrix of Eq. 18: the gradients are constant).  Kq [ne][nq][npe][npe],
+ * Nq [nq][npe].  Returns 0, or 1 + e for the first element e with det J <= 0.
+ */
+int64_t orc_precompute_qp(int64_t ne, int32_t npe, const double *xyz, const int32_t *conn, const int32_t *elem_mat,
+                          const double *mat_k0, int32_t one_point, double *Kq, double *Nq)
+{
+    double xe[8 * 3];
+    const int nq = (npe == 8 && !one_point) ? 8 : 1;
+    for (int64_t e = 0; e < ne; ++e) {
+        const int m = elem_mat ? elem_mat[e] : 0;
+        for (int i = 0; i < npe; ++i)
+            for (int r = 0; r < 3; ++r) xe[3 * i + r] = xyz[3 * (int64_t)conn[npe * e + i] + r];
+        double *K = Kq + (int64_t)nq * npe * npe * e;
+        if (npe == 8 && nq == 8) {
+            double N[64];
+            if (orc_hex_matrices_qp(xe, mat_k0 + 9 * m, K, N)) return 1 + e;
+            if (e == 0) memcpy(Nq, N, sizeof(N));
+        } else if (npe == 8) {
+            if (orc_hex_matrix_centre(xe, mat_k0 + 9 * m, K)) return 1 + e;
+            for (int i = 0; i < 8; ++i) Nq[i] = 1.0 / 8.0;
+        } else {
+            double w[4], v;
+            if (orc_tet_matrices(xe, mat_k0 + 9 * m, K, w, &v)) return 1 + e;
+            for (int i = 0; i < 4; ++i) Nq[i] = 0.25;
+        }
+    }
+    return 0;
 }

@@ -18,6 +18,10 @@ Function map (paper passages):
   OracleModel.dt_crit         Section 3.4, Eq. 29
   OracleModel.adjoint         reverse-time discrete adjoint of Eq. 16/20 (derived, no paper
                               counterpart)
+  kT_eval = 1 (problem field)  conductivity at the quadrature points: Eq. 20 with D(T) inside
+                              the integral (orc_precompute_qp, orc_element_loads)
+  face_quadrature = 1         consistent integration of Eq. 4 / 7 over the boundary faces
+                              (orc_face_rule, orc_face_consistent, orc_surface_loads)
 """
 from __future__ import annotations
 
@@ -58,7 +62,11 @@ class _Model(C.Structure):
                 ("T_amb", C.c_double), ("T_zero", C.c_double), ("T_ref", C.c_double),
                 ("q_sched", C.c_void_p), ("Tinf_sched", C.c_void_p), ("n_sched", C.c_int64),
                 ("sched_step0", C.c_int64), ("Tdir", C.c_void_p), ("Tdir_sched", C.c_void_p),
-                ("n_tab", C.c_int64), ("tab_T", C.c_void_p), ("tab_fk", C.c_void_p), ("tab_fc", C.c_void_p)]
+                ("n_tab", C.c_int64), ("tab_T", C.c_void_p), ("tab_fk", C.c_void_p), ("tab_fc", C.c_void_p),
+                ("nq", C.c_int64), ("Kq", C.c_void_p), ("Nq", C.c_void_p),
+                ("n_cf", C.c_int64), ("n_rf", C.c_int64), ("nvf", C.c_int32), ("nfq", C.c_int32),
+                ("cfaces", C.c_void_p), ("rfaces", C.c_void_p), ("Mf", C.c_void_p), ("Wf", C.c_void_p),
+                ("Nf", C.c_void_p)]
 
 
 def lib():
@@ -82,9 +90,16 @@ def lib():
             L.orc_run.argtypes = [P, C.c_double, C.c_int64, P, P, P, C.c_int32, C.c_int32, P]
             L.orc_run_mt.argtypes = [P, C.c_double, C.c_int64, P, P, P, C.c_int32, C.c_int32, P, C.c_int32]
             L.orc_dt_crit.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_int64, P]
+            L.orc_dt_crit_mt.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_int64, P, C.c_int32]
             L.orc_dt_from_lambda.argtypes = [P, C.c_double, C.c_double, C.c_double]
             L.orc_dt_from_lambda.restype = C.c_double
             L.orc_adjoint.argtypes = [P, C.c_double, C.c_int64, P, P, C.c_int32, C.c_int32, P, P, P]
+            L.orc_hex_matrices_qp.argtypes = [P, P, P, P]
+            L.orc_face_rule.argtypes = [C.c_int, P, P]
+            L.orc_face_consistent.argtypes = [C.c_int64, C.c_int32, P, P, P, P]
+            L.orc_precompute_qp.argtypes = [C.c_int64, C.c_int32, P, P, P, P, C.c_int32, P, P]
+            L.orc_precompute_qp.restype = C.c_int64
+            L.orc_surface_loads.argtypes = [P, P, C.c_int64, P]
             _lib = L
     return _lib
 
@@ -139,6 +154,32 @@ def tet_matrices(x, k):
 def face_area(x):
     x = _f64(x)
     return lib().orc_face_area(_p(x), int(x.shape[0]))
+
+
+def hex_matrices_qp(x, k):
+    """(Kq [8,8,8], Nq [8,8]): the 2x2x2 Gauss-point matrices det J B^T k B and shape values."""
+    x, k = _f64(x), _f64(k)
+    Kq, Nq = np.zeros((8, 8, 8)), np.zeros((8, 8))
+    if lib().orc_hex_matrices_qp(_p(x), _p(k), _p(Kq), _p(Nq)):
+        raise ValueError("det J <= 0")
+    return Kq, Nq
+
+
+def face_rule(nv):
+    """(Nf [nfq, nv], reference weights [nfq]) of the consistent face quadrature."""
+    Nf, w = np.zeros(9 * 4), np.zeros(9)
+    nfq = lib().orc_face_rule(int(nv), _p(Nf), _p(w))
+    return Nf[:nfq * nv].reshape(nfq, nv).copy(), w[:nfq].copy()
+
+
+def face_consistent(faces, xyz):
+    """(Mf [n, nv, nv] face mass matrices, Wf [n, nfq] weights x area Jacobian)."""
+    faces, xyz = _i32(faces), _f64(xyz)
+    n, nv = faces.shape
+    nfq = face_rule(nv)[0].shape[0]
+    Mf, Wf = np.zeros((n, nv, nv)), np.zeros((n, nfq))
+    lib().orc_face_consistent(n, nv, _p(faces), _p(xyz), _p(Mf), _p(Wf))
+    return Mf, Wf
 
 
 class OracleModel:
@@ -203,6 +244,31 @@ class OracleModel:
                         T_zero=float(p.T_zero), T_ref=float(getattr(mats[0], "T_ref", 0.0)),
                         Tdir=_p(self.Tdir))
         self.mref = C.byref(self.m)
+        self.variants = (int(getattr(p, "kT_eval", 0)), int(getattr(p, "face_quadrature", 0)))
+        if self.variants[0] == 1:
+            # conductivity at the quadrature points (Eq. 20 with D(T) inside the integral)
+            one = 1 if (npe == 8 and getattr(p, "quadrature", 8) == 1) else 0
+            nq = 8 if (npe == 8 and not one) else 1
+            self.Kq = np.zeros((ne, nq, npe, npe))
+            self.Nq = np.zeros((nq, npe))
+            rc = L.orc_precompute_qp(ne, npe, _p(self.xyz), _p(self.conn), _p(self.elem_mat), _p(self.mat_k0), one,
+                                     _p(self.Kq), _p(self.Nq))
+            if rc:
+                raise ValueError(f"element {rc - 1} has det J <= 0")
+            self.m.nq, self.m.Kq, self.m.Nq = nq, _p(self.Kq), _p(self.Nq)
+        if self.variants[1] == 1:
+            # consistent integration of the surface loads over the boundary faces
+            nv = conv.shape[1] if conv is not None else (rad.shape[1] if rad is not None else (4 if npe == 8 else 3))
+            self.Nf, _ = face_rule(nv)
+            self.Nf = np.ascontiguousarray(self.Nf)
+            z = np.zeros((0, nv), np.int32)
+            self.cf = conv if conv is not None else z
+            self.rf = rad if rad is not None else z
+            self.Mf, _ = face_consistent(self.cf, self.xyz)
+            _, self.Wf = face_consistent(self.rf, self.xyz)
+            self.m.n_cf, self.m.n_rf, self.m.nvf, self.m.nfq = len(self.cf), len(self.rf), nv, self.Nf.shape[0]
+            self.m.cfaces, self.m.rfaces = _p(self.cf), _p(self.rf)
+            self.m.Mf, self.m.Wf, self.m.Nf = _p(self.Mf), _p(self.Wf), _p(self.Nf)
         if getattr(p, "table_T", None) is not None:
             self.set_table(p.table_T, p.table_fk, p.table_fc)
         self._sched = (None, None, None)
@@ -254,6 +320,11 @@ class OracleModel:
     def nodal_Q(self, T):
         T = _f64(T)
         L = lib()
+        if self.variants[1] == 1:
+            Qs = np.zeros(len(T))
+            L.orc_surface_loads(self.mref, _p(T), int(self.m.sched_step0), _p(Qs))
+            q = 1.0 if self._sched[0] is None else self._sched[0][min(int(self.m.sched_step0), len(self._sched[0]) - 1)]
+            return q * self.Qext + Qs
         return np.array([L.orc_nodal_Q(self.mref, i, float(T[i])) for i in range(len(T))])
 
     def run(self, T, dt, nsteps, energy=False, sensors=None, sample_every=0, step0=0, threads=1):
@@ -281,12 +352,17 @@ class OracleModel:
             out.append(trace)
         return out[0] if len(out) == 1 else tuple(out)
 
-    def dt_crit(self, T_lo=None, T_hi=None, tol=1e-12, max_iter=200000):
-        """(dt_crit, lambda_cond, iterations) of Section 3.4."""
+    def dt_crit(self, T_lo=None, T_hi=None, tol=1e-12, max_iter=200000, threads=1):
+        """(dt_crit, lambda_cond, iterations) of Section 3.4 (threads != 1: the same power
+        iteration with the internal loads over several threads, bitwise the same result)."""
         T_lo = self.p.T_lo if T_lo is None else T_lo
         T_hi = self.p.T_hi if T_hi is None else T_hi
         out = np.zeros(3)
-        lib().orc_dt_crit(self.mref, float(T_lo), float(T_hi), float(tol), int(max_iter), _p(out))
+        if threads == 1:
+            lib().orc_dt_crit(self.mref, float(T_lo), float(T_hi), float(tol), int(max_iter), _p(out))
+        else:
+            lib().orc_dt_crit_mt(self.mref, float(T_lo), float(T_hi), float(tol), int(max_iter), _p(out),
+                                 int(threads if threads > 0 else host_threads()))
         return float(out[0]), float(out[1]), int(out[2])
 
     def dt_from_lambda(self, lam, T_lo, T_hi):
@@ -309,6 +385,8 @@ class OracleModel:
 
     def adjoint(self, dt, nsteps, T0, sensors, sample_every, dLdtrace):
         """(dL/dtheta [E], dL/dsource [E]) for a loss of the sensor trace."""
+        if self.variants != (0, 0):
+            raise ValueError("the adjoint covers the element-mean conductivity and lumped surface loads only")
         self.m.sched_step0 = 0
         T0 = _f64(T0)
         sens = _i32(sensors)

@@ -189,3 +189,63 @@ def hex_shape_integrals_exact(x):
         return f
     w = [integ(sp.expand(Ni * dj)) for Ni in N]
     return np.array([float(v) for v in w]), float(integ(dj))
+
+
+def hex_load_exact_qp(x, k, T, fk, order=3):
+    """F_i = int_Ve grad N_i . k fk(T(x)) grad T dV on a trilinear hexahedron (VTK order) for the
+    nodal field T, by 3x3x3 Gauss-Legendre points with shape functions written as products of
+    1-D linear functions: exact on rectangular bricks when fk is linear (the integrand then has
+    degree <= 3 per coordinate).  fk: callable of the temperature; order: Gauss points per
+    direction (order = 2 applies the 2x2x2 rule itself, for distorted elements)."""
+    x = np.asarray(x, float)
+    T = np.asarray(T, float)
+    k = np.asarray(k, float)
+    g, gw = np.polynomial.legendre.leggauss(order)
+    sgn = 2.0 * VTK_CORNERS - 1.0
+    F = np.zeros(8)
+    for a, wa in zip(g, gw):
+        for b, wb in zip(g, gw):
+            for c, wc in zip(g, gw):
+                p = np.array([a, b, c])
+                lin = 0.5 * (1.0 + sgn * p)
+                N = np.prod(lin, axis=1)
+                dN = np.empty((8, 3))
+                for d in range(3):
+                    o = [q for q in range(3) if q != d]
+                    dN[:, d] = 0.5 * sgn[:, d] * lin[:, o[0]] * lin[:, o[1]]
+                J = x.T @ dN
+                B = dN @ np.linalg.inv(J)          # [8, 3] physical gradients
+                gradT = B.T @ T
+                F += wa * wb * wc * np.linalg.det(J) * fk(N @ T) * (B @ (k @ gradT))
+    return F
+
+
+def bar_lateral_convection(nx, h, w, dt, nsteps, T0, Ts, k, rho, c0, hc, Tinf, consistent):
+    """Forward-Euler recurrence of a bar of nx bricks (h along x, cross-section w x w), T = Ts
+    held at x = 0, convection hc (T - Tinf) on the four lateral faces, for fields constant over
+    each cross-section.  Per node (lumped brick mass rho c0 w^2 h / 4 inside, half at the end):
+      conduction  k w^2 / (4 h) (T_{j-1} - 2 T_j + T_{j+1})
+      lumped      -hc w h T'_j                        (T' = T - Tinf; area share w h / 4 per face)
+      consistent  -(hc w h / 6)(T'_{j-1} + 4 T'_j + T'_{j+1}), end node -(hc w h / 6)(2 T'_n + T'_{n-1})
+    from the bilinear face mass matrix (w h / 36)[4 2 1 2; 2 4 2 1; 1 2 4 2; 2 1 2 4]."""
+    T = np.full(nx + 1, float(T0))
+    T[0] = Ts
+    m_in = rho * c0 * w * w * h / 4.0
+    for _ in range(nsteps):
+        Tp = T - Tinf
+        cond = np.zeros(nx + 1)
+        cond[1:-1] = k * w * w / (4.0 * h) * (T[:-2] - 2.0 * T[1:-1] + T[2:])
+        cond[-1] = k * w * w / (4.0 * h) * (T[-2] - T[-1])
+        if consistent:
+            conv = np.zeros(nx + 1)
+            conv[1:-1] = -(hc * w * h / 6.0) * (Tp[:-2] + 4.0 * Tp[1:-1] + Tp[2:])
+            conv[-1] = -(hc * w * h / 6.0) * (2.0 * Tp[-1] + Tp[-2])
+        else:
+            conv = -hc * w * h * Tp
+            conv[-1] = -hc * w * h / 2.0 * Tp[-1]
+        m = np.full(nx + 1, m_in)
+        m[-1] = m_in / 2.0
+        Tn = T + dt * (cond + conv) / m
+        Tn[0] = Ts
+        T = Tn
+    return T

@@ -745,3 +745,160 @@ def test_threaded_run_is_bitwise_the_serial_run(case):
                   threads=threads)
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+
+
+def test_threaded_power_iteration_is_bitwise_the_serial_one():
+    """The critical-step power iteration with the internal loads over several threads gives the
+    serial result bitwise (dt_crit, lambda and the iteration count)."""
+    for p in (fi.nonlinear_cube(7, "hex", jitter=0.2), fi.nonlinear_cube(5, "tet"), fi.plain_cube(6)):
+        m = O.OracleModel(p)
+        a = m.dt_crit(tol=1e-9, max_iter=3000)
+        for threads in (3, 0):
+            assert m.dt_crit(tol=1e-9, max_iter=3000, threads=threads) == a
+
+
+# ------------------------------------------- method variants: quadrature-point k(T), faces --
+
+def test_quadrature_point_conductivity_on_bricks_is_the_exact_integral():
+    """Eq. 20 with D(T) inside the integral: on a rectangular brick with a linear law the 2x2x2
+    Gauss-point loads equal the exact integral of grad N_i . k0 f_k(T(x)) grad T (independent
+    3x3x3 integration), and differ from the element-mean reading of Section 4.2.2."""
+    rng = np.random.default_rng(31)
+    for _ in range(3):
+        dims = rng.uniform(0.3, 1.5, 3)
+        x = brute.VTK_CORNERS * dims + rng.uniform(-1, 1, 3)
+        k = _rand_spd(rng)
+        T = rng.uniform(10, 300, 8)
+        a = 0.004
+        Kq, Nq = O.hex_matrices_qp(x, k)
+        F = sum((1 + a * (Nq[q] @ T)) * (Kq[q] @ T) for q in range(8))
+        Fe = brute.hex_load_exact_qp(x, k, T, lambda t: 1 + a * t)
+        assert np.max(np.abs(F - Fe)) <= 1e-13 * np.max(np.abs(Fe))
+        K, _, _ = O.hex_matrices(x, k)
+        assert np.max(np.abs(np.mean(1 + a * T) * (K @ T) - Fe)) > 1e-3 * np.max(np.abs(Fe))
+        assert np.max(np.abs(Kq.sum(axis=0) - K)) <= 1e-14 * np.max(np.abs(K))
+
+
+def test_quadrature_point_conductivity_assembly(patch_nodes):
+    """The oracle's internal loads with kT_eval = 1 on the distorted patch and a jittered cube
+    against a dense assembly of independently integrated element loads (the same 2x2x2 rule,
+    numpy shape functions), with a property table; a constant field carries no load; for linear
+    tetrahedra the single centroid point gives the element mean of a linear law."""
+    k = _rand_spd(np.random.default_rng(5))
+    tT, tk = np.array([20.0, 90.0, 150.0, 260.0]), np.array([1.0, 2.2, 0.7, 1.5])
+    fk = lambda t: np.interp(t, tT, tk)
+    for p in (fi.patch_problem(patch_nodes, "hex", k0=k), fi.nonlinear_cube(3, "hex", jitter=0.25)):
+        p.kT_eval = 1
+        p.table_T, p.table_fk, p.table_fc = tT, tk, np.ones(4)
+        theta = np.random.default_rng(8).uniform(0.5, 2.0, p.n_elems)
+        p.elem_kscale = theta
+        m = O.OracleModel(p)
+        T = np.random.default_rng(9).uniform(0, 300, p.n_nodes)
+        ref = np.zeros(p.n_nodes)
+        for e, c in enumerate(p.conn):
+            k0 = np.asarray(p.mats[0].k0, float)
+            ref[c] += theta[e] * brute.hex_load_exact_qp(p.xyz[c], k0, T[c], fk, order=2)
+        got = m.internal_loads(T)
+        assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+        assert np.max(np.abs(m.internal_loads(np.full(p.n_nodes, 42.0)))) <= 1e-12 * 42.0 * np.max(np.abs(m.K))
+    q = fi.nonlinear_cube(4, "tet", jitter=0.2)
+    a = O.OracleModel(q).run(q.initial_T(), 50.0, 60)
+    q.kT_eval = 1
+    b = O.OracleModel(q).run(q.initial_T(), 50.0, 60)
+    assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(a))
+
+
+def test_quadrature_point_conductivity_bar_reduces_to_1d():
+    """A bar of bricks with a field constant over each cross-section: with the conductivity at
+    the 2x2x2 points, the element factor of the 1-D recurrence is the mean of f_k at the two
+    Gauss abscissae along the bar (T_L + (T_R - T_L)(1 -+ 1/sqrt 3)/2), here a property table."""
+    nx, T0, Ts = 12, 20.0, 400.0
+    tT, tk, tc = np.array([0.0, 100.0, 250.0, 450.0]), np.array([1.0, 1.6, 1.2, 2.5]), np.array([1.0, 0.8, 1.4, 1.1])
+    p = fi.slab(nx, 1, 1, Lx=1.0, k=(3.0, 3.0, 3.0), rho=2.0, c0=5.0, T0=T0, T_s=Ts)
+    p.table_T, p.table_fk, p.table_fc = tT, tk, tc
+    p.kT_eval = 1
+    m = O.OracleModel(p)
+    h = 1.0 / nx
+    dt = 0.2 * 2.0 * 5.0 * h * h / (3.0 * 2.5)
+    got = m.run(p.initial_T(), dt, 300)
+    g = 1.0 / np.sqrt(3.0)
+    T = np.full(nx + 1, T0)
+    T[0] = Ts
+    for _ in range(300):
+        TL, TR = T[:-1], T[1:]
+        f = 0.5 * (np.interp(TL + (TR - TL) * (1 - g) / 2, tT, tk) + np.interp(TL + (TR - TL) * (1 + g) / 2, tT, tk))
+        c = 5.0 * np.interp(T, tT, tc)
+        Tn = T.copy()
+        Tn[1:-1] = T[1:-1] + dt * 3.0 / (2.0 * c[1:-1] * h * h) * (f[1:] * (T[2:] - T[1:-1]) + f[:-1] * (T[:-2] - T[1:-1]))
+        Tn[-1] = T[-1] + 2.0 * dt * 3.0 / (2.0 * c[-1] * h * h) * f[-1] * (T[-2] - T[-1])
+        T = Tn
+    x = np.round(p.xyz[:, 0] / h).astype(int)
+    assert np.max(np.abs(got - T[x])) <= 1e-12 * Ts
+
+
+def test_consistent_face_matrices_closed_forms():
+    """Face mass matrices of the consistent surface integration: a rectangle a x b,
+    (ab/36)[4 2 1 2; 2 4 2 1; 1 2 4 2; 2 1 2 4], a triangle of area A, (A/12)[2 1 1; 1 2 1;
+    1 1 2]; the radiation weights sum to the area; on a rectangle with a bilinear field the
+    quadrature of N_i ((T - T_z)^4 - (T_a - T_z)^4) equals a 10x10 Gauss-Legendre integral."""
+    a, b = 0.7, 1.9
+    rect = np.array([[0, 0, 0], [a, 0, 0], [a, b, 0], [0, b, 0]], float)
+    Mf, Wf = O.face_consistent(np.array([[0, 1, 2, 3]]), rect)
+    ref = a * b / 36.0 * np.array([[4, 2, 1, 2], [2, 4, 2, 1], [1, 2, 4, 2], [2, 1, 2, 4]])
+    assert np.max(np.abs(Mf[0] - ref)) <= 1e-15 * 4
+    assert Wf[0].sum() == pytest.approx(a * b, rel=1e-14)
+    tri = np.array([[0.1, 0.2, 0.3], [1.4, 0.1, 0.5], [0.4, 1.3, 0.9]])
+    Mt, Wt = O.face_consistent(np.array([[0, 1, 2]]), tri)
+    A = 0.5 * np.linalg.norm(np.cross(tri[1] - tri[0], tri[2] - tri[0]))
+    assert np.max(np.abs(Mt[0] - A / 12.0 * (np.ones((3, 3)) + np.eye(3)))) <= 1e-15 * A
+    assert Wt[0].sum() == pytest.approx(A, rel=1e-14)
+    # radiation quadrature vs brute force on the rectangle
+    Tn = np.array([300.0, 520.0, 610.0, 410.0])
+    Tz, Ta = -273.15, 20.0
+    Nf, _ = O.face_rule(4)
+    Tp = Nf @ Tn
+    got = (Wf[0][:, None] * Nf * ((Tp - Tz) ** 4 - (Ta - Tz) ** 4)[:, None]).sum(axis=0)
+    g, gw = np.polynomial.legendre.leggauss(10)
+    S = np.array([[-1, -1], [1, -1], [1, 1], [-1, 1]], float)
+    want = np.zeros(4)
+    for s, ws in zip(g, gw):
+        for t, wt in zip(g, gw):
+            N = (1 + s * S[:, 0]) * (1 + t * S[:, 1]) / 4
+            T = N @ Tn
+            want += ws * wt * (a * b / 4) * N * ((T - Tz) ** 4 - (Ta - Tz) ** 4)
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("consistent", [False, True])
+def test_face_integration_bar_with_lateral_convection(consistent):
+    """A bar with convection on its four lateral faces and T held at x = 0: lumped (nodal
+    quadrature) and consistent face integration against their exact 1-D recurrences."""
+    nx, w, T0, Ts, hc, Tinf = 10, 0.1, 20.0, 300.0, 40.0, 5.0
+    p = fi.slab(nx, 1, 1, Lx=1.0, k=(2.0, 2.0, 2.0), rho=3.0, c0=4.0, T0=T0, T_s=Ts)
+    h = 1.0 / nx
+    # cross-section w x w instead of h x h
+    p.xyz = p.xyz * np.array([1.0, w / h, w / h])
+    bf = fi.boundary_faces(p.conn)
+    p.conv_faces = np.concatenate([fi.faces_on_side(p.xyz, bf, sd) for sd in ("y0", "y1", "z0", "z1")])
+    p.h, p.T_inf = hc, Tinf
+    p.face_quadrature = 1 if consistent else 0
+    m = O.OracleModel(p)
+    dt = 0.5 * m.dt_crit(T_lo=0.0, T_hi=Ts)[0]
+    got = m.run(p.initial_T(), dt, 400)
+    ref = brute.bar_lateral_convection(nx, h, w, dt, 400, T0, Ts, 2.0, 3.0, 4.0, hc, Tinf, consistent)
+    x = np.round(p.xyz[:, 0] / h).astype(int)
+    assert np.max(np.abs(got - ref[x])) <= 1e-12 * Ts
+    other = brute.bar_lateral_convection(nx, h, w, dt, 400, T0, Ts, 2.0, 3.0, 4.0, hc, Tinf, not consistent)
+    assert np.max(np.abs(got - other[x])) > 1e-6 * Ts
+
+
+def test_consistent_faces_keep_the_energy_balance():
+    """With consistent face integration (convection and radiation) the per-step energy terms
+    still balance: stored heat change = dt (sum of free-node loads + Dirichlet reactions)."""
+    p = fi.nonlinear_cube(5, "hex", jitter=0.2)
+    p.face_quadrature = 1
+    p.kT_eval = 1
+    m = O.OracleModel(p)
+    dt = 0.9 * m.dt_crit()[0]
+    _, E = m.run(p.initial_T(), dt, 200, energy=True)
+    assert np.max(np.abs(E[:, 0] - E[:, 1])) <= 1e-12 * np.max(np.abs(E))
