@@ -42,9 +42,50 @@ NODE_BYTES_FP64 = 16 + 8 + 8
 TET_BYTES_FP32 = 6 * 4 + 4 * 4
 TET_BYTES_FP64 = 6 * 8 + 4 * 4
 L2_BYTES = 129e6
-# time step of the oracle samples on the 128^3 cube (below its critical step, 0.65 s, so the
-# timed arithmetic stays on finite values)
-ORACLE_DT = 0.5
+# the benchmark workload (both arms)
+WORKLOAD = ("large_hex_128: 128^3 hex nonlinear cube (orthotropic k(T), c(T), conv+rad on all faces, "
+            "central source), FP32 + Kahan")
+L2_NOTE = "inputs larger than L2 (element stream > 129 MB), no flush"
+
+
+def round_dt(dt):
+    """The time step both arms use: 0.9 dt_crit rounded to 3 significant digits (the GPU's
+    Lanczos and the oracle's power iteration agree far below that rounding)."""
+    return float(f"{dt:.3g}")
+
+
+def workload_config(p, dt, n=128):
+    """The config dict of the JSON line, the same in both arms."""
+    wl = WORKLOAD if n == 128 else WORKLOAD.replace("128", str(n))
+    return {"workload": wl, "elements": int(p.n_elems), "nodes": int(p.n_nodes), "dt": dt, "l2": L2_NOTE,
+            "parallelism": "single device (replicas with --gpus N)"}
+
+
+def host_info():
+    """Host cores this process may use and the CPU model."""
+    from oracle import oracle as O
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": O.host_threads(), "cpu_model": model}
+
+
+def oracle_dt(p, threads=0):
+    """0.9 dt_crit of problem p from the oracle's power iteration (internal loads over the host
+    cores), rounded as the GPU arm rounds its own."""
+    from oracle import oracle as O
+    m = O.OracleModel(p)
+    dtc, _, _ = m.dt_crit(tol=1e-7, max_iter=600, threads=threads)
+    return m, round_dt(0.9 * dtc)
 
 # The paper's own timings (Section 4.3): C++ on one thread of an Intel i7-6700 @ 3.40 GHz,
 # 0.1 m cube with 40,021 tets / 7,872 nodes, dt = 0.005 s, 2000 steps
@@ -58,6 +99,80 @@ def peaks():
             d = json.load(fh)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read through NVML (libnvidia-ml, read-only queries) by a
+    thread polling every `period_s` while the timed region runs, so that even a region of a
+    millisecond or two gets samples."""
+
+    # clock-event reason bits of nvmlDeviceGetCurrentClocksEventReasons
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, index, period_s=0.0002):
+        import ctypes as C
+        self.C = C
+        self.period = period_s
+        self.rows = []
+        self.stop_flag = False
+        self.thread = None
+        self.nv = C.CDLL("libnvidia-ml.so.1")
+        if self.nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = C.c_void_p()
+        bus = None
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(index)
+            bus = "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        except Exception:
+            bus = None
+        rc = self.nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), C.byref(self.h)) if bus else 1
+        if rc != 0 and self.nv.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        mx = C.c_uint()
+        self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, C.byref(mx))  # NVML_CLOCK_SM = 1
+        self.max_mhz = float(mx.value)
+        fn = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = fn if fn is not None else self.nv.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        C = self.C
+        clk, rs = C.c_uint(), C.c_ulonglong()
+        if self.nv.nvmlDeviceGetClockInfo(self.h, 1, C.byref(clk)) == 0 and self.reasons_fn(self.h, C.byref(rs)) == 0:
+            self.rows.append((float(clk.value), int(rs.value)))
+
+    def _loop(self):
+        while not self.stop_flag:
+            self.sample()
+            time.sleep(self.period)
+
+    def start(self):
+        self.sample()
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.stop_flag = True
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        self.sample()
+        try:
+            self.nv.nvmlShutdown()
+        except Exception:
+            pass
+        sm = [r[0] for r in self.rows]
+        reasons = sorted({nm for _, bits in self.rows for b, nm in self.REASONS.items() if bits & b})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(sm), "source": "nvml"}
+
+
+def clock_sampler(index):
+    """NVML sampler when libnvidia-ml is available, else nvidia-smi."""
+    try:
+        return NvmlClockSampler(index)
+    except Exception:
+        return ClockSampler(index)
 
 
 class ClockSampler:
@@ -109,7 +224,7 @@ class ClockSampler:
             except Exception:
                 continue
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi"}
 
 
 def traffic_from_profile(kernel_src_hash):
@@ -187,9 +302,70 @@ def time_workload(p, precision, steps, stream, peak, dt=None, warm=20):
             "grid": info["grid"], "block": info["block"], "finite": bool(np.all(np.isfinite(T)))}
 
 
-def extra_workloads(stream, peak):
+def plan_sweep(p, dt, stream, steps=512):
+    """Throughput of the 128^3 step over launch plans: CTA size (consumer threads + the producer
+    warp) 128 / 256 / 512, steps per launch 1 / 8 / 64 / 512, colour scatter and the atomic
+    variant (device-resident, CUDA events around `steps` steps after a warm-up)."""
+    import torch
+    from paper_1909_03355_gb300.fedfem import FedFem
+    rows = []
+    for block in (96, 224, 480):
+        for scatter in (0, 1):
+            for spl in (1, 8, 64, 512):
+                row = {"cta_threads": block + 32, "steps_per_launch": spl,
+                       "scatter": "atomic" if scatter else "colour"}
+                try:
+                    f = FedFem(p, precision=32, stream=stream, block=block, steps_per_launch=spl, scatter=scatter)
+                    f.precompute()
+                    f.set_dt(dt)
+                    f.set_T(p.initial_T())
+                    f.step(max(spl, 16))
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    with torch.cuda.stream(stream):
+                        e0.record(stream)
+                        f.step_async(steps)
+                        e1.record(stream)
+                    f.sync()
+                    us = 1e3 * e0.elapsed_time(e1) / steps
+                    info = f.info()
+                    f.close()
+                    row.update({"us_per_step": us, "value": p.n_elems / (us * 1e-6), "grid": info["grid"],
+                                "stages": info["stages"]})
+                except Exception as e:  # a plan that does not fit is reported, not timed
+                    row["error"] = str(e)[:200]
+                rows.append(row)
+    return {"workload": "large_hex_128", "steps": steps, "rows": rows}
+
+
+def dd_workload(stream, n_subs=(2, 4), steps=20):
+    """The 128^3 cube as slab sub-domains on one device (one launch per sub-domain and step, then
+    the halo exchange): wall time per step and the halo bytes a multi-GPU run would send."""
+    import fedfem_inputs as fi
+    from paper_1909_03355_gb300.dd import FedFemDD
+    p = fi.large_cube(128)
+    out = {"workload": "large_hex_128 decomposed", "note": "all sub-domains on one GPU (emulation of the exchange); "
+           "multi-GPU scaling is unmeasured on hardware", "rows": []}
+    for k in n_subs:
+        d = FedFemDD(p, k, precision=32, stream=stream)
+        dtc = d.precompute()
+        d.set_dt(round_dt(0.9 * dtc))
+        d.set_T(p.initial_T())
+        d.step(3)
+        t0 = time.perf_counter()
+        d.step(steps)
+        el = time.perf_counter() - t0
+        info = d.info()
+        d.close()
+        out["rows"].append({"n_sub": k, "ms_per_step": 1e3 * el / steps, "value": p.n_elems * steps / el,
+                            "halo_bytes_per_step": info["halo_bytes_per_step"], "messages": info["n_messages"],
+                            "ghost_elements": info["ghost_elements"], "dt_crit": dtc})
+    return out
+
+
+def extra_workloads(stream, peak, own=None):
     """The paper-shaped cube, the 64^3 nonlinear hex and tet cubes, a long slab and the
-    jittered 128^3 cube, each in FP32 + Kahan and (where stated) FP64."""
+    jittered 128^3 cube, each in FP32 + Kahan and (where stated) FP64; the L2-resident ones also
+    against the L2 copy bandwidth of own_peaks."""
     import fedfem_inputs as fi
     from oracle import oracle as O
     out = {}
@@ -241,6 +417,15 @@ def extra_workloads(stream, peak):
     out["large_hex_128_jitter"] = {"elements": jc.n_elems, "nodes": jc.n_nodes,
                                    "note": "interior nodes jittered by +-0.2 h (seeded): every element differs",
                                    "gpu_fp32": time_workload(jc, 32, 2000, stream, peak)}
+    l2 = (own or {}).get("l2_copy_GBps")
+    if l2:
+        for key, rec in out.items():
+            for leg in ("gpu_fp32", "gpu_fp64", "gpu_fp32_temperature_dependent", "gpu_fp32_temperature_dependent_table"):
+                r = rec.get(leg) if isinstance(rec, dict) else None
+                if isinstance(r, dict) and r.get("working_set") == "L2-resident":
+                    r["l2_frac"] = r["achieved_GBps"] / l2
+                    r["l2_peak_GBps"] = l2
+    out["domain_decomposition_128"] = dd_workload(stream)
     return out
 
 
@@ -279,50 +464,87 @@ def whole_job_rate(units_per_rank, world, seconds):
 
 
 def run_reference(args, world, rank):
-    """FP64 CPU oracle timed on the host cores (the reference arm)."""
+    """FP64 CPU oracle timed on the host cores (the reference arm): the same workload, time step,
+    warm-up and step count as the GPU arm, the oracle's time stepping over all host cores."""
     if rank != 0:
         return
     import fedfem_inputs as fi
-    from oracle import oracle as O
     n = 128
     p = fi.large_cube(n)
-    m = O.OracleModel(p)
+    m, dt = oracle_dt(p)
+    hi = host_info()
     T = p.initial_T()
-    dt = ORACLE_DT
-    steps = max(1, min(args.steps, 100))
-    warm = max(0, min(args.warmup, 3))
-    T = m.run(T, dt, warm)
+    steps = max(1, min(args.steps, 2000))
+    warm = max(0, min(args.warmup, 200))
+    T = m.run(T, dt, warm, threads=0)
     t0 = time.perf_counter()
-    T = m.run(T, dt, steps)
+    T = m.run(T, dt, steps, threads=0)
     el = time.perf_counter() - t0
     v = p.n_elems * steps / el
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": steps, "warmup": warm,
             "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"large_hex_{n}: {n}^3 hex nonlinear cube (bounded sample: {steps} steps)",
-                       "elements": p.n_elems, "nodes": p.n_nodes, "dt": dt},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{steps} explicit steps of the {n}^3 hex problem (dt = {dt} s < dt_crit), "
-                                       "single-threaded FP64 C oracle"},
+            "config": workload_config(p, dt, n),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": hi["nproc"], "kind": "oracle",
+                             "cpu_model": hi["cpu_model"],
+                             "sample": f"{steps} explicit steps of the {n}^3 hex problem after {warm} warm-up steps, "
+                                       f"FP64 C oracle over {hi['nproc']} host threads (element pass, node gather)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_sample():
-    """Oracle element-steps/s on a bounded sample: 100 steps of the 128^3 problem (~10-30 s)."""
+def cpu_baseline_sample(dt):
+    """Oracle element-steps/s on bounded samples of the 128^3 problem: over all host cores (300
+    steps, the reported value) and single-threaded as in the paper (40 steps)."""
     import fedfem_inputs as fi
     from oracle import oracle as O
     p = fi.large_cube(128)
     m = O.OracleModel(p)
+    hi = host_info()
     T = p.initial_T()
-    dt = ORACLE_DT
-    steps = 100
-    t0 = time.perf_counter()
-    m.run(T, dt, steps)
-    el = time.perf_counter() - t0
-    return {"value": p.n_elems * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} explicit steps of the 128^3 hex problem (dt = {dt} s < dt_crit), "
-                      "single-threaded FP64 C oracle"}
+    out = {}
+    for threads, steps in ((0, 300), (1, 40)):
+        t0 = time.perf_counter()
+        m.run(T, dt, steps, threads=threads)
+        el = time.perf_counter() - t0
+        out[threads] = (p.n_elems * steps / el, steps)
+    v, steps = out[0]
+    v1, steps1 = out[1]
+    return {"value": v, "unit": UNIT, "cores": hi["nproc"], "kind": "oracle", "cpu_model": hi["cpu_model"],
+            "sample": f"{steps} explicit steps of the 128^3 hex problem (dt = {dt} s), FP64 C oracle over "
+                      f"{hi['nproc']} host threads",
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": f"{steps1} steps of the same problem, single-threaded (the paper's mode)"}}
+
+
+def own_peaks(stream):
+    """Roofline denominators measured with the library's own kernels: copy bandwidth of a working
+    set held in L2 (two 24 MB buffers), of one streaming from HBM (two 2 GB buffers), and the FP64
+    fused-multiply-add rate."""
+    import ctypes as C
+    import torch
+    from paper_1909_03355_gb300 import capi
+    L = capi.load()
+    h = int(stream.cuda_stream)
+    out = {}
+    for name, nbytes, reps in (("l2", 24 << 20, 200), ("hbm", 2 << 30, 5)):
+        a = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+        b = torch.empty_like(a)
+        a.fill_(1.0)
+        best = 0.0
+        for bps in (2, 4):
+            ms = C.c_double()
+            if L.fedfem_probe_copy(b.data_ptr(), a.data_ptr(), nbytes, reps, bps, h, C.byref(ms)) == 0:
+                best = max(best, 2.0 * nbytes * reps / (ms.value * 1e-3) / 1e9)
+        out[f"{name}_copy_GBps"] = best
+        del a, b
+    ms, fl = C.c_double(), C.c_double()
+    if L.fedfem_probe_fp64(20000, 8, h, C.byref(ms), C.byref(fl)) == 0:
+        out["fp64_TFLOPs"] = fl.value / (ms.value * 1e-3) / 1e12
+    torch.cuda.synchronize()
+    out["how"] = ("own vector copy kernel (read + write bytes / time, L2: 2 x 24 MB buffers x 200 passes; HBM: 2 x 2 GB "
+                  "x 5 passes); own FP64 kernel, 8 independent FMA chains per thread (2 flops per FMA)")
+    return out
 
 
 def main():
@@ -337,6 +559,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_setup(args)
@@ -357,17 +580,17 @@ def main():
 
     barrier = make_barrier(world, torch.cuda.synchronize)
 
-    # CPU baseline first (rank 0, N = 1 only), before the GPU work
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample()
-
     p = fi.large_cube(args.n)
     stream = torch.cuda.Stream()
     f = FedFem(p, precision=32, stream=stream)
     dtc = f.precompute()
-    dt = 0.9 * dtc
+    dt = round_dt(0.9 * dtc)
     f.set_dt(dt)
+
+    # CPU baseline (rank 0, N = 1 only), before the timed GPU work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(dt)
     T0 = p.initial_T()
     info = f.info()
     spl = info["steps_per_launch"]
@@ -378,7 +601,7 @@ def main():
     K = args.steps
     n_launch = int(math.ceil(K / spl))
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch + 1)]
-    clocks = ClockSampler(local)
+    clocks = clock_sampler(local)
     clocks.start()
     barrier()
     t_wall = time.perf_counter()
@@ -528,22 +751,36 @@ def main():
                    "plan": best, "tuned": [[r[0], None if r[1] == float("inf") else r[1]] for r in tuned]}
         fb.close()
 
+    own = own_peaks(stream) if rank == 0 else None
+    # FP64 form against the FP64 rate: FP64 instructions per element-step, counted from the
+    # kernel: per hexahedron 8 adds (mean T), 28 x (subtract + 2 FMA) for the pair loads, 2 for
+    # the law and 8 scalings = 102; per node about 24 (update with the IEEE division sequence)
+    fp64_instr = 102.0 + 24.0 * N / E
+    fp64_alu = None
+    if own and own.get("fp64_TFLOPs"):
+        rate = fp64_instr * v64 / world  # per GPU
+        peak_instr = own["fp64_TFLOPs"] * 1e12 / 2.0
+        fp64_alu = {"bound": "alu", "fp64_instructions_per_element_step": fp64_instr,
+                    "achieved_T_instr_per_s": rate / 1e12, "peak_T_fma_per_s": peak_instr / 1e12,
+                    "frac": rate / peak_instr, "peak_kind": "own FP64 FMA kernel (own_peaks)"}
+
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        sweep = plan_sweep(p, dt, stream)
+
     extras = None
     if rank == 0 and not args.no_extras:
-        extras = extra_workloads(stream, peak)
+        extras = extra_workloads(stream, peak, own)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"large_hex_{args.n}: {args.n}^3 hex nonlinear cube (orthotropic k(T), c(T), "
-                                   "conv+rad on all faces, central source), FP32 + Kahan",
-                       "elements": E, "nodes": N, "dt": dt, "steps_per_launch": spl, "grid": info["grid"],
-                       "block": info["block"], "tiles": info["n_tiles"], "stages": info["stages"],
-                       "element_stream_MB": info["elem_bytes"] / 1e6,
-                       "l2": "inputs larger than L2 (element stream > 129 MB), no flush",
-                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "config": workload_config(p, dt, args.n),
+            "plan": {"steps_per_launch": spl, "grid": info["grid"], "block": info["block"], "tiles": info["n_tiles"],
+                     "stages": info["stages"], "element_stream_MB": info["elem_bytes"] / 1e6,
+                     "ranks": "replicas" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": None if tr is None else tr * E * launch_steps,
@@ -556,7 +793,9 @@ def main():
             "gpu_launches": n_launch,
             "clocks": clk,
             "fp64": {"value": v64, "unit": UNIT, "ms_per_step": ms64 / K64, "steps": K64,
-                     "achieved_GBps": bytes64 / (ms64 * 1e-3 / K64) / 1e9},
+                     "achieved_GBps": bytes64 / (ms64 * 1e-3 / K64) / 1e9, "roofline_alu": fp64_alu},
+            "own_peaks": own,
+            "plan_sweep": sweep,
             "fp32_over_fp64": value / v64,
             "fp32_vs_fp64": prec,
             "adjoint": adj,

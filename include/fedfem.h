@@ -453,6 +453,23 @@ fedfem_status fedfem_dd_get_info(fedfem_dd *dd, fedfem_dd_info *info);
  * the counts first.  Errors: ARG, MESH (node id out of range). */
 fedfem_status fedfem_dd_subdomain(const fedfem_mesh *mesh, int32_t n_sub, int32_t s, int64_t *n_elems,
                                   int32_t *elems, int64_t *n_nodes, int32_t *nodes, int32_t *ghost_owner);
+/* ---------------------------------------------------------------------------------------
+ * Measurement helpers (no counterpart in the paper): the denominators of the roofline
+ * fractions of kernels that HBM does not bound.
+ * ------------------------------------------------------------------------------------- */
+/* Copy `bytes` (a multiple of 16) from src_dev to dst_dev (DEVICE buffers, 16-byte aligned)
+ * `reps` times with the library's own vector copy kernel (blocks_per_sm x SMs blocks of 512
+ * threads), after one untimed pass; *ms_out = the device time of the reps passes (CUDA events
+ * on `stream`).  Bandwidth = 2 bytes reps / time: an L2 figure when both buffers fit in L2, an
+ * HBM figure when they are much larger.  Synchronises the stream.  Errors: ARG, CUDA. */
+fedfem_status fedfem_probe_copy(void *dst_dev, const void *src_dev, int64_t bytes, int32_t reps,
+                                int32_t blocks_per_sm, void *stream, double *ms_out);
+/* FP64 fused multiply-add rate: blocks_per_sm x SMs blocks of 256 threads, each running eight
+ * independent chains of `iters` FMAs; *flops_out = 2 x FMAs issued, *ms_out = their device time.
+ * Synchronises the stream.  Errors: ARG, OOM (8-byte sink), CUDA. */
+fedfem_status fedfem_probe_fp64(int64_t iters, int32_t blocks_per_sm, void *stream, double *ms_out,
+                                double *flops_out);
+
 /* Message of the last error on dd; with NULL, of the last fedfem_dd_create on this thread. */
 const char *fedfem_dd_error_string(fedfem_dd *dd);
 /* Release all sub-domains.  NULL is ignored. */

@@ -120,6 +120,8 @@ SIGNATURES = {
     "fedfem_dd_subdomain": (I32, [P, I32, I32, P, P, P, P, P]),
     "fedfem_dd_error_string": (C.c_char_p, [P]),
     "fedfem_dd_destroy": (None, [P]),
+    "fedfem_probe_copy": (I32, [P, P, I64, I32, I32, P, P]),
+    "fedfem_probe_fp64": (I32, [I64, I32, P, P, P]),
 }
 
 _lib = None

@@ -468,13 +468,15 @@ static fedfem_status batch_build(fedfem_batch *b, const fedfem_scenario *sc, int
     launch_impose_dirichlet((int64_t)c->dir_nodes.size(), c->d_dir_new, c->d_dir_T, 0.0, c->d_v[0], c->d_old_of_new, stm);
     launch_set_state(c->precision, nn, c->d_v[0], c->d_old_of_new, c->d_T[0], c->kahan ? c->d_comp[0] : nullptr, stm);
     int64_t n = 0;
+    // tile progress counters: reset once per replay, then launch j starts from base n
+    cudaMemsetAsync(c->d_tile_done, 0, c->til.n_tiles * sizeof(unsigned int), stm);
     for (int j = 0; j < J; ++j) {
         a.cta_tile = d_ranges[j];
         while (n < distinct[j]) {
             const int64_t k = std::min<int64_t>(spl, distinct[j] - n);
             a.n0 = n;
             a.nsteps = (int32_t)k;
-            cudaMemsetAsync(c->d_tile_done, 0, c->til.n_tiles * sizeof(unsigned int), stm);
+            a.progress_base = (uint32_t)n;
             launch_step(a, c->precision, c->kahan, c->npe, 0, grids[j], c->block, c->smem, c->ts_cap, stm);
             n += k;
         }

@@ -86,6 +86,7 @@ struct fedfem_ctx {
     int32_t *d_colptr = nullptr;
     int32_t *d_nbr_ptr = nullptr, *d_nbr = nullptr;
     unsigned int *d_tile_done = nullptr;
+    uint32_t progress_base = 0;  // tile progress counters at the next launch's start (below 2^31)
     fedfem::PhysParams *d_phys = nullptr;
     int32_t *d_cta_tile = nullptr;  // NULL: tiles_per_cta consecutive tiles per CTA
     void *d_T[2] = {nullptr, nullptr};

@@ -411,6 +411,8 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
     CK(upload(c, (void **)&c->d_nbr_ptr, T.nbr_ptr.data(), T.nbr_ptr.size() * sizeof(int32_t)), "upload neighbours");
     CK(upload(c, (void **)&c->d_nbr, T.nbr.data(), T.nbr.size() * sizeof(int32_t)), "upload neighbours");
     CK(dalloc(c, (void **)&c->d_tile_done, (T.n_tiles + 16) * sizeof(unsigned int)), "alloc tile progress");
+    CK(cudaMemsetAsync(c->d_tile_done, 0, (T.n_tiles + 16) * sizeof(unsigned int), c->stream), "memset");
+    c->progress_base = 0;
     const size_t n_slots = T.sptr.empty() ? 0 : (size_t)T.sptr.back();
     for (int b = 0; b < 2; ++b) {
         CK(dalloc(c, &c->d_T[b], (nn + NODE_PAD) * rs), "alloc T");
@@ -825,9 +827,17 @@ fedfem_status enqueue_steps(fedfem_ctx *c, int64_t n, void *rec, int64_t rec_str
         a.nsteps = (int32_t)k;
         a.rec = rec ? (uint8_t *)rec + (size_t)done * rec_stride * (c->precision == 64 ? 8 : 4) : nullptr;
         a.rec_stride = rec_stride;
-        CK(cudaMemsetAsync(c->d_tile_done, 0, c->til.n_tiles * sizeof(unsigned int), c->stream), "reset tile progress");
+        // the progress counters keep growing from launch to launch (every launch waits for
+        // values above its base, which no earlier launch wrote); they restart from 0 only
+        // before they would reach 2^31
+        if ((uint64_t)c->progress_base + (uint64_t)k >= (1ull << 31)) {
+            CK(cudaMemsetAsync(c->d_tile_done, 0, c->til.n_tiles * sizeof(unsigned int), c->stream), "reset tile progress");
+            c->progress_base = 0;
+        }
+        a.progress_base = c->progress_base;
         CK(launch_step(a, c->precision, c->kahan, c->npe, c->n_tab > 0, c->grid, c->block, c->smem, c->ts_cap, c->stream),
            "step launch");
+        c->progress_base += (uint32_t)k;
         c->step += k;
         done += k;
     }

@@ -109,7 +109,8 @@ struct StepArgs {
     const void *Ac;             // Real [nn]
     const void *Ar;             // Real [nn]
     void *part[2];              // Real [n_slots] halo partial sums, step parity
-    unsigned int *tile_done;    // [n_tiles] steps completed by each tile in this launch (zeroed per launch)
+    unsigned int *tile_done;    // [n_tiles] progress_base + steps completed by each tile in this launch
+    uint32_t progress_base;     // counter value at launch start (the counters only grow between resets)
     const int32_t *nbr_ptr;     // tile neighbours (CSR over tiles)
     const int32_t *nbr;
     int32_t *err;               // device error word

@@ -208,9 +208,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// Neighbour synchronisation (in place of a grid barrier).  A tile publishes how many steps of
-// this launch it has completed; before step s it waits until every tile it shares a node with
-// has completed step s - 1.  Neighbours therefore never drift apart by more than one step, which
+// Neighbour synchronisation (in place of a grid barrier).  A tile publishes how many steps it
+// has completed, counted from the launch's progress base (the counters only grow from launch to
+// launch, so they need no reset between launches); before step s it waits until every tile it
+// shares a node with has completed step s - 1.  Neighbours therefore never drift apart by more than one step, which
 // is what the step-parity double buffers of T, the compensation and the halo partials allow.
 // Entered by the NC consumer threads; thread 0 does the memory operations.
 __device__ __forceinline__ void tile_publish(unsigned int *done, int t, unsigned int steps, bool withhold, int nc)
@@ -767,7 +768,8 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                     if (KAHAN) l2_prefetch_bulk(a.comp[cur] + i0, (uint32_t)((i1 - i0) * 4), pk);
                 }
             }
-            if (s > 0 && !tile_wait(a.tile_done, a.nbr_ptr, a.nbr, t, (unsigned)s, a.err, a.timeout_ns, NC, &s_ok)) {
+            if (s > 0 && !tile_wait(a.tile_done, a.nbr_ptr, a.nbr, t, a.progress_base + (unsigned)s, a.err,
+                                    a.timeout_ns, NC, &s_ok)) {
                 ok = false;
                 break;
             }
@@ -900,7 +902,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
             {
                 // publish the step: the interior updates below touch only this tile's own nodes
                 const bool withhold = a.withhold > 0 && (int)blockIdx.x == a.withhold - 1;
-                tile_publish(a.tile_done, t, (unsigned)(s + 1), withhold, NC);
+                tile_publish(a.tile_done, t, a.progress_base + (unsigned)(s + 1), withhold, NC);
             }
             // ---- update interior nodes: aligned groups of four consecutive nodes per thread
             //      (vector loads), UG groups in flight; scalar head and tail
@@ -974,7 +976,8 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
         const R *Tp = reinterpret_cast<const R *>(a.T[prv]);
         const R *part = reinterpret_cast<const R *>(a.part[prv]);
         for (int t = t0; t < t1 && ok; ++t) {
-            if (!tile_wait(a.tile_done, a.nbr_ptr, a.nbr, t, (unsigned)a.nsteps, a.err, a.timeout_ns, NC, &s_ok)) {
+            if (!tile_wait(a.tile_done, a.nbr_ptr, a.nbr, t, a.progress_base + (unsigned)a.nsteps, a.err, a.timeout_ns,
+                           NC, &s_ok)) {
                 ok = false;
                 break;
             }
