@@ -129,6 +129,24 @@ typedef struct {
                                    element matrix has rank 3).  Lumped masses, source loads and
                                    face areas keep their exact integration.  Ignored for tets;
                                    other values give FEDFEM_ERR_ARG */
+    int32_t kT_eval;            /* where k(T) is evaluated: 0 = element mean of the nodal factors
+                                   (Section 4.2.2, default); 1 = at the quadrature points (Eq. 20
+                                   with D(T) inside the integral: the 2x2x2 points of a hexahedron,
+                                   its centre with quadrature = 1, the centroid of a tet) */
+    int32_t face_quadrature;    /* surface loads of Eq. 4 / 7: 0 = nodal lumping of the face areas
+                                   (default); 1 = consistent integration over every boundary face
+                                   (face mass matrices for convection; radiation by 3x3 Gauss points
+                                   on quadrilaterals, Radon's 7-point degree-5 rule on triangles).
+                                   With either variant the step runs as three plain launches per
+                                   step (elements, faces, nodes; deterministic gathers) instead of
+                                   the persistent kernel; fedfem_energy, the adjoint, batches and
+                                   the domain decomposition then return FEDFEM_ERR_UNSUPPORTED */
+    int32_t reserved2;
+    double start_stagger_us;    /* staggered start of the persistent launch (launches of >= 8 steps):
+                                   the consumers of CTA b begin stagger * b / grid us late, which
+                                   spreads the CTAs' element and node phases in time from the first
+                                   step.  0 = auto (half the time of one step's element stream at
+                                   6.5 TB/s, at most 50 us), < 0 = off, > 0 = this many us */
 } fedfem_options;
 
 /* Fill *opt with defaults (FP32 + Kahan, colour scatter, automatic launch plan). */
@@ -227,6 +245,10 @@ fedfem_status fedfem_internal_loads(fedfem_ctx *ctx, const double *T_host, doubl
  * nodal loads).  The time step and dt_crit are left unchanged.  Arrays: [n_elems] FP64 host.
  */
 fedfem_status fedfem_set_params(fedfem_ctx *ctx, const double *kscale, const double *source);
+/* The same with DEVICE arrays [n_elems] (e.g. torch tensors), copied on the context's stream;
+ * kscale is checked (smallest value > 0, largest finite) from a few partial minima and maxima
+ * read back, not from the array.  Errors: ARG (kscale not > 0), STATE, CUDA. */
+fedfem_status fedfem_set_params_device(fedfem_ctx *ctx, const double *kscale_dev, const double *source_dev);
 
 /*
  * Time-dependent loads and prescribed temperatures (the paper's boundary data are constant;
@@ -278,6 +300,10 @@ fedfem_status fedfem_set_state(fedfem_ctx *ctx, const void *buf);
 fedfem_status fedfem_forward_record(fedfem_ctx *ctx, int64_t n_steps, const int32_t *sensors,
                                     int32_t n_sensors, int32_t sample_every, int32_t ckpt_every,
                                     double *trace);
+/* The same with the trace written to a DEVICE array (sensors stay a host array). */
+fedfem_status fedfem_forward_record_device(fedfem_ctx *ctx, int64_t n_steps, const int32_t *sensors,
+                                           int32_t n_sensors, int32_t sample_every, int32_t ckpt_every,
+                                           double *trace_dev);
 
 /*
  * Reverse-time discrete adjoint of the recorded forward run (derived from Eq. 16 and Eq. 20;
@@ -289,6 +315,12 @@ fedfem_status fedfem_forward_record(fedfem_ctx *ctx, int64_t n_steps, const int3
  */
 fedfem_status fedfem_adjoint(fedfem_ctx *ctx, const double *dL_dtrace, double *dL_dkscale,
                              double *dL_dsource);
+/* The same with DEVICE input and outputs.  On a GPU that can keep all the sweep's blocks
+ * resident, each checkpoint segment's reverse steps run in one cooperative launch with grid
+ * barriers (bounded waits, FEDFEM_ERR_TIMEOUT when one runs out) between the element and node
+ * passes; otherwise the passes are separate launches (same results). */
+fedfem_status fedfem_adjoint_device(fedfem_ctx *ctx, const double *dL_dtrace_dev, double *dL_dkscale_dev,
+                                    double *dL_dsource_dev);
 
 /* Physical constants of the energy-balance terms (the context's values for fedfem_energy). */
 typedef struct {

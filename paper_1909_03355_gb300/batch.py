@@ -19,6 +19,9 @@ class FedFemBatch:
             for f in ("q_schedule", "Tinf_schedule", "Tdir_schedule", "table_T"):
                 if getattr(p, f, None) is not None:
                     raise ValueError(f"{f} is not available for batched scenarios")
+            for f in ("kT_eval", "face_quadrature"):
+                if getattr(p, f, 0):
+                    raise ValueError(f"{f} is not available for batched scenarios")
         self.L = capi.load()
         keep = []
         S = len(problems)

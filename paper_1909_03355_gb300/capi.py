@@ -43,7 +43,8 @@ class Options(C.Structure):
     _fields_ = [("precision", I32), ("kahan", I32), ("scatter", I32), ("block", I32),
                 ("steps_per_launch", I32), ("ctas_per_sm", I32), ("tiles_per_cta", I32), ("stages", I32),
                 ("chunk", I32), ("l2_policy", I32), ("barrier_timeout_s", F64), ("T_guard", F64), ("stream", P), ("device", I32),
-                ("verbose", I32), ("debug_withhold_barrier", I32), ("quadrature", I32)]
+                ("verbose", I32), ("debug_withhold_barrier", I32), ("quadrature", I32), ("kT_eval", I32),
+                ("face_quadrature", I32), ("reserved2", I32), ("start_stagger_us", F64)]
 
 
 class Info(C.Structure):
@@ -98,6 +99,9 @@ SIGNATURES = {
     "fedfem_set_state": (I32, [P, P]),
     "fedfem_forward_record": (I32, [P, I64, P, I32, I32, I32, P]),
     "fedfem_adjoint": (I32, [P, P, P, P]),
+    "fedfem_adjoint_device": (I32, [P, P, P, P]),
+    "fedfem_forward_record_device": (I32, [P, I64, P, I32, I32, I32, P]),
+    "fedfem_set_params_device": (I32, [P, P, P]),
     "fedfem_get_info": (I32, [P, P]),
     "fedfem_check_tiling": (I32, [P, I64, P, I32, I32, P]),
     "fedfem_energy_terms_noalloc": (I32, [I64, P, P, P, P, P, P, P, P, P, P, P]),

@@ -72,62 +72,112 @@ __global__ void k_gather_sensors(int ns, const int32_t *sens, const R *T, const 
 
 // mu_i = a_i lambda_i, a_i = A_i / f_c(T_i) (A = -0.0 on Dirichlet nodes); musum += mu
 template <typename R>
+__device__ __forceinline__ void adj_mu_one(int64_t g, const R *Tn, const double *A, const double *lam,
+                                           const AdjPhys &ph, double qs, double *mu, double *musum)
+{
+    const double t = (double)Tn[g];
+    const double m = A[g] / adj_fc(ph, t) * __ldcg(lam + g);
+    mu[g] = m;
+    musum[g] += qs * m;  // d Q_g / d s_e = qs w_ge
+}
+
+// Element pass of element e: forward loads F_e = f_k (c T_e) and adjoint loads
+// G_e = f_k (c mu_e) + (mu_e . c T_e) f_k'(T_j) / npe into per-element slots; theta gradient.
+template <int NPE, typename R>
+__device__ __forceinline__ void adj_elem_one(int64_t e, const int32_t *gconn, const double *cond64, const R *Tn,
+                                             const double *mu, const double *theta, const AdjPhys &ph, double *YF,
+                                             double *YG, double *gtheta)
+{
+    constexpr int NC = NPE * (NPE - 1) / 2;
+    double T[NPE], m[NPE], cT[NPE], cm[NPE];
+    double sum = 0.0;
+    for (int k = 0; k < NPE; ++k) {
+        const int g = gconn[NPE * e + k];
+        T[k] = (double)Tn[g];
+        m[k] = __ldcg(mu + g);
+        sum += ph.tab ? hinge_value(ph.tk, T[k]) : T[k];
+        cT[k] = 0.0;
+        cm[k] = 0.0;
+    }
+    const double *ce = cond64 + NC * e;
+    int p = 0;
+    for (int i = 0; i < NPE; ++i)
+        for (int j = i + 1; j < NPE; ++j, ++p) {
+            const double gt = ce[p] * (T[i] - T[j]);
+            const double gm = ce[p] * (m[i] - m[j]);
+            cT[i] += gt;
+            cT[j] -= gt;
+            cm[i] += gm;
+            cm[j] -= gm;
+        }
+    const double fk = ph.tab ? sum / NPE : ph.k_a + ph.k_lin * (sum / NPE);
+    double mcT = 0.0;
+    for (int k = 0; k < NPE; ++k) mcT += m[k] * cT[k];
+    for (int k = 0; k < NPE; ++k) {
+        YF[NPE * e + k] = fk * cT[k];
+        YG[NPE * e + k] = fk * cm[k] + mcT * (ph.tab ? hinge_slope(ph.tk, T[k]) : ph.k_lin) / NPE;
+    }
+    gtheta[e] -= fk * mcT / theta[e];
+}
+
+// Node pass of node g: gather F and G in fixed (ascending element) order and form lambda^n.
+// With Tprev (the state one step earlier) the pass also prepares the next reverse step:
+// lambda^n += dL/dT^n at the sensors (dl_next, sensor index per node), mu = A / f_c(T^(n-1))
+// lambda^n written over mu (each thread touches only its node), musum += qs_prev mu.
+template <typename R>
+__device__ __forceinline__ void adj_node_one(int64_t g, int npe, const int32_t *n2e_ptr, const int64_t *n2e,
+                                             const double *YF, const double *YG, const R *Tn, const double *lam,
+                                             double *mu, const double *A, const double *Qext, const double *Ac,
+                                             const double *Ar, const uint8_t *isdir, const AdjPhys &ph, double *lam_out,
+                                             const R *Tprev, const int32_t *sens_idx, const double *dl_next,
+                                             double qs_prev, double *musum)
+{
+    double F = 0.0, G = 0.0;
+    for (int q = n2e_ptr[g]; q < n2e_ptr[g + 1]; ++q) {
+        const int64_t ek = n2e[q];
+        const int64_t s = npe * (ek >> 3) + (ek & 7);
+        F += __ldcg(YF + s);
+        G += __ldcg(YG + s);
+    }
+    const double lg = __ldcg(lam + g);
+    double l;
+    if (isdir[g]) {
+        l = lg - G;
+    } else {
+        const double t = (double)Tn[g];
+        const double fc = adj_fc(ph, t);
+        const double a = A[g] / fc;
+        const double u = t - ph.T_zero, b = ph.T_amb - ph.T_zero;
+        const double Q = ph.qs * Qext[g] - Ac[g] * ph.h * (t - ph.T_inf) - Ar[g] * ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
+        const double dQ = -Ac[g] * ph.h - Ar[g] * ph.eps_sigma * 4.0 * u * u * u;
+        const double d = -a * adj_dfc(ph, t) / fc * (Q - F);
+        l = lg * (1.0 + d) + __ldcg(mu + g) * dQ - G;
+    }
+    if (Tprev) {
+        if (dl_next && sens_idx[g] >= 0) l += dl_next[sens_idx[g]];
+        const double m = A[g] / adj_fc(ph, (double)Tprev[g]) * l;
+        mu[g] = m;
+        musum[g] += qs_prev * m;
+    }
+    lam_out[g] = l;
+}
+
+template <typename R>
 __global__ void k_adj_mu(int64_t nn, const R *Tn, const double *A, const double *lam, AdjPhys ph, double qs,
                          double *mu, double *musum)
 {
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
-        const double t = (double)Tn[g];
-        const double m = A[g] / adj_fc(ph, t) * lam[g];
-        mu[g] = m;
-        musum[g] += qs * m;  // d Q_g / d s_e = qs w_ge
-    }
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x)
+        adj_mu_one<R>(g, Tn, A, lam, ph, qs, mu, musum);
 }
 
-// Element pass: forward loads F_e = f_k (c T_e) and adjoint loads
-// G_e = f_k (c mu_e) + (mu_e . c T_e) f_k'(T_j) / npe into per-element slots; theta gradient.
 template <int NPE, typename R>
 __global__ void k_adj_elem(int64_t ne, const int32_t *gconn, const double *cond64, const R *Tn, const double *mu,
                            const double *theta, AdjPhys ph, double *YF, double *YG, double *gtheta)
 {
-    constexpr int NC = NPE * (NPE - 1) / 2;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
-        double T[NPE], m[NPE], cT[NPE], cm[NPE];
-        double sum = 0.0;
-        for (int k = 0; k < NPE; ++k) {
-            const int g = gconn[NPE * e + k];
-            T[k] = (double)Tn[g];
-            m[k] = mu[g];
-            sum += ph.tab ? hinge_value(ph.tk, T[k]) : T[k];
-            cT[k] = 0.0;
-            cm[k] = 0.0;
-        }
-        const double *ce = cond64 + NC * e;
-        int p = 0;
-        for (int i = 0; i < NPE; ++i)
-            for (int j = i + 1; j < NPE; ++j, ++p) {
-                const double gt = ce[p] * (T[i] - T[j]);
-                const double gm = ce[p] * (m[i] - m[j]);
-                cT[i] += gt;
-                cT[j] -= gt;
-                cm[i] += gm;
-                cm[j] -= gm;
-            }
-        const double fk = ph.tab ? sum / NPE : ph.k_a + ph.k_lin * (sum / NPE);
-        double mcT = 0.0;
-        for (int k = 0; k < NPE; ++k) mcT += m[k] * cT[k];
-        for (int k = 0; k < NPE; ++k) {
-            YF[NPE * e + k] = fk * cT[k];
-            YG[NPE * e + k] = fk * cm[k] + mcT * (ph.tab ? hinge_slope(ph.tk, T[k]) : ph.k_lin) / NPE;
-        }
-        gtheta[e] -= fk * mcT / theta[e];
-    }
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x)
+        adj_elem_one<NPE, R>(e, gconn, cond64, Tn, mu, theta, ph, YF, YG, gtheta);
 }
 
-// Node pass: gather F and G in fixed (ascending element) order and form lambda^n.
-// With Tprev (the state one step earlier) the pass also prepares the next reverse step, as
-// k_adj_inject and k_adj_mu would: lambda^n += dL/dT^n at the sensors (dl_next, sensor index per
-// node), mu = A / f_c(T^(n-1)) lambda^n written over mu (each thread touches only its node),
-// musum += qs_prev mu.
 template <typename R>
 __global__ void k_adj_node(int64_t nn, int npe, const int32_t *n2e_ptr, const int64_t *n2e, const double *YF,
                            const double *YG, const R *Tn, const double *lam, double *mu, const double *A,
@@ -135,34 +185,113 @@ __global__ void k_adj_node(int64_t nn, int npe, const int32_t *n2e_ptr, const in
                            double *lam_out, const R *Tprev, const int32_t *sens_idx, const double *dl_next,
                            double qs_prev, double *musum)
 {
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
-        double F = 0.0, G = 0.0;
-        for (int q = n2e_ptr[g]; q < n2e_ptr[g + 1]; ++q) {
-            const int64_t ek = n2e[q];
-            const int64_t s = npe * (ek >> 3) + (ek & 7);
-            F += YF[s];
-            G += YG[s];
-        }
-        double l;
-        if (isdir[g]) {
-            l = lam[g] - G;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x)
+        adj_node_one<R>(g, npe, n2e_ptr, n2e, YF, YG, Tn, lam, mu, A, Qext, Ac, Ar, isdir, ph, lam_out, Tprev,
+                        sens_idx, dl_next, qs_prev, musum);
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks co-resident): a generation counter
+// bumped by the last block to arrive.  Bounded: after timeout_ns (or once another block has
+// raised an error) a waiting block sets ERRBIT_TIMEOUT and the barrier returns false.
+__device__ bool adj_grid_barrier(unsigned int *count, unsigned int *gen, int32_t *err, long long timeout_ns)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned int g;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(gen) : "memory");
+        __threadfence();
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(gen), "r"(g + 1u) : "memory");
         } else {
-            const double t = (double)Tn[g];
-            const double fc = adj_fc(ph, t);
-            const double a = A[g] / fc;
-            const double u = t - ph.T_zero, b = ph.T_amb - ph.T_zero;
-            const double Q = ph.qs * Qext[g] - Ac[g] * ph.h * (t - ph.T_inf) - Ar[g] * ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
-            const double dQ = -Ac[g] * ph.h - Ar[g] * ph.eps_sigma * 4.0 * u * u * u;
-            const double d = -a * adj_dfc(ph, t) / fc * (Q - F);
-            l = lam[g] * (1.0 + d) + mu[g] * dQ - G;
+            unsigned long long t0;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            for (unsigned spin = 0;; ++spin) {
+                unsigned int v;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gen) : "memory");
+                if (v != g) break;
+                if ((spin & 15u) == 15u) {
+                    unsigned long long t;
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                    if (*(volatile int32_t *)err) {
+                        ok = 0;
+                        break;
+                    }
+                    if ((long long)(t - t0) > timeout_ns) {
+                        atomicOr(err, ERRBIT_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+                __nanosleep(32);
+            }
         }
-        if (Tprev) {
-            if (dl_next && sens_idx[g] >= 0) l += dl_next[sens_idx[g]];
-            const double m = A[g] / adj_fc(ph, (double)Tprev[g]) * l;
-            mu[g] = m;
-            musum[g] += qs_prev * m;
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// One checkpoint segment of the reverse sweep in a single cooperative launch: for s = K-1 .. 0
+// the element pass and the node pass of the step from T^(n) (n = step0 + s), separated by grid
+// barriers; at the segment's first reverse step the sensor injection and mu pass come first.
+// The arithmetic per element and node is that of the per-pass kernels above (same order, so
+// the same results); only the launches between the passes are replaced by barriers.  Values
+// written by other blocks within the launch (mu, lambda, the element slots) are read through
+// L2 (ld.cg), never from a possibly stale L1 line.
+struct AdjSegArgs {
+    int64_t nn, ne;
+    int K, ns, se;
+    int64_t rel0;                 // record steps before the segment's first state
+    const int32_t *gconn, *n2e_ptr, *sens, *sens_idx;
+    const int64_t *n2e;
+    const double *cond64, *theta, *A, *Qext, *Ac, *Ar, *dl;
+    const uint8_t *isdir;
+    const void *rec;              // [K][nn] recorded states of the segment
+    const double *step_Tinf, *step_qs;  // per recorded step (index: record step)
+    double *lam0, *lam1, *mu, *musum, *YF, *YG, *gth;
+    unsigned int *bar_count, *bar_gen;
+    int32_t *err;
+    long long timeout_ns;
+    int cur;                      // lambda buffer holding lambda at the segment's end
+};
+
+template <int NPE, typename R>
+__global__ void __launch_bounds__(128) k_adj_segment(AdjSegArgs a, AdjPhys ph)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const R *rec = static_cast<const R *>(a.rec);
+    double *lam[2] = {a.lam0, a.lam1};
+    int cur = a.cur;
+    for (int s = a.K - 1; s >= 0; --s) {
+        const int64_t rel = a.rel0 + s + 1;  // record steps up to the state T^{n+1}
+        const int64_t ri = a.rel0 + s;       // record index of the step from T^n
+        const R *Tn = rec + (size_t)s * a.nn;
+        ph.T_inf = a.step_Tinf[ri];
+        ph.qs = a.step_qs[ri];
+        if (s == a.K - 1) {  // no earlier node pass prepared this step
+            if (rel % a.se == 0)
+                for (int64_t q = tid0; q < a.ns; q += stride) lam[cur][a.sens[q]] += a.dl[(rel / a.se - 1) * a.ns + q];
+            if (!adj_grid_barrier(a.bar_count, a.bar_gen, a.err, a.timeout_ns)) return;
+            for (int64_t g = tid0; g < a.nn; g += stride) adj_mu_one<R>(g, Tn, a.A, lam[cur], ph, ph.qs, a.mu, a.musum);
+            if (!adj_grid_barrier(a.bar_count, a.bar_gen, a.err, a.timeout_ns)) return;
         }
-        lam_out[g] = l;
+        for (int64_t e = tid0; e < a.ne; e += stride)
+            adj_elem_one<NPE, R>(e, a.gconn, a.cond64, Tn, a.mu, a.theta, ph, a.YF, a.YG, a.gth);
+        if (!adj_grid_barrier(a.bar_count, a.bar_gen, a.err, a.timeout_ns)) return;
+        const R *Tprev = s > 0 ? rec + (size_t)(s - 1) * a.nn : nullptr;
+        const double *dl_next = (s > 0 && (rel - 1) % a.se == 0) ? a.dl + ((rel - 1) / a.se - 1) * a.ns : nullptr;
+        const double qs_prev = s > 0 ? a.step_qs[ri - 1] : 0.0;
+        for (int64_t g = tid0; g < a.nn; g += stride)
+            adj_node_one<R>(g, NPE, a.n2e_ptr, a.n2e, a.YF, a.YG, Tn, lam[cur], a.mu, a.A, a.Qext, a.Ac, a.Ar, a.isdir,
+                            ph, lam[cur ^ 1], Tprev, a.sens_idx, dl_next, qs_prev, a.musum);
+        cur ^= 1;
+        if (!adj_grid_barrier(a.bar_count, a.bar_gen, a.err, a.timeout_ns)) return;
     }
 }
 
@@ -248,11 +377,12 @@ void adj_step(fedfem_ctx *c, bool first, const void *Tn, const void *Tprev, cons
 
 }  // namespace
 
-extern "C" fedfem_status fedfem_forward_record(fedfem_ctx *c, int64_t n_steps, const int32_t *sensors,
-                                               int32_t n_sensors, int32_t sample_every, int32_t ckpt_every,
-                                               double *trace)
+static fedfem_status forward_record_impl(fedfem_ctx *c, int64_t n_steps, const int32_t *sensors, int32_t n_sensors,
+                                         int32_t sample_every, int32_t ckpt_every, double *trace, bool trace_on_device)
 {
     if (!c) return FEDFEM_ERR_ARG;
+    if (c->variant())
+        return fail(c, FEDFEM_ERR_UNSUPPORTED, "the adjoint covers kT_eval = 0 and face_quadrature = 0 only");
     if (!c->has_dt || !c->has_T) return fail(c, FEDFEM_ERR_STATE, "call fedfem_set_dt and fedfem_set_T first");
     if (n_steps <= 0 || sample_every <= 0 || ckpt_every <= 0 || n_steps % sample_every || n_steps % ckpt_every ||
         ckpt_every % sample_every)
@@ -296,7 +426,9 @@ extern "C" fedfem_status fedfem_forward_record(fedfem_ctx *c, int64_t n_steps, c
     // the end state, restored after the reverse sweep
     fedfem_status s = copy_state(c, c->step, (uint8_t *)c->d_ckpt + n_ckpt * c->ckpt_bytes, true);
     if (s != FEDFEM_OK) return s;
-    CK(cudaMemcpyAsync(trace, d_trace, n_samp * n_sensors * 8, cudaMemcpyDeviceToHost, c->stream), "download trace");
+    CK(cudaMemcpyAsync(trace, d_trace, n_samp * n_sensors * 8,
+                       trace_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+       "copy trace");
     int32_t bits = 0;
     CK(cudaMemcpyAsync(&bits, c->d_err, 4, cudaMemcpyDeviceToHost, c->stream), "status");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
@@ -312,7 +444,22 @@ extern "C" fedfem_status fedfem_forward_record(fedfem_ctx *c, int64_t n_steps, c
     return FEDFEM_OK;
 }
 
-extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, double *dL_dkscale, double *dL_dsource)
+extern "C" fedfem_status fedfem_forward_record(fedfem_ctx *c, int64_t n_steps, const int32_t *sensors,
+                                               int32_t n_sensors, int32_t sample_every, int32_t ckpt_every,
+                                               double *trace)
+{
+    return forward_record_impl(c, n_steps, sensors, n_sensors, sample_every, ckpt_every, trace, false);
+}
+
+extern "C" fedfem_status fedfem_forward_record_device(fedfem_ctx *c, int64_t n_steps, const int32_t *sensors,
+                                                      int32_t n_sensors, int32_t sample_every, int32_t ckpt_every,
+                                                      double *trace_dev)
+{
+    return forward_record_impl(c, n_steps, sensors, n_sensors, sample_every, ckpt_every, trace_dev, true);
+}
+
+static fedfem_status adjoint_impl(fedfem_ctx *c, const double *dL_dtrace, double *dL_dkscale, double *dL_dsource,
+                                  bool on_device)
 {
     if (!c) return FEDFEM_ERR_ARG;
     if (!c->recorded) return fail(c, FEDFEM_ERR_STATE, "call fedfem_forward_record first");
@@ -352,7 +499,9 @@ extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, 
             return cuda_fail(c, e_, where);    \
         }                                      \
     } while (0)
-    CKR(cudaMemcpyAsync(d_dl, dL_dtrace, n_samp * ns * 8, cudaMemcpyHostToDevice, c->stream), "upload dL/dtrace");
+    CKR(cudaMemcpyAsync(d_dl, dL_dtrace, n_samp * ns * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        c->stream),
+        "copy dL/dtrace");
     CKR(cudaMemsetAsync(lam[0], 0, nn * 8, c->stream), "memset");
     CKR(cudaMemsetAsync(musum, 0, nn * 8, c->stream), "memset");
     CKR(cudaMemsetAsync(gth, 0, ne * 8, c->stream), "memset");
@@ -363,6 +512,38 @@ extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, 
     k_sensor_index<<<nblk(ns), 256, 0, c->stream>>>(ns, c->d_sensors, sens_idx);
     AdjPhys ph{c->k_lin, c->c_lin, c->h,   c->T_inf, c->eps * kSigma, c->T_amb, c->T_zero, c->k_a(), c->c_a(), 1.0,
                c->n_tab > 0, c->hk,    c->hc};
+    // per recorded step: convection temperature and load multiplier (schedules), and the grid
+    // barrier of the one-launch-per-segment sweep
+    double *step_Tinf = nullptr, *step_qs = nullptr;
+    unsigned int *bar = nullptr;
+    CKR(talloc((void **)&step_Tinf, c->rec_steps * 8), "adjoint buffers");
+    CKR(talloc((void **)&step_qs, c->rec_steps * 8), "adjoint buffers");
+    CKR(talloc((void **)&bar, 64), "adjoint buffers");
+    {
+        std::vector<double> ti(c->rec_steps), qs(c->rec_steps);
+        for (int64_t i = 0; i < c->rec_steps; ++i) {
+            ti[i] = c->Tinf_at(c->rec_step0 + i);
+            qs[i] = c->qs_at(c->rec_step0 + i);
+        }
+        CKR(cudaMemcpyAsync(step_Tinf, ti.data(), ti.size() * 8, cudaMemcpyHostToDevice, c->stream), "upload");
+        CKR(cudaMemcpyAsync(step_qs, qs.data(), qs.size() * 8, cudaMemcpyHostToDevice, c->stream), "upload");
+        CKR(cudaMemsetAsync(bar, 0, 64, c->stream), "memset");
+        CKR(cudaStreamSynchronize(c->stream), "synchronize");
+    }
+    void *seg_kernel = nullptr;
+    if (npe == 8)
+        seg_kernel = c->precision == 64 ? (void *)k_adj_segment<8, double> : (void *)k_adj_segment<8, float>;
+    else
+        seg_kernel = c->precision == 64 ? (void *)k_adj_segment<4, double> : (void *)k_adj_segment<4, float>;
+    int seg_grid = 0;
+    {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seg_kernel, 128, 0) == cudaSuccess && per_sm > 0) {
+            const int64_t want = (std::max(nn, ne) + 127) / 128;
+            seg_grid = (int)std::min<int64_t>((int64_t)per_sm * c->num_sms, want);
+        }
+    }
+    bool persistent = seg_grid > 0;
     int cur = 0;
     for (int64_t k = n_ckpt - 1; k >= 0; --k) {
         // recompute the segment from its checkpoint, recording T^n for every step
@@ -373,6 +554,62 @@ extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, 
         if (st != FEDFEM_OK) {
             release();
             return st;
+        }
+        if (persistent) {
+            AdjSegArgs sa;
+            sa.nn = nn;
+            sa.ne = ne;
+            sa.K = K;
+            sa.ns = ns;
+            sa.se = se;
+            sa.rel0 = k * K;
+            sa.gconn = c->d_gconn;
+            sa.n2e_ptr = c->d_n2e_ptr;
+            sa.sens = c->d_sensors;
+            sa.sens_idx = sens_idx;
+            sa.n2e = c->d_n2e;
+            sa.cond64 = c->d_cond64;
+            sa.theta = c->d_kscale;
+            sa.A = c->d_A;
+            sa.Qext = c->d_Qext64;
+            sa.Ac = c->d_Ac64;
+            sa.Ar = c->d_Ar64;
+            sa.dl = d_dl;
+            sa.isdir = c->d_isdir;
+            sa.rec = rec;
+            sa.step_Tinf = step_Tinf;
+            sa.step_qs = step_qs;
+            sa.lam0 = lam[0];
+            sa.lam1 = lam[1];
+            sa.mu = mu;
+            sa.musum = musum;
+            sa.YF = YF;
+            sa.YG = YG;
+            sa.gth = gth;
+            sa.bar_count = bar;
+            sa.bar_gen = bar + 1;
+            sa.err = c->d_err;
+            sa.timeout_ns = (long long)(c->opt.barrier_timeout_s * 1e9);
+            sa.cur = cur;
+            void *params[] = {(void *)&sa, (void *)&ph};
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(seg_grid);
+            cfg.blockDim = dim3(128);
+            cfg.stream = c->stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            const cudaError_t le = cudaLaunchKernelExC(&cfg, seg_kernel, params);
+            if (le == cudaSuccess) {
+                cur ^= (K & 1);
+                continue;
+            }
+            // a cooperative launch that cannot run (e.g. too few resident blocks): the passes as
+            // separate launches from this segment on
+            (void)cudaGetLastError();
+            persistent = false;
         }
         for (int s = K - 1; s >= 0; --s) {
             const int64_t rel = k * K + s + 1;  // steps after the record start of the state T^{n+1}
@@ -402,8 +639,9 @@ extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, 
     else
         k_adj_source<4><<<nblk(ne), 256, 0, c->stream>>>(ne, c->d_gconn, c->d_W, musum, gs);
     CKR(cudaGetLastError(), "source gradient");
-    CKR(cudaMemcpyAsync(dL_dkscale, gth, ne * 8, cudaMemcpyDeviceToHost, c->stream), "download");
-    CKR(cudaMemcpyAsync(dL_dsource, gs, ne * 8, cudaMemcpyDeviceToHost, c->stream), "download");
+    const cudaMemcpyKind out_kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CKR(cudaMemcpyAsync(dL_dkscale, gth, ne * 8, out_kind, c->stream), "copy dL/dkscale");
+    CKR(cudaMemcpyAsync(dL_dsource, gs, ne * 8, out_kind, c->stream), "copy dL/dsource");
     // leave the context in the state at the end of the recorded run
     c->step = c->rec_step0 + c->rec_steps;
     fedfem_status st = copy_state(c, c->step, (uint8_t *)c->d_ckpt + n_ckpt * c->ckpt_bytes, false);
@@ -418,4 +656,15 @@ extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, 
     }
     return FEDFEM_OK;
 #undef CKR
+}
+
+extern "C" fedfem_status fedfem_adjoint(fedfem_ctx *c, const double *dL_dtrace, double *dL_dkscale, double *dL_dsource)
+{
+    return adjoint_impl(c, dL_dtrace, dL_dkscale, dL_dsource, false);
+}
+
+extern "C" fedfem_status fedfem_adjoint_device(fedfem_ctx *c, const double *dL_dtrace_dev, double *dL_dkscale_dev,
+                                               double *dL_dsource_dev)
+{
+    return adjoint_impl(c, dL_dtrace_dev, dL_dkscale_dev, dL_dsource_dev, true);
 }

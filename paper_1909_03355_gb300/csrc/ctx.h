@@ -15,6 +15,7 @@ struct fedfem_ctx {
     int npe = 8;
     int64_t nn = 0, ne = 0;
     std::vector<double> xyz, kscale, source, nodal_Q, dir_T;
+    bool params_on_device = false;  // kscale / source last set from device arrays (d_kscale, d_source)
     std::vector<int32_t> conn, elem_mat, dir_nodes, conv_faces, rad_faces;
     std::vector<fedfem_material> mats;
     int face_nv = 4;
@@ -87,6 +88,7 @@ struct fedfem_ctx {
     int32_t *d_nbr_ptr = nullptr, *d_nbr = nullptr;
     unsigned int *d_tile_done = nullptr;
     uint32_t progress_base = 0;  // tile progress counters at the next launch's start (below 2^31)
+    long long stagger_ns = 0;    // start stagger of the last CTA of a launch (launches of >= 8 steps)
     fedfem::PhysParams *d_phys = nullptr;
     int32_t *d_cta_tile = nullptr;  // NULL: tiles_per_cta consecutive tiles per CTA
     void *d_T[2] = {nullptr, nullptr};
@@ -123,6 +125,21 @@ struct fedfem_ctx {
     int64_t step = 0;
     std::string err;
 
+    // method variants run by plain launches (variant.cu): conductivity at the quadrature points
+    // (kT_eval = 1) and consistent integration of the face loads (face_quadrature = 1)
+    int kT_qp = 0, face_cons = 0;
+    int nq = 0, nfq = 0;                 // quadrature points per element / per boundary face
+    double *d_cond_qp64 = nullptr;       // [ne][8][28] pair conductances per 2x2x2 point (hexahedra)
+    double *d_vq64 = nullptr;            // [nq * n_pairs][ne] pair conductances per point, FP64 (SoA)
+    void *d_vq = nullptr;                // the same in the working precision
+    void *d_Yv = nullptr;                // [ne][npe] element loads of a step, working precision
+    int32_t *d_cf_new = nullptr, *d_rf_new = nullptr;  // boundary faces in the tiling's node ids
+    double *d_Mf64 = nullptr, *d_Wf64 = nullptr;       // [n_conv][nv][nv] face mass, [n_rad][nfq] weights
+    void *d_Mf = nullptr, *d_Wf = nullptr;             // the same in the working precision
+    void *d_Yf = nullptr;                // [n_conv + n_rad][nv] face loads of a step, working precision
+    double *d_Yf64 = nullptr;            // the same in FP64 (energy and load queries)
+    bool variant() const { return kT_qp || face_cons; }
+
     // adjoint record (adjoint.cu)
     std::vector<void *> adj_allocs;
     bool recorded = false;
@@ -151,4 +168,10 @@ fedfem_status install_T(fedfem_ctx *c, const double *T0_dev_old);
 fedfem_status state_f64_new(fedfem_ctx *c, int64_t step, double *dst);
 StepArgs step_args(fedfem_ctx *c);
 fedfem_status enqueue_steps(fedfem_ctx *c, int64_t n, void *rec, int64_t rec_stride);
+// method variants (variant.cu): device arrays at set-up, their pre-computation, n steps by plain
+// launches, and the FP64 internal loads / surface loads of a state (new node order)
+fedfem_status variant_init(fedfem_ctx *c);
+fedfem_status variant_precompute(fedfem_ctx *c);
+fedfem_status variant_steps(fedfem_ctx *c, int64_t n);
+fedfem_status variant_loads64(fedfem_ctx *c, const double *T_new, int64_t step, double *F_new, double *Qs_new);
 }  // namespace fedfem

@@ -159,6 +159,11 @@ extern "C" fedfem_status fedfem_dd_create(const fedfem_mesh *mesh, const fedfem_
     fedfem_options o;
     fedfem_default_options(&o);
     if (opt) o = *opt;
+    if (o.kT_eval || o.face_quadrature) {
+        g_dd_create_error = "the decomposed mesh runs the persistent kernel only: kT_eval and face_quadrature must be 0";
+        delete d;
+        return FEDFEM_ERR_UNSUPPORTED;
+    }
     d->precision = o.precision == 64 ? 64 : 32;
     d->kahan = (d->precision == 32 && o.kahan) ? 1 : 0;
     d->stream = static_cast<cudaStream_t>(o.stream);

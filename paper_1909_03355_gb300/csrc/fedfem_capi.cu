@@ -225,6 +225,15 @@ static fedfem_status make_plan(fedfem_ctx *c, const std::vector<uint8_t> &is_bnd
             c->smem = smem;
             c->chunk_bytes = cb;
             c->ts_cap = step_ts_cap(c->precision, c->til.max_local);
+            // start stagger: half of the time one step's element stream takes at 6.5 TB/s,
+            // at most 50 us (option: > 0 given in us, < 0 off)
+            {
+                const double stream_us = (double)c->til.n_chunks * cb / 6.5e12 * 1e6;
+                const double us = c->opt.start_stagger_us > 0 ? c->opt.start_stagger_us
+                                  : c->opt.start_stagger_us < 0 ? 0.0
+                                                                : std::min(50.0, 0.5 * stream_us);
+                c->stagger_ns = (long long)(us * 1e3);
+            }
             if (c->opt.verbose)
                 std::fprintf(stderr,
                              "fedfem plan: tiles=%d grid=%d block=%d chunk=%d stages=%d tpc=%d max_local=%d "
@@ -309,6 +318,18 @@ fedfem_status create_ctx(const fedfem_mesh *mesh, const fedfem_material *mats, i
         delete c;
         return FEDFEM_ERR_ARG;
     }
+    if ((o.kT_eval != 0 && o.kT_eval != 1) || (o.face_quadrature != 0 && o.face_quadrature != 1)) {
+        err = "kT_eval and face_quadrature must be 0 or 1";
+        delete c;
+        return FEDFEM_ERR_ARG;
+    }
+    if (group_elem && (o.kT_eval || o.face_quadrature)) {
+        err = "batched scenarios run the persistent kernel only: kT_eval and face_quadrature must be 0";
+        delete c;
+        return FEDFEM_ERR_UNSUPPORTED;
+    }
+    c->kT_qp = o.kT_eval;
+    c->face_cons = o.face_quadrature;
     c->opt = o;
     c->precision = o.precision;
     c->kahan = (o.precision == 32 && o.kahan) ? 1 : 0;
@@ -512,6 +533,7 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
     CK(dalloc(c, (void **)&c->d_red, 2 * 1024 * 8 + 64), "alloc scratch");
     CK(dalloc(c, (void **)&c->d_lz, 4 * (size_t)c->power_max_iter * 8), "alloc Lanczos coefficients");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
+    if (c->variant()) return variant_init(c);
     return FEDFEM_OK;
 }
 
@@ -523,9 +545,12 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
 fedfem_status fedfem::run_precompute_arrays(fedfem_ctx *c)
 {
     const int npe = c->npe;
-    CK(cudaMemcpyAsync(c->d_kscale, c->kscale.data(), c->ne * 8, cudaMemcpyHostToDevice, c->stream), "upload kscale");
-    if (!c->source.empty())
-        CK(cudaMemcpyAsync(c->d_source, c->source.data(), c->ne * 8, cudaMemcpyHostToDevice, c->stream), "upload source");
+    if (!c->params_on_device) {
+        CK(cudaMemcpyAsync(c->d_kscale, c->kscale.data(), c->ne * 8, cudaMemcpyHostToDevice, c->stream), "upload kscale");
+        if (!c->source.empty())
+            CK(cudaMemcpyAsync(c->d_source, c->source.data(), c->ne * 8, cudaMemcpyHostToDevice, c->stream),
+               "upload source");
+    }
     unsigned long long big = ~0ULL;
     CK(cudaMemcpyAsync(c->d_bad_elem, &big, 8, cudaMemcpyHostToDevice, c->stream), "init");
     ElemArgs ea;
@@ -544,6 +569,7 @@ fedfem_status fedfem::run_precompute_arrays(fedfem_ctx *c)
     ea.cond64 = c->d_cond64;
     ea.W = c->d_W;
     ea.quad = c->opt.quadrature == 1 ? 1 : 8;
+    ea.cond_qp = c->nq == 8 ? c->d_cond_qp64 : nullptr;
     ea.err = c->d_err;
     ea.bad_elem = c->d_bad_elem;
     launch_elem(npe, ea, c->stream);
@@ -558,7 +584,7 @@ fedfem_status fedfem::run_precompute_arrays(fedfem_ctx *c)
     na.W = c->d_W;
     na.mat = c->d_mat;
     na.mat_rhoc = c->d_matrhoc;
-    na.source = c->source.empty() ? nullptr : c->d_source;
+    na.source = (c->source.empty() && !c->params_on_device) ? nullptr : c->d_source;
     na.nodal_Q = c->d_nodalQ;
     na.old_of_new = c->d_old_of_new;
     na.fc_ptr = c->n_conv ? c->d_fc_ptr : nullptr;
@@ -585,6 +611,10 @@ fedfem_status fedfem::run_precompute_arrays(fedfem_ctx *c)
         CK(cudaMemsetAsync(c->d_err, 0, 4, c->stream), "clear");
         CK(cudaStreamSynchronize(c->stream), "synchronize");
         return fail(c, FEDFEM_ERR_MESH, "element " + std::to_string(bad) + " has det J <= 0 (inverted or degenerate)");
+    }
+    if (c->variant()) {
+        const fedfem_status vs = variant_precompute(c);
+        if (vs != FEDFEM_OK) return vs;
     }
     if (c->has_dt) launch_set_A(c->nn, c->dt, c->d_C0, c->d_isdir, c->d_A, c->d_A2, c->stream);
     return FEDFEM_OK;
@@ -810,6 +840,10 @@ StepArgs step_args(fedfem_ctx *c)
 // Enqueue n steps as persistent launches of at most steps_per_launch steps.
 fedfem_status enqueue_steps(fedfem_ctx *c, int64_t n, void *rec, int64_t rec_stride)
 {
+    if (c->variant()) {
+        if (rec) return fail(c, FEDFEM_ERR_UNSUPPORTED, "the adjoint record needs kT_eval = 0 and face_quadrature = 0");
+        return variant_steps(c, n);
+    }
     StepArgs a = step_args(c);
     int64_t spl = c->opt.steps_per_launch > 0 ? c->opt.steps_per_launch : 200;
     // the kernel counts the chunks of one launch in 32 bits
@@ -835,6 +869,8 @@ fedfem_status enqueue_steps(fedfem_ctx *c, int64_t n, void *rec, int64_t rec_str
             c->progress_base = 0;
         }
         a.progress_base = c->progress_base;
+        // staggered start only for launches long enough to amortise it
+        a.stagger_ns = k >= 8 ? c->stagger_ns : 0;
         CK(launch_step(a, c->precision, c->kahan, c->npe, c->n_tab > 0, c->grid, c->block, c->smem, c->ts_cap, c->stream),
            "step launch");
         c->progress_base += (uint32_t)k;
@@ -917,8 +953,13 @@ extern "C" fedfem_status fedfem_internal_loads(fedfem_ctx *c, const double *T_ho
     if (!c->precomputed) return fail(c, FEDFEM_ERR_STATE, "call fedfem_precompute first");
     CK(cudaMemcpyAsync(c->d_v[0], T_host, c->nn * 8, cudaMemcpyHostToDevice, c->stream), "upload");
     launch_permute_old_to_new(c->nn, c->d_v[0], c->d_old_of_new, c->d_v[1], c->stream);
-    launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, c->d_v[1], c->d_v[1], c->k_a(), c->k_lin,
-                 c->tk_ptr(), c->d_Y, c->d_v[2], c->stream);
+    if (c->variant()) {
+        const fedfem_status vs = variant_loads64(c, c->d_v[1], c->step, c->d_v[2], nullptr);
+        if (vs != FEDFEM_OK) return vs;
+    } else {
+        launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, c->d_v[1], c->d_v[1], c->k_a(),
+                     c->k_lin, c->tk_ptr(), c->d_Y, c->d_v[2], c->stream);
+    }
     launch_permute_new_to_old(c->nn, c->d_v[2], c->d_old_of_new, c->d_v[3], c->stream);
     CK(cudaGetLastError(), "internal loads");
     CK(cudaMemcpyAsync(F_host, c->d_v[3], c->nn * 8, cudaMemcpyDeviceToHost, c->stream), "download");
@@ -935,13 +976,28 @@ extern "C" fedfem_status fedfem_energy(fedfem_ctx *c, double *stored_change, dou
     if (s != FEDFEM_OK) return s;
     s = state_f64_new(c, c->step, T1);
     if (s != FEDFEM_OK) return s;
-    launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, T0, T0, c->k_a(), c->k_lin,
-                 c->tk_ptr(), c->d_Y, F, c->stream);
     // the step from T^(n-1) to T^n with the loads of step n - 1
     EnergyPhys ph{c->dt,     c->c_lin,  c->h,   c->Tinf_at(c->step - 1), c->eps * 5.67e-8, c->T_amb, c->T_zero, c->c_a(),
                   c->qs_at(c->step - 1), c->n_tab > 0, c->hc};
+    const double *Qin = c->d_Qext64;
+    if (c->variant()) {
+        // element loads of the variant; with consistent faces the whole nodal heat flow (external
+        // and surface loads) comes from the face integration, so the lumped surface terms are off
+        double *Qtot = c->face_cons ? c->d_v[3] : nullptr;
+        s = variant_loads64(c, T0, c->step - 1, F, Qtot);
+        if (s != FEDFEM_OK) return s;
+        if (Qtot) {
+            Qin = Qtot;
+            ph.h = 0.0;
+            ph.eps_sigma = 0.0;
+            ph.qs = 1.0;
+        }
+    } else {
+        launch_apply(c->npe, c->ne, c->nn, c->d_gconn, c->d_cond64, c->d_n2e_ptr, c->d_n2e, T0, T0, c->k_a(), c->k_lin,
+                     c->tk_ptr(), c->d_Y, F, c->stream);
+    }
     double *partial = c->d_red, *sums = c->d_red + 2 * 1024;
-    launch_energy(c->nn, T0, T1, F, c->d_C0, c->d_Qext64, c->d_Ac64, c->d_Ar64, c->d_isdir, ph, partial, sums, c->stream);
+    launch_energy(c->nn, T0, T1, F, c->d_C0, Qin, c->d_Ac64, c->d_Ar64, c->d_isdir, ph, partial, sums, c->stream);
     CK(cudaGetLastError(), "energy");
     double h2[2];
     CK(cudaMemcpyAsync(h2, sums, 16, cudaMemcpyDeviceToHost, c->stream), "read");
@@ -1040,6 +1096,46 @@ extern "C" fedfem_status fedfem_set_params(fedfem_ctx *c, const double *kscale, 
         c->kscale.assign(kscale, kscale + c->ne);
     }
     if (source) c->source.assign(source, source + c->ne);
+    if (c->params_on_device) {
+        // the other parameter still lives on the device only: bring it back to the host copy
+        if (!kscale) {
+            c->kscale.resize(c->ne);
+            CK(cudaMemcpyAsync(c->kscale.data(), c->d_kscale, c->ne * 8, cudaMemcpyDeviceToHost, c->stream), "read");
+        }
+        if (!source) {
+            c->source.resize(c->ne);
+            CK(cudaMemcpyAsync(c->source.data(), c->d_source, c->ne * 8, cudaMemcpyDeviceToHost, c->stream), "read");
+        }
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        c->params_on_device = false;
+    }
+    return run_precompute_arrays(c);
+}
+
+extern "C" fedfem_status fedfem_set_params_device(fedfem_ctx *c, const double *kscale_dev, const double *source_dev)
+{
+    if (!c) return FEDFEM_ERR_ARG;
+    if (!c->precomputed) return fail(c, FEDFEM_ERR_STATE, "call fedfem_precompute first");
+    if (!c->params_on_device) {
+        // the parameter not given keeps its current value: make the device copies current
+        CK(cudaMemcpyAsync(c->d_kscale, c->kscale.data(), c->ne * 8, cudaMemcpyHostToDevice, c->stream), "upload");
+        if (c->source.empty())
+            CK(cudaMemsetAsync(c->d_source, 0, c->ne * 8, c->stream), "memset");
+        else
+            CK(cudaMemcpyAsync(c->d_source, c->source.data(), c->ne * 8, cudaMemcpyHostToDevice, c->stream), "upload");
+    }
+    if (kscale_dev) {
+        CK(cudaMemcpyAsync(c->d_kscale, kscale_dev, c->ne * 8, cudaMemcpyDeviceToDevice, c->stream), "copy kscale");
+        // every theta_e > 0 and finite: the smallest and largest value, read back (a few partials)
+        const int nb = launch_minmax(c->ne, c->d_kscale, c->d_red, c->stream);
+        std::vector<double> pr(2 * nb);
+        CK(cudaMemcpyAsync(pr.data(), c->d_red, pr.size() * 8, cudaMemcpyDeviceToHost, c->stream), "read");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        for (int b = 0; b < nb; ++b)
+            if (!(pr[2 * b] > 0) || !std::isfinite(pr[2 * b + 1])) return fail(c, FEDFEM_ERR_ARG, "kscale must be > 0");
+    }
+    if (source_dev) CK(cudaMemcpyAsync(c->d_source, source_dev, c->ne * 8, cudaMemcpyDeviceToDevice, c->stream), "copy source");
+    c->params_on_device = true;
     return run_precompute_arrays(c);
 }
 

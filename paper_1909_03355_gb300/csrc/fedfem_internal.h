@@ -135,6 +135,7 @@ struct StepArgs {
     int32_t l2_stream_policy;   // 0: evict_normal, 1: evict_first for the element stream
     int32_t scatter;
     int32_t withhold;           // test hook: CTA withhold-1 skips its first barrier arrival
+    long long stagger_ns;       // consumers of CTA b start the launch stagger_ns * b / grid late
     long long timeout_ns;
     // optional per-step recording of the state (adjoint segments): rec + s*rec_stride
     void *rec;

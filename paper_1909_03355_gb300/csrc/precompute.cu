@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "fedfem_internal.h"
+#include "hexpoint.cuh"
 #include "precompute.cuh"
 
 namespace fedfem {
@@ -65,42 +66,10 @@ __global__ void k_elem_hex(ElemArgs a)
             const bool is_c = q == 8;
             const double xi = is_c ? 0.0 : g * c_hex_sign[q][0], et = is_c ? 0.0 : g * c_hex_sign[q][1],
                          ze = is_c ? 0.0 : g * c_hex_sign[q][2];
-            double dN[8][3], N[8];
-            for (int i = 0; i < 8; ++i) {
-                const double sx = c_hex_sign[i][0], sy = c_hex_sign[i][1], sz = c_hex_sign[i][2];
-                const double a0 = 1.0 + sx * xi, b0 = 1.0 + sy * et, c0 = 1.0 + sz * ze;
-                N[i] = 0.125 * a0 * b0 * c0;
-                dN[i][0] = 0.125 * sx * b0 * c0;
-                dN[i][1] = 0.125 * sy * a0 * c0;
-                dN[i][2] = 0.125 * sz * a0 * b0;
-            }
-            // Jacobian J[r][s] = d x_r / d xi_s
-            double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-            for (int i = 0; i < 8; ++i)
-                for (int r = 0; r < 3; ++r)
-                    for (int s = 0; s < 3; ++s) J[r][s] = fma(x[i][r], dN[i][s], J[r][s]);
-            // cofactors: inv(J) = adj(J) / det
-            const double C00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-            const double C01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-            const double C02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-            const double det = J[0][0] * C00 + J[0][1] * C01 + J[0][2] * C02;
-            if (!(det > 0.0)) {
+            double N[8], B[8][3], det;
+            if (!hex_point(x, xi, et, ze, N, B, det)) {
                 bad = true;
                 break;
-            }
-            const double C10 = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-            const double C11 = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-            const double C12 = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-            const double C20 = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-            const double C21 = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-            const double C22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-            // grad_x N = J^{-T} grad_xi N: (grad_x N)_r = sum_s C[r][s] dN_s / det
-            const double id = 1.0 / det;
-            double B[8][3];
-            for (int i = 0; i < 8; ++i) {
-                B[i][0] = (C00 * dN[i][0] + C01 * dN[i][1] + C02 * dN[i][2]) * id;
-                B[i][1] = (C10 * dN[i][0] + C11 * dN[i][1] + C12 * dN[i][2]) * id;
-                B[i][2] = (C20 * dN[i][0] + C21 * dN[i][1] + C22 * dN[i][2]) * id;
             }
             const bool add_K = centre ? is_c : true;
             const double wk = is_c ? 8.0 * det : det;
@@ -110,7 +79,12 @@ __global__ void k_elem_hex(ElemArgs a)
                 const double kb1 = k[3] * B[i][0] + k[4] * B[i][1] + k[5] * B[i][2];
                 const double kb2 = k[6] * B[i][0] + k[7] * B[i][1] + k[8] * B[i][2];
                 if (add_K)
-                    for (int j = i + 1; j < 8; ++j) K[p++] += wk * (B[j][0] * kb0 + B[j][1] * kb1 + B[j][2] * kb2);
+                    for (int j = i + 1; j < 8; ++j) {
+                        const double t = wk * (B[j][0] * kb0 + B[j][1] * kb1 + B[j][2] * kb2);
+                        // the point's own pair conductances (conductivity evaluated at the points)
+                        if (a.cond_qp && !is_c) a.cond_qp[(8 * e + q) * 28 + p] = -t;
+                        K[p++] += t;
+                    }
                 if (!is_c) w[i] += det * N[i];
             }
         }

@@ -21,6 +21,7 @@ struct ElemArgs {
     double *cond64;             // [ne][n_pairs] FP64 copy
     double *W;                  // [ne][npe] int_e N_i dV
     int quad;                   // hexahedron conduction matrix: 8 = 2x2x2 Gauss, 1 = centre point
+    double *cond_qp;            // [ne][8][28] pair conductances of each 2x2x2 point, or NULL
     int32_t *err;
     unsigned long long *bad_elem;
 };

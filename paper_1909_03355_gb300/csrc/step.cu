@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include "fedfem_internal.h"
+#include "update.cuh"
 
 namespace fedfem {
 
@@ -432,21 +433,6 @@ __device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int la
     for (int k = 0; k < NPE; ++k) F[k] *= fk;
 }
 
-// Physical constants of the step in the working precision (converted once per launch).
-template <typename R>
-struct Phys {
-    R k_lin, c_lin, h, T_inf, eps_sigma, T_amb, T_zero, T_guard, k_a, c_a;
-    R qs, qs_prev;  // external-load multiplier of this step and of the previous one
-    R dD, dD_prev;  // change of the prescribed temperatures over this step and the previous one
-    Phys() = default;
-    __device__ explicit Phys(const PhysParams &p)
-        : k_lin((R)p.k_lin), c_lin((R)p.c_lin), h((R)p.h), T_inf((R)p.T_inf), eps_sigma((R)p.eps_sigma),
-          T_amb((R)p.T_amb), T_zero((R)p.T_zero), T_guard((R)p.T_guard), k_a((R)p.k_a), c_a((R)p.c_a), qs((R)1),
-          qs_prev((R)1), dD((R)0), dD_prev((R)0)
-    {
-    }
-};
-
 // Time-dependent loads of global step n: the load multiplier of steps n and n - 1 (the halo
 // nodes are finished for step n - 1), the convection ambient temperature of step n and the
 // changes d(n + 1) - d(n), d(n) - d(n - 1) of the prescribed-temperature offset d (formed in
@@ -469,24 +455,6 @@ __device__ __forceinline__ void apply_schedule(Phys<R> &ph, const StepArgs &a, l
         ph.dD_prev = (R)(a.sched_Tdir[i] - a.sched_Tdir[ip]);
     }
 }
-
-// A_i = dt / C0_i: FP64 in the FP64 form; in the FP32 form the FP64 value is kept as an
-// unevaluated pair of floats (hi + lo, 48 significant bits) and A q is formed with one FMA and
-// rounded once.  Dirichlet nodes carry A = -0.0 (dir() reads the sign bit).
-template <typename R>
-struct ACoef;
-template <>
-struct ACoef<float> {
-    float2 v;
-    __device__ __forceinline__ float mul(float q) const { return fmaf(v.x, q, v.y * q); }
-    __device__ __forceinline__ bool dir() const { return (__float_as_uint(v.x) >> 31) != 0u; }
-};
-template <>
-struct ACoef<double> {
-    double v;
-    __device__ __forceinline__ double mul(double q) const { return v * q; }
-    __device__ __forceinline__ bool dir() const { return __double_as_longlong(v) < 0; }
-};
 
 template <typename R>
 __device__ __forceinline__ ACoef<R> load_A(const StepArgs &a, int g);
@@ -561,39 +529,6 @@ template <>
 __device__ __forceinline__ const HingeLaw<double> &law_c<double>(const StepArgs &a)
 {
     return a.tc64;
-}
-
-// Explicit nodal update (Eq. 16): T' = T + A / f_c(T) (Q - F), Kahan-compensated in FP32; a
-// Dirichlet node moves by dD, the change of its prescribed value over the step.  f_c is the
-// linear law of ph or (TAB) the table tc.
-template <typename R, bool KAHAN, bool TAB>
-__device__ __forceinline__ R node_update(R T, float comp, ACoef<R> A, R Q, R F, R dD, const Phys<R> &ph,
-                                         const HingeLaw<R> &tc, float &comp_out, int32_t *err)
-{
-    const R fc = TAB ? hinge_value(tc, T) : ph.c_a + ph.c_lin * T;
-    const R inc = A.dir() ? dD : A.mul((Q - F) / fc);
-    R Tn;
-    if constexpr (KAHAN) {
-        const float y = inc - comp;
-        const float t = T + y;
-        comp_out = (t - T) - y;
-        Tn = t;
-    } else {
-        Tn = T + inc;
-        comp_out = 0.0f;
-    }
-    if (!(fabs(Tn) <= ph.T_guard)) atomicOr(err, ERRBIT_DIVERGED);
-    return Tn;
-}
-
-// Convection + radiation outflow of a boundary node (Eq. 4 and Eq. 7 lumped to the node);
-// the quartic difference is evaluated as (a-b)(a+b)(a^2+b^2).
-template <typename R>
-__device__ __forceinline__ R surface_outflow(R T, R Ac, R Ar, const Phys<R> &ph)
-{
-    const R u = T - ph.T_zero, b = ph.T_amb - ph.T_zero;
-    const R rad = ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
-    return Ac * ph.h * (T - ph.T_inf) + Ar * rad;
 }
 
 // Operands of the update of one halo node: T^{n-1}, its compensation, A, Q and the first four
@@ -721,6 +656,15 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
     }
 
     // ---------------------------------------------------------------- consumers
+    // Staggered start: CTAs that begin a launch in lockstep stream their elements at the same
+    // time and then leave DRAM idle together in their node phases; delaying CTA b by
+    // stagger * b / grid (at most a few tens of us, once per launch) spreads the phases from the
+    // first step on.  The producer warp starts at once and fills the ring meanwhile.
+    if (a.stagger_ns > 0) {
+        const long long dl = a.stagger_ns * (long long)blockIdx.x / (long long)gridDim.x;
+        const unsigned long long d0 = global_ns();
+        while ((long long)(global_ns() - d0) < dl) __nanosleep(256);
+    }
     const R *Qext = reinterpret_cast<const R *>(a.Qext);
     const R *Ac = reinterpret_cast<const R *>(a.Ac);
     const R *Ar = reinterpret_cast<const R *>(a.Ar);

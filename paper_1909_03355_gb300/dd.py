@@ -43,6 +43,8 @@ class FedFemDD:
         keep = []
         mesh, mats, bcs = problem_structs(problem, keep)
         plan.setdefault("quadrature", getattr(problem, "quadrature", 8))
+        plan.setdefault("kT_eval", getattr(problem, "kT_eval", 0))
+        plan.setdefault("face_quadrature", getattr(problem, "face_quadrature", 0))
         self.opt = make_options(precision=precision, kahan=kahan, stream=_stream_handle(stream), **plan)
         h = C.c_void_p()
         rc = self.L.fedfem_dd_create(C.byref(mesh), mats, len(problem.mats), C.byref(bcs), C.byref(self.opt),

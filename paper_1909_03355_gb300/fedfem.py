@@ -59,7 +59,8 @@ def problem_structs(p, keep):
 
 def make_options(precision=32, kahan=True, scatter=0, block=0, steps_per_launch=0, ctas_per_sm=0,
                  tiles_per_cta=0, stages=0, chunk=0, l2_policy=0, barrier_timeout_s=1.0, T_guard=1e6, stream=None, device=-1,
-                 verbose=False, debug_withhold_barrier=0, quadrature=0):
+                 verbose=False, debug_withhold_barrier=0, quadrature=0, kT_eval=0, face_quadrature=0,
+                 start_stagger_us=0.0):
     L = capi.load()
     o = capi.Options()
     L.fedfem_default_options(C.byref(o))
@@ -80,6 +81,9 @@ def make_options(precision=32, kahan=True, scatter=0, block=0, steps_per_launch=
     o.verbose = 1 if verbose else 0
     o.debug_withhold_barrier = debug_withhold_barrier
     o.quadrature = quadrature
+    o.kT_eval = kT_eval
+    o.face_quadrature = face_quadrature
+    o.start_stagger_us = start_stagger_us
     return o
 
 
@@ -118,6 +122,8 @@ class FedFem:
         keep = []
         mesh, mats, bcs = problem_structs(problem, keep)
         plan.setdefault("quadrature", getattr(problem, "quadrature", 8))
+        plan.setdefault("kT_eval", getattr(problem, "kT_eval", 0))
+        plan.setdefault("face_quadrature", getattr(problem, "face_quadrature", 0))
         self.opt = make_options(precision=precision, kahan=kahan, stream=_stream_handle(stream), **plan)
         h = C.c_void_p()
         st = self.L.fedfem_create(C.byref(mesh), mats, len(problem.mats), C.byref(bcs), C.byref(self.opt),
@@ -242,6 +248,13 @@ class FedFem:
         k, s = _f64(kscale), _f64(source)
         self._ck(self.L.fedfem_set_params(self.h, _ptr(k), _ptr(s)))
 
+    def set_params_device(self, kscale=None, source=None):
+        """Per-element conductivity scales / sources from contiguous FP64 CUDA tensors."""
+        for t in (kscale, source):
+            assert t is None or (t.is_cuda and t.dtype.itemsize == 8 and t.is_contiguous() and t.numel() == self.n_elems)
+        self._ck(self.L.fedfem_set_params_device(self.h, None if kscale is None else kscale.data_ptr(),
+                                                 None if source is None else source.data_ptr()))
+
     def get_state(self):
         n = C.c_size_t()
         self._ck(self.L.fedfem_state_bytes(self.h, C.byref(n)))
@@ -259,6 +272,22 @@ class FedFem:
         self._ck(self.L.fedfem_forward_record(self.h, int(n_steps), _ptr(s), len(s), int(sample_every),
                                               int(ckpt_every), _ptr(trace)))
         return trace
+
+    def forward_record_device(self, n_steps, sensors, sample_every, ckpt_every, trace):
+        """forward_record with the trace written into a contiguous FP64 CUDA tensor
+        [n_steps / sample_every, n_sensors]."""
+        s = _i32(sensors)
+        assert trace.is_cuda and trace.is_contiguous() and trace.numel() == (n_steps // sample_every) * len(s)
+        self._ck(self.L.fedfem_forward_record_device(self.h, int(n_steps), _ptr(s), len(s), int(sample_every),
+                                                     int(ckpt_every), trace.data_ptr()))
+        return trace
+
+    def adjoint_device(self, dL_dtrace, dL_dkscale, dL_dsource):
+        """adjoint with contiguous FP64 CUDA tensors in and out."""
+        for t in (dL_dtrace, dL_dkscale, dL_dsource):
+            assert t.is_cuda and t.is_contiguous() and t.dtype.itemsize == 8
+        self._ck(self.L.fedfem_adjoint_device(self.h, dL_dtrace.data_ptr(), dL_dkscale.data_ptr(),
+                                              dL_dsource.data_ptr()))
 
     def adjoint(self, dL_dtrace):
         g = _f64(dL_dtrace)

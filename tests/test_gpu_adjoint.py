@@ -166,3 +166,41 @@ def test_inverse_problem_full_size(precision):
     assert np.max(np.abs(gt - gt_o)) <= tol * np.max(np.abs(gt_o))
     assert np.max(np.abs(gs - gs_o)) <= tol * np.max(np.abs(gs_o))
     f.close()
+
+
+def test_device_entry_points_match_host_ones():
+    """set_params / forward_record / adjoint with CUDA tensors give bitwise the host entry
+    points' results; a non-positive conductivity scale on the device is refused."""
+    import torch
+
+    from paper_1909_03355_gb300.capi import FedFemError
+    p, sensors = small_setup("hex", 5)
+    f = FedFem(p, precision=64)
+    dt = 0.9 * f.precompute()
+    f.set_dt(dt)
+    rng = np.random.default_rng(12)
+    th = np.exp(0.2 * rng.standard_normal(p.n_elems))
+    src = rng.uniform(0, 1e5, p.n_elems)
+    w = rng.standard_normal((6, len(sensors)))
+    f.set_params(th, src)
+    f.set_T(p.initial_T())
+    tr_h = f.forward_record(60, sensors, 10, 20)
+    gk_h, gs_h = f.adjoint(w)
+    dev = torch.device("cuda")
+    f.set_params(np.ones(p.n_elems), np.zeros(p.n_elems))
+    f.set_params_device(torch.tensor(th, device=dev), torch.tensor(src, device=dev))
+    f.set_T_device(torch.tensor(p.initial_T(), device=dev))
+    tr_d = torch.empty((6, len(sensors)), dtype=torch.float64, device=dev)
+    f.forward_record_device(60, sensors, 10, 20, tr_d)
+    gk_d = torch.empty(p.n_elems, dtype=torch.float64, device=dev)
+    gs_d = torch.empty_like(gk_d)
+    f.adjoint_device(torch.tensor(w, device=dev), gk_d, gs_d)
+    assert np.array_equal(tr_d.cpu().numpy(), tr_h)
+    assert np.array_equal(gk_d.cpu().numpy(), gk_h)
+    assert np.array_equal(gs_d.cpu().numpy(), gs_h)
+    bad = torch.tensor(th, device=dev)
+    bad[7] = -1.0
+    with pytest.raises(FedFemError) as ei:
+        f.set_params_device(bad, None)
+    assert ei.value.name == "ERR_ARG"
+    f.close()
