@@ -143,10 +143,14 @@ typedef struct {
                                    the domain decomposition then return FEDFEM_ERR_UNSUPPORTED */
     int32_t reserved2;
     double start_stagger_us;    /* staggered start of the persistent launch (launches of >= 8 steps):
-                                   the consumers of CTA b begin stagger * b / grid us late, which
-                                   spreads the CTAs' element and node phases in time from the first
-                                   step.  0 = auto (half the time of one step's element stream at
-                                   6.5 TB/s, at most 50 us), < 0 = off, > 0 = this many us */
+                                   the consumers of CTA b begin stagger * b / grid us late (at most
+                                   1000 us), which spreads the CTAs' element and node phases in time
+                                   from the first step.  <= 0 = off (default) */
+    int32_t energy_audit;       /* 1: the step kernel also accumulates, in FP64, the stored-heat
+                                   change and the boundary input of every step (an instantiation
+                                   of the kernel with the extra work; colour scatter, linear laws,
+                                   FP32 + Kahan or FP64); read by fedfem_energy_totals.  0 = off */
+    int32_t reserved3;
 } fedfem_options;
 
 /* Fill *opt with defaults (FP32 + Kahan, colour scatter, automatic launch plan). */
@@ -321,6 +325,17 @@ fedfem_status fedfem_adjoint(fedfem_ctx *ctx, const double *dL_dtrace, double *d
  * passes; otherwise the passes are separate launches (same results). */
 fedfem_status fedfem_adjoint_device(fedfem_ctx *ctx, const double *dL_dtrace_dev, double *dL_dkscale_dev,
                                     double *dL_dsource_dev);
+
+/*
+ * Cumulative energy balance since the last fedfem_set_T / fedfem_set_T_device / fedfem_set_state
+ * (contexts created with energy_audit = 1): the sums over all steps taken since then of the
+ * stored-heat change sum_free C0_i f_c(T_i^n) (T_i^{n+1} - T_i^n) and of the boundary input
+ * dt (sum_free Q_i^n + sum_Dirichlet F_i^n), both accumulated in FP64 by the step kernel from the
+ * working-precision state (values with their Kahan compensation) and loads; n_steps = steps
+ * summed.  Energy conservation of the scheme (the internal loads sum to zero) makes the two
+ * equal up to rounding.  Synchronises the stream.  Errors: UNSUPPORTED (no audit), CUDA.
+ */
+fedfem_status fedfem_energy_totals(fedfem_ctx *ctx, double *stored_change, double *boundary_in, int64_t *n_steps);
 
 /* Physical constants of the energy-balance terms (the context's values for fedfem_energy). */
 typedef struct {

@@ -44,7 +44,8 @@ class Options(C.Structure):
                 ("steps_per_launch", I32), ("ctas_per_sm", I32), ("tiles_per_cta", I32), ("stages", I32),
                 ("chunk", I32), ("l2_policy", I32), ("barrier_timeout_s", F64), ("T_guard", F64), ("stream", P), ("device", I32),
                 ("verbose", I32), ("debug_withhold_barrier", I32), ("quadrature", I32), ("kT_eval", I32),
-                ("face_quadrature", I32), ("reserved2", I32), ("start_stagger_us", F64)]
+                ("face_quadrature", I32), ("reserved2", I32), ("start_stagger_us", F64), ("energy_audit", I32),
+                ("reserved3", I32)]
 
 
 class Info(C.Structure):
@@ -90,6 +91,7 @@ SIGNATURES = {
     "fedfem_get_T_device": (I32, [P, P]),
     "fedfem_get_step": (I32, [P, P]),
     "fedfem_energy": (I32, [P, P, P]),
+    "fedfem_energy_totals": (I32, [P, P, P, P]),
     "fedfem_internal_loads": (I32, [P, P, P]),
     "fedfem_set_params": (I32, [P, P, P]),
     "fedfem_set_schedule": (I32, [P, I64, P, P, P]),

@@ -10,7 +10,7 @@
 //   G_j = sum_{e∋j} [ f_k,e (c_e mu_e)_j + (mu_e . c_e T_e) f_k'(T_j) / npe ],
 // (f' = k_lin, c_lin for the linear laws; the segment slope, 0 where the end values are held,
 // for tabulated factors)
-//   dL/dtheta_e = -sum_n f_k,e (mu_e . c_e T_e) / theta_e,
+//   dL/dtheta_e = -sum_n f_k,e (mu_e . c_e T_e) / theta_e  (the sum first, then the division),
 //   dL/ds_e     =  sum_{i in e} w_ie sum_n mu_i^n.
 // The forward run keeps checkpoints of the state every K steps; each segment is recomputed
 // (bit-identically: the forward is deterministic) with the per-step state recorded, then swept
@@ -83,33 +83,44 @@ __device__ __forceinline__ void adj_mu_one(int64_t g, const R *Tn, const double 
 
 // Element pass of element e: forward loads F_e = f_k (c T_e) and adjoint loads
 // G_e = f_k (c mu_e) + (mu_e . c T_e) f_k'(T_j) / npe into per-element slots; theta gradient.
-template <int NPE, typename R>
+// P is the precision of the two pair products (FP64 for an FP64 forward run; FP32 for an FP32
+// one, whose states carry FP32 rounding anyway); the rest of the sweep is FP64.
+template <int NPE, typename R, typename P>
 __device__ __forceinline__ void adj_elem_one(int64_t e, const int32_t *gconn, const double *cond64, const R *Tn,
                                              const double *mu, const double *theta, const AdjPhys &ph, double *YF,
                                              double *YG, double *gtheta)
 {
     constexpr int NC = NPE * (NPE - 1) / 2;
-    double T[NPE], m[NPE], cT[NPE], cm[NPE];
+    double T[NPE], m[NPE];
+    P Tp[NPE], mp[NPE], cTp[NPE], cmp[NPE];
     double sum = 0.0;
     for (int k = 0; k < NPE; ++k) {
         const int g = gconn[NPE * e + k];
         T[k] = (double)Tn[g];
         m[k] = __ldcg(mu + g);
+        Tp[k] = (P)T[k];
+        mp[k] = (P)m[k];
         sum += ph.tab ? hinge_value(ph.tk, T[k]) : T[k];
-        cT[k] = 0.0;
-        cm[k] = 0.0;
+        cTp[k] = 0;
+        cmp[k] = 0;
     }
     const double *ce = cond64 + NC * e;
     int p = 0;
     for (int i = 0; i < NPE; ++i)
         for (int j = i + 1; j < NPE; ++j, ++p) {
-            const double gt = ce[p] * (T[i] - T[j]);
-            const double gm = ce[p] * (m[i] - m[j]);
-            cT[i] += gt;
-            cT[j] -= gt;
-            cm[i] += gm;
-            cm[j] -= gm;
+            const P c = (P)ce[p];
+            const P gt = c * (Tp[i] - Tp[j]);
+            const P gm = c * (mp[i] - mp[j]);
+            cTp[i] += gt;
+            cTp[j] -= gt;
+            cmp[i] += gm;
+            cmp[j] -= gm;
         }
+    double cT[NPE], cm[NPE];
+    for (int k = 0; k < NPE; ++k) {
+        cT[k] = (double)cTp[k];
+        cm[k] = (double)cmp[k];
+    }
     const double fk = ph.tab ? sum / NPE : ph.k_a + ph.k_lin * (sum / NPE);
     double mcT = 0.0;
     for (int k = 0; k < NPE; ++k) mcT += m[k] * cT[k];
@@ -117,14 +128,14 @@ __device__ __forceinline__ void adj_elem_one(int64_t e, const int32_t *gconn, co
         YF[NPE * e + k] = fk * cT[k];
         YG[NPE * e + k] = fk * cm[k] + mcT * (ph.tab ? hinge_slope(ph.tk, T[k]) : ph.k_lin) / NPE;
     }
-    gtheta[e] -= fk * mcT / theta[e];
+    gtheta[e] += fk * mcT;  // scaled by -1 / theta_e once, after the sweep
 }
 
 // Node pass of node g: gather F and G in fixed (ascending element) order and form lambda^n.
 // With Tprev (the state one step earlier) the pass also prepares the next reverse step:
 // lambda^n += dL/dT^n at the sensors (dl_next, sensor index per node), mu = A / f_c(T^(n-1))
 // lambda^n written over mu (each thread touches only its node), musum += qs_prev mu.
-template <typename R>
+template <typename R, typename P>
 __device__ __forceinline__ void adj_node_one(int64_t g, int npe, const int32_t *n2e_ptr, const int64_t *n2e,
                                              const double *YF, const double *YG, const R *Tn, const double *lam,
                                              double *mu, const double *A, const double *Qext, const double *Ac,
@@ -144,14 +155,16 @@ __device__ __forceinline__ void adj_node_one(int64_t g, int npe, const int32_t *
     if (isdir[g]) {
         l = lg - G;
     } else {
-        const double t = (double)Tn[g];
-        const double fc = adj_fc(ph, t);
-        const double a = A[g] / fc;
-        const double u = t - ph.T_zero, b = ph.T_amb - ph.T_zero;
-        const double Q = ph.qs * Qext[g] - Ac[g] * ph.h * (t - ph.T_inf) - Ar[g] * ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
-        const double dQ = -Ac[g] * ph.h - Ar[g] * ph.eps_sigma * 4.0 * u * u * u;
-        const double d = -a * adj_dfc(ph, t) / fc * (Q - F);
-        l = lg * (1.0 + d) + __ldcg(mu + g) * dQ - G;
+        // the factors of the recursion in P (FP32 for an FP32 forward run), accumulated in FP64
+        const P t = (P)Tn[g];
+        const P fc = (P)adj_fc(ph, (double)t);
+        const P a = (P)A[g] / fc;
+        const P u = t - (P)ph.T_zero, b = (P)ph.T_amb - (P)ph.T_zero;
+        const P Q = (P)ph.qs * (P)Qext[g] - (P)Ac[g] * (P)ph.h * (t - (P)ph.T_inf) -
+                    (P)Ar[g] * (P)ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
+        const P dQ = -(P)Ac[g] * (P)ph.h - (P)Ar[g] * (P)ph.eps_sigma * (P)4 * u * u * u;
+        const P d = -a * (P)adj_dfc(ph, (double)t) / fc * (Q - (P)F);
+        l = lg * (1.0 + (double)d) + __ldcg(mu + g) * (double)dQ - G;
     }
     if (Tprev) {
         if (dl_next && sens_idx[g] >= 0) l += dl_next[sens_idx[g]];
@@ -175,7 +188,7 @@ __global__ void k_adj_elem(int64_t ne, const int32_t *gconn, const double *cond6
                            const double *theta, AdjPhys ph, double *YF, double *YG, double *gtheta)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x)
-        adj_elem_one<NPE, R>(e, gconn, cond64, Tn, mu, theta, ph, YF, YG, gtheta);
+        adj_elem_one<NPE, R, R>(e, gconn, cond64, Tn, mu, theta, ph, YF, YG, gtheta);
 }
 
 template <typename R>
@@ -186,8 +199,8 @@ __global__ void k_adj_node(int64_t nn, int npe, const int32_t *n2e_ptr, const in
                            double qs_prev, double *musum)
 {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x)
-        adj_node_one<R>(g, npe, n2e_ptr, n2e, YF, YG, Tn, lam, mu, A, Qext, Ac, Ar, isdir, ph, lam_out, Tprev,
-                        sens_idx, dl_next, qs_prev, musum);
+        adj_node_one<R, R>(g, npe, n2e_ptr, n2e, YF, YG, Tn, lam, mu, A, Qext, Ac, Ar, isdir, ph, lam_out, Tprev,
+                           sens_idx, dl_next, qs_prev, musum);
 }
 
 // Grid-wide barrier of a cooperative launch (all blocks co-resident): a generation counter
@@ -282,14 +295,14 @@ __global__ void __launch_bounds__(128) k_adj_segment(AdjSegArgs a, AdjPhys ph)
             if (!adj_grid_barrier(a.bar_count, a.bar_gen, a.err, a.timeout_ns)) return;
         }
         for (int64_t e = tid0; e < a.ne; e += stride)
-            adj_elem_one<NPE, R>(e, a.gconn, a.cond64, Tn, a.mu, a.theta, ph, a.YF, a.YG, a.gth);
+            adj_elem_one<NPE, R, R>(e, a.gconn, a.cond64, Tn, a.mu, a.theta, ph, a.YF, a.YG, a.gth);
         if (!adj_grid_barrier(a.bar_count, a.bar_gen, a.err, a.timeout_ns)) return;
         const R *Tprev = s > 0 ? rec + (size_t)(s - 1) * a.nn : nullptr;
         const double *dl_next = (s > 0 && (rel - 1) % a.se == 0) ? a.dl + ((rel - 1) / a.se - 1) * a.ns : nullptr;
         const double qs_prev = s > 0 ? a.step_qs[ri - 1] : 0.0;
         for (int64_t g = tid0; g < a.nn; g += stride)
-            adj_node_one<R>(g, NPE, a.n2e_ptr, a.n2e, a.YF, a.YG, Tn, lam[cur], a.mu, a.A, a.Qext, a.Ac, a.Ar, a.isdir,
-                            ph, lam[cur ^ 1], Tprev, a.sens_idx, dl_next, qs_prev, a.musum);
+            adj_node_one<R, R>(g, NPE, a.n2e_ptr, a.n2e, a.YF, a.YG, Tn, lam[cur], a.mu, a.A, a.Qext, a.Ac, a.Ar,
+                               a.isdir, ph, lam[cur ^ 1], Tprev, a.sens_idx, dl_next, qs_prev, a.musum);
         cur ^= 1;
         if (!adj_grid_barrier(a.bar_count, a.bar_gen, a.err, a.timeout_ns)) return;
     }
@@ -306,6 +319,13 @@ __global__ void k_adj_inject(int ns, const int32_t *sens, const double *dl, doub
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < ns) lam[sens[s]] += dl[s];  // sensors are distinct nodes
+}
+
+// dL/dtheta_e = -(sum over the steps) / theta_e
+__global__ void k_adj_theta(int64_t ne, const double *theta, double *gth)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x)
+        gth[e] = -gth[e] / theta[e];
 }
 
 // dL/ds_e = sum_k w_ek musum[node_k]
@@ -634,6 +654,7 @@ static fedfem_status adjoint_impl(fedfem_ctx *c, const double *dL_dtrace, double
         }
         CKR(cudaGetLastError(), "adjoint sweep");
     }
+    k_adj_theta<<<nblk(ne), 256, 0, c->stream>>>(ne, c->d_kscale, gth);
     if (npe == 8)
         k_adj_source<8><<<nblk(ne), 256, 0, c->stream>>>(ne, c->d_gconn, c->d_W, musum, gs);
     else

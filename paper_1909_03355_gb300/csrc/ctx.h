@@ -89,6 +89,8 @@ struct fedfem_ctx {
     unsigned int *d_tile_done = nullptr;
     uint32_t progress_base = 0;  // tile progress counters at the next launch's start (below 2^31)
     long long stagger_ns = 0;    // start stagger of the last CTA of a launch (launches of >= 8 steps)
+    double *d_energy_acc = nullptr;  // energy audit: per-CTA running sums [grid][2]
+    int64_t energy_steps = 0;        // steps summed there since the last set_T / set_state
     fedfem::PhysParams *d_phys = nullptr;
     int32_t *d_cta_tile = nullptr;  // NULL: tiles_per_cta consecutive tiles per CTA
     void *d_T[2] = {nullptr, nullptr};

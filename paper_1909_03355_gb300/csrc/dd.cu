@@ -159,8 +159,9 @@ extern "C" fedfem_status fedfem_dd_create(const fedfem_mesh *mesh, const fedfem_
     fedfem_options o;
     fedfem_default_options(&o);
     if (opt) o = *opt;
-    if (o.kT_eval || o.face_quadrature) {
-        g_dd_create_error = "the decomposed mesh runs the persistent kernel only: kT_eval and face_quadrature must be 0";
+    if (o.kT_eval || o.face_quadrature || o.energy_audit) {
+        g_dd_create_error = "the decomposed mesh runs the persistent kernel without the energy audit: kT_eval, "
+                            "face_quadrature and energy_audit must be 0";
         delete d;
         return FEDFEM_ERR_UNSUPPORTED;
     }

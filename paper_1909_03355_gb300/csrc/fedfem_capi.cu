@@ -225,15 +225,8 @@ static fedfem_status make_plan(fedfem_ctx *c, const std::vector<uint8_t> &is_bnd
             c->smem = smem;
             c->chunk_bytes = cb;
             c->ts_cap = step_ts_cap(c->precision, c->til.max_local);
-            // start stagger: half of the time one step's element stream takes at 6.5 TB/s,
-            // at most 50 us (option: > 0 given in us, < 0 off)
-            {
-                const double stream_us = (double)c->til.n_chunks * cb / 6.5e12 * 1e6;
-                const double us = c->opt.start_stagger_us > 0 ? c->opt.start_stagger_us
-                                  : c->opt.start_stagger_us < 0 ? 0.0
-                                                                : std::min(50.0, 0.5 * stream_us);
-                c->stagger_ns = (long long)(us * 1e3);
-            }
+            // start stagger (off unless given: measured neutral on the 128^3 cube)
+            c->stagger_ns = c->opt.start_stagger_us > 0 ? (long long)(std::min(c->opt.start_stagger_us, 1000.0) * 1e3) : 0;
             if (c->opt.verbose)
                 std::fprintf(stderr,
                              "fedfem plan: tiles=%d grid=%d block=%d chunk=%d stages=%d tpc=%d max_local=%d "
@@ -330,6 +323,12 @@ fedfem_status create_ctx(const fedfem_mesh *mesh, const fedfem_material *mats, i
     }
     c->kT_qp = o.kT_eval;
     c->face_cons = o.face_quadrature;
+    if (o.energy_audit && (o.kT_eval || o.face_quadrature || group_elem || o.scatter == FEDFEM_SCATTER_ATOMIC ||
+                           (o.precision == 32 && !o.kahan))) {
+        err = "energy_audit needs the persistent kernel with colour scatter and FP32 + Kahan or FP64";
+        delete c;
+        return FEDFEM_ERR_UNSUPPORTED;
+    }
     c->opt = o;
     c->precision = o.precision;
     c->kahan = (o.precision == 32 && o.kahan) ? 1 : 0;
@@ -468,6 +467,10 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
                             c->opt.T_guard, c->k_a(), c->c_a()};
         CK(upload(c, (void **)&c->d_phys, &ph, sizeof(ph)), "upload physics");
         CK(cudaStreamSynchronize(c->stream), "synchronize");
+    }
+    if (c->opt.energy_audit) {
+        CK(dalloc(c, (void **)&c->d_energy_acc, 2 * (size_t)c->grid * 8), "alloc energy sums");
+        CK(cudaMemsetAsync(c->d_energy_acc, 0, 2 * (size_t)c->grid * 8, c->stream), "memset");
     }
     CK(dalloc(c, (void **)&c->d_err, 64), "alloc status");
     CK(cudaMemsetAsync(c->d_err, 0, 64, c->stream), "memset");
@@ -715,6 +718,14 @@ extern "C" fedfem_status fedfem_set_dt(fedfem_ctx *c, double dt, int32_t force)
 // ------------------------------------------------------------------------------------------
 namespace fedfem {
 
+// Energy-audit totals restart (a new initial state).
+fedfem_status reset_energy_totals(fedfem_ctx *c)
+{
+    c->energy_steps = 0;
+    if (c->d_energy_acc) CK(cudaMemsetAsync(c->d_energy_acc, 0, 2 * (size_t)c->grid * 8, c->stream), "memset");
+    return FEDFEM_OK;
+}
+
 // Install a field given in original node order (device FP64) as the state at step 0.
 fedfem_status install_T(fedfem_ctx *c, const double *T0_dev_old)
 {
@@ -726,7 +737,7 @@ fedfem_status install_T(fedfem_ctx *c, const double *T0_dev_old)
     CK(cudaGetLastError(), "set T");
     c->step = 0;
     c->has_T = true;
-    return FEDFEM_OK;
+    return reset_energy_totals(c);
 }
 
 // Current state as FP64 in new node order into dst (device).
@@ -834,6 +845,9 @@ StepArgs step_args(fedfem_ctx *c)
     a.scatter = c->opt.scatter;
     a.withhold = c->opt.debug_withhold_barrier;
     a.timeout_ns = (long long)(c->opt.barrier_timeout_s * 1e9);
+    a.energy_acc = c->d_energy_acc;
+    a.C0 = c->d_C0;
+    a.dt = c->dt;
     return a;
 }
 
@@ -874,6 +888,7 @@ fedfem_status enqueue_steps(fedfem_ctx *c, int64_t n, void *rec, int64_t rec_str
         CK(launch_step(a, c->precision, c->kahan, c->npe, c->n_tab > 0, c->grid, c->block, c->smem, c->ts_cap, c->stream),
            "step launch");
         c->progress_base += (uint32_t)k;
+        if (c->d_energy_acc) c->energy_steps += k;
         c->step += k;
         done += k;
     }
@@ -964,6 +979,26 @@ extern "C" fedfem_status fedfem_internal_loads(fedfem_ctx *c, const double *T_ho
     CK(cudaGetLastError(), "internal loads");
     CK(cudaMemcpyAsync(F_host, c->d_v[3], c->nn * 8, cudaMemcpyDeviceToHost, c->stream), "download");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return FEDFEM_OK;
+}
+
+extern "C" fedfem_status fedfem_energy_totals(fedfem_ctx *c, double *stored_change, double *boundary_in,
+                                              int64_t *n_steps)
+{
+    if (!c || !stored_change || !boundary_in || !n_steps) return c ? fail(c, FEDFEM_ERR_ARG, "NULL output") : FEDFEM_ERR_ARG;
+    if (!c->d_energy_acc) return fail(c, FEDFEM_ERR_UNSUPPORTED, "create the context with energy_audit = 1");
+    std::vector<double> acc(2 * (size_t)c->grid);
+    CK(cudaMemcpyAsync(acc.data(), c->d_energy_acc, acc.size() * 8, cudaMemcpyDeviceToHost, c->stream), "read");
+    const fedfem_status s = check_device(c);
+    if (s != FEDFEM_OK) return s;
+    double S = 0.0, B = 0.0;  // CTA order: deterministic
+    for (int b = 0; b < c->grid; ++b) {
+        S += acc[2 * b];
+        B += acc[2 * b + 1];
+    }
+    *stored_change = S;
+    *boundary_in = B;
+    *n_steps = c->energy_steps;
     return FEDFEM_OK;
 }
 
@@ -1180,6 +1215,10 @@ extern "C" fedfem_status fedfem_set_state(fedfem_ctx *c, const void *buf)
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     c->step = step;
     c->has_T = true;
+    {
+        const fedfem_status es = reset_energy_totals(c);
+        if (es != FEDFEM_OK) return es;
+    }
     return FEDFEM_OK;
 }
 

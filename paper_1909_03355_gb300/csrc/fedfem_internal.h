@@ -136,6 +136,11 @@ struct StepArgs {
     int32_t scatter;
     int32_t withhold;           // test hook: CTA withhold-1 skips its first barrier arrival
     long long stagger_ns;       // consumers of CTA b start the launch stagger_ns * b / grid late
+    // energy audit (non-NULL energy_acc selects the audit instantiation): per-CTA running sums
+    // [grid][2] (stored heat change, boundary input), lumped masses at f_c = 1, the time step
+    double *energy_acc;
+    const double *C0;
+    double dt;
     long long timeout_ns;
     // optional per-step recording of the state (adjoint segments): rec + s*rec_stride
     void *rec;

@@ -573,20 +573,52 @@ __device__ __forceinline__ void halo_load(HaloIn<R> &h, const int4 sh, const R *
 // partials of step n-1.
 template <typename R, bool KAHAN, bool TAB>
 __device__ __forceinline__ R halo_finish(const HaloIn<R> &h, const R *part, const Phys<R> &ph,
-                                         const HingeLaw<R> &tc, float &cn, int32_t *err)
+                                         const HingeLaw<R> &tc, float &cn, int32_t *err, R &F)
 {
-    R F = 0;
+    F = 0;
     F += h.p[0];
     F += h.p[1];
     for (int q = 2; q < h.cnt; ++q) F += ld_cg(part + h.z + q);
     return node_update<R, KAHAN, TAB>(h.T, h.cp, h.A, h.Q * ph.qs_prev, F, ph.dD_prev, ph, tc, cn, err);
 }
 
+// Energy audit (an instantiation of the step kernel): every node update adds, in FP64, the
+// stored-heat change C0_i f_c(T_i) (T_i' - T_i) of a free node (values with their Kahan
+// compensation) and the boundary input dt Q_i (free node) or dt F_i (Dirichlet node), F here
+// including the node's surface outflow, which the surface pass subtracts again as -dt outflow;
+// shared nodes are counted by their owner tile only.  Sums per thread, per CTA at launch end.
+template <bool EN>
+struct EnergyAcc {
+    double S = 0.0, B = 0.0;
+    double c_a = 0.0, c_lin = 0.0;  // capacity law of the current tile's problem (FP64)
+    __device__ __forceinline__ void set_law(const PhysParams *pp)
+    {
+        if constexpr (EN) {
+            c_a = pp->c_a;
+            c_lin = pp->c_lin;
+        }
+    }
+    template <typename R>
+    __device__ __forceinline__ void node(const StepArgs &a, int g, R T, float c, R Tn, float cn, bool dir, R Q, R F)
+    {
+        if constexpr (EN) {
+            const double t0 = (double)T - (double)c, t1 = (double)Tn - (double)cn;
+            if (!dir) S += a.C0[g] * (c_a + c_lin * t0) * (t1 - t0);
+            B += a.dt * (double)(dir ? F : Q);
+        }
+    }
+    template <typename R>
+    __device__ __forceinline__ void outflow(const StepArgs &a, R o)
+    {
+        if constexpr (EN) B -= a.dt * (double)o;
+    }
+};
+
 // Shared-memory layout: [stages][chunk_bytes] ring | MBAR_BYTES of mbarriers (full[S], empty[S],
 // node) | Ts[ts_cap] | Fs[ts_cap].  Threads [0, NC) are consumers; the last warp is the
 // producer of the element ring.  With at most 15 consumer warps + 1 producer warp every SM
 // sub-partition holds at most 4 warps, which leaves 128 registers per thread.
-template <typename R, int NPE, bool KAHAN, int SCATTER, bool TAB>
+template <typename R, int NPE, bool KAHAN, int SCATTER, bool TAB, bool EN>
 __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -670,6 +702,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
     const R *Ar = reinterpret_cast<const R *>(a.Ar);
     const int col_off = a.colour_offset;
 
+    EnergyAcc<EN> en;
     int kc = 0;           // chunks consumed (fits in 32 bits per launch)
     uint32_t tphase = 0;  // phase of the node-load barrier
     bool ok = true;
@@ -687,6 +720,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
             csync(NC);
             const TileInfo &ti = s_ti;
             const Phys<R> &ph = s_ph;
+            en.set_law(a.phys + ti.scenario);
             const int nb = ti.node_begin;
             const int a0 = nb & ~(ALN - 1);
             const int a1 = (nb + ti.n_owned + ALN - 1) & ~(ALN - 1);
@@ -750,10 +784,12 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                         continue;
                     }
                     float cn;
-                    const R v = halo_finish<R, KAHAN, TAB>(hin[u], pprev, ph, law_c<R>(a), cn, a.err);
+                    R Fh;
+                    const R v = halo_finish<R, KAHAN, TAB>(hin[u], pprev, ph, law_c<R>(a), cn, a.err, Fh);
                     if ((sh[u].w >> 16) == 0) {  // owner writes T^n back
                         Tc[sh[u].y] = v;
                         if (KAHAN) a.comp[cur][sh[u].y] = cn;
+                        en.node(a, sh[u].y, hin[u].T, hin[u].cp, v, cn, hin[u].A.dir(), hin[u].Q * ph.qs_prev, Fh);
                     }
                     Hs[sh[u].x] = v;
                 }
@@ -833,7 +869,9 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
             // ---- surface loads of owned boundary nodes
             for (int q = tid; q < ti.bnd_count; q += NC) {
                 const int2 b = a.bnd[ti.bnd_begin + q];
-                Fs[b.x] += surface_outflow<R>(Ts[b.x], Ac[b.y], Ar[b.y], ph);
+                const R o = surface_outflow<R>(Ts[b.x], Ac[b.y], Ar[b.y], ph);
+                Fs[b.x] += o;
+                en.outflow(a, o);
             }
             csync(NC);
             // ---- halo partials (the only data other tiles read after the barrier): entry q is
@@ -878,9 +916,12 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 float cn;
-                                out.v[e] = node_update<R, KAHAN, TAB>(Ts[l + e], KAHAN ? (float)cpv[u].v[e] : 0.0f,
+                                const R Told = Ts[l + e];
+                                out.v[e] = node_update<R, KAHAN, TAB>(Told, KAHAN ? (float)cpv[u].v[e] : 0.0f,
                                                                        Av[u][e], Qv[u].v[e] * ph.qs, Fs[l + e], ph.dD,
                                                                        ph, law_c<R>(a), cn, a.err);
+                                en.node(a, g + e, Told, KAHAN ? (float)cpv[u].v[e] : 0.0f, out.v[e], cn,
+                                        Av[u][e].dir(), Qv[u].v[e] * ph.qs, Fs[l + e]);
                                 cout.v[e] = (R)cn;
                                 Ts[l + e] = out.v[e];  // kept for the next step
                             }
@@ -893,9 +934,11 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                     if (l >= head && l < tail0) continue;
                     const int g = nb + l;
                     float cn;
-                    const R v = node_update<R, KAHAN, TAB>(Ts[l], KAHAN ? ld_cg(a.comp[cur] + g) : 0.0f,
-                                                           load_A<R>(a, g), Qext[g] * ph.qs, Fs[l], ph.dD, ph,
+                    const float c0 = KAHAN ? ld_cg(a.comp[cur] + g) : 0.0f;
+                    const ACoef<R> Ag = load_A<R>(a, g);
+                    const R v = node_update<R, KAHAN, TAB>(Ts[l], c0, Ag, Qext[g] * ph.qs, Fs[l], ph.dD, ph,
                                                            law_c<R>(a), cn, a.err);
+                    en.node(a, g, Ts[l], c0, v, cn, Ag.dir(), Qext[g] * ph.qs, Fs[l]);
                     Tn[g] = v;
                     Ts[l] = v;
                     if (KAHAN) a.comp[nxt][g] = cn;
@@ -928,16 +971,44 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
             const TileInfo ti = a.tiles[t];
             Phys<R> ph(a.phys[ti.scenario]);
             apply_schedule(ph, a, n);  // qs_prev: the loads of step n - 1
+            en.set_law(a.phys + ti.scenario);
             for (int q = tid; q < ti.sh_count; q += NC) {
                 const int4 sh = a.sh[ti.sh_begin + q];
                 if ((sh.w >> 16) != 0) continue;
                 float cn;
                 HaloIn<R> h;
                 halo_load<R, KAHAN>(h, sh, Tp, KAHAN ? a.comp[prv] : nullptr, part, Qext, a);
-                const R v = halo_finish<R, KAHAN, TAB>(h, part, ph, law_c<R>(a), cn, a.err);
+                R Fh;
+                const R v = halo_finish<R, KAHAN, TAB>(h, part, ph, law_c<R>(a), cn, a.err, Fh);
                 Tc[sh.y] = v;
                 if (KAHAN) a.comp[cur][sh.y] = cn;
+                en.node(a, sh.y, h.T, h.cp, v, cn, h.A.dir(), h.Q * ph.qs_prev, Fh);
             }
+        }
+    }
+    if constexpr (EN) {
+        // the CTA's sums in a fixed order: lanes by shuffle, then warps in order; added to the
+        // CTA's own running totals.  The node accumulators (Fs, free after the last update and
+        // 16-byte aligned) hold the per-warp sums, so the audit adds no shared memory.
+        double *e_red = reinterpret_cast<double *>(Fs);
+        double eS = en.S, eB = en.B;
+        for (int o = 16; o > 0; o >>= 1) {
+            eS += __shfl_down_sync(0xffffffffu, eS, o);
+            eB += __shfl_down_sync(0xffffffffu, eB, o);
+        }
+        if (lane32 == 0) {
+            e_red[2 * wid] = eS;
+            e_red[2 * wid + 1] = eB;
+        }
+        csync(NC);
+        if (tid == 0 && ok) {
+            double S = 0.0, B = 0.0;
+            for (int w = 0; w < NW; ++w) {
+                S += e_red[2 * w];
+                B += e_red[2 * w + 1];
+            }
+            a.energy_acc[2 * blockIdx.x] += S;
+            a.energy_acc[2 * blockIdx.x + 1] += B;
         }
     }
 }
@@ -958,8 +1029,19 @@ size_t step_smem_bytes(int precision, int npe, int chunk, int stages, int max_lo
 template <typename R, int NPE, bool KAHAN, int SCATTER>
 static void *kernel_ptr(int table)
 {
-    return table ? (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER, true>
-                 : (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER, false>;
+    return table ? (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER, true, false>
+                 : (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER, false, false>;
+}
+
+// Energy-audit instantiations: colour scatter and the linear laws, FP32 + Kahan or FP64.
+static void *select_energy_kernel(int precision, int kahan, int npe)
+{
+    if (precision == 64)
+        return npe == 8 ? (void *)fed_step_kernel<double, 8, false, FEDFEM_SCATTER_COLOR, false, true>
+                        : (void *)fed_step_kernel<double, 4, false, FEDFEM_SCATTER_COLOR, false, true>;
+    if (!kahan) return nullptr;
+    return npe == 8 ? (void *)fed_step_kernel<float, 8, true, FEDFEM_SCATTER_COLOR, false, true>
+                    : (void *)fed_step_kernel<float, 4, true, FEDFEM_SCATTER_COLOR, false, true>;
 }
 
 static void *select_kernel(int precision, int kahan, int npe, int scatter, int table)
@@ -998,7 +1080,8 @@ cudaError_t prepare_step(int precision, int kahan, int npe, int scatter, int tab
 cudaError_t launch_step(const StepArgs &a, int precision, int kahan, int npe, int table, int grid, int block,
                         size_t smem, int ts_cap, cudaStream_t st)
 {
-    void *k = select_kernel(precision, kahan, npe, a.scatter, table);
+    void *k = a.energy_acc ? select_energy_kernel(precision, kahan, npe) : select_kernel(precision, kahan, npe, a.scatter, table);
+    if (!k) return cudaErrorInvalidValue;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(st, &cs);
     if (e != cudaSuccess) return e;

@@ -60,7 +60,7 @@ def problem_structs(p, keep):
 def make_options(precision=32, kahan=True, scatter=0, block=0, steps_per_launch=0, ctas_per_sm=0,
                  tiles_per_cta=0, stages=0, chunk=0, l2_policy=0, barrier_timeout_s=1.0, T_guard=1e6, stream=None, device=-1,
                  verbose=False, debug_withhold_barrier=0, quadrature=0, kT_eval=0, face_quadrature=0,
-                 start_stagger_us=0.0):
+                 start_stagger_us=0.0, energy_audit=False):
     L = capi.load()
     o = capi.Options()
     L.fedfem_default_options(C.byref(o))
@@ -84,6 +84,7 @@ def make_options(precision=32, kahan=True, scatter=0, block=0, steps_per_launch=
     o.kT_eval = kT_eval
     o.face_quadrature = face_quadrature
     o.start_stagger_us = start_stagger_us
+    o.energy_audit = 1 if energy_audit else 0
     return o
 
 
@@ -237,6 +238,13 @@ class FedFem:
         s, b = C.c_double(), C.c_double()
         self._ck(self.L.fedfem_energy(self.h, C.byref(s), C.byref(b)))
         return s.value, b.value
+
+    def energy_totals(self):
+        """(stored heat change, boundary input, steps) summed since the last set_T (contexts
+        created with energy_audit=True)."""
+        s, b, n = C.c_double(), C.c_double(), C.c_int64()
+        self._ck(self.L.fedfem_energy_totals(self.h, C.byref(s), C.byref(b), C.byref(n)))
+        return s.value, b.value, n.value
 
     def internal_loads(self, T):
         a = _f64(T)
