@@ -51,8 +51,16 @@ typedef enum {
 enum { FEDFEM_FP32 = 32, FEDFEM_FP64 = 64 };
 /* Accumulation of element loads into nodal loads. */
 enum {
-    FEDFEM_SCATTER_COLOR = 0,   /* deterministic: colour phases in shared memory + fixed-order halo sums */
-    FEDFEM_SCATTER_ATOMIC = 1   /* shared-memory atomics (non-deterministic order), measured variant */
+    FEDFEM_SCATTER_COLOR = 0,   /* deterministic (default): colour phases in shared memory +
+                                   fixed-order halo sums; the plan takes the slot gather instead
+                                   when the colour classes pad the tiles to >= 1.5x the chunks
+                                   their elements need and a tile's element loads fit in 48 KB
+                                   of shared memory (many small classes: small tet meshes) */
+    FEDFEM_SCATTER_ATOMIC = 1,  /* shared-memory atomics (non-deterministic order), measured variant */
+    FEDFEM_SCATTER_SLOTS = 2,   /* deterministic slot gather: one class per tile, element loads
+                                   into per-element shared-memory slots, then every node sums its
+                                   slots in ascending order (one barrier instead of one per colour) */
+    FEDFEM_SCATTER_CLASSES = 3  /* deterministic colour phases, never the slot gather */
 };
 
 /* Mesh (Section 2: the domain divided into elements).  nodes_per_elem = 8: trilinear
@@ -105,7 +113,7 @@ typedef struct {
 typedef struct {
     int32_t precision;          /* FEDFEM_FP32 (default) or FEDFEM_FP64                   */
     int32_t kahan;              /* FP32 only: 1 (default) Kahan-compensated T accumulator  */
-    int32_t scatter;            /* FEDFEM_SCATTER_COLOR (default) or FEDFEM_SCATTER_ATOMIC */
+    int32_t scatter;            /* FEDFEM_SCATTER_COLOR (default), _ATOMIC, _SLOTS or _CLASSES */
     int32_t block;              /* consumer threads per CTA (multiple of 32, <= 480; one producer
                                    warp is added), 0 = auto                                  */
     int32_t steps_per_launch;   /* explicit steps fused in one persistent launch, 0 = auto */
@@ -376,7 +384,8 @@ fedfem_status fedfem_energy_terms_noalloc(int64_t n_nodes, const double *T_prev,
 /* Launch plan and sizes chosen by create: a fixed-size record for logging and benchmarks. */
 typedef struct {
     int64_t n_nodes, n_elems;
-    int32_t n_tiles, grid, block, stages, chunk, reserved;
+    int32_t n_tiles, grid, block, stages, chunk, scatter;  /* scatter: the accumulation in use
+                                                            (FEDFEM_SCATTER_COLOR, _ATOMIC, _SLOTS) */
     int32_t steps_per_launch, max_tile_nodes, n_colors_max, smem_bytes;
     int64_t n_shared_nodes, n_halo_slots, elem_bytes;   /* element stream bytes per step */
     double dt, dt_crit;
@@ -389,6 +398,9 @@ fedfem_status fedfem_get_info(fedfem_ctx *ctx, fedfem_info *info);
  * equal element counts) of `chunk`-element chunks (32 or 64), colours every tile and checks
  * every index the kernel would read: tile node ranges, tile-local element ids, halo entries and
  * their partial-load slots, boundary entries, and colour classes whose elements share no node.
+ * single_class = 1 builds the tiles of the slot-gather accumulation instead (one class per
+ * tile, chunks in Morton order) with their gather lists, and checks that every element slot
+ * position is gathered exactly once by the node it belongs to.
  * For checking a mesh before it goes to a GPU, and for host-side tests of the tiling.
  *   mesh: as for fedfem_create (elem_mat and elem_kscale are not used);
  *   boundary_nodes [n_boundary] (nodes with surface loads) or NULL;  stats: out, or NULL.
@@ -401,7 +413,7 @@ typedef struct {
     int64_t n_padding_slots;               /* element slots of the chunks left empty            */
 } fedfem_tiling_stats;
 fedfem_status fedfem_check_tiling(const fedfem_mesh *mesh, int64_t n_boundary, const int32_t *boundary_nodes,
-                                  int32_t n_tiles, int32_t chunk, fedfem_tiling_stats *stats);
+                                  int32_t n_tiles, int32_t chunk, int32_t single_class, fedfem_tiling_stats *stats);
 
 /* Message of the last error on this context ("" if none).  Valid until the next call. */
 const char *fedfem_error_string(fedfem_ctx *ctx);

@@ -20,7 +20,7 @@ OK = 0
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_UNSTABLE", 4: "ERR_DIVERGED", 5: "ERR_TIMEOUT",
           6: "ERR_CUDA", 7: "ERR_OOM", 8: "ERR_STATE", 9: "ERR_UNSUPPORTED"}
 FP32, FP64 = 32, 64
-SCATTER_COLOR, SCATTER_ATOMIC = 0, 1
+SCATTER_COLOR, SCATTER_ATOMIC, SCATTER_SLOTS, SCATTER_CLASSES = 0, 1, 2, 3
 
 
 class Mesh(C.Structure):
@@ -50,7 +50,7 @@ class Options(C.Structure):
 
 class Info(C.Structure):
     _fields_ = [("n_nodes", I64), ("n_elems", I64), ("n_tiles", I32), ("grid", I32), ("block", I32),
-                ("stages", I32), ("chunk", I32), ("reserved", I32), ("steps_per_launch", I32), ("max_tile_nodes", I32), ("n_colors_max", I32),
+                ("stages", I32), ("chunk", I32), ("scatter", I32), ("steps_per_launch", I32), ("max_tile_nodes", I32), ("n_colors_max", I32),
                 ("smem_bytes", I32), ("n_shared_nodes", I64), ("n_halo_slots", I64), ("elem_bytes", I64),
                 ("dt", F64), ("dt_crit", F64)]
 
@@ -105,7 +105,7 @@ SIGNATURES = {
     "fedfem_forward_record_device": (I32, [P, I64, P, I32, I32, I32, P]),
     "fedfem_set_params_device": (I32, [P, P, P]),
     "fedfem_get_info": (I32, [P, P]),
-    "fedfem_check_tiling": (I32, [P, I64, P, I32, I32, P]),
+    "fedfem_check_tiling": (I32, [P, I64, P, I32, I32, I32, P]),
     "fedfem_energy_terms_noalloc": (I32, [I64, P, P, P, P, P, P, P, P, P, P, P]),
     "fedfem_error_string": (C.c_char_p, [P]),
     "fedfem_create_error": (C.c_char_p, []),

@@ -452,7 +452,7 @@ static fedfem_status batch_build(fedfem_batch *b, const fedfem_scenario *sc, int
     }
 
     // ---- capture the whole run in a CUDA graph
-    BCK(prepare_step(c->precision, c->kahan, c->npe, c->opt.scatter, 0, c->smem), "kernel attributes");
+    BCK(prepare_step(c->precision, c->kahan, c->npe, c->scatter_mode, 0, c->smem), "kernel attributes");
     StepArgs a = step_args(c);
     const int64_t spl = c->opt.steps_per_launch > 0 ? c->opt.steps_per_launch : 200;
     // capture on a private stream (the legacy default stream cannot be captured); the graph is

@@ -67,6 +67,7 @@ struct fedfem_ctx {
     }
     fedfem_options opt;
     int precision = 32, kahan = 1;
+    int scatter_mode = 0;  // accumulation the plan chose: FEDFEM_SCATTER_COLOR, _ATOMIC or _SLOTS
 
     std::vector<int64_t> group_elem;  // batched scenarios: element range of each packed mesh
 
@@ -85,6 +86,7 @@ struct fedfem_ctx {
     int32_t *d_sptr = nullptr;
     int2 *d_bnd = nullptr;
     int32_t *d_colptr = nullptr;
+    int32_t *d_gptr = nullptr, *d_gidx = nullptr;  // slot gather lists (single-class tiling)
     int32_t *d_nbr_ptr = nullptr, *d_nbr = nullptr;
     unsigned int *d_tile_done = nullptr;
     uint32_t progress_base = 0;  // tile progress counters at the next launch's start (below 2^31)

@@ -153,6 +153,9 @@ static int default_chunk(int precision, int npe)
     return 32;
 }
 
+// Shared memory for the element-load slots up to which the default plan takes the slot gather.
+static constexpr size_t kSlotBudget = 48 * 1024;
+
 // Deepest element ring the plan tries when the stage count is not given.
 static constexpr int kMaxAutoStages = 16;
 
@@ -182,9 +185,32 @@ static fedfem_status make_plan(fedfem_ctx *c, const std::vector<uint8_t> &is_bnd
         n_tiles = std::min<int64_t>(n_tiles, std::max<int64_t>(1, c->ne / block));
         int grid = (int)((n_tiles + tpc - 1) / tpc);
         std::string e;
+        // accumulation: the slot gather when forced; by default when the colour classes pad
+        // the tiles to at least 1.5 times the chunks their elements need (many small classes:
+        // each class costs a barrier and a padded chunk) and a tile's element loads fit in 48 KB
+        bool slots = c->group_elem.empty() && !c->opt.energy_audit && c->opt.scatter == FEDFEM_SCATTER_SLOTS;
         if (c->group_elem.empty()) {
             e = build_tiling(npe, c->ne, c->nn, c->conn.data(), c->xyz.data(), is_bnd.data(), (int)n_tiles, chunk,
-                             c->til);
+                             c->til, slots);
+            if (e.empty() && !slots && c->opt.scatter == FEDFEM_SCATTER_COLOR && !c->opt.energy_audit) {
+                int64_t need = 0;
+                int max_need = 0;
+                for (const TileInfo &ti : c->til.tiles) {
+                    int64_t m = 0;
+                    for (int u = 0; u < ti.n_chunks; ++u)
+                        for (int l = 0; l < chunk; ++l)
+                            if (c->til.elem_col[(size_t)(ti.chunk_begin + u) * chunk + l] != 0xFF) ++m;
+                    const int nc = (int)((m + chunk - 1) / chunk);
+                    need += nc;
+                    max_need = std::max(max_need, nc);
+                }
+                const size_t rs_ = c->precision == 64 ? 8 : 4;
+                if (2 * (int64_t)c->til.n_chunks >= 3 * need && (size_t)max_need * chunk * npe * rs_ <= kSlotBudget) {
+                    slots = true;
+                    e = build_tiling(npe, c->ne, c->nn, c->conn.data(), c->xyz.data(), is_bnd.data(), (int)n_tiles,
+                                     chunk, c->til, true);
+                }
+            }
         } else {
             // batched scenarios: tiles of about ne / n_tiles elements, never spanning two scenarios
             const int64_t te = std::max<int64_t>(block, (c->ne + n_tiles - 1) / n_tiles);
@@ -195,6 +221,9 @@ static fedfem_status make_plan(fedfem_ctx *c, const std::vector<uint8_t> &is_bnd
                                     per, chunk, c->til);
             grid = (int)std::min<int64_t>(n_ctas, c->til.n_tiles);
         }
+        c->scatter_mode = c->opt.scatter == FEDFEM_SCATTER_ATOMIC ? FEDFEM_SCATTER_ATOMIC
+                          : slots                                 ? FEDFEM_SCATTER_SLOTS
+                                                                  : FEDFEM_SCATTER_COLOR;
         if (!e.empty()) {
             if (e.find("65535") != std::string::npos) {
                 tpc *= 2;
@@ -206,13 +235,14 @@ static fedfem_status make_plan(fedfem_ctx *c, const std::vector<uint8_t> &is_bnd
         if (!e.empty()) return fail(c, FEDFEM_ERR_MESH, "tiling check failed: " + e);
         // fewer stages before smaller tiles, unless the stage count was given
         int st = stages;
-        size_t smem = step_smem_bytes(c->precision, npe, chunk, st, c->til.max_local);
+        const int slot_cap = slots ? c->til.max_chunks * chunk : 0;
+        size_t smem = step_smem_bytes(c->precision, npe, chunk, st, c->til.max_local, slot_cap);
         auto fits = [&](size_t sm) {
             return sm <= (size_t)c->max_smem && step_max_blocks_per_sm(c->precision, c->kahan, npe, block, sm) >= cps;
         };
         while (!c->opt.stages && st > 4 && !fits(smem)) {
             --st;
-            smem = step_smem_bytes(c->precision, npe, chunk, st, c->til.max_local);
+            smem = step_smem_bytes(c->precision, npe, chunk, st, c->til.max_local, slot_cap);
         }
         int nb = 0;
         if (smem <= (size_t)c->max_smem) nb = step_max_blocks_per_sm(c->precision, c->kahan, npe, block, smem);
@@ -311,6 +341,11 @@ fedfem_status create_ctx(const fedfem_mesh *mesh, const fedfem_material *mats, i
         delete c;
         return FEDFEM_ERR_ARG;
     }
+    if (o.scatter < FEDFEM_SCATTER_COLOR || o.scatter > FEDFEM_SCATTER_CLASSES) {
+        err = "scatter must be FEDFEM_SCATTER_COLOR, _ATOMIC, _SLOTS or _CLASSES";
+        delete c;
+        return FEDFEM_ERR_ARG;
+    }
     if ((o.kT_eval != 0 && o.kT_eval != 1) || (o.face_quadrature != 0 && o.face_quadrature != 1)) {
         err = "kT_eval and face_quadrature must be 0 or 1";
         delete c;
@@ -324,6 +359,7 @@ fedfem_status create_ctx(const fedfem_mesh *mesh, const fedfem_material *mats, i
     c->kT_qp = o.kT_eval;
     c->face_cons = o.face_quadrature;
     if (o.energy_audit && (o.kT_eval || o.face_quadrature || group_elem || o.scatter == FEDFEM_SCATTER_ATOMIC ||
+                           o.scatter == FEDFEM_SCATTER_SLOTS ||
                            (o.precision == 32 && !o.kahan))) {
         err = "energy_audit needs the persistent kernel with colour scatter and FP32 + Kahan or FP64";
         delete c;
@@ -428,6 +464,10 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
     CK(upload(c, (void **)&c->d_sptr, T.sptr.data(), T.sptr.size() * sizeof(int32_t)), "upload halo ptr");
     CK(upload(c, (void **)&c->d_bnd, T.bnd.data(), T.bnd.size() * sizeof(int2)), "upload boundary");
     CK(upload(c, (void **)&c->d_colptr, T.colptr.data(), T.colptr.size() * sizeof(int32_t)), "upload colours");
+    if (T.single_class) {
+        CK(upload(c, (void **)&c->d_gptr, T.gptr.data(), T.gptr.size() * sizeof(int32_t)), "upload gather lists");
+        CK(upload(c, (void **)&c->d_gidx, T.gidx.data(), T.gidx.size() * sizeof(int32_t)), "upload gather lists");
+    }
     CK(upload(c, (void **)&c->d_nbr_ptr, T.nbr_ptr.data(), T.nbr_ptr.size() * sizeof(int32_t)), "upload neighbours");
     CK(upload(c, (void **)&c->d_nbr, T.nbr.data(), T.nbr.size() * sizeof(int32_t)), "upload neighbours");
     CK(dalloc(c, (void **)&c->d_tile_done, (T.n_tiles + 16) * sizeof(unsigned int)), "alloc tile progress");
@@ -806,6 +846,8 @@ StepArgs step_args(fedfem_ctx *c)
     a.sptr = c->d_sptr;
     a.bnd = c->d_bnd;
     a.colptr = c->d_colptr;
+    a.gptr = c->d_gptr;
+    a.gidx = c->d_gidx;
     for (int b = 0; b < 2; ++b) {
         a.T[b] = c->d_T[b];
         a.comp[b] = c->d_comp[b];
@@ -842,7 +884,7 @@ StepArgs step_args(fedfem_ctx *c)
         a.tk32 = hinge_law_f32(c->hk);
         a.tc32 = hinge_law_f32(c->hc);
     }
-    a.scatter = c->opt.scatter;
+    a.scatter = c->scatter_mode;
     a.withhold = c->opt.debug_withhold_barrier;
     a.timeout_ns = (long long)(c->opt.barrier_timeout_s * 1e9);
     a.energy_acc = c->d_energy_acc;
@@ -1233,6 +1275,7 @@ extern "C" fedfem_status fedfem_get_info(fedfem_ctx *c, fedfem_info *info)
     info->block = c->block;
     info->stages = c->stages;
     info->chunk = c->chunk;
+    info->scatter = c->scatter_mode;
     info->steps_per_launch = c->opt.steps_per_launch > 0 ? c->opt.steps_per_launch : 200;
     info->max_tile_nodes = c->til.max_local;
     info->n_colors_max = c->til.max_colors;
@@ -1250,7 +1293,8 @@ extern "C" const char *fedfem_error_string(fedfem_ctx *c) { return c ? c->err.c_
 extern "C" const char *fedfem_create_error(void) { return g_create_error.c_str(); }
 
 extern "C" fedfem_status fedfem_check_tiling(const fedfem_mesh *mesh, int64_t n_boundary, const int32_t *boundary_nodes,
-                                             int32_t n_tiles, int32_t chunk, fedfem_tiling_stats *stats)
+                                             int32_t n_tiles, int32_t chunk, int32_t single_class,
+                                             fedfem_tiling_stats *stats)
 {
     g_create_error.clear();
     // the mesh checks of fedfem_create, with a neutral material and no boundary data
@@ -1277,7 +1321,7 @@ extern "C" fedfem_status fedfem_check_tiling(const fedfem_mesh *mesh, int64_t n_
     }
     Tiling T;
     e = build_tiling(mesh->nodes_per_elem, mesh->n_elems, mesh->n_nodes, mesh->conn, mesh->xyz, is_bnd.data(), n_tiles,
-                     chunk, T);
+                     chunk, T, single_class != 0);
     if (e.empty()) e = validate_tiling(T);
     if (!e.empty()) {
         g_create_error = "tiling: " + e;

@@ -35,7 +35,8 @@ struct TileInfo {
     int32_t bnd_begin, bnd_count;    // owned boundary nodes (surface loads)
     int32_t col_begin, n_colors;     // colour classes: chunks colptr[col_begin + c] .. [.. + c + 1]
     int32_t scenario;                // index into the physics table (batched scenarios)
-    int32_t pad0, pad1, pad2;
+    int32_t gp_begin;                // slot gather: the tile's node list offsets start at gptr[gp_begin]
+    int32_t pad1, pad2;
 };
 
 // Physical constants of one problem (one scenario of a batch).
@@ -60,6 +61,12 @@ struct Tiling {
     std::vector<int2> bnd;                         // {local, gid} owned boundary nodes
     std::vector<int32_t> colptr;                   // per tile: first chunk of each colour class
     std::vector<int32_t> nbr_ptr, nbr;             // per tile: tiles sharing a node (CSR)
+    // slot gather (single-class tiles): per tile and local node, the element slots that touch
+    // the node, ascending: gidx[gptr[gp_begin + l] .. gptr[gp_begin + l + 1]) = slot * npe + k
+    // (slot relative to the tile's first chunk)
+    bool single_class = false;
+    int max_chunks = 0;                            // most chunks of one tile
+    std::vector<int32_t> gptr, gidx;
     // incidence (new node ids), ascending element / face order inside each list
     std::vector<int32_t> n2e_ptr;                  // [nn+1]
     std::vector<int64_t> n2e;                      // (e << 3) | k
@@ -67,15 +74,18 @@ struct Tiling {
 
 // Build the tiling.  conn [ne][npe] original ids; is_bnd [nn] (original ids) marks nodes
 // with surface loads.  Returns "" on success, else a message.
+// single_class: one class per tile (no colouring; chunks in Morton order) and the slot gather
+// lists of every tile, for the slot-gather accumulation.
 std::string build_tiling(int npe, int64_t ne, int64_t nn, const int32_t *conn, const double *xyz,
-                         const uint8_t *is_bnd, int n_tiles, int CH, Tiling &out);
+                         const uint8_t *is_bnd, int n_tiles, int CH, Tiling &out, bool single_class = false);
 
 // Tiling of a batch of independent meshes packed one after the other: elements
 // [group_elem[g], group_elem[g+1]) form scenario g and get tiles_per_group[g] tiles of their
 // own (tiles never span scenarios); tiles, chunks and node numbers follow the group order.
 std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *conn, const double *xyz,
                                 const uint8_t *is_bnd, const std::vector<int64_t> &group_elem,
-                                const std::vector<int> &tiles_per_group, int CH, Tiling &out);
+                                const std::vector<int> &tiles_per_group, int CH, Tiling &out,
+                                bool single_class = false);
 
 // Check every index the step kernel will use against its buffers ("" if all in range).
 std::string validate_tiling(const Tiling &T);
@@ -101,6 +111,7 @@ struct StepArgs {
     const int32_t *sptr;
     const int2 *bnd;
     const int32_t *colptr;      // tile-relative chunk offsets of the colour classes
+    const int32_t *gptr, *gidx; // slot gather lists (SCATTER = slots)
     void *T[2];                 // Real [nn]
     float *comp[2];             // [nn] (FP32 + Kahan)
     const double *A;            // [nn] dt / C0 (-0.0 on Dirichlet nodes: the sign bit marks them), FP64 form
@@ -151,7 +162,7 @@ struct StepArgs {
 cudaError_t launch_step(const StepArgs &a, int precision, int kahan, int npe, int table, int grid, int block,
                         size_t smem, int ts_cap, cudaStream_t st);
 cudaError_t prepare_step(int precision, int kahan, int npe, int scatter, int table, size_t smem);
-size_t step_smem_bytes(int precision, int npe, int chunk, int stages, int max_local);
+size_t step_smem_bytes(int precision, int npe, int chunk, int stages, int max_local, int slot_cap = 0);
 int step_ts_cap(int precision, int max_local);
 int step_max_blocks_per_sm(int precision, int kahan, int npe, int block, size_t smem);
 int chunk_bytes_for(int precision, int npe, int CH);

@@ -492,6 +492,14 @@ __device__ __forceinline__ ACoef<double> load_A<double>(const StepArgs &a, int g
     return ACoef<double>{__ldg(a.A + g)};
 }
 
+// Store one element's nodal loads into its slot (slot gather accumulation).
+template <typename R, int NPE>
+__device__ __forceinline__ void store_slot(R *Ys, int slot, const R *F)
+{
+#pragma unroll
+    for (int q = 0; q < NPE; ++q) Ys[slot * NPE + q] = F[q];
+}
+
 // Add one element's nodal loads into the tile accumulators.
 template <typename R, int NPE, int SCATTER>
 __device__ __forceinline__ void add_loads(R *Fs, const R *F, const int *id)
@@ -642,6 +650,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
     volatile int *tag = reinterpret_cast<volatile int *>(tbar + 1);  // chunk index held by each slot
     R *Ts_raw = reinterpret_cast<R *>(smem + (size_t)S * a.chunk_bytes + MBAR_BYTES);
     R *Fs = Ts_raw + ts_cap;
+    R *Ys = Fs + ts_cap;  // slot gather: element load slots of the current tile
 
     const int t0 = a.cta_tile ? a.cta_tile[blockIdx.x] : blockIdx.x * a.tiles_per_cta;
     const int t1 = a.cta_tile ? a.cta_tile[blockIdx.x + 1] : min(t0 + a.tiles_per_cta, a.n_tiles);
@@ -821,10 +830,10 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
             //      atomic variant treats the whole tile as one class and adds with atomics.
             {
                 const int kbase = kc;
-                const int ncls = SCATTER == FEDFEM_SCATTER_ATOMIC ? 1 : ti.n_colors;
+                const int ncls = SCATTER == FEDFEM_SCATTER_COLOR ? ti.n_colors : 1;
                 for (int c = 0; c < ncls; ++c) {
                     int u0 = 0, u1 = ti.n_chunks;
-                    if (SCATTER != FEDFEM_SCATTER_ATOMIC) {
+                    if (SCATTER == FEDFEM_SCATTER_COLOR) {
                         u0 = __ldg(a.colptr + ti.col_begin + c);
                         u1 = __ldg(a.colptr + ti.col_begin + c + 1);
                     }
@@ -844,7 +853,12 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                             element_loads<R, NPE, TAB>(blk, CH, lane32, Ts, ph.k_a, ph.k_lin, law_k<R>(a), F, id);
                             __syncwarp();
                             if (lane32 == 0) mbar_arrive(&empty[slot]);  // stage back to the producer
-                            if (col != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F, id);
+                            if (col != 0xFF) {
+                                if (SCATTER == FEDFEM_SCATTER_SLOTS)
+                                    store_slot<R, NPE>(Ys, u * CH + lane32, F);
+                                else
+                                    add_loads<R, NPE, SCATTER>(Fs, F, id);
+                            }
                         } else {
                             R F0[NPE], F1[NPE];
                             int id0[NPE], id1[NPE];
@@ -854,8 +868,13 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                                                        id1);
                             __syncwarp();
                             if (lane32 == 0) mbar_arrive(&empty[slot]);
-                            if (col0 != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F0, id0);
-                            if (col1 != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F1, id1);
+                            if (SCATTER == FEDFEM_SCATTER_SLOTS) {
+                                if (col0 != 0xFF) store_slot<R, NPE>(Ys, u * CH + lane32, F0);
+                                if (col1 != 0xFF) store_slot<R, NPE>(Ys, u * CH + lane32 + 32, F1);
+                            } else {
+                                if (col0 != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F0, id0);
+                                if (col1 != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F1, id1);
+                            }
                         }
                     }
                     if (csync_or(NC, bad)) {
@@ -866,6 +885,18 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                 kc += ti.n_chunks;
             }
             if (!ok) break;
+            // ---- slot gather: every local node sums the element slots that touch it, in
+            //      ascending slot order (after the class barrier above, all slots are written)
+            if (SCATTER == FEDFEM_SCATTER_SLOTS) {
+                const int32_t *gp = a.gptr + ti.gp_begin;
+                for (int l = tid; l < ti.n_local; l += NC) {
+                    const int q1 = __ldg(gp + l + 1);
+                    R f = 0;
+                    for (int q = __ldg(gp + l); q < q1; ++q) f += Ys[__ldg(a.gidx + q)];
+                    Fs[l] = f;
+                }
+                csync(NC);
+            }
             // ---- surface loads of owned boundary nodes
             for (int q = tid; q < ti.bnd_count; q += NC) {
                 const int2 b = a.bnd[ti.bnd_begin + q];
@@ -1019,11 +1050,11 @@ int step_ts_cap(int precision, int max_local)
     return ((max_local + 2 * aln) + 3) & ~3;
 }
 
-size_t step_smem_bytes(int precision, int npe, int chunk, int stages, int max_local)
+size_t step_smem_bytes(int precision, int npe, int chunk, int stages, int max_local, int slot_cap)
 {
     const size_t rs = precision == 64 ? 8 : 4;
     return (size_t)stages * chunk_bytes_for(precision, npe, chunk) + MBAR_BYTES +
-           2 * (size_t)step_ts_cap(precision, max_local) * rs;
+           2 * (size_t)step_ts_cap(precision, max_local) * rs + (size_t)slot_cap * npe * rs;
 }
 
 template <typename R, int NPE, bool KAHAN, int SCATTER>
@@ -1031,6 +1062,12 @@ static void *kernel_ptr(int table)
 {
     return table ? (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER, true, false>
                  : (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER, false, false>;
+}
+
+template <typename R, int NPE, bool KAHAN>
+static void *slots_kernel_ptr(int table)
+{
+    return kernel_ptr<R, NPE, KAHAN, FEDFEM_SCATTER_SLOTS>(table);
 }
 
 // Energy-audit instantiations: colour scatter and the linear laws, FP32 + Kahan or FP64.
@@ -1047,8 +1084,9 @@ static void *select_energy_kernel(int precision, int kahan, int npe)
 static void *select_kernel(int precision, int kahan, int npe, int scatter, int table)
 {
 #define FEDFEM_SEL(R, N, K)                                                                        \
-    return scatter == FEDFEM_SCATTER_ATOMIC ? kernel_ptr<R, N, K, FEDFEM_SCATTER_ATOMIC>(table)    \
-                                            : kernel_ptr<R, N, K, FEDFEM_SCATTER_COLOR>(table)
+    return scatter == FEDFEM_SCATTER_ATOMIC  ? kernel_ptr<R, N, K, FEDFEM_SCATTER_ATOMIC>(table)   \
+           : scatter == FEDFEM_SCATTER_SLOTS ? slots_kernel_ptr<R, N, K>(table)                    \
+                                             : kernel_ptr<R, N, K, FEDFEM_SCATTER_COLOR>(table)
     if (precision == 64) {
         if (npe == 8) FEDFEM_SEL(double, 8, false);
         FEDFEM_SEL(double, 4, false);

@@ -123,18 +123,19 @@ static bool hex_lattice_parity(int64_t ne, int64_t nn, const int32_t *conn, std:
 }
 
 std::string build_tiling(int npe, int64_t ne, int64_t nn, const int32_t *conn, const double *xyz,
-                         const uint8_t *is_bnd, int n_tiles, int CH, Tiling &T)
+                         const uint8_t *is_bnd, int n_tiles, int CH, Tiling &T, bool single_class)
 {
     if (n_tiles < 1) n_tiles = 1;
     if (n_tiles > ne) n_tiles = (int)std::max<int64_t>(1, ne);
-    return build_tiling_groups(npe, ne, nn, conn, xyz, is_bnd, {0, ne}, {n_tiles}, CH, T);
+    return build_tiling_groups(npe, ne, nn, conn, xyz, is_bnd, {0, ne}, {n_tiles}, CH, T, single_class);
 }
 
 std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *conn, const double *xyz,
                                 const uint8_t *is_bnd, const std::vector<int64_t> &group_elem,
-                                const std::vector<int> &tiles_per_group, int CH, Tiling &T)
+                                const std::vector<int> &tiles_per_group, int CH, Tiling &T, bool single_class)
 {
     T = Tiling();
+    T.single_class = single_class;
     T.npe = npe;
     T.ne = ne;
     T.nn = nn;
@@ -294,9 +295,11 @@ std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *
         // (Culberson: recolouring class by class, classes in reverse order, never needs more
         // colours)
         const int64_t m = tb[t + 1] - tb[t];
-        std::vector<uint8_t> col(m);
-        int ncol_best = 0;
-        {
+        std::vector<uint8_t> col(m, 0);
+        int ncol_best = single_class ? 1 : 0;
+        if (single_class) {
+            T.max_colors = std::max(T.max_colors, 1);
+        } else {
             // raster order of the element centroids quantised to the mean element edge
             std::vector<int64_t> raster(m);
             std::vector<uint8_t> parity(m);  // candidate 8-colouring (validated below)
@@ -441,6 +444,30 @@ std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *
             }
         }
 
+        // slot gather lists: for every local node the slots (and node positions) that touch it,
+        // in ascending slot order
+        if (single_class) {
+            T.max_chunks = std::max(T.max_chunks, ti.n_chunks);
+            ti.gp_begin = (int32_t)T.gptr.size();
+            std::vector<int32_t> cntl(ti.n_local + 1, 0);
+            const int64_t s0 = (int64_t)ti.chunk_begin * CH, s1 = (int64_t)(ti.chunk_begin + ti.n_chunks) * CH;
+            for (int64_t s = s0; s < s1; ++s)
+                if (T.elem_of_slot[s] >= 0)
+                    for (int k = 0; k < npe; ++k) ++cntl[T.lconn[s * npe + k] + 1];
+            if (T.gidx.size() + (size_t)m * npe > (size_t)INT32_MAX) return "too many slot gather entries";
+            const int32_t base = (int32_t)T.gidx.size();
+            for (int32_t l = 0; l < ti.n_local; ++l) cntl[l + 1] += cntl[l];
+            for (int32_t l = 0; l <= ti.n_local; ++l) T.gptr.push_back(base + cntl[l]);
+            T.gidx.resize(T.gidx.size() + (size_t)cntl[ti.n_local]);
+            std::vector<int32_t> fill(cntl.begin(), cntl.end() - 1);
+            for (int64_t s = s0; s < s1; ++s)
+                if (T.elem_of_slot[s] >= 0)
+                    for (int k = 0; k < npe; ++k) {
+                        const int l = T.lconn[s * npe + k];
+                        T.gidx[base + fill[l]++] = (int32_t)((s - s0) * npe + k);
+                    }
+        }
+
         // shared entries: owned-shared then ghosts
         ti.sh_begin = (int32_t)T.sh.size();
         for (int32_t l = ti.n_interior; l < ti.n_local; ++l) {
@@ -501,8 +528,39 @@ std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *
     return "";
 }
 
+// Slot gather lists: every list entry names a filled slot of the tile whose position k is the
+// list's node, the lists of a tile cover each (slot, k) of the tile exactly once.
+static std::string validate_gather(const Tiling &T)
+{
+    for (int t = 0; t < T.n_tiles; ++t) {
+        const TileInfo &ti = T.tiles[t];
+        if (ti.gp_begin < 0 || (size_t)ti.gp_begin + ti.n_local >= T.gptr.size()) return "gather list offsets";
+        const int64_t n_slots = (int64_t)ti.n_chunks * T.CH;
+        std::vector<uint8_t> seen((size_t)n_slots * T.npe, 0);
+        for (int32_t l = 0; l < ti.n_local; ++l) {
+            const int32_t q0 = T.gptr[ti.gp_begin + l], q1 = T.gptr[ti.gp_begin + l + 1];
+            if (q0 > q1 || q0 < 0 || (size_t)q1 > T.gidx.size()) return "gather list range";
+            for (int32_t q = q0; q < q1; ++q) {
+                const int64_t v = T.gidx[q];
+                if (v < 0 || v >= n_slots * T.npe) return "gather entry outside the tile";
+                const int64_t s = (int64_t)ti.chunk_begin * T.CH + v / T.npe;
+                if (T.elem_of_slot[s] < 0) return "gather entry on a padding slot";
+                if (T.lconn[s * T.npe + v % T.npe] != l) return "gather entry of another node";
+                if (seen[v]++) return "gather entry twice";
+            }
+        }
+        for (int64_t v = 0; v < n_slots * T.npe; ++v)
+            if (T.elem_of_slot[(int64_t)ti.chunk_begin * T.CH + v / T.npe] >= 0 && !seen[v]) return "slot not gathered";
+    }
+    return "";
+}
+
 std::string validate_tiling(const Tiling &T)
 {
+    if (T.single_class) {
+        const std::string g = validate_gather(T);
+        if (!g.empty()) return g;
+    }
     const int64_t n_slots = T.sptr.empty() ? 0 : T.sptr.back();
     int32_t chunks = 0;
     for (int t = 0; t < T.n_tiles; ++t) {
@@ -549,8 +607,9 @@ std::string validate_tiling(const Tiling &T)
         }
     }
     // a colour class is a set of elements without a common node: the step kernel adds their
-    // loads into shared memory without atomics
-    {
+    // loads into shared memory without atomics (single-class tiles write per-element slots
+    // instead and need no such class; their gather lists were checked above)
+    if (!T.single_class) {
         std::vector<int64_t> stamp(T.max_local > 0 ? T.max_local : 1, -1);
         int64_t cls = 0;
         for (int t = 0; t < T.n_tiles; ++t) {

@@ -88,7 +88,7 @@ def make_options(precision=32, kahan=True, scatter=0, block=0, steps_per_launch=
     return o
 
 
-def check_tiling(problem, n_tiles, chunk=32):
+def check_tiling(problem, n_tiles, chunk=32, single_class=False):
     """Host-only check of the tiling the step kernel would use for `problem` (no GPU needed):
     returns its statistics, or raises FedFemError with the reason.  The nodes of the problem's
     convection and radiation faces are the boundary nodes, as in fedfem_create."""
@@ -99,7 +99,7 @@ def check_tiling(problem, n_tiles, chunk=32):
     bnd = _i32(np.unique(np.concatenate([np.asarray(f).ravel() for f in faces]))) if faces else None
     st = capi.TilingStats()
     rc = L.fedfem_check_tiling(C.byref(mesh), 0 if bnd is None else len(bnd), _ptr(bnd), int(n_tiles), int(chunk),
-                               C.byref(st))
+                               1 if single_class else 0, C.byref(st))
     if rc != capi.OK:
         raise FedFemError(rc, L.fedfem_create_error().decode())
     return {f: getattr(st, f) for f, _ in capi.TilingStats._fields_}

@@ -51,8 +51,9 @@ def test_audit_totals_match_oracle_and_balance(kind, precision):
     tol = 1e-10 if precision == 64 else 2e-4
     assert S == pytest.approx(S_o, rel=tol) and B == pytest.approx(B_o, rel=tol)
     assert abs(S - B) <= (1e-12 if precision == 64 else 1e-7) * abs(B)
-    # the audit does not change the trajectory: same field as without it
-    g = FedFem(p, precision=precision)
+    # the audit does not change the trajectory: same field as without it (the audit runs with
+    # colour phases, so the comparison run takes them too)
+    g = FedFem(p, precision=precision, scatter=3)
     g.precompute()
     g.set_dt(dt, force=True)
     g.set_T(p.initial_T())

@@ -98,3 +98,33 @@ def test_mixed_element_orientation_still_colours_properly(check):
     p.conn = c
     s = check(p, 8)
     assert s["n_tiles"] == 8 and 8 <= s["n_colors_max"] <= 64
+
+
+@pytest.mark.parametrize("case", ["hex", "hex_jitter", "tet", "paper_cube", "renumbered"])
+@pytest.mark.parametrize("chunk", [32, 64])
+def test_single_class_tiling_and_gather_lists(case, chunk, check):
+    """The slot-gather tiling: one class per tile (padding only in a tile's last chunk), and
+    gather lists that name every filled slot position exactly once, by its own node (checked
+    by the library's validation, which rejects the tiling otherwise)."""
+    if case == "hex":
+        p = fi.nonlinear_cube(9, "hex")
+    elif case == "hex_jitter":
+        p = fi.nonlinear_cube(9, "hex", jitter=0.25)
+    elif case == "tet":
+        p = fi.nonlinear_cube(6, "tet")
+    elif case == "paper_cube":
+        p = fi.paper_cube("tet", 7)
+    else:
+        p = fi.nonlinear_cube(7, "hex")
+        perm = np.random.default_rng(4).permutation(p.n_nodes)
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(p.n_nodes)
+        p.xyz = p.xyz[perm]
+        p.conn = inv[p.conn].astype(np.int32)
+        p.conv_faces = inv[p.conv_faces].astype(np.int32) if p.conv_faces is not None else None
+        p.rad_faces = inv[p.rad_faces].astype(np.int32) if p.rad_faces is not None else None
+    for n_tiles in (1, 5, 23):
+        st = check(p, n_tiles, chunk, single_class=True)
+        assert st["n_colors_max"] == 1
+        # one class per tile: at most one partly filled chunk per tile
+        assert st["n_padding_slots"] < st["n_tiles"] * chunk
