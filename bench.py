@@ -636,13 +636,16 @@ def main():
     peak, peak_kind = peaks()
     tr = traffic_from_profile(src_hash())
 
-    # ---- end to end through the C ABI with host buffers (H2D of T0, D2H of T inside)
+    # ---- end to end through the C ABI with host buffers (H2D of T0, D2H of T inside), both in
+    # pinned host memory
+    T0_pin = torch.from_numpy(np.ascontiguousarray(T0, dtype=np.float64)).pin_memory()
+    Tout_pin = torch.empty(N, dtype=torch.float64, pin_memory=True)
     barrier()
     torch.cuda.synchronize()
     te = time.perf_counter()
-    f.set_T(T0)
+    f.set_T(T0_pin.numpy())
     f.step(K)
-    Tout = f.get_T()
+    Tout = f.get_T(out=Tout_pin.numpy())
     e2e_s = time.perf_counter() - te
     e2e_s = max_over_ranks(e2e_s, world)
     e2e_v = whole_job_rate(E * K, world, e2e_s)
@@ -709,7 +712,10 @@ def main():
         torch.cuda.synchronize()
         free_c = torch.cuda.mem_get_info()[0]
         nn_a, ne_a, npe_a = pi.n_nodes, pi.n_elems, pi.npe
-        sweep_tmp = (trc.size * 8 + 100 * nn_a * 4 + 4 * nn_a * 8 + 2 * ne_a * npe_a * 8 + 2 * ne_a * 8 + nn_a * 4)
+        # FP32 run: dL/dtrace, one segment of states, lambda pair + sum mu (FP64), mu (FP32),
+        # element slots (FP32), two gradients (FP64), sensor map, FP32 conductances
+        sweep_tmp = (trc.size * 8 + 100 * nn_a * 4 + 3 * nn_a * 8 + nn_a * 4 + 2 * ne_a * npe_a * 4 + 2 * ne_a * 8
+                     + nn_a * 4 + ne_a * (npe_a * (npe_a - 1) // 2) * 4)
         adj = {"workload": "inverse_32: 32^3 hex, 2000 FP32 steps, 512 sensors every 10 steps, checkpoints every 100",
                "forward_ms": 1e3 * t_fwd, "adjoint_ms": 1e3 * t_adj, "adjoint_over_forward": t_adj / t_fwd,
                "context_device_MB": (free_a - free_b) / 1e6,
@@ -719,7 +725,8 @@ def main():
                "memory_note": "cudaMemGetInfo deltas (2 MB granularity) for the context after precompute and for "
                               "what forward_record + adjoint keep (checkpoints, trace); the reverse sweep's own "
                               "buffers (one segment of states, lambda pair, mu, sum mu, element F/G slots, two "
-                              "gradients, dL/dtrace, sensor map) are freed on return and counted by size"}
+                              "gradients, dL/dtrace, sensor map, FP32 conductances) are freed on return and "
+                              "counted by size"}
         fa.close()
 
     # ---- batched scenarios: 256 independent cubes (n ~ U{8..48}, steps ~ U{500..5000}) in one
@@ -789,7 +796,7 @@ def main():
                          "avg_launch_ms": avg_launch_ms},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 8 * N / K, "d2h_bytes_per_step": 8 * N / K,
-                    "seconds": e2e_s},
+                    "seconds": e2e_s, "host_buffers": "pinned"},
             "gpu_launches": n_launch,
             "clocks": clk,
             "fp64": {"value": v64, "unit": UNIT, "ms_per_step": ms64 / K64, "steps": K64,

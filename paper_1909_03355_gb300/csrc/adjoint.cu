@@ -14,8 +14,10 @@
 //   dL/ds_e     =  sum_{i in e} w_ie sum_n mu_i^n.
 // The forward run keeps checkpoints of the state every K steps; each segment is recomputed
 // (bit-identically: the forward is deterministic) with the per-step state recorded, then swept
-// backwards.  The reverse sweep runs in FP64 on the recorded states of either forward
-// precision, with fixed-order (deterministic) node gathers.
+// backwards, with fixed-order (deterministic) node gathers.  After an FP64 forward run the
+// sweep is FP64 throughout.  After an FP32 run (whose states carry FP32 rounding) the per-step
+// element and node products, mu and the element slots are FP32, with FP32 conductances; lambda,
+// sum mu and the theta gradient are carried in FP64 from step to step.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,6 +56,19 @@ __device__ __forceinline__ double adj_dfc(const AdjPhys &ph, double t)
     return ph.tab ? hinge_slope(ph.tc, t) : ph.c_lin;
 }
 
+// f_c, f_k and f_k' in precision P (tabulated laws evaluated in FP64, then rounded)
+template <typename P>
+__device__ __forceinline__ P adj_fc_p(const AdjPhys &ph, P t)
+{
+    return ph.tab ? (P)hinge_value(ph.tc, (double)t) : (P)ph.c_a + (P)ph.c_lin * t;
+}
+
+template <typename P>
+__device__ __forceinline__ P adj_dfk_p(const AdjPhys &ph, P t)
+{
+    return ph.tab ? (P)hinge_slope(ph.tk, (double)t) : (P)ph.k_lin;
+}
+
 int nblk(int64_t n, int bs = 256)
 {
     int64_t b = (n + bs - 1) / bs;
@@ -70,65 +85,58 @@ __global__ void k_gather_sensors(int ns, const int32_t *sens, const R *T, const 
     }
 }
 
-// mu_i = a_i lambda_i, a_i = A_i / f_c(T_i) (A = -0.0 on Dirichlet nodes); musum += mu
-template <typename R>
+// mu_i = a_i lambda_i, a_i = A_i / f_c(T_i) (A = -0.0 on Dirichlet nodes); musum += mu.
+// a_i in precision P, the product with lambda and the sum in FP64; mu is stored in P.
+template <typename R, typename P>
 __device__ __forceinline__ void adj_mu_one(int64_t g, const R *Tn, const double *A, const double *lam,
-                                           const AdjPhys &ph, double qs, double *mu, double *musum)
+                                           const AdjPhys &ph, double qs, P *mu, double *musum)
 {
-    const double t = (double)Tn[g];
-    const double m = A[g] / adj_fc(ph, t) * __ldcg(lam + g);
-    mu[g] = m;
+    const P t = (P)Tn[g];
+    const double m = (double)((P)A[g] / adj_fc_p<P>(ph, t)) * __ldcg(lam + g);
+    mu[g] = (P)m;
     musum[g] += qs * m;  // d Q_g / d s_e = qs w_ge
 }
 
 // Element pass of element e: forward loads F_e = f_k (c T_e) and adjoint loads
 // G_e = f_k (c mu_e) + (mu_e . c T_e) f_k'(T_j) / npe into per-element slots; theta gradient.
-// P is the precision of the two pair products (FP64 for an FP64 forward run; FP32 for an FP32
-// one, whose states carry FP32 rounding anyway); the rest of the sweep is FP64.
+// Everything per element is in precision P (FP64 for an FP64 forward run; FP32 for an FP32
+// one, whose states carry FP32 rounding anyway, with FP32 conductances and mu); the theta
+// gradient is accumulated in FP64.
 template <int NPE, typename R, typename P>
-__device__ __forceinline__ void adj_elem_one(int64_t e, const int32_t *gconn, const double *cond64, const R *Tn,
-                                             const double *mu, const double *theta, const AdjPhys &ph, double *YF,
-                                             double *YG, double *gtheta)
+__device__ __forceinline__ void adj_elem_one(int64_t e, const int32_t *gconn, const P *cond, const R *Tn,
+                                             const P *mu, const AdjPhys &ph, P *YF, P *YG, double *gtheta)
 {
     constexpr int NC = NPE * (NPE - 1) / 2;
-    double T[NPE], m[NPE];
-    P Tp[NPE], mp[NPE], cTp[NPE], cmp[NPE];
-    double sum = 0.0;
+    P T[NPE], m[NPE], cT[NPE], cm[NPE];
+    P sum = 0;
     for (int k = 0; k < NPE; ++k) {
         const int g = gconn[NPE * e + k];
-        T[k] = (double)Tn[g];
+        T[k] = (P)Tn[g];
         m[k] = __ldcg(mu + g);
-        Tp[k] = (P)T[k];
-        mp[k] = (P)m[k];
-        sum += ph.tab ? hinge_value(ph.tk, T[k]) : T[k];
-        cTp[k] = 0;
-        cmp[k] = 0;
+        sum += ph.tab ? (P)hinge_value(ph.tk, (double)T[k]) : T[k];
+        cT[k] = 0;
+        cm[k] = 0;
     }
-    const double *ce = cond64 + NC * e;
+    const P *ce = cond + NC * e;
     int p = 0;
     for (int i = 0; i < NPE; ++i)
         for (int j = i + 1; j < NPE; ++j, ++p) {
-            const P c = (P)ce[p];
-            const P gt = c * (Tp[i] - Tp[j]);
-            const P gm = c * (mp[i] - mp[j]);
-            cTp[i] += gt;
-            cTp[j] -= gt;
-            cmp[i] += gm;
-            cmp[j] -= gm;
+            const P c = ce[p];
+            const P gt = c * (T[i] - T[j]);
+            const P gm = c * (m[i] - m[j]);
+            cT[i] += gt;
+            cT[j] -= gt;
+            cm[i] += gm;
+            cm[j] -= gm;
         }
-    double cT[NPE], cm[NPE];
-    for (int k = 0; k < NPE; ++k) {
-        cT[k] = (double)cTp[k];
-        cm[k] = (double)cmp[k];
-    }
-    const double fk = ph.tab ? sum / NPE : ph.k_a + ph.k_lin * (sum / NPE);
-    double mcT = 0.0;
+    const P fk = ph.tab ? sum / NPE : (P)ph.k_a + (P)ph.k_lin * (sum / NPE);
+    P mcT = 0;
     for (int k = 0; k < NPE; ++k) mcT += m[k] * cT[k];
     for (int k = 0; k < NPE; ++k) {
         YF[NPE * e + k] = fk * cT[k];
-        YG[NPE * e + k] = fk * cm[k] + mcT * (ph.tab ? hinge_slope(ph.tk, T[k]) : ph.k_lin) / NPE;
+        YG[NPE * e + k] = fk * cm[k] + mcT * adj_dfk_p<P>(ph, T[k]) / NPE;
     }
-    gtheta[e] += fk * mcT;  // scaled by -1 / theta_e once, after the sweep
+    gtheta[e] += (double)(fk * mcT);  // scaled by -1 / theta_e once, after the sweep
 }
 
 // Node pass of node g: gather F and G in fixed (ascending element) order and form lambda^n.
@@ -137,13 +145,13 @@ __device__ __forceinline__ void adj_elem_one(int64_t e, const int32_t *gconn, co
 // lambda^n written over mu (each thread touches only its node), musum += qs_prev mu.
 template <typename R, typename P>
 __device__ __forceinline__ void adj_node_one(int64_t g, int npe, const int32_t *n2e_ptr, const int64_t *n2e,
-                                             const double *YF, const double *YG, const R *Tn, const double *lam,
-                                             double *mu, const double *A, const double *Qext, const double *Ac,
-                                             const double *Ar, const uint8_t *isdir, const AdjPhys &ph, double *lam_out,
-                                             const R *Tprev, const int32_t *sens_idx, const double *dl_next,
-                                             double qs_prev, double *musum)
+                                             const P *YF, const P *YG, const R *Tn, const double *lam, P *mu,
+                                             const double *A, const double *Qext, const double *Ac, const double *Ar,
+                                             const uint8_t *isdir, const AdjPhys &ph, double *lam_out, const R *Tprev,
+                                             const int32_t *sens_idx, const double *dl_next, double qs_prev,
+                                             double *musum)
 {
-    double F = 0.0, G = 0.0;
+    P F = 0, G = 0;
     for (int q = n2e_ptr[g]; q < n2e_ptr[g + 1]; ++q) {
         const int64_t ek = n2e[q];
         const int64_t s = npe * (ek >> 3) + (ek & 7);
@@ -153,23 +161,23 @@ __device__ __forceinline__ void adj_node_one(int64_t g, int npe, const int32_t *
     const double lg = __ldcg(lam + g);
     double l;
     if (isdir[g]) {
-        l = lg - G;
+        l = lg - (double)G;
     } else {
         // the factors of the recursion in P (FP32 for an FP32 forward run), accumulated in FP64
         const P t = (P)Tn[g];
-        const P fc = (P)adj_fc(ph, (double)t);
+        const P fc = adj_fc_p<P>(ph, t);
         const P a = (P)A[g] / fc;
         const P u = t - (P)ph.T_zero, b = (P)ph.T_amb - (P)ph.T_zero;
         const P Q = (P)ph.qs * (P)Qext[g] - (P)Ac[g] * (P)ph.h * (t - (P)ph.T_inf) -
                     (P)Ar[g] * (P)ph.eps_sigma * ((u - b) * (u + b) * (u * u + b * b));
         const P dQ = -(P)Ac[g] * (P)ph.h - (P)Ar[g] * (P)ph.eps_sigma * (P)4 * u * u * u;
-        const P d = -a * (P)adj_dfc(ph, (double)t) / fc * (Q - (P)F);
-        l = lg * (1.0 + (double)d) + __ldcg(mu + g) * (double)dQ - G;
+        const P d = -a * (P)adj_dfc(ph, (double)t) / fc * (Q - F);
+        l = lg * (1.0 + (double)d) + (double)(__ldcg(mu + g) * dQ) - (double)G;
     }
     if (Tprev) {
         if (dl_next && sens_idx[g] >= 0) l += dl_next[sens_idx[g]];
-        const double m = A[g] / adj_fc(ph, (double)Tprev[g]) * l;
-        mu[g] = m;
+        const double m = (double)((P)A[g] / adj_fc_p<P>(ph, (P)Tprev[g])) * l;
+        mu[g] = (P)m;
         musum[g] += qs_prev * m;
     }
     lam_out[g] = l;
@@ -177,23 +185,23 @@ __device__ __forceinline__ void adj_node_one(int64_t g, int npe, const int32_t *
 
 template <typename R>
 __global__ void k_adj_mu(int64_t nn, const R *Tn, const double *A, const double *lam, AdjPhys ph, double qs,
-                         double *mu, double *musum)
+                         R *mu, double *musum)
 {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x)
-        adj_mu_one<R>(g, Tn, A, lam, ph, qs, mu, musum);
+        adj_mu_one<R, R>(g, Tn, A, lam, ph, qs, mu, musum);
 }
 
 template <int NPE, typename R>
-__global__ void k_adj_elem(int64_t ne, const int32_t *gconn, const double *cond64, const R *Tn, const double *mu,
-                           const double *theta, AdjPhys ph, double *YF, double *YG, double *gtheta)
+__global__ void k_adj_elem(int64_t ne, const int32_t *gconn, const R *cond, const R *Tn, const R *mu, AdjPhys ph,
+                           R *YF, R *YG, double *gtheta)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x)
-        adj_elem_one<NPE, R, R>(e, gconn, cond64, Tn, mu, theta, ph, YF, YG, gtheta);
+        adj_elem_one<NPE, R, R>(e, gconn, cond, Tn, mu, ph, YF, YG, gtheta);
 }
 
 template <typename R>
-__global__ void k_adj_node(int64_t nn, int npe, const int32_t *n2e_ptr, const int64_t *n2e, const double *YF,
-                           const double *YG, const R *Tn, const double *lam, double *mu, const double *A,
+__global__ void k_adj_node(int64_t nn, int npe, const int32_t *n2e_ptr, const int64_t *n2e, const R *YF,
+                           const R *YG, const R *Tn, const double *lam, R *mu, const double *A,
                            const double *Qext, const double *Ac, const double *Ar, const uint8_t *isdir, AdjPhys ph,
                            double *lam_out, const R *Tprev, const int32_t *sens_idx, const double *dl_next,
                            double qs_prev, double *musum)
@@ -262,11 +270,13 @@ struct AdjSegArgs {
     int64_t rel0;                 // record steps before the segment's first state
     const int32_t *gconn, *n2e_ptr, *sens, *sens_idx;
     const int64_t *n2e;
-    const double *cond64, *theta, *A, *Qext, *Ac, *Ar, *dl;
+    const double *A, *Qext, *Ac, *Ar, *dl;
+    const void *cond;             // pair conductances in the forward precision R
     const uint8_t *isdir;
     const void *rec;              // [K][nn] recorded states of the segment
     const double *step_Tinf, *step_qs;  // per recorded step (index: record step)
-    double *lam0, *lam1, *mu, *musum, *YF, *YG, *gth;
+    double *lam0, *lam1, *musum, *gth;
+    void *mu, *YF, *YG;           // in the forward precision R
     unsigned int *bar_count, *bar_gen;
     int32_t *err;
     long long timeout_ns;
@@ -279,6 +289,8 @@ __global__ void __launch_bounds__(128) k_adj_segment(AdjSegArgs a, AdjPhys ph)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const R *rec = static_cast<const R *>(a.rec);
+    const R *cond = static_cast<const R *>(a.cond);
+    R *mu = static_cast<R *>(a.mu), *YF = static_cast<R *>(a.YF), *YG = static_cast<R *>(a.YG);
     double *lam[2] = {a.lam0, a.lam1};
     int cur = a.cur;
     for (int s = a.K - 1; s >= 0; --s) {
@@ -291,21 +303,28 @@ __global__ void __launch_bounds__(128) k_adj_segment(AdjSegArgs a, AdjPhys ph)
             if (rel % a.se == 0)
                 for (int64_t q = tid0; q < a.ns; q += stride) lam[cur][a.sens[q]] += a.dl[(rel / a.se - 1) * a.ns + q];
             if (!adj_grid_barrier(a.bar_count, a.bar_gen, a.err, a.timeout_ns)) return;
-            for (int64_t g = tid0; g < a.nn; g += stride) adj_mu_one<R>(g, Tn, a.A, lam[cur], ph, ph.qs, a.mu, a.musum);
+            for (int64_t g = tid0; g < a.nn; g += stride) adj_mu_one<R, R>(g, Tn, a.A, lam[cur], ph, ph.qs, mu, a.musum);
             if (!adj_grid_barrier(a.bar_count, a.bar_gen, a.err, a.timeout_ns)) return;
         }
         for (int64_t e = tid0; e < a.ne; e += stride)
-            adj_elem_one<NPE, R, R>(e, a.gconn, a.cond64, Tn, a.mu, a.theta, ph, a.YF, a.YG, a.gth);
+            adj_elem_one<NPE, R, R>(e, a.gconn, cond, Tn, mu, ph, YF, YG, a.gth);
         if (!adj_grid_barrier(a.bar_count, a.bar_gen, a.err, a.timeout_ns)) return;
         const R *Tprev = s > 0 ? rec + (size_t)(s - 1) * a.nn : nullptr;
         const double *dl_next = (s > 0 && (rel - 1) % a.se == 0) ? a.dl + ((rel - 1) / a.se - 1) * a.ns : nullptr;
         const double qs_prev = s > 0 ? a.step_qs[ri - 1] : 0.0;
         for (int64_t g = tid0; g < a.nn; g += stride)
-            adj_node_one<R, R>(g, NPE, a.n2e_ptr, a.n2e, a.YF, a.YG, Tn, lam[cur], a.mu, a.A, a.Qext, a.Ac, a.Ar,
+            adj_node_one<R, R>(g, NPE, a.n2e_ptr, a.n2e, YF, YG, Tn, lam[cur], mu, a.A, a.Qext, a.Ac, a.Ar,
                                a.isdir, ph, lam[cur ^ 1], Tprev, a.sens_idx, dl_next, qs_prev, a.musum);
         cur ^= 1;
         if (!adj_grid_barrier(a.bar_count, a.bar_gen, a.err, a.timeout_ns)) return;
     }
+}
+
+// FP32 copy of an FP64 array (the pair conductances of an FP32 run's reverse sweep)
+__global__ void k_to_f32(int64_t n, const double *x, float *y)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
 }
 
 // sens_idx[sensor node] = its index in the sensor list (the array is -1 elsewhere)
@@ -376,20 +395,20 @@ fedfem_status copy_state(fedfem_ctx *c, int64_t step, uint8_t *dst, bool save)
 // spread the few warps of small meshes over all SMs (32^3: 94.7 -> 90.8 ms per adjoint).
 template <typename R>
 void adj_step(fedfem_ctx *c, bool first, const void *Tn, const void *Tprev, const double *dl_next, double qs_prev,
-              const AdjPhys &ph, const double *lam_in, double *lam_out, double *mu, double *musum, double *YF,
-              double *YG, double *gth, const int32_t *sens_idx)
+              const AdjPhys &ph, const double *lam_in, double *lam_out, void *mu_, double *musum, const void *cond_,
+              void *YF_, void *YG_, double *gth, const int32_t *sens_idx)
 {
     const int64_t nn = c->nn, ne = c->ne;
     const int npe = c->npe;
     const R *T = static_cast<const R *>(Tn);
+    const R *cond = static_cast<const R *>(cond_);
+    R *mu = static_cast<R *>(mu_), *YF = static_cast<R *>(YF_), *YG = static_cast<R *>(YG_);
     if (first)
         k_adj_mu<R><<<nblk(nn, 128), 128, 0, c->stream>>>(nn, T, c->d_A, lam_in, ph, ph.qs, mu, musum);
     if (npe == 8)
-        k_adj_elem<8, R><<<nblk(ne, 64), 64, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, T, mu, c->d_kscale, ph, YF, YG,
-                                                         gth);
+        k_adj_elem<8, R><<<nblk(ne, 64), 64, 0, c->stream>>>(ne, c->d_gconn, cond, T, mu, ph, YF, YG, gth);
     else
-        k_adj_elem<4, R><<<nblk(ne, 64), 64, 0, c->stream>>>(ne, c->d_gconn, c->d_cond64, T, mu, c->d_kscale, ph, YF, YG,
-                                                         gth);
+        k_adj_elem<4, R><<<nblk(ne, 64), 64, 0, c->stream>>>(ne, c->d_gconn, cond, T, mu, ph, YF, YG, gth);
     k_adj_node<R><<<nblk(nn, 128), 128, 0, c->stream>>>(nn, npe, c->d_n2e_ptr, c->d_n2e, YF, YG, T, lam_in, mu, c->d_A,
                                                    c->d_Qext64, c->d_Ac64, c->d_Ar64, c->d_isdir, ph, lam_out,
                                                    static_cast<const R *>(Tprev), sens_idx, dl_next, qs_prev, musum);
@@ -499,17 +518,28 @@ static fedfem_status adjoint_impl(fedfem_ctx *c, const double *dL_dtrace, double
         for (void *p : tmp) cudaFree(p);
         tmp.clear();
     };
-    double *d_dl = nullptr, *lam[2] = {nullptr, nullptr}, *mu = nullptr, *musum = nullptr, *YF = nullptr, *YG = nullptr,
-           *gth = nullptr, *gs = nullptr;
-    void *rec = nullptr;
+    // mu, the element slots and the conductances in the forward precision (rs bytes)
+    double *d_dl = nullptr, *lam[2] = {nullptr, nullptr}, *musum = nullptr, *gth = nullptr, *gs = nullptr;
+    void *rec = nullptr, *mu = nullptr, *YF = nullptr, *YG = nullptr;
+    const void *cond = c->d_cond64;
+    const int64_t n_cond = ne * (int64_t)(npe * (npe - 1) / 2);
     cudaError_t e = cudaSuccess;
     if ((e = talloc((void **)&d_dl, n_samp * ns * 8)) != cudaSuccess || (e = talloc(&rec, (size_t)K * nn * rs)) != cudaSuccess ||
         (e = talloc((void **)&lam[0], nn * 8)) != cudaSuccess || (e = talloc((void **)&lam[1], nn * 8)) != cudaSuccess ||
-        (e = talloc((void **)&mu, nn * 8)) != cudaSuccess || (e = talloc((void **)&musum, nn * 8)) != cudaSuccess ||
-        (e = talloc((void **)&YF, ne * npe * 8)) != cudaSuccess || (e = talloc((void **)&YG, ne * npe * 8)) != cudaSuccess ||
+        (e = talloc(&mu, nn * rs)) != cudaSuccess || (e = talloc((void **)&musum, nn * 8)) != cudaSuccess ||
+        (e = talloc(&YF, ne * npe * rs)) != cudaSuccess || (e = talloc(&YG, ne * npe * rs)) != cudaSuccess ||
         (e = talloc((void **)&gth, ne * 8)) != cudaSuccess || (e = talloc((void **)&gs, ne * 8)) != cudaSuccess) {
         release();
         return cuda_fail(c, e, "adjoint buffers");
+    }
+    if (c->precision != 64) {
+        float *c32 = nullptr;
+        if ((e = talloc((void **)&c32, n_cond * 4)) != cudaSuccess) {
+            release();
+            return cuda_fail(c, e, "adjoint buffers");
+        }
+        k_to_f32<<<nblk(n_cond), 256, 0, c->stream>>>(n_cond, c->d_cond64, c32);
+        cond = c32;
     }
 #define CKR(call, where)                       \
     do {                                       \
@@ -588,8 +618,7 @@ static fedfem_status adjoint_impl(fedfem_ctx *c, const double *dL_dtrace, double
             sa.sens = c->d_sensors;
             sa.sens_idx = sens_idx;
             sa.n2e = c->d_n2e;
-            sa.cond64 = c->d_cond64;
-            sa.theta = c->d_kscale;
+            sa.cond = cond;
             sa.A = c->d_A;
             sa.Qext = c->d_Qext64;
             sa.Ac = c->d_Ac64;
@@ -645,10 +674,10 @@ static fedfem_status adjoint_impl(fedfem_ctx *c, const double *dL_dtrace, double
             const double *dl_next = (s > 0 && (rel - 1) % se == 0) ? d_dl + ((rel - 1) / se - 1) * ns : nullptr;
             const double qs_prev = s > 0 ? c->qs_at(n - 1) : 0.0;
             if (c->precision == 64)
-                adj_step<double>(c, first, Tn, Tprev, dl_next, qs_prev, ph, lam[cur], lam[cur ^ 1], mu, musum, YF, YG,
+                adj_step<double>(c, first, Tn, Tprev, dl_next, qs_prev, ph, lam[cur], lam[cur ^ 1], mu, musum, cond, YF, YG,
                                  gth, sens_idx);
             else
-                adj_step<float>(c, first, Tn, Tprev, dl_next, qs_prev, ph, lam[cur], lam[cur ^ 1], mu, musum, YF, YG,
+                adj_step<float>(c, first, Tn, Tprev, dl_next, qs_prev, ph, lam[cur], lam[cur ^ 1], mu, musum, cond, YF, YG,
                                 gth, sens_idx);
             cur ^= 1;
         }

@@ -219,8 +219,12 @@ class FedFem:
     def sync(self):
         self._ck(self.L.fedfem_sync(self.h))
 
-    def get_T(self):
-        out = np.empty(self.n_nodes)
+    def get_T(self, out=None):
+        """Current field (original node order) into a new array, or into `out` (float64,
+        contiguous, n_nodes; e.g. a view of pinned host memory)."""
+        if out is None:
+            out = np.empty(self.n_nodes)
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.shape == (self.n_nodes,)
         self._ck(self.L.fedfem_get_T(self.h, _ptr(out)))
         return out
 
