@@ -30,14 +30,17 @@ struct HingeLaw {
     R d[kHinges];  // s_j - s_{j-1}
 };
 
-template <typename R>
+// NH: the number of hinges evaluated (the interior points of the table; the unused hinges,
+// j >= n - 2, carry zero coefficients, so any NH >= n - 2 gives the same value)
+template <int NH = kHinges, typename R>
 __host__ __device__ __forceinline__ R hinge_value(const HingeLaw<R> &t, R T)
 {
+    static_assert(NH >= 0 && NH <= kHinges, "hinge count");
     const R x = T - t.lo;
     const R u = x < (R)0 ? (R)0 : (x > t.span ? t.span : x);
     R f = t.v0 + t.s0 * u;
 FEDFEM_UNROLL
-    for (int j = 0; j < kHinges; ++j) {
+    for (int j = 0; j < NH; ++j) {
         const R h = u - t.u[j];
         f += t.d[j] * (h > (R)0 ? h : (R)0);
     }

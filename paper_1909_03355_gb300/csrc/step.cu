@@ -396,7 +396,7 @@ __device__ __forceinline__ void store4<double>(double *p, const Vec4<double> &v)
 // Element conduction loads of the element in lane `lane` of a staged chunk (Eq. 20):
 // F_i = f_k,e sum_{j != i} c_ij (T_i - T_j), f_k,e = k_a + k_lin mean_i T_i, or with a table
 // (TAB) the mean of the tabulated nodal factors (Section 4.2.2).
-template <typename R, int NPE, bool TAB>
+template <typename R, int NPE, bool TAB, int NH = kHinges>
 __device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int lane, const R *Ts, R k_a, R k_lin,
                                               const HingeLaw<R> &tk, R *F, int *id)
 {
@@ -426,7 +426,7 @@ __device__ __forceinline__ void element_loads(const uint8_t *blk, int CH, int la
         }
     if (TAB) {  // after the pair loop, when the conductances are no longer live
 #pragma unroll
-        for (int k = 0; k < NPE; ++k) sum += hinge_value(tk, T[k]);
+        for (int k = 0; k < NPE; ++k) sum += hinge_value<NH>(tk, T[k]);
     }
     const R fk = TAB ? sum * ((R)1 / (R)NPE) : k_a + k_lin * (sum * ((R)1 / (R)NPE));
 #pragma unroll
@@ -579,7 +579,7 @@ __device__ __forceinline__ void halo_load(HaloIn<R> &h, const int4 sh, const R *
 
 // T^n of a halo node from T^{n-1}, its compensation and the fixed-order sum of the halo
 // partials of step n-1.
-template <typename R, bool KAHAN, bool TAB>
+template <typename R, bool KAHAN, bool TAB, int NH = kHinges>
 __device__ __forceinline__ R halo_finish(const HaloIn<R> &h, const R *part, const Phys<R> &ph,
                                          const HingeLaw<R> &tc, float &cn, int32_t *err, R &F)
 {
@@ -587,7 +587,7 @@ __device__ __forceinline__ R halo_finish(const HaloIn<R> &h, const R *part, cons
     F += h.p[0];
     F += h.p[1];
     for (int q = 2; q < h.cnt; ++q) F += ld_cg(part + h.z + q);
-    return node_update<R, KAHAN, TAB>(h.T, h.cp, h.A, h.Q * ph.qs_prev, F, ph.dD_prev, ph, tc, cn, err);
+    return node_update<R, KAHAN, TAB, NH>(h.T, h.cp, h.A, h.Q * ph.qs_prev, F, ph.dD_prev, ph, tc, cn, err);
 }
 
 // Energy audit (an instantiation of the step kernel): every node update adds, in FP64, the
@@ -626,9 +626,12 @@ struct EnergyAcc {
 // node) | Ts[ts_cap] | Fs[ts_cap].  Threads [0, NC) are consumers; the last warp is the
 // producer of the element ring.  With at most 15 consumer warps + 1 producer warp every SM
 // sub-partition holds at most 4 warps, which leaves 128 registers per thread.
-template <typename R, int NPE, bool KAHAN, int SCATTER, bool TAB, bool EN>
+template <typename R, int NPE, bool KAHAN, int SCATTER, int TABN, bool EN>
 __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
 {
+    // TABN: 0 = the linear laws; else tabulated factors with up to TABN hinges evaluated
+    constexpr bool TAB = TABN > 0;
+    constexpr int NH = TAB ? TABN : kHinges;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_ok;
     // the current tile's record and physics, staged once per tile (kept out of registers)
@@ -794,7 +797,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                     }
                     float cn;
                     R Fh;
-                    const R v = halo_finish<R, KAHAN, TAB>(hin[u], pprev, ph, law_c<R>(a), cn, a.err, Fh);
+                    const R v = halo_finish<R, KAHAN, TAB, NH>(hin[u], pprev, ph, law_c<R>(a), cn, a.err, Fh);
                     if ((sh[u].w >> 16) == 0) {  // owner writes T^n back
                         Tc[sh[u].y] = v;
                         if (KAHAN) a.comp[cur][sh[u].y] = cn;
@@ -850,7 +853,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                             R F[NPE];
                             int id[NPE];
                             const int col = blk[col_off + lane32];
-                            element_loads<R, NPE, TAB>(blk, CH, lane32, Ts, ph.k_a, ph.k_lin, law_k<R>(a), F, id);
+                            element_loads<R, NPE, TAB, NH>(blk, CH, lane32, Ts, ph.k_a, ph.k_lin, law_k<R>(a), F, id);
                             __syncwarp();
                             if (lane32 == 0) mbar_arrive(&empty[slot]);  // stage back to the producer
                             if (col != 0xFF) {
@@ -863,8 +866,8 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                             R F0[NPE], F1[NPE];
                             int id0[NPE], id1[NPE];
                             const int col0 = blk[col_off + lane32], col1 = blk[col_off + lane32 + 32];
-                            element_loads<R, NPE, TAB>(blk, CH, lane32, Ts, ph.k_a, ph.k_lin, law_k<R>(a), F0, id0);
-                            element_loads<R, NPE, TAB>(blk, CH, lane32 + 32, Ts, ph.k_a, ph.k_lin, law_k<R>(a), F1,
+                            element_loads<R, NPE, TAB, NH>(blk, CH, lane32, Ts, ph.k_a, ph.k_lin, law_k<R>(a), F0, id0);
+                            element_loads<R, NPE, TAB, NH>(blk, CH, lane32 + 32, Ts, ph.k_a, ph.k_lin, law_k<R>(a), F1,
                                                        id1);
                             __syncwarp();
                             if (lane32 == 0) mbar_arrive(&empty[slot]);
@@ -948,7 +951,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                             for (int e = 0; e < 4; ++e) {
                                 float cn;
                                 const R Told = Ts[l + e];
-                                out.v[e] = node_update<R, KAHAN, TAB>(Told, KAHAN ? (float)cpv[u].v[e] : 0.0f,
+                                out.v[e] = node_update<R, KAHAN, TAB, NH>(Told, KAHAN ? (float)cpv[u].v[e] : 0.0f,
                                                                        Av[u][e], Qv[u].v[e] * ph.qs, Fs[l + e], ph.dD,
                                                                        ph, law_c<R>(a), cn, a.err);
                                 en.node(a, g + e, Told, KAHAN ? (float)cpv[u].v[e] : 0.0f, out.v[e], cn,
@@ -967,7 +970,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                     float cn;
                     const float c0 = KAHAN ? ld_cg(a.comp[cur] + g) : 0.0f;
                     const ACoef<R> Ag = load_A<R>(a, g);
-                    const R v = node_update<R, KAHAN, TAB>(Ts[l], c0, Ag, Qext[g] * ph.qs, Fs[l], ph.dD, ph,
+                    const R v = node_update<R, KAHAN, TAB, NH>(Ts[l], c0, Ag, Qext[g] * ph.qs, Fs[l], ph.dD, ph,
                                                            law_c<R>(a), cn, a.err);
                     en.node(a, g, Ts[l], c0, v, cn, Ag.dir(), Qext[g] * ph.qs, Fs[l]);
                     Tn[g] = v;
@@ -1010,7 +1013,7 @@ __global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
                 HaloIn<R> h;
                 halo_load<R, KAHAN>(h, sh, Tp, KAHAN ? a.comp[prv] : nullptr, part, Qext, a);
                 R Fh;
-                const R v = halo_finish<R, KAHAN, TAB>(h, part, ph, law_c<R>(a), cn, a.err, Fh);
+                const R v = halo_finish<R, KAHAN, TAB, NH>(h, part, ph, law_c<R>(a), cn, a.err, Fh);
                 Tc[sh.y] = v;
                 if (KAHAN) a.comp[cur][sh.y] = cn;
                 en.node(a, sh.y, h.T, h.cp, v, cn, h.A.dir(), h.Q * ph.qs_prev, Fh);
@@ -1057,11 +1060,15 @@ size_t step_smem_bytes(int precision, int npe, int chunk, int stages, int max_lo
            2 * (size_t)step_ts_cap(precision, max_local) * rs + (size_t)slot_cap * npe * rs;
 }
 
+// table: the number of points of the property tables (0 = the linear laws).  Tables of up to
+// five points (at most three hinges) take an instance that evaluates three hinges, larger
+// ones all kHinges.
 template <typename R, int NPE, bool KAHAN, int SCATTER>
 static void *kernel_ptr(int table)
 {
-    return table ? (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER, true, false>
-                 : (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER, false, false>;
+    if (table <= 0) return (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER, 0, false>;
+    if (table - 2 <= 3) return (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER, 3, false>;
+    return (void *)fed_step_kernel<R, NPE, KAHAN, SCATTER, kHinges, false>;
 }
 
 template <typename R, int NPE, bool KAHAN>
@@ -1074,11 +1081,11 @@ static void *slots_kernel_ptr(int table)
 static void *select_energy_kernel(int precision, int kahan, int npe)
 {
     if (precision == 64)
-        return npe == 8 ? (void *)fed_step_kernel<double, 8, false, FEDFEM_SCATTER_COLOR, false, true>
-                        : (void *)fed_step_kernel<double, 4, false, FEDFEM_SCATTER_COLOR, false, true>;
+        return npe == 8 ? (void *)fed_step_kernel<double, 8, false, FEDFEM_SCATTER_COLOR, 0, true>
+                        : (void *)fed_step_kernel<double, 4, false, FEDFEM_SCATTER_COLOR, 0, true>;
     if (!kahan) return nullptr;
-    return npe == 8 ? (void *)fed_step_kernel<float, 8, true, FEDFEM_SCATTER_COLOR, false, true>
-                    : (void *)fed_step_kernel<float, 4, true, FEDFEM_SCATTER_COLOR, false, true>;
+    return npe == 8 ? (void *)fed_step_kernel<float, 8, true, FEDFEM_SCATTER_COLOR, 0, true>
+                    : (void *)fed_step_kernel<float, 4, true, FEDFEM_SCATTER_COLOR, 0, true>;
 }
 
 static void *select_kernel(int precision, int kahan, int npe, int scatter, int table)

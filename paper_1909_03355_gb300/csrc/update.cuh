@@ -46,11 +46,11 @@ struct ACoef<double> {
 // Explicit nodal update (Eq. 16): T' = T + A / f_c(T) (Q - F), Kahan-compensated in FP32; a
 // Dirichlet node moves by dD, the change of its prescribed value over the step.  f_c is the
 // linear law of ph or (TAB) the table tc.
-template <typename R, bool KAHAN, bool TAB>
+template <typename R, bool KAHAN, bool TAB, int NH = kHinges>
 __device__ __forceinline__ R node_update(R T, float comp, ACoef<R> A, R Q, R F, R dD, const Phys<R> &ph,
                                          const HingeLaw<R> &tc, float &comp_out, int32_t *err)
 {
-    const R fc = TAB ? hinge_value(tc, T) : ph.c_a + ph.c_lin * T;
+    const R fc = TAB ? hinge_value<NH>(tc, T) : ph.c_a + ph.c_lin * T;
     const R inc = A.dir() ? dD : A.mul((Q - F) / fc);
     R Tn;
     if constexpr (KAHAN) {

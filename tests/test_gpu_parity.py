@@ -263,23 +263,30 @@ def test_time_dependent_dirichlet(kind, precision):
     f.close()
 
 
-def _table_cube(kind):
-    """Nonlinear cube with tabulated k(T), c(T): five points across the 20-820 degree range of
-    the run, the hottest nodes past the last point (held end values)."""
+def _table_cube(kind, npts=5):
+    """Nonlinear cube with tabulated k(T), c(T): five (or eight) points across the 20-820 degree
+    range of the run, the hottest nodes past the last point (held end values)."""
     p = fi.nonlinear_cube(9, kind, jitter=0.2 if kind == "hex" else 0.0)
-    p.table_T = np.array([0.0, 100.0, 250.0, 450.0, 650.0])
-    p.table_fk = np.array([1.0, 1.6, 1.2, 2.5, 2.0])
-    p.table_fc = np.array([1.0, 0.8, 1.4, 1.1, 1.6])
+    if npts == 5:
+        p.table_T = np.array([0.0, 100.0, 250.0, 450.0, 650.0])
+        p.table_fk = np.array([1.0, 1.6, 1.2, 2.5, 2.0])
+        p.table_fc = np.array([1.0, 0.8, 1.4, 1.1, 1.6])
+    else:
+        p.table_T = np.array([0.0, 50.0, 120.0, 200.0, 300.0, 400.0, 480.0, 560.0])
+        p.table_fk = np.array([1.0, 1.4, 1.1, 1.9, 1.5, 2.6, 2.1, 2.3])
+        p.table_fc = np.array([1.0, 0.7, 1.2, 1.5, 1.0, 1.3, 1.8, 1.4])
     return p
 
 
-@pytest.mark.parametrize("kind", ["hex", "tet"])
+@pytest.mark.parametrize("kind,npts", [("hex", 5), ("tet", 5), ("hex", 8), ("tet", 8)])
 @pytest.mark.parametrize("precision", [64, 32])
-def test_property_table(kind, precision):
+def test_property_table(kind, npts, precision):
     """Tabulated factors (linear between points, end values held, nodal k averaged per element):
     dt_crit and internal loads at a random state against the oracle, then 300 steps in launches
-    of 37 with the run split across two calls, and the energy terms of the last step."""
-    p = _table_cube(kind)
+    of 37 with the run split across two calls, and the energy terms of the last step.  Five
+    points run in the step kernel that evaluates three hinges, eight points in the one that
+    evaluates all six."""
+    p = _table_cube(kind, npts)
     m = O.OracleModel(p)
     f = FedFem(p, precision=precision, steps_per_launch=37)
     dtc = f.precompute()
