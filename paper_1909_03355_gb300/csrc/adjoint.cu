@@ -283,8 +283,11 @@ struct AdjSegArgs {
     int cur;                      // lambda buffer holding lambda at the segment's end
 };
 
+// threads per block of the one-launch-per-segment sweep (fewer blocks arrive at each grid barrier)
+constexpr int kSegThreads = 256;
+
 template <int NPE, typename R>
-__global__ void __launch_bounds__(128) k_adj_segment(AdjSegArgs a, AdjPhys ph)
+__global__ void __launch_bounds__(kSegThreads) k_adj_segment(AdjSegArgs a, AdjPhys ph)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -588,8 +591,9 @@ static fedfem_status adjoint_impl(fedfem_ctx *c, const double *dL_dtrace, double
     int seg_grid = 0;
     {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seg_kernel, 128, 0) == cudaSuccess && per_sm > 0) {
-            const int64_t want = (std::max(nn, ne) + 127) / 128;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seg_kernel, kSegThreads, 0) == cudaSuccess &&
+            per_sm > 0) {
+            const int64_t want = (std::max(nn, ne) + kSegThreads - 1) / kSegThreads;
             seg_grid = (int)std::min<int64_t>((int64_t)per_sm * c->num_sms, want);
         }
     }
@@ -643,7 +647,7 @@ static fedfem_status adjoint_impl(fedfem_ctx *c, const double *dL_dtrace, double
             void *params[] = {(void *)&sa, (void *)&ph};
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(seg_grid);
-            cfg.blockDim = dim3(128);
+            cfg.blockDim = dim3(kSegThreads);
             cfg.stream = c->stream;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeCooperative;

@@ -627,7 +627,7 @@ struct EnergyAcc {
 // producer of the element ring.  With at most 15 consumer warps + 1 producer warp every SM
 // sub-partition holds at most 4 warps, which leaves 128 registers per thread.
 template <typename R, int NPE, bool KAHAN, int SCATTER, int TABN, bool EN>
-__global__ void __maxnreg__(128) fed_step_kernel(const StepArgs a, int ts_cap)
+__global__ void __maxnreg__(sizeof(R) == 8 ? 168 : 128) fed_step_kernel(const StepArgs a, int ts_cap)
 {
     // TABN: 0 = the linear laws; else tabulated factors with up to TABN hinges evaluated
     constexpr bool TAB = TABN > 0;
