@@ -272,12 +272,13 @@ def algorithmic_bytes(p, precision):
     return eb * p.n_elems + nb * p.n_nodes
 
 
-def time_workload(p, precision, steps, stream, peak, dt=None, warm=20):
+def time_workload(p, precision, steps, stream, peak, dt=None, warm=20, **plan):
     """Device-resident ms/step of `steps` explicit steps of problem p (CUDA events on the
-    launching stream, after `warm` untimed steps), with its algorithmic bandwidth."""
+    launching stream, after `warm` untimed steps), with its algorithmic bandwidth.  With
+    energy_audit=True in `plan` the line adds the cumulative energy balance of all the steps."""
     import torch
     from paper_1909_03355_gb300.fedfem import FedFem
-    f = FedFem(p, precision=precision, stream=stream)
+    f = FedFem(p, precision=precision, stream=stream, **plan)
     dtc = f.precompute()
     dt = 0.9 * dtc if dt is None else dt
     f.set_dt(dt)
@@ -292,14 +293,23 @@ def time_workload(p, precision, steps, stream, peak, dt=None, warm=20):
     ms = e0.elapsed_time(e1) / steps
     info = f.info()
     T = f.get_T()
+    balance = None
+    if plan.get("energy_audit"):
+        S, B, n = f.energy_totals()
+        balance = {"steps": n, "stored_change_J": S, "boundary_and_source_in_J": B,
+                   "rel_residual": abs(S - B) / abs(B) if B else None}
     f.close()
     nbytes = algorithmic_bytes(p, precision)
     gbs = nbytes / (ms * 1e-3) / 1e9
-    return {"precision": "f32+kahan" if precision == 32 else "f64", "steps": steps, "ms_per_step": ms,
-            "value": p.n_elems / (ms * 1e-3), "unit": UNIT, "dt": dt, "dt_crit": dtc,
-            "algorithmic_MB_per_step": nbytes / 1e6, "achieved_GBps": gbs, "hbm_frac": gbs / peak,
-            "working_set": "L2-resident" if nbytes < L2_BYTES else "larger than L2",
-            "grid": info["grid"], "block": info["block"], "finite": bool(np.all(np.isfinite(T)))}
+    out = {"precision": "f32+kahan" if precision == 32 else "f64", "steps": steps, "ms_per_step": ms,
+           "value": p.n_elems / (ms * 1e-3), "unit": UNIT, "dt": dt, "dt_crit": dtc,
+           "algorithmic_MB_per_step": nbytes / 1e6, "achieved_GBps": gbs, "hbm_frac": gbs / peak,
+           "working_set": "L2-resident" if nbytes < L2_BYTES else "larger than L2",
+           "grid": info["grid"], "block": info["block"], "chunk": info["chunk"], "scatter": info["scatter"],
+           "finite": bool(np.all(np.isfinite(T)))}
+    if balance is not None:
+        out["energy_balance_since_start"] = balance
+    return out
 
 
 def plan_sweep(p, dt, stream, steps=512):
@@ -413,6 +423,14 @@ def extra_workloads(stream, peak, own=None):
                                   "note": "the 128^3 cube with a five-point table for k(T), c(T) instead of the "
                                           "linear laws (nodal factors averaged per element)",
                                   "gpu_fp32": time_workload(tc, 32, 2000, stream, peak)}
+    ea = fi.large_cube(128)
+    out["large_hex_128_energy_audit"] = {
+        "elements": ea.n_elems, "nodes": ea.n_nodes,
+        "note": "the 128^3 workload with the energy-audit instantiation of the step kernel (FP64 stored-heat "
+                "change and boundary input of every node update, summed per CTA); the balance covers the "
+                "warm-up and the timed steps",
+        "gpu_fp32": time_workload(ea, 32, 2000, stream, peak, energy_audit=True),
+        "gpu_fp64": time_workload(ea, 64, 400, stream, peak, energy_audit=True)}
     jc = fi.large_cube(128, jitter=0.2)
     out["large_hex_128_jitter"] = {"elements": jc.n_elems, "nodes": jc.n_nodes,
                                    "note": "interior nodes jittered by +-0.2 h (seeded): every element differs",
