@@ -869,6 +869,7 @@ StepArgs step_args(fedfem_ctx *c)
     a.tiles_per_cta = c->tpc;
     a.chunk_bytes = c->chunk_bytes;
     a.stages = c->stages;
+    a.stage_magic = ~0ULL / (uint64_t)c->stages + 1;
     a.chunk = c->chunk;
     a.colour_offset = chunk_colour_offset(c->precision, c->npe, c->chunk);
     // the element stream is evicted first when it cannot stay resident in L2 (> 64 MB);

@@ -143,6 +143,7 @@ struct StepArgs {
     int32_t nsteps;
     int32_t n_tiles, tiles_per_cta;
     int32_t chunk_bytes, stages, chunk, colour_offset;
+    uint64_t stage_magic;       // ceil(2^64 / stages): k / stages = high 64 bits of k * stage_magic
     int32_t l2_stream_policy;   // 0: evict_normal, 1: evict_first for the element stream
     int32_t scatter;
     int32_t withhold;           // test hook: CTA withhold-1 skips its first barrier arrival

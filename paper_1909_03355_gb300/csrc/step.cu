@@ -834,17 +834,46 @@ __global__ void __maxnreg__(sizeof(R) == 8 ? 168 : 128) fed_step_kernel(const St
             {
                 const int kbase = kc;
                 const int ncls = SCATTER == FEDFEM_SCATTER_COLOR ? ti.n_colors : 1;
+                // This warp consumes the tile's chunks k = wk, wk + NW, ... with k = wid (mod NW)
+                // (in every class, chunk u goes to warp (kbase + u) mod NW).  For tets (a warp
+                // takes about one chunk per class) the ring slot and phase parity of its next
+                // chunk advance incrementally; the hexahedral kernels, whose registers are taken
+                // by the element, form k / S as the high half of k * ceil(2^64 / S) (exact for
+                // k < 2^58).  Either way no integer division per chunk.
+                constexpr bool INCR = NPE == 4;
+                int wk = kbase + (wid - kbase % NW + NW) % NW;
+                int wslot = 0;
+                uint32_t wpar = 0;
+                if constexpr (INCR) {
+                    wslot = wk % S;
+                    wpar = (uint32_t)((wk / S) & 1);
+                }
                 for (int c = 0; c < ncls; ++c) {
-                    int u0 = 0, u1 = ti.n_chunks;
-                    if (SCATTER == FEDFEM_SCATTER_COLOR) {
-                        u0 = __ldg(a.colptr + ti.col_begin + c);
-                        u1 = __ldg(a.colptr + ti.col_begin + c + 1);
-                    }
+                    int u1 = ti.n_chunks;
+                    if (SCATTER == FEDFEM_SCATTER_COLOR) u1 = __ldg(a.colptr + ti.col_begin + c + 1);
+                    const int k1 = kbase + u1;
                     int bad = 0;
-                    for (int u = u0 + (wid - (kbase + u0) % NW + NW) % NW; u < u1; u += NW) {
-                        const int k = kbase + u;
-                        const int slot = k % S;
-                        if (!wait_chunk(&full[slot], tag + slot, k, (uint32_t)((k / S) & 1), a.timeout_ns, a.err)) {
+                    // the class holds chunks [kbase + u0, k1); this warp's next chunk wk is the
+                    // first of them with wk = wid (mod NW), since the previous class ended at u0
+                    for (; wk < k1; wk += NW) {
+                        const int k = wk;
+                        const int u = k - kbase;
+                        int slot;
+                        uint32_t par;
+                        if constexpr (INCR) {
+                            slot = wslot;
+                            par = wpar;
+                            wslot += NW;
+                            while (wslot >= S) {
+                                wslot -= S;
+                                wpar ^= 1u;
+                            }
+                        } else {
+                            const uint64_t q = __umul64hi((uint64_t)k, a.stage_magic);
+                            slot = k - (int)q * S;
+                            par = (uint32_t)(q & 1);
+                        }
+                        if (!wait_chunk(&full[slot], tag + slot, k, par, a.timeout_ns, a.err)) {
                             bad = 1;
                             break;
                         }
