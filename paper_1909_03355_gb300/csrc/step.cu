@@ -500,16 +500,45 @@ __device__ __forceinline__ void store_slot(R *Ys, int slot, const R *F)
     for (int q = 0; q < NPE; ++q) Ys[slot * NPE + q] = F[q];
 }
 
-// Add one element's nodal loads into the tile accumulators.
+// Add one element's nodal loads into the tile accumulators.  With colour classes the element's
+// nodes are distinct (a tet that lists a node twice has zero volume and is refused by the
+// pre-computation) and no other element of the class touches them, so a tet issues all its
+// loads before the stores (one shared-memory round trip instead of four in a row); hexahedra
+// add node by node (their registers are taken by the element).
 template <typename R, int NPE, int SCATTER>
 __device__ __forceinline__ void add_loads(R *Fs, const R *F, const int *id)
 {
+    if (SCATTER == FEDFEM_SCATTER_ATOMIC) {
+#pragma unroll
+        for (int q = 0; q < NPE; ++q) atomicAdd(&Fs[id[q]], F[q]);
+    } else if (NPE == 8) {
+#pragma unroll
+        for (int q = 0; q < NPE; ++q) Fs[id[q]] += F[q];
+    } else {
+        R f[NPE];
+#pragma unroll
+        for (int q = 0; q < NPE; ++q) f[q] = Fs[id[q]];
+#pragma unroll
+        for (int q = 0; q < NPE; ++q) Fs[id[q]] = f[q] + F[q];
+    }
+}
+
+// The same for the two elements of a lane in a 64-element chunk (one colour: all their nodes
+// are distinct); padding slots (use = false) add nothing.
+template <typename R, int NPE>
+__device__ __forceinline__ void add_loads2(R *Fs, const R *F0, const int *id0, bool use0, const R *F1,
+                                           const int *id1, bool use1)
+{
+    R f0[NPE], f1[NPE];
 #pragma unroll
     for (int q = 0; q < NPE; ++q) {
-        if (SCATTER == FEDFEM_SCATTER_ATOMIC)
-            atomicAdd(&Fs[id[q]], F[q]);
-        else
-            Fs[id[q]] += F[q];
+        if (use0) f0[q] = Fs[id0[q]];
+        if (use1) f1[q] = Fs[id1[q]];
+    }
+#pragma unroll
+    for (int q = 0; q < NPE; ++q) {
+        if (use0) Fs[id0[q]] = f0[q] + F0[q];
+        if (use1) Fs[id1[q]] = f1[q] + F1[q];
     }
 }
 
@@ -903,6 +932,8 @@ __global__ void __maxnreg__(sizeof(R) == 8 ? 168 : 128) fed_step_kernel(const St
                             if (SCATTER == FEDFEM_SCATTER_SLOTS) {
                                 if (col0 != 0xFF) store_slot<R, NPE>(Ys, u * CH + lane32, F0);
                                 if (col1 != 0xFF) store_slot<R, NPE>(Ys, u * CH + lane32 + 32, F1);
+                            } else if (SCATTER == FEDFEM_SCATTER_COLOR && NPE == 4) {
+                                add_loads2<R, NPE>(Fs, F0, id0, col0 != 0xFF, F1, id1, col1 != 0xFF);
                             } else {
                                 if (col0 != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F0, id0);
                                 if (col1 != 0xFF) add_loads<R, NPE, SCATTER>(Fs, F1, id1);
