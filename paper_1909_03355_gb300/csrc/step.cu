@@ -665,6 +665,7 @@ __global__ void __maxnreg__(sizeof(R) == 8 ? 168 : 128) fed_step_kernel(const St
     __shared__ int s_ok;
     // the current tile's record and physics, staged once per tile (kept out of registers)
     __shared__ TileInfo s_ti;
+    __shared__ int s_colptr[65];  // the tile's colour-class chunk offsets (at most 64 classes)
     __shared__ Phys<R> s_ph;
     constexpr int ALN = 16 / sizeof(R);  // nodes per 16 bytes
     const int NC = blockDim.x - 32;      // consumer threads
@@ -761,6 +762,8 @@ __global__ void __maxnreg__(sizeof(R) == 8 ? 168 : 128) fed_step_kernel(const St
             csync(NC);
             const TileInfo &ti = s_ti;
             const Phys<R> &ph = s_ph;
+            if (SCATTER == FEDFEM_SCATTER_COLOR && tid <= ti.n_colors)  // read after the barrier
+                s_colptr[tid] = __ldg(a.colptr + ti.col_begin + tid);     // before the elements
             en.set_law(a.phys + ti.scenario);
             const int nb = ti.node_begin;
             const int a0 = nb & ~(ALN - 1);
@@ -879,7 +882,7 @@ __global__ void __maxnreg__(sizeof(R) == 8 ? 168 : 128) fed_step_kernel(const St
                 }
                 for (int c = 0; c < ncls; ++c) {
                     int u1 = ti.n_chunks;
-                    if (SCATTER == FEDFEM_SCATTER_COLOR) u1 = __ldg(a.colptr + ti.col_begin + c + 1);
+                    if (SCATTER == FEDFEM_SCATTER_COLOR) u1 = s_colptr[c + 1];
                     const int k1 = kbase + u1;
                     int bad = 0;
                     // the class holds chunks [kbase + u0, k1); this warp's next chunk wk is the
