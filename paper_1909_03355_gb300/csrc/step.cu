@@ -666,7 +666,7 @@ __global__ void __maxnreg__(sizeof(R) == 8 ? 168 : 128) fed_step_kernel(const St
     // the current tile's record and physics, staged once per tile (kept out of registers)
     __shared__ TileInfo s_ti;
     __shared__ int s_colptr[65];  // the tile's colour-class chunk offsets (at most 64 classes)
-    __shared__ Phys<R> s_ph;
+    __shared__ Phys<R> s_ph, s_ph0;
     constexpr int ALN = 16 / sizeof(R);  // nodes per 16 bytes
     const int NC = blockDim.x - 32;      // consumer threads
     const int NW = NC / 32;              // consumer warps
@@ -755,8 +755,12 @@ __global__ void __maxnreg__(sizeof(R) == 8 ? 168 : 128) fed_step_kernel(const St
         R *Tn = reinterpret_cast<R *>(a.T[nxt]);
         for (int t = t0; t < t1 && ok; ++t) {
             if (tid == 0) {
-                s_ti = a.tiles[t];
-                s_ph = Phys<R>(a.phys[s_ti.scenario]);
+                // a CTA with one tile reads its record and physics once per launch
+                if (s == 0 || t1 - t0 > 1) {
+                    s_ti = a.tiles[t];
+                    s_ph0 = Phys<R>(a.phys[s_ti.scenario]);
+                }
+                s_ph = s_ph0;
                 apply_schedule(s_ph, a, a.n0 + s);
             }
             csync(NC);
