@@ -371,6 +371,77 @@ std::string build_tiling_groups(int npe, int64_t ne, int64_t nn, const int32_t *
             std::vector<int64_t> seq(m);
             std::iota(seq.begin(), seq.end(), 0);
             std::vector<uint8_t> trial(m);
+            // saturation-degree order (Brelaz's DSATUR): colour next the uncoloured element
+            // whose nodes already carry the most distinct colours (ties: the earliest in the
+            // tile's element order), with the lowest colour free at its nodes.  Levels of
+            // saturation are kept as bit sets over the element positions.
+            if (ncol_best != deg_max && m > 0) {
+                std::vector<int32_t> nptr(ti.n_local + 1, 0), nlist((size_t)m * npe);
+                for (int64_t p = 0; p < m; ++p)
+                    for (int k = 0; k < npe; ++k) ++nptr[loc[conn[npe * order[tb[t] + p] + k]] + 1];
+                for (int32_t l = 0; l < ti.n_local; ++l) nptr[l + 1] += nptr[l];
+                {
+                    std::vector<int32_t> fill(nptr.begin(), nptr.end() - 1);
+                    for (int64_t p = 0; p < m; ++p)
+                        for (int k = 0; k < npe; ++k) nlist[fill[loc[conn[npe * order[tb[t] + p] + k]]]++] = (int32_t)p;
+                }
+                const int64_t W = (m + 63) / 64;
+                std::vector<uint64_t> level((size_t)65 * W, 0);
+                std::vector<int64_t> cnt(65, 0);
+                std::vector<uint8_t> sat(m, 0), done(m, 0);
+                for (int64_t p = 0; p < m; ++p) level[p >> 6] |= 1ULL << (p & 63);
+                cnt[0] = m;
+                mask.assign(ti.n_local, 0);
+                auto seen = [&](int64_t p) {
+                    const int64_t e = order[tb[t] + p];
+                    uint64_t u = 0;
+                    for (int k = 0; k < npe; ++k) u |= mask[loc[conn[npe * e + k]]];
+                    return u;
+                };
+                int top = 0, nc = 0;
+                for (int64_t it = 0; it < m; ++it) {
+                    while (cnt[top] == 0) --top;
+                    int64_t p = -1;
+                    for (int64_t w = 0; w < W; ++w) {
+                        const uint64_t v = level[(size_t)top * W + w];
+                        if (v) {
+                            p = w * 64 + __builtin_ctzll(v);
+                            break;
+                        }
+                    }
+                    level[(size_t)top * W + (p >> 6)] &= ~(1ULL << (p & 63));
+                    --cnt[top];
+                    done[p] = 1;
+                    const uint64_t used = seen(p);
+                    if (~used == 0) return "more than 64 colours needed in a tile";
+                    const int c = __builtin_ctzll(~used);
+                    trial[p] = (uint8_t)c;
+                    nc = std::max(nc, c + 1);
+                    const int64_t e = order[tb[t] + p];
+                    for (int k = 0; k < npe; ++k) {
+                        const int32_t v = loc[conn[npe * e + k]];
+                        if (mask[v] & (1ULL << c)) continue;
+                        mask[v] |= 1ULL << c;
+                        for (int32_t j = nptr[v]; j < nptr[v + 1]; ++j) {
+                            const int32_t f = nlist[j];
+                            if (done[f]) continue;
+                            const int sf = __builtin_popcountll(seen(f));
+                            if (sf != sat[f]) {
+                                level[(size_t)sat[f] * W + (f >> 6)] &= ~(1ULL << (f & 63));
+                                --cnt[sat[f]];
+                                sat[f] = (uint8_t)sf;
+                                level[(size_t)sf * W + (f >> 6)] |= 1ULL << (f & 63);
+                                ++cnt[sf];
+                                top = std::max(top, sf);
+                            }
+                        }
+                    }
+                }
+                if (ncol_best == 0 || nc < ncol_best) {
+                    col = trial;
+                    ncol_best = nc;
+                }
+            }
             for (int pass = 0; pass < kColourPasses && ncol_best != deg_max; ++pass) {
                 if (pass == 1) seq = raster;
                 mask.assign(ti.n_local, 0);
