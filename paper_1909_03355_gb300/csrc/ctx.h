@@ -85,6 +85,7 @@ struct fedfem_ctx {
     int4 *d_sh = nullptr;
     int32_t *d_sptr = nullptr;
     int2 *d_bnd = nullptr;
+    void *d_bnd_area = nullptr;  // (A^c, A^r) per boundary entry, working precision
     int32_t *d_colptr = nullptr;
     int32_t *d_gptr = nullptr, *d_gidx = nullptr;  // slot gather lists (single-class tiling)
     int32_t *d_nbr_ptr = nullptr, *d_nbr = nullptr;

@@ -464,6 +464,8 @@ fedfem_status fedfem_ctx_init_device(fedfem_ctx *c)
     CK(upload(c, (void **)&c->d_sh, T.sh.data(), T.sh.size() * sizeof(int4)), "upload halo");
     CK(upload(c, (void **)&c->d_sptr, T.sptr.data(), T.sptr.size() * sizeof(int32_t)), "upload halo ptr");
     CK(upload(c, (void **)&c->d_bnd, T.bnd.data(), T.bnd.size() * sizeof(int2)), "upload boundary");
+    CK(dalloc(c, &c->d_bnd_area, std::max<size_t>(T.bnd.size(), 1) * 2 * (c->precision == 64 ? 8 : 4)),
+       "alloc boundary areas");
     CK(upload(c, (void **)&c->d_colptr, T.colptr.data(), T.colptr.size() * sizeof(int32_t)), "upload colours");
     if (T.single_class) {
         CK(upload(c, (void **)&c->d_gptr, T.gptr.data(), T.gptr.size() * sizeof(int32_t)), "upload gather lists");
@@ -645,7 +647,10 @@ fedfem_status fedfem::run_precompute_arrays(fedfem_ctx *c)
     na.Ac32 = c->precision == 32 ? (float *)c->d_Ac : nullptr;
     na.Ar32 = c->precision == 32 ? (float *)c->d_Ar : nullptr;
     launch_node_sums(na, c->stream);
-    CK(cudaGetLastError(), "node pre-computation");
+    if (!c->til.bnd.empty())
+        CK(launch_bnd_areas(c->precision, (int64_t)c->til.bnd.size(), c->d_bnd, c->d_Ac, c->d_Ar, c->d_bnd_area,
+                            c->stream),
+           "boundary areas");    CK(cudaGetLastError(), "node pre-computation");
     int32_t bits = 0;
     unsigned long long bad = 0;
     CK(cudaMemcpyAsync(&bits, c->d_err, 4, cudaMemcpyDeviceToHost, c->stream), "read status");
@@ -846,6 +851,7 @@ StepArgs step_args(fedfem_ctx *c)
     a.sh = c->d_sh;
     a.sptr = c->d_sptr;
     a.bnd = c->d_bnd;
+    a.bnd_area = c->d_bnd_area;
     a.colptr = c->d_colptr;
     a.gptr = c->d_gptr;
     a.gidx = c->d_gidx;

@@ -110,6 +110,7 @@ struct StepArgs {
     const int4 *sh;
     const int32_t *sptr;
     const int2 *bnd;
+    const void *bnd_area;       // per boundary entry (A^c, A^r) of its node, working precision
     const int32_t *colptr;      // tile-relative chunk offsets of the colour classes
     const int32_t *gptr, *gidx; // slot gather lists (SCATTER = slots)
     void *T[2];                 // Real [nn]
@@ -164,6 +165,9 @@ cudaError_t launch_step(const StepArgs &a, int precision, int kahan, int npe, in
                         size_t smem, int ts_cap, cudaStream_t st);
 cudaError_t prepare_step(int precision, int kahan, int npe, int scatter, int table, size_t smem);
 size_t step_smem_bytes(int precision, int npe, int chunk, int stages, int max_local, int slot_cap = 0);
+// (A^c, A^r) of the node of every boundary entry, gathered once after the pre-computation
+cudaError_t launch_bnd_areas(int precision, int64_t n, const int2 *bnd, const void *Ac, const void *Ar, void *out,
+                             cudaStream_t st);
 int step_ts_cap(int precision, int max_local);
 int step_max_blocks_per_sm(int precision, int kahan, int npe, int block, size_t smem);
 int chunk_bytes_for(int precision, int npe, int CH);

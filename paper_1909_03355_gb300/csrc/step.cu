@@ -28,6 +28,9 @@
 //   16-byte header {u8 first colour, u8 last colour, ...}
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <type_traits>
+
 #include "fedfem_internal.h"
 #include "update.cuh"
 
@@ -740,8 +743,6 @@ __global__ void __maxnreg__(sizeof(R) == 8 ? 168 : 128) fed_step_kernel(const St
         while ((long long)(global_ns() - d0) < dl) __nanosleep(256);
     }
     const R *Qext = reinterpret_cast<const R *>(a.Qext);
-    const R *Ac = reinterpret_cast<const R *>(a.Ac);
-    const R *Ar = reinterpret_cast<const R *>(a.Ar);
     const int col_off = a.colour_offset;
 
     EnergyAcc<EN> en;
@@ -969,8 +970,11 @@ __global__ void __maxnreg__(sizeof(R) == 8 ? 168 : 128) fed_step_kernel(const St
             }
             // ---- surface loads of owned boundary nodes
             for (int q = tid; q < ti.bnd_count; q += NC) {
+                // the entry and its node's areas are independent loads (one round trip)
+                using R2 = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
                 const int2 b = a.bnd[ti.bnd_begin + q];
-                const R o = surface_outflow<R>(Ts[b.x], Ac[b.y], Ar[b.y], ph);
+                const R2 ar = reinterpret_cast<const R2 *>(a.bnd_area)[ti.bnd_begin + q];
+                const R o = surface_outflow<R>(Ts[b.x], ar.x, ar.y, ph);
                 Fs[b.x] += o;
                 en.outflow(a, o);
             }
@@ -1112,6 +1116,29 @@ __global__ void __maxnreg__(sizeof(R) == 8 ? 168 : 128) fed_step_kernel(const St
             a.energy_acc[2 * blockIdx.x + 1] += B;
         }
     }
+}
+
+template <typename R>
+__global__ void k_bnd_areas(int64_t n, const int2 *bnd, const R *Ac, const R *Ar, R *out)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int g = bnd[q].y;
+        out[2 * q] = Ac[g];
+        out[2 * q + 1] = Ar[g];
+    }
+}
+
+cudaError_t launch_bnd_areas(int precision, int64_t n, const int2 *bnd, const void *Ac, const void *Ar, void *out,
+                             cudaStream_t st)
+{
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    if (precision == 64)
+        k_bnd_areas<double><<<blocks, 256, 0, st>>>(n, bnd, static_cast<const double *>(Ac),
+                                                    static_cast<const double *>(Ar), static_cast<double *>(out));
+    else
+        k_bnd_areas<float><<<blocks, 256, 0, st>>>(n, bnd, static_cast<const float *>(Ac),
+                                                   static_cast<const float *>(Ar), static_cast<float *>(out));
+    return cudaGetLastError();
 }
 
 int step_ts_cap(int precision, int max_local)
