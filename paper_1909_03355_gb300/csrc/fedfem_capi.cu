@@ -165,8 +165,15 @@ static fedfem_status make_plan(fedfem_ctx *c, const std::vector<uint8_t> &is_bnd
 {
     const int npe = c->npe;
     // consumer threads per CTA (one producer warp is added at launch); the FP32 default runs
-    // two CTAs of 7 consumer warps + 1 producer warp per SM (16 warps, 128 registers each)
-    const int block = c->opt.block ? c->opt.block : (c->precision == 64 ? 256 : 224);
+    // two CTAs of 7 consumer warps + 1 producer warp per SM (16 warps, 128 registers each).
+    // FP32 hexahedral meshes whose element stream stays in L2 (at most 64 MB) run one CTA of 15
+    // consumer warps per SM instead, on tiles twice as large, with fewer halo nodes per element
+    // (64^3 hex cube: 16.8 -> 16.4 us/step; the 64^3 tet cube is slower that way, 24.3 ->
+    // 32.7, and so is the 128^3 cube, whose node phases then leave the SM's DRAM stream idle)
+    const bool small_hex = c->precision == 32 && npe == 8 && c->group_elem.empty() && !c->opt.block &&
+                           !c->opt.ctas_per_sm &&
+                           (int64_t)c->ne * chunk_bytes_for(32, 8, 32) / 32 <= (64LL << 20);
+    const int block = c->opt.block ? c->opt.block : (c->precision == 64 ? 256 : small_hex ? 480 : 224);
     if (block % 32 || block < 64 || block > 480) return fail(c, FEDFEM_ERR_ARG, "block must be a multiple of 32 in [64, 480]");
     const int chunk = c->opt.chunk ? c->opt.chunk : default_chunk(c->precision, npe);
     if (chunk != 32 && chunk != 64) return fail(c, FEDFEM_ERR_ARG, "chunk must be 32 or 64");
