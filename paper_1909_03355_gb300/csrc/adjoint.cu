@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 #include <vector>
 
@@ -97,6 +98,58 @@ __device__ __forceinline__ void adj_mu_one(int64_t g, const R *Tn, const double 
     musum[g] += qs * m;  // d Q_g / d s_e = qs w_ge
 }
 
+// N consecutive values at src into registers, with 16-byte (else 8-byte) vector loads when N
+// values fill them (src aligned accordingly: the per-element rows of the arrays read here are).
+template <typename V, int N>
+__device__ __forceinline__ void vload(const V *src, V *dst)
+{
+    if constexpr (sizeof(V) == 4 && N % 4 == 0) {
+        using V4 = typename std::conditional<std::is_same<V, float>::value, float4, int4>::type;
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            const V4 v = reinterpret_cast<const V4 *>(src)[i];
+            dst[4 * i] = v.x;
+            dst[4 * i + 1] = v.y;
+            dst[4 * i + 2] = v.z;
+            dst[4 * i + 3] = v.w;
+        }
+    } else if constexpr (N % 2 == 0) {
+        using V2 = typename std::conditional<sizeof(V) == 8, double2,
+                                             typename std::conditional<std::is_same<V, float>::value, float2,
+                                                                       int2>::type>::type;
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            const V2 v = reinterpret_cast<const V2 *>(src)[i];
+            dst[2 * i] = v.x;
+            dst[2 * i + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) dst[i] = src[i];
+    }
+}
+
+// The same for stores.
+template <typename V, int N>
+__device__ __forceinline__ void vstore(V *dst, const V *src)
+{
+    if constexpr (sizeof(V) == 4 && N % 4 == 0) {
+        using V4 = typename std::conditional<std::is_same<V, float>::value, float4, int4>::type;
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i)
+            reinterpret_cast<V4 *>(dst)[i] = V4{src[4 * i], src[4 * i + 1], src[4 * i + 2], src[4 * i + 3]};
+    } else if constexpr (N % 2 == 0) {
+        using V2 = typename std::conditional<sizeof(V) == 8, double2,
+                                             typename std::conditional<std::is_same<V, float>::value, float2,
+                                                                       int2>::type>::type;
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) reinterpret_cast<V2 *>(dst)[i] = V2{src[2 * i], src[2 * i + 1]};
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) dst[i] = src[i];
+    }
+}
+
 // Element pass of element e: forward loads F_e = f_k (c T_e) and adjoint loads
 // G_e = f_k (c mu_e) + (mu_e . c T_e) f_k'(T_j) / npe into per-element slots; theta gradient.
 // Everything per element is in precision P (FP64 for an FP64 forward run; FP32 for an FP32
@@ -109,15 +162,18 @@ __device__ __forceinline__ void adj_elem_one(int64_t e, const int32_t *gconn, co
     constexpr int NC = NPE * (NPE - 1) / 2;
     P T[NPE], m[NPE], cT[NPE], cm[NPE];
     P sum = 0;
+    int gid[NPE];
+    vload<int32_t, NPE>(gconn + NPE * e, gid);
     for (int k = 0; k < NPE; ++k) {
-        const int g = gconn[NPE * e + k];
+        const int g = gid[k];
         T[k] = (P)Tn[g];
         m[k] = __ldcg(mu + g);
         sum += ph.tab ? (P)hinge_value(ph.tk, (double)T[k]) : T[k];
         cT[k] = 0;
         cm[k] = 0;
     }
-    const P *ce = cond + NC * e;
+    P ce[NC];
+    vload<P, NC>(cond + NC * e, ce);
     int p = 0;
     for (int i = 0; i < NPE; ++i)
         for (int j = i + 1; j < NPE; ++j, ++p) {
@@ -132,10 +188,13 @@ __device__ __forceinline__ void adj_elem_one(int64_t e, const int32_t *gconn, co
     const P fk = ph.tab ? sum / NPE : (P)ph.k_a + (P)ph.k_lin * (sum / NPE);
     P mcT = 0;
     for (int k = 0; k < NPE; ++k) mcT += m[k] * cT[k];
+    P yf[NPE], yg[NPE];
     for (int k = 0; k < NPE; ++k) {
-        YF[NPE * e + k] = fk * cT[k];
-        YG[NPE * e + k] = fk * cm[k] + mcT * adj_dfk_p<P>(ph, T[k]) / NPE;
+        yf[k] = fk * cT[k];
+        yg[k] = fk * cm[k] + mcT * adj_dfk_p<P>(ph, T[k]) / NPE;
     }
+    vstore<P, NPE>(YF + NPE * e, yf);
+    vstore<P, NPE>(YG + NPE * e, yg);
     gtheta[e] += (double)(fk * mcT);  // scaled by -1 / theta_e once, after the sweep
 }
 
