@@ -210,12 +210,31 @@ __device__ __forceinline__ void adj_node_one(int64_t g, int npe, const int32_t *
                                              const int32_t *sens_idx, const double *dl_next, double qs_prev,
                                              double *musum)
 {
+    // eight incident elements at a time: their slot indices, then their slots, are loaded
+    // together (one round trip each) and added in ascending order
     P F = 0, G = 0;
-    for (int q = n2e_ptr[g]; q < n2e_ptr[g + 1]; ++q) {
-        const int64_t ek = n2e[q];
-        const int64_t s = npe * (ek >> 3) + (ek & 7);
-        F += __ldcg(YF + s);
-        G += __ldcg(YG + s);
+    const int q0 = n2e_ptr[g], q1 = n2e_ptr[g + 1];
+    for (int qb = q0; qb < q1; qb += 8) {
+        int64_t sl[8];
+        P yf[8], yg[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (qb + j < q1) {
+                const int64_t ek = n2e[qb + j];
+                sl[j] = npe * (ek >> 3) + (ek & 7);
+            }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (qb + j < q1) {
+                yf[j] = __ldcg(YF + sl[j]);
+                yg[j] = __ldcg(YG + sl[j]);
+            }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (qb + j < q1) {
+                F += yf[j];
+                G += yg[j];
+            }
     }
     const double lg = __ldcg(lam + g);
     double l;
