@@ -63,6 +63,16 @@ def test_tet_meshes(check, chunk):
     assert check(q, 304)["n_tiles"] == 304
 
 
+def test_tet_colouring_close_to_the_clique_bound(check):
+    """The Kuhn-type 6-tet cube puts 24 tets on an interior node, so no colouring of a tile
+    needs fewer than 24 classes; the tiling's saturation-degree candidate keeps the 64^3 cube's
+    tiles within 28 (plain greedy orders needed 30), and the paper-shaped cube's within 24."""
+    s = check(fi.nonlinear_cube(64, "tet"), 304, 64)
+    assert 24 <= s["n_colors_max"] <= 28
+    q = check(fi.paper_cube("tet", 19), 183, 64)
+    assert q["n_colors_max"] <= 24
+
+
 def test_one_element_per_tile(check):
     p = fi.nonlinear_cube(3, "hex")
     s = check(p, p.n_elems)
