@@ -86,13 +86,18 @@ def test_plan_chooses_slots_for_padded_tiles_only():
     f = FedFem(small, precision=32)
     assert f.info()["scatter"] == SLOTS
     f.close()
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     for q in (fi.nonlinear_cube(64, "hex"), fi.nonlinear_cube(64, "tet")):
         g = FedFem(q, precision=32)
         assert g.info()["scatter"] == COLOR
+        # an L2-resident hexahedral mesh runs one CTA of 15 consumer warps per SM, tets two of 7
+        assert (g.info()["block"], g.info()["grid"]) == ((480, sms) if q.npe == 8 else (224, 2 * sms))
         g.close()
     big = fi.large_cube(128)
     g = FedFem(big, precision=32)
     assert g.info()["scatter"] == COLOR and g.info()["n_colors_max"] >= 8
+    assert (g.info()["block"], g.info()["grid"]) == (224, 2 * sms)
     g.close()
     h = FedFem(fi.paper_cube("tet", 19), precision=32, scatter=CLASSES)
     assert h.info()["scatter"] == COLOR
