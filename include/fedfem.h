@@ -115,12 +115,16 @@ typedef struct {
     int32_t kahan;              /* FP32 only: 1 (default) Kahan-compensated T accumulator  */
     int32_t scatter;            /* FEDFEM_SCATTER_COLOR (default), _ATOMIC, _SLOTS or _CLASSES */
     int32_t block;              /* consumer threads per CTA (multiple of 32, <= 480; one producer
-                                   warp is added), 0 = auto                                  */
+                                   warp is added), 0 = auto: 256 for FP64, 480 for FP32
+                                   hexahedral meshes whose element stream fits in 64 MB
+                                   (with one CTA per SM), else 224                           */
     int32_t steps_per_launch;   /* explicit steps fused in one persistent launch, 0 = auto */
-    int32_t ctas_per_sm;        /* resident CTAs per SM, 0 = auto                          */
+    int32_t ctas_per_sm;        /* resident CTAs per SM, 0 = auto (two for FP32 with at most
+                                   224 consumer threads, else one)                           */
     int32_t tiles_per_cta;      /* element tiles per CTA, 0 = auto                          */
     int32_t stages;             /* depth of the element-chunk TMA ring (2..63), 0 = auto     */
-    int32_t chunk;              /* elements per TMA chunk, 32 or 64 (one chunk per warp), 0 = auto */
+    int32_t chunk;              /* elements per TMA chunk, 32 or 64 (one chunk per warp), 0 = auto
+                                   (64 for FP32 tets, else 32)                               */
     int32_t l2_policy;          /* element stream L2 policy: 0 = auto, 1 = evict_normal, 2 = evict_first
                                    (node operands are then prefetched evict_last) */
     double barrier_timeout_s;   /* device-side wait limit (default 1.0 s)                   */
